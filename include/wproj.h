@@ -1,0 +1,250 @@
+/*
+ * wproj.h -- C ABI of the GB300 w-projection library (libwproj.so).
+ *
+ * Hankel-accelerated w-projection (Lucas, Skipper & Scaife, "Fast W-Projection for
+ * Wide-field Imaging", MNRAS 2019): per-|w|-plane oversampled convolution kernels are
+ * generated by an order-0 Hankel transform of the radially symmetric product
+ * (anti-aliasing taper) x (w-screen) instead of a 2D FFT (Section 4.3, Alg. 2), then
+ * visibilities are convolved onto the uv-grid with the kernel of their nearest plane
+ * (Alg. 1 / Alg. 2 gridding step) and inverse transformed to a dirty image (Section 3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every array argument is a DEVICE pointer unless its comment says "host".
+ *    Device memory is owned by the caller; the library allocates no device memory
+ *    except cuFFT plans/work areas (wp_dirty_image, wp_image_to_grid,
+ *    wp_fft_wkernels), which it caches per device and size until wp_release().
+ *  - Complex values are interleaved float pairs (re, im) -- the layout of CUDA's
+ *    float2 / cuFloatComplex / torch.complex64.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*; NULL is
+ *    the legacy default stream) and returns 0 (WP_OK) when all launches were queued.
+ *    Invalid arguments are detected on the host BEFORE any launch and return a negative
+ *    WP_ERR_* code with nothing launched.  WP_ERR_CUDA reports a failed launch (the
+ *    CUDA error string is available from wp_last_error_string()).  Device-side data
+ *    errors (e.g. a bounded wait that expired) are reported through the `status` word
+ *    of the calls that take one.
+ *  - Units: cell_size in radians (direction-cosine units), u, v, w in wavelengths.
+ *
+ * Geometry (Sections 3-5 of the paper):
+ *    N = image_size, dl = cell_size, FOV = N dl, du = 1/FOV (uv cell),
+ *    r_max = FOV/2 (radius of the circular image region), os = oversampling,
+ *    S = kernel support (half-width in cells; full width 2S+1),
+ *    R = radial_samples, radial nodes r_i = (i + 1/2) r_max / R,
+ *    K_out = os (S_max + 2) rounded up to a multiple of 128 radial kernel samples at
+ *            rho_k = k du / os.
+ */
+#ifndef WPROJ_H
+#define WPROJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------ */
+#define WP_OK              0
+#define WP_ERR_NULL       -1   /* a required pointer is NULL                          */
+#define WP_ERR_SIZE       -2   /* a size/count argument is out of range               */
+#define WP_ERR_PLAN       -3   /* inconsistent wp_plan fields                         */
+#define WP_ERR_WORKSPACE  -4   /* workspace too small or misaligned                   */
+#define WP_ERR_CUDA       -5   /* a CUDA / cuFFT call failed                          */
+#define WP_ERR_TIMEOUT    -6   /* a bounded device-side wait expired                  */
+#define WP_ERR_DEVICE     -7   /* current device is not sm_103 (GB300)                */
+#define WP_ERR_UNSUPPORTED -8  /* valid request outside what this build implements    */
+
+/* plan.interp (Section 4.3.2: linear or cubic-spline interpolation of the radial line) */
+#define WP_INTERP_CUBIC    0
+#define WP_INTERP_LINEAR   1
+
+/* plan.kernelgen: how the radial line is obtained */
+#define WP_KG_FP32         0   /* Hankel transform as FP32 SIMT matrix product          */
+#define WP_KG_TF32X3       1   /* Hankel transform on tcgen05 tensor cores, TF32 hi/lo
+                                  split (3 products), FP32 accumulation in TMEM          */
+
+/*
+ * Imager settings (Section 5: image size, cell size, oversampling, maximum support,
+ * truncation percentage, interpolation type; Section 4.2: workspace undersampling).
+ * All fields are host values.
+ */
+typedef struct wp_plan {
+    int32_t image_size;     /* N, even, 16 <= N <= 65536                               */
+    double  cell_size;      /* dl (radians), N*dl/2 < 1                                */
+    int32_t oversampling;   /* os, 1 <= os <= 16                                       */
+    int32_t max_support;    /* S_max, 1 <= S_max <= 511 (Section 5: 127 <-> 255x255)    */
+    int32_t min_support;    /* S_min, 1 <= S_min <= S_max                              */
+    double  trunc_frac;     /* tau in (0, 1): support = last radius with |C| >= tau*max
+                               (Section 3.1, default 0.01); <= 0: supports are given   */
+    int32_t radial_samples; /* R, 8 <= R <= 65536                                      */
+    int32_t interp;         /* WP_INTERP_CUBIC | WP_INTERP_LINEAR                      */
+    int32_t kernelgen;      /* WP_KG_FP32 | WP_KG_TF32X3                               */
+} wp_plan;
+
+/* Derived sizes of a plan (host struct filled by wp_plan_geometry). */
+typedef struct wp_geometry {
+    int32_t k_out;          /* radial kernel samples K_out (multiple of 128)           */
+    int32_t r_pad;          /* R rounded up to a multiple of 32                        */
+    int32_t fft_workspace;  /* M of the 2D-FFT route: power of two >= 2 S_max + 1      */
+    int32_t reserved;
+    double  du;             /* uv cell, wavelengths                                   */
+    double  r_max;          /* radius of the circular image region                    */
+} wp_geometry;
+
+/*
+ * A generated kernel set (all DEVICE pointers, caller-owned; the struct itself is a
+ * host value).  Plane p's cache block starts at complex element offsets[p] of `cache`
+ * and holds os*os sub-kernels [fv][fu], each (2 S_p + 1)^2 taps [jy][jx], where the
+ * tap (jx, jy) of sub-kernel (fu, fv) is the kernel at uv offset
+ * (jx - S_p - fu/os, jy - S_p - fv/os) cells.  Kernels are for +|w|; a visibility with
+ * w < 0 uses the complex conjugate (Section 4.1).
+ */
+typedef struct wp_wkernels {
+    int32_t        P;         /* number of |w| planes                                  */
+    int32_t        reserved;
+    const double*  w_planes;  /* [P] plane |w| values, ascending, >= 0                 */
+    const int32_t* support;   /* [P] support S_p, min_support <= S_p <= max_support    */
+    const int64_t* offsets;   /* [P+1] complex-element offsets into cache              */
+    const float*   cache;     /* interleaved complex taps                              */
+} wp_wkernels;
+
+/* ---- plan helpers (host only, no device work) -------------------------------------- */
+
+/* Validate `plan` and fill `geom`.  Returns WP_OK or WP_ERR_NULL / WP_ERR_PLAN. */
+int wp_plan_geometry(const wp_plan* plan, wp_geometry* geom);
+
+/*
+ * Compact cache layout for known supports: offsets[p+1] = offsets[p] + os^2 (2 S_p + 1)^2
+ * (host arrays: support [P] in, offsets [P+1] out).  With truncation on (trunc_frac > 0)
+ * the supports are only known after wp_hankel_radial; a caller that does not want to
+ * read them back sizes every block for max_support (wp_kernel_layout_max).
+ */
+int wp_kernel_layout(const wp_plan* plan, int32_t P, const int32_t* support_host,
+                     int64_t* offsets_host);
+int wp_kernel_layout_max(const wp_plan* plan, int32_t P, int64_t* offsets_host);
+
+/* ---- kernel generation (Alg. 2 with the Hankel transform, Section 4.3) ------------- */
+
+/* Bytes of scratch that wp_hankel_radial / wp_make_wkernels need for P planes. */
+size_t wp_kernelgen_workspace_bytes(const wp_plan* plan, int32_t P);
+
+/*
+ * Once per plan geometry (Section 4.3: the transform matrix does not depend on the plane, so it is built once):
+ * builds in `workspace` the K_out x R transform matrix H[k][i] = du^2 2 pi r_i dr
+ * J0(2 pi rho_k r_i) (J0 evaluated in FP64 on the device, stored as FP32 and as a TF32
+ * hi/lo pair) and the band of the inverse of the spline system.  Must precede
+ * wp_hankel_radial / wp_make_wkernels on that workspace; they then accept any P' whose
+ * workspace size still fits.  Synchronizes `stream` (a small host table is uploaded).
+ */
+int wp_kernelgen_prepare(const wp_plan* plan, int32_t P, void* workspace,
+                         size_t workspace_bytes, void* stream);
+
+/*
+ * Radial kernel lines of P planes: for each plane p (|w| = w_planes[p]):
+ *   f_p(r_i) = taper[i] * exp(+2 pi j w_p (sqrt(1 - r_i^2) - 1))          (Eq. 9, adjoint sign)
+ *   radial[p][k] = du^2 * sum_i 2 pi r_i dr J0(2 pi rho_k r_i) f_p(r_i)  (Eq. 12, matrix form)
+ * computed as one batched matrix product (K_out x R) x (R x 2P).  Also writes the cubic
+ * spline second derivatives of each line (Section 4.3.2; clamped slope 0 at rho = 0,
+ * natural at rho_{K_out-1}) and, if plan->trunc_frac > 0, the support of each plane
+ * (Section 3.1: last rho_k with |radial| >= trunc_frac * max, ceil to whole cells,
+ * clamped to [S_min, S_max]).
+ *   taper     [R] float, t(r_i) (the radial anti-aliasing function)
+ *   w_planes  [P] double, >= 0
+ *   workspace scratch of wp_kernelgen_workspace_bytes(plan, P) bytes, 256-byte aligned,
+ *             prepared by wp_kernelgen_prepare with the same plan geometry
+ *   radial    [P][K_out] complex out;  spline_m [P][K_out] complex out (may be NULL when
+ *             plan->interp == WP_INTERP_LINEAR);  support [P] int32 out (ignored, may be
+ *             NULL, when trunc_frac <= 0)
+ */
+int wp_hankel_radial(const wp_plan* plan, const float* taper, const double* w_planes,
+                     int32_t P, void* workspace, size_t workspace_bytes, float* radial,
+                     float* spline_m, int32_t* support, void* stream);
+
+/*
+ * Oversampled kernel cache from the radial lines (Section 4.3.2 and the cache step of
+ * Alg. 2): tap (jx, jy) of sub-kernel (fu, fv) of plane p is the interpolated radial
+ * line at radius x = sqrt((os (jx - S) - fu)^2 + (os (jy - S) - fv)^2) samples, and 0 when
+ * x > os S (the truncated line rotated about rho = 0 has circular support).
+ *   radial, spline_m  as written by wp_hankel_radial (spline_m unused for linear)
+ *   support [P] int32, offsets [P+1] int64 (device), cache out.
+ */
+int wp_resample(const wp_plan* plan, const float* radial, const float* spline_m, int32_t P,
+                const int32_t* support, const int64_t* offsets, float* cache, void* stream);
+
+/*
+ * wp_hankel_radial followed by wp_resample, for supports fixed by the caller
+ * (plan->trunc_frac <= 0; support [P] is then an input) or computed by truncation
+ * (support is then an output and offsets must give every block room for max_support).
+ */
+int wp_make_wkernels(const wp_plan* plan, const float* taper, const double* w_planes,
+                     int32_t P, int32_t* support, const int64_t* offsets, void* workspace,
+                     size_t workspace_bytes, float* radial, float* spline_m, float* cache,
+                     void* stream);
+
+/* ---- gridding (Alg. 1 / Alg. 2 gridding step) and its adjoint ----------------------- */
+
+/* Bytes of scratch that wp_grid / wp_degrid need for V visibilities. */
+size_t wp_grid_workspace_bytes(const wp_plan* plan, int32_t P, int64_t V);
+
+/*
+ * Convolutional gridding: for every visibility k (u, v, w = uvw[k][0..2]):
+ *   plane p = nearest |w| plane (ties -> lower index), conj = (w < 0),
+ *   t = rint((u/du + N/2) os), iu = floor(t/os), fu = t - iu os   (same for v),
+ *   grid[iv - S + jy][iu - S + jx] += weight[k] vis[k] K            for jx, jy in [0, 2S],
+ * K = tap (jx, jy) of sub-kernel (fu, fv) of plane p, conjugated when w < 0.  These
+ * integer decisions are taken in FP64.  A visibility whose footprint leaves [0, N)^2 is
+ * dropped.  The grid (rows v, columns u) is ACCUMULATED into (not cleared).
+ *   uvw [V][3] float, vis [V] complex, weight [V] float or NULL (all 1)
+ *   workspace  wp_grid_workspace_bytes(plan, P, V) bytes, 256-byte aligned
+ *   grid       [N][N] complex in/out
+ *   stats      double[2] or NULL: stats[0] += sum of weights gridded,
+ *              stats[1] += number of dropped visibilities
+ */
+int wp_grid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw,
+            const float* vis, const float* weight, int64_t V, void* workspace,
+            size_t workspace_bytes, float* grid, double* stats, void* stream);
+
+/*
+ * Degridding, the adjoint of wp_grid with unit weights:
+ *   vis_out[k] = sum_taps conj(K) grid[iv - S + jy][iu - S + jx]   (0 if dropped)
+ * Same binning rules and workspace as wp_grid.
+ */
+int wp_degrid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw,
+              const float* grid, int64_t V, void* workspace, size_t workspace_bytes,
+              float* vis_out, void* stream);
+
+/* ---- image <-> grid (Section 3: inverse transform and anti-aliasing correction) ----- */
+
+/*
+ * Dirty image from a grid:
+ *   image[m][l] = Re sum_{v,u} grid[v][u] exp(+2 pi j ((u - N/2)(l - N/2) + (v - N/2)(m - N/2)) / N)
+ *                 / (t(r) * weight_sum)    inside the circle (l - N/2)^2 + (m - N/2)^2 <= (N/2)^2,
+ *   image = 0 outside it (Section 6: the Hankel image is valid in that circle), where
+ *   t(r) is the taper linearly interpolated between its nodes r_i (clamped at the end
+ *   nodes), r = dl sqrt((l - N/2)^2 + (m - N/2)^2).
+ *   taper [R] float; grid [N][N] complex, OVERWRITTEN (transformed in place);
+ *   image [N][N] float out.  Uses a cached cuFFT plan.
+ */
+int wp_dirty_image(const wp_plan* plan, const float* taper, float* grid, double weight_sum,
+                   float* image, void* stream);
+
+/*
+ * Adjoint of wp_dirty_image's linear map (without taking the real part), used to
+ * predict visibilities of a model image with wp_degrid:
+ *   grid[v][u] = sum_{m,l inside circle} image[m][l] / (t(r) weight_sum)
+ *                exp(-2 pi j ((u - N/2)(l - N/2) + (v - N/2)(m - N/2)) / N)
+ *   image [N][N] float in; grid [N][N] complex out (overwritten).
+ */
+int wp_image_to_grid(const wp_plan* plan, const float* taper, const float* image,
+                     double weight_sum, float* grid, void* stream);
+
+/* ---- misc ---------------------------------------------------------------------------- */
+const char* wp_strerror(int code);
+const char* wp_last_error_string(void);   /* last CUDA/cuFFT error text (thread-local) */
+int wp_version(void);                      /* major*10000 + minor*100 + patch           */
+void wp_release(void);                     /* free cached cuFFT plans of this process   */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WPROJ_H */

@@ -1,0 +1,272 @@
+"""Python binding of the C ABI over torch CUDA tensors.
+
+Functions carry the C names without the ``wp_`` prefix.  They check dtypes, devices and
+contiguity, pass raw device pointers and the current torch stream to libwproj.so, and
+allocate outputs with torch.  No numerical work happens here.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import torch
+
+from . import _lib
+
+_ALIGN = 256
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t: torch.Tensor, dtype, name: str, numel: int | None = None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return t
+
+
+@dataclasses.dataclass(frozen=True)
+class Plan:
+    """Imager settings (Section 5 of the paper); mirrors ``wp_plan``."""
+
+    image_size: int
+    cell_size: float
+    oversampling: int = 8
+    max_support: int = 15
+    min_support: int = 3
+    trunc_frac: float = 0.01
+    radial_samples: int = 512
+    interp: str = "cubic"
+    kernelgen: str = "fp32"
+
+    def c(self) -> _lib.WpPlan:
+        return _lib.WpPlan(self.image_size, self.cell_size, self.oversampling, self.max_support,
+                           self.min_support, self.trunc_frac, self.radial_samples,
+                           _lib.INTERP[self.interp], _lib.KERNELGEN[self.kernelgen])
+
+    def geometry(self) -> _lib.WpGeometry:
+        g = _lib.WpGeometry()
+        _lib.check("wp_plan_geometry", _lib.load().wp_plan_geometry(ctypes.byref(self.c()), ctypes.byref(g)))
+        return g
+
+    def replace(self, **kw) -> "Plan":
+        return dataclasses.replace(self, **kw)
+
+
+@dataclasses.dataclass
+class WKernels:
+    """A generated kernel set on the device (see ``wp_wkernels``)."""
+
+    w_planes: torch.Tensor      # [P] float64
+    support: torch.Tensor       # [P] int32
+    offsets: torch.Tensor       # [P+1] int64
+    cache: torch.Tensor         # [n] complex64
+    radial: torch.Tensor | None = None     # [P][K_out] complex64
+    spline_m: torch.Tensor | None = None   # [P][K_out] complex64
+
+    @property
+    def P(self) -> int:
+        return int(self.w_planes.numel())
+
+    def c(self) -> _lib.WpWkernels:
+        return _lib.WpWkernels(self.P, 0, self.w_planes.data_ptr(), self.support.data_ptr(),
+                               self.offsets.data_ptr(), self.cache.data_ptr())
+
+    def subkernel(self, p: int, os_: int, support_host=None) -> torch.Tensor:
+        s = int(self.support[p]) if support_host is None else int(support_host[p])
+        a, b = int(self.offsets[p]), int(self.offsets[p + 1])
+        W = 2 * s + 1
+        return self.cache[a:a + os_ * os_ * W * W].view(os_, os_, W, W)
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    """A byte tensor usable as library scratch (torch allocations are 512-byte aligned)."""
+    t = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device or "cuda")
+    if t.data_ptr() % _ALIGN:
+        raise RuntimeError("workspace allocation is not 256-byte aligned")
+    return t
+
+
+# ------------------------------------------------------------------------------- layout
+def kernel_layout(plan: Plan, support) -> list[int]:
+    sup = (ctypes.c_int32 * len(support))(*[int(s) for s in support])
+    off = (ctypes.c_int64 * (len(support) + 1))()
+    _lib.check("wp_kernel_layout", _lib.load().wp_kernel_layout(ctypes.byref(plan.c()), len(support), sup, off))
+    return list(off)
+
+
+def kernel_layout_max(plan: Plan, P: int) -> list[int]:
+    off = (ctypes.c_int64 * (P + 1))()
+    _lib.check("wp_kernel_layout_max", _lib.load().wp_kernel_layout_max(ctypes.byref(plan.c()), P, off))
+    return list(off)
+
+
+# --------------------------------------------------------------------- kernel generation
+def kernelgen_workspace_bytes(plan: Plan, P: int) -> int:
+    return int(_lib.load().wp_kernelgen_workspace_bytes(ctypes.byref(plan.c()), P))
+
+
+def kernelgen_prepare(plan: Plan, P: int, ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    nbytes = kernelgen_workspace_bytes(plan, P)
+    if ws is None:
+        ws = workspace(nbytes)
+    _need(ws, torch.uint8, "workspace")
+    _lib.check("wp_kernelgen_prepare", _lib.load().wp_kernelgen_prepare(
+        ctypes.byref(plan.c()), P, _ptr(ws), ws.numel(), _stream(stream)))
+    return ws
+
+
+def hankel_radial(plan: Plan, taper: torch.Tensor, w_planes: torch.Tensor, ws: torch.Tensor,
+                  radial: torch.Tensor | None = None, spline_m: torch.Tensor | None = None,
+                  support: torch.Tensor | None = None, stream=None):
+    """Radial kernel lines (+ spline second derivatives, + supports when truncating)."""
+    g = plan.geometry()
+    P = int(w_planes.numel())
+    _need(taper, torch.float32, "taper", plan.radial_samples)
+    _need(w_planes, torch.float64, "w_planes")
+    dev = taper.device
+    if radial is None:
+        radial = torch.empty((P, g.k_out), dtype=torch.complex64, device=dev)
+    if spline_m is None and plan.interp == "cubic":
+        spline_m = torch.empty((P, g.k_out), dtype=torch.complex64, device=dev)
+    if support is None and plan.trunc_frac > 0:
+        support = torch.empty(P, dtype=torch.int32, device=dev)
+    _lib.check("wp_hankel_radial", _lib.load().wp_hankel_radial(
+        ctypes.byref(plan.c()), _ptr(taper), _ptr(w_planes), P, _ptr(ws), ws.numel(), _ptr(radial),
+        _ptr(spline_m), _ptr(support), _stream(stream)))
+    return radial, spline_m, support
+
+
+def resample(plan: Plan, radial: torch.Tensor, spline_m: torch.Tensor | None, support: torch.Tensor,
+             offsets: torch.Tensor, cache: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    P = int(support.numel())
+    _need(radial, torch.complex64, "radial")
+    _need(support, torch.int32, "support")
+    _need(offsets, torch.int64, "offsets", P + 1)
+    if cache is None:
+        cache = torch.empty(int(offsets[-1].item()), dtype=torch.complex64, device=radial.device)
+    _lib.check("wp_resample", _lib.load().wp_resample(
+        ctypes.byref(plan.c()), _ptr(radial), _ptr(spline_m), P, _ptr(support), _ptr(offsets),
+        _ptr(cache), _stream(stream)))
+    return cache
+
+
+def make_wkernels(plan: Plan, taper: torch.Tensor, w_planes, supports=None,
+                  ws: torch.Tensor | None = None, prepare: bool = True, stream=None) -> WKernels:
+    """Hankel w-kernels of every plane (Alg. 2).  With ``supports`` given (or
+    ``plan.trunc_frac <= 0``) the layout is compact and nothing is read back; otherwise the
+    1 % truncation supports are read back to lay the cache out compactly."""
+    dev = taper.device
+    w_planes = torch.as_tensor(w_planes, dtype=torch.float64, device=dev).contiguous()
+    wp_host = w_planes.cpu()
+    if (wp_host < 0).any() or (wp_host[1:] < wp_host[:-1]).any():
+        raise ValueError("w_planes must be ascending and >= 0 (|w| planes)")
+    P = int(w_planes.numel())
+    if ws is None:
+        ws = workspace(kernelgen_workspace_bytes(plan, P), dev)
+        prepare = True
+    if prepare:
+        kernelgen_prepare(plan, P, ws, stream)
+    if supports is not None:
+        sup_host = [int(s) for s in supports]
+        off = torch.tensor(kernel_layout(plan, sup_host), dtype=torch.int64, device=dev)
+        sup = torch.tensor(sup_host, dtype=torch.int32, device=dev)
+        p_fixed = plan.replace(trunc_frac=0.0)
+        radial, spline_m, _ = hankel_radial(p_fixed, taper, w_planes, ws, stream=stream)
+        cache = resample(p_fixed, radial, spline_m, sup, off, stream=stream)
+        return WKernels(w_planes, sup, off, cache, radial, spline_m)
+    if plan.trunc_frac <= 0:
+        raise ValueError("supports are required when plan.trunc_frac <= 0")
+    radial, spline_m, sup = hankel_radial(plan, taper, w_planes, ws, stream=stream)
+    sup_host = sup.cpu().tolist()
+    off = torch.tensor(kernel_layout(plan, sup_host), dtype=torch.int64, device=dev)
+    cache = resample(plan, radial, spline_m, sup, off, stream=stream)
+    return WKernels(w_planes, sup, off, cache, radial, spline_m)
+
+
+# ----------------------------------------------------------------------------- gridding
+def grid_workspace_bytes(plan: Plan, P: int, V: int) -> int:
+    return int(_lib.load().wp_grid_workspace_bytes(ctypes.byref(plan.c()), P, V))
+
+
+def grid(plan: Plan, wk: WKernels, uvw: torch.Tensor, vis: torch.Tensor, weight: torch.Tensor | None = None,
+         out: torch.Tensor | None = None, ws: torch.Tensor | None = None, stats: torch.Tensor | None = None,
+         stream=None):
+    """Grid visibilities (accumulating into ``out``); returns (grid, stats) with
+    stats = [sum of gridded weights, number dropped] (float64, device)."""
+    V = int(vis.numel())
+    _need(uvw, torch.float32, "uvw", 3 * V)
+    _need(vis, torch.complex64, "vis")
+    if weight is not None:
+        _need(weight, torch.float32, "weight", V)
+    N = plan.image_size
+    dev = vis.device
+    if out is None:
+        out = torch.zeros((N, N), dtype=torch.complex64, device=dev)
+    _need(out, torch.complex64, "grid", N * N)
+    if ws is None:
+        ws = workspace(grid_workspace_bytes(plan, wk.P, V), dev)
+    if stats is None:
+        stats = torch.zeros(2, dtype=torch.float64, device=dev)
+    kc = wk.c()
+    _lib.check("wp_grid", _lib.load().wp_grid(
+        ctypes.byref(plan.c()), ctypes.byref(kc), _ptr(uvw), _ptr(vis), _ptr(weight), V, _ptr(ws),
+        ws.numel(), _ptr(out), _ptr(stats), _stream(stream)))
+    return out, stats
+
+
+def degrid(plan: Plan, wk: WKernels, uvw: torch.Tensor, grid_: torch.Tensor, out: torch.Tensor | None = None,
+           ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    V = int(uvw.numel() // 3)
+    _need(uvw, torch.float32, "uvw", 3 * V)
+    N = plan.image_size
+    _need(grid_, torch.complex64, "grid", N * N)
+    dev = uvw.device
+    if out is None:
+        out = torch.empty(V, dtype=torch.complex64, device=dev)
+    if ws is None:
+        ws = workspace(grid_workspace_bytes(plan, wk.P, V), dev)
+    kc = wk.c()
+    _lib.check("wp_degrid", _lib.load().wp_degrid(
+        ctypes.byref(plan.c()), ctypes.byref(kc), _ptr(uvw), _ptr(grid_), V, _ptr(ws), ws.numel(),
+        _ptr(out), _stream(stream)))
+    return out
+
+
+def dirty_image(plan: Plan, taper: torch.Tensor, grid_: torch.Tensor, weight_sum: float,
+                out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Dirty image; ``grid_`` is transformed in place (consumed)."""
+    N = plan.image_size
+    _need(taper, torch.float32, "taper", plan.radial_samples)
+    _need(grid_, torch.complex64, "grid", N * N)
+    if out is None:
+        out = torch.empty((N, N), dtype=torch.float32, device=grid_.device)
+    _lib.check("wp_dirty_image", _lib.load().wp_dirty_image(
+        ctypes.byref(plan.c()), _ptr(taper), _ptr(grid_), float(weight_sum), _ptr(out), _stream(stream)))
+    return out
+
+
+def image_to_grid(plan: Plan, taper: torch.Tensor, image: torch.Tensor, weight_sum: float,
+                  out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    N = plan.image_size
+    _need(taper, torch.float32, "taper", plan.radial_samples)
+    _need(image, torch.float32, "image", N * N)
+    if out is None:
+        out = torch.empty((N, N), dtype=torch.complex64, device=image.device)
+    _lib.check("wp_image_to_grid", _lib.load().wp_image_to_grid(
+        ctypes.byref(plan.c()), _ptr(taper), _ptr(image), float(weight_sum), _ptr(out), _stream(stream)))
+    return out

@@ -1,0 +1,322 @@
+// C ABI entry points of libwproj.so: argument validation on the host, workspace carving,
+// and the launch sequence of each call.  Nothing here computes on the host beyond sizes.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "wp_internal.cuh"
+
+#define WP_VERSION 100   // 0.1.0
+
+namespace wp {
+
+static thread_local char g_err[512] = "";
+
+void set_last_error(const char* where, const char* what) {
+    snprintf(g_err, sizeof(g_err), "%s: %s", where, what);
+}
+
+int cuda_fail(const char* where, cudaError_t e) {
+    set_last_error(where, cudaGetErrorString(e));
+    return WP_ERR_CUDA;
+}
+
+int make_geom(const wp_plan* plan, Geom* g) {
+    if (!plan || !g) return WP_ERR_NULL;
+    const int N = plan->image_size;
+    if (N < 16 || N > 65536 || (N & 1)) return WP_ERR_PLAN;
+    if (!(plan->cell_size > 0.0) || !(0.5 * N * plan->cell_size < 1.0)) return WP_ERR_PLAN;
+    if (plan->oversampling < 1 || plan->oversampling > 16) return WP_ERR_PLAN;
+    if (plan->max_support < 1 || plan->max_support > 511) return WP_ERR_PLAN;
+    if (2 * plan->max_support + 1 > N) return WP_ERR_PLAN;
+    if (plan->min_support < 1 || plan->min_support > plan->max_support) return WP_ERR_PLAN;
+    if (!(plan->trunc_frac < 1.0)) return WP_ERR_PLAN;
+    if (plan->radial_samples < 8 || plan->radial_samples > 65536) return WP_ERR_PLAN;
+    if (plan->interp != WP_INTERP_CUBIC && plan->interp != WP_INTERP_LINEAR) return WP_ERR_PLAN;
+    if (plan->kernelgen != WP_KG_FP32 && plan->kernelgen != WP_KG_TF32X3) return WP_ERR_PLAN;
+    g->N = N;
+    g->dl = plan->cell_size;
+    g->du = 1.0 / ((double)N * plan->cell_size);
+    g->r_max = 0.5 * (double)N * plan->cell_size;
+    g->os = plan->oversampling;
+    g->s_max = plan->max_support;
+    g->s_min = plan->min_support;
+    g->tau = plan->trunc_frac;
+    g->R = plan->radial_samples;
+    g->r_pad = (int)round_up(plan->radial_samples, 32);
+    g->k_out = (int)round_up((int64_t)plan->oversampling * (plan->max_support + 2), 128);
+    g->interp = plan->interp;
+    g->kernelgen = plan->kernelgen;
+    int m = 1;
+    while (m < 2 * plan->max_support + 1) m *= 2;
+    g->fft_m = m;
+    return WP_OK;
+}
+
+size_t carve_kg(const Geom& g, int P, void* ws, size_t bytes, KgWork* out) {
+    Carver c(ws, bytes);
+    const size_t hk = (size_t)g.k_out * g.r_pad;
+    const size_t fk = (size_t)2 * p_pad(P) * g.r_pad;
+    KgWork w;
+    w.h32 = c.take<float>(hk);
+    w.h_hi = c.take<float>(hk);
+    w.h_lo = c.take<float>(hk);
+    w.band = c.take<float>((size_t)g.k_out * 65);
+    w.f32 = c.take<float>(fk);
+    w.f_hi = c.take<float>(fk);
+    w.f_lo = c.take<float>(fk);
+    w.status = c.take<int>(64);
+    if (out) *out = w;
+    return (size_t)round_up((int64_t)c.off, 256);
+}
+
+size_t carve_grid(const Geom& g, int P, int64_t V, void* ws, size_t bytes, GridWork* out) {
+    Carver c(ws, bytes);
+    GridWork w;
+    w.T = 64;
+    w.ntx = (g.N + w.T - 1) / w.T;
+    w.ntiles = w.ntx * w.ntx;
+    w.nbins = (int64_t)P * w.ntiles;
+    w.count = c.take<int>((size_t)w.nbins + 1);
+    w.cursor = c.take<int>((size_t)w.nbins + 1);
+    w.key = c.take<int>((size_t)V);
+    w.rec = c.take<int4>((size_t)V);
+    w.srec = c.take<int4>((size_t)V);
+    w.svis = c.take<float2>((size_t)V);
+    w.flags = c.take<int>((size_t)w.nbins + 1);
+    w.items = c.take<int>((size_t)w.nbins + 1);
+    w.scan_tmp = c.take<int>(scan_tmp_ints(w.nbins + 1));
+    w.ctrl = c.take<int>(64);
+    w.red = c.take<double>(8);
+    if (out) *out = w;
+    return (size_t)round_up((int64_t)c.off, 256);
+}
+
+static int check_device() {
+    static int cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return WP_ERR_CUDA;
+    if (dev < 0 || dev >= 64) return WP_ERR_DEVICE;
+    if (cached[dev] == 0) {
+        int major = 0, minor = 0;
+        if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+            return WP_ERR_CUDA;
+        cached[dev] = (major == 10 && minor == 3) ? 1 : -1;
+    }
+    return cached[dev] == 1 ? WP_OK : WP_ERR_DEVICE;
+}
+
+static bool aligned256(const void* p) { return ((uintptr_t)p & 255u) == 0; }
+
+}  // namespace wp
+
+using namespace wp;
+
+extern "C" {
+
+int wp_version(void) { return WP_VERSION; }
+
+const char* wp_last_error_string(void) { return g_err; }
+
+const char* wp_strerror(int code) {
+    switch (code) {
+        case WP_OK: return "ok";
+        case WP_ERR_NULL: return "a required pointer is NULL";
+        case WP_ERR_SIZE: return "a size or count argument is out of range";
+        case WP_ERR_PLAN: return "inconsistent plan";
+        case WP_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
+        case WP_ERR_CUDA: return "CUDA or cuFFT call failed";
+        case WP_ERR_TIMEOUT: return "a bounded device-side wait expired";
+        case WP_ERR_DEVICE: return "current device is not sm_103 (GB300)";
+        case WP_ERR_UNSUPPORTED: return "request not supported by this build";
+        default: return "unknown status";
+    }
+}
+
+void wp_release(void) { release_fft_plans(); }
+
+int wp_plan_geometry(const wp_plan* plan, wp_geometry* geom) {
+    if (!plan || !geom) return WP_ERR_NULL;
+    Geom g;
+    int rc = make_geom(plan, &g);
+    if (rc) return rc;
+    geom->k_out = g.k_out;
+    geom->r_pad = g.r_pad;
+    geom->fft_workspace = g.fft_m;
+    geom->reserved = 0;
+    geom->du = g.du;
+    geom->r_max = g.r_max;
+    return WP_OK;
+}
+
+int wp_kernel_layout(const wp_plan* plan, int32_t P, const int32_t* support_host, int64_t* offsets_host) {
+    Geom g;
+    int rc = make_geom(plan, &g);
+    if (rc) return rc;
+    if (!support_host || !offsets_host) return WP_ERR_NULL;
+    if (P < 1) return WP_ERR_SIZE;
+    const int64_t os2 = (int64_t)g.os * g.os;
+    offsets_host[0] = 0;
+    for (int p = 0; p < P; ++p) {
+        int s = support_host[p];
+        if (s < 1 || s > g.s_max) return WP_ERR_SIZE;
+        offsets_host[p + 1] = offsets_host[p] + os2 * (2 * s + 1) * (2 * s + 1);
+    }
+    return WP_OK;
+}
+
+int wp_kernel_layout_max(const wp_plan* plan, int32_t P, int64_t* offsets_host) {
+    Geom g;
+    int rc = make_geom(plan, &g);
+    if (rc) return rc;
+    if (!offsets_host) return WP_ERR_NULL;
+    if (P < 1) return WP_ERR_SIZE;
+    const int64_t blk = (int64_t)g.os * g.os * (2 * g.s_max + 1) * (2 * g.s_max + 1);
+    for (int p = 0; p <= P; ++p) offsets_host[p] = blk * p;
+    return WP_OK;
+}
+
+size_t wp_kernelgen_workspace_bytes(const wp_plan* plan, int32_t P) {
+    Geom g;
+    if (make_geom(plan, &g) || P < 1) return 0;
+    return carve_kg(g, P, nullptr, 0, nullptr);
+}
+
+int wp_kernelgen_prepare(const wp_plan* plan, int32_t P, void* workspace, size_t workspace_bytes,
+                         void* stream) {
+    Geom g;
+    int rc = make_geom(plan, &g);
+    if (rc) return rc;
+    if (P < 1 || P > 65536) return WP_ERR_SIZE;
+    if (!workspace) return WP_ERR_NULL;
+    if (!aligned256(workspace) || workspace_bytes < carve_kg(g, P, nullptr, 0, nullptr)) return WP_ERR_WORKSPACE;
+    if ((rc = check_device())) return rc;
+    KgWork w;
+    carve_kg(g, P, workspace, workspace_bytes, &w);
+    return kg_prepare(g, w, (cudaStream_t)stream);
+}
+
+int wp_hankel_radial(const wp_plan* plan, const float* taper, const double* w_planes, int32_t P,
+                     void* workspace, size_t workspace_bytes, float* radial, float* spline_m,
+                     int32_t* support, void* stream) {
+    Geom g;
+    int rc = make_geom(plan, &g);
+    if (rc) return rc;
+    if (P < 1 || P > 65536) return WP_ERR_SIZE;
+    if (!taper || !w_planes || !workspace || !radial) return WP_ERR_NULL;
+    if (g.interp == WP_INTERP_CUBIC && !spline_m) return WP_ERR_NULL;
+    if (g.tau > 0.0 && !support) return WP_ERR_NULL;
+    if (!aligned256(workspace) || workspace_bytes < carve_kg(g, P, nullptr, 0, nullptr)) return WP_ERR_WORKSPACE;
+    if ((rc = check_device())) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    KgWork w;
+    carve_kg(g, P, workspace, workspace_bytes, &w);
+    if ((rc = kg_screen(g, w, taper, w_planes, P, st))) return rc;
+    if (g.kernelgen == WP_KG_TF32X3)
+        rc = kg_gemm_tf32x3(g, w, P, reinterpret_cast<float2*>(radial), w.status, st);
+    else
+        rc = kg_gemm_fp32(g, w, P, reinterpret_cast<float2*>(radial), st);
+    if (rc) return rc;
+    return kg_trunc_spline(g, w, P, reinterpret_cast<const float2*>(radial),
+                           reinterpret_cast<float2*>(spline_m), support, st);
+}
+
+int wp_resample(const wp_plan* plan, const float* radial, const float* spline_m, int32_t P,
+                const int32_t* support, const int64_t* offsets, float* cache, void* stream) {
+    Geom g;
+    int rc = make_geom(plan, &g);
+    if (rc) return rc;
+    if (P < 1 || P > 65536) return WP_ERR_SIZE;
+    if (!radial || !support || !offsets || !cache) return WP_ERR_NULL;
+    if (g.interp == WP_INTERP_CUBIC && !spline_m) return WP_ERR_NULL;
+    if ((rc = check_device())) return rc;
+    return kg_resample(g, P, reinterpret_cast<const float2*>(radial),
+                       reinterpret_cast<const float2*>(spline_m), support, offsets,
+                       reinterpret_cast<float2*>(cache), (cudaStream_t)stream);
+}
+
+int wp_make_wkernels(const wp_plan* plan, const float* taper, const double* w_planes, int32_t P,
+                     int32_t* support, const int64_t* offsets, void* workspace, size_t workspace_bytes,
+                     float* radial, float* spline_m, float* cache, void* stream) {
+    if (!support || !offsets || !cache) return WP_ERR_NULL;
+    int rc = wp_hankel_radial(plan, taper, w_planes, P, workspace, workspace_bytes, radial, spline_m,
+                              support, stream);
+    if (rc) return rc;
+    return wp_resample(plan, radial, spline_m, P, support, offsets, cache, stream);
+}
+
+size_t wp_grid_workspace_bytes(const wp_plan* plan, int32_t P, int64_t V) {
+    Geom g;
+    if (make_geom(plan, &g) || P < 1 || V < 0) return 0;
+    return carve_grid(g, P, V, nullptr, 0, nullptr);
+}
+
+static int check_grid_args(const wp_plan* plan, const wp_wkernels* k, const float* uvw, int64_t V,
+                           void* workspace, size_t workspace_bytes, Geom* g) {
+    int rc = make_geom(plan, g);
+    if (rc) return rc;
+    if (!k || !workspace) return WP_ERR_NULL;
+    if (k->P < 1 || k->P > 8192) return WP_ERR_SIZE;
+    if (!k->w_planes || !k->support || !k->offsets || !k->cache) return WP_ERR_NULL;
+    if (V < 0 || V > 2147483647LL) return WP_ERR_SIZE;
+    if (V > 0 && !uvw) return WP_ERR_NULL;
+    if ((int64_t)k->P * ((g->N + 63) / 64) * ((g->N + 63) / 64) >= 2147483647LL) return WP_ERR_SIZE;
+    if (!aligned256(workspace) || workspace_bytes < carve_grid(*g, k->P, V, nullptr, 0, nullptr))
+        return WP_ERR_WORKSPACE;
+    return check_device();
+}
+
+int wp_grid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw, const float* vis,
+            const float* weight, int64_t V, void* workspace, size_t workspace_bytes, float* grid,
+            double* stats, void* stream) {
+    Geom g;
+    int rc = check_grid_args(plan, kernels, uvw, V, workspace, workspace_bytes, &g);
+    if (rc) return rc;
+    if (!grid || (V > 0 && !vis)) return WP_ERR_NULL;
+    cudaStream_t st = (cudaStream_t)stream;
+    GridWork w;
+    carve_grid(g, kernels->P, V, workspace, workspace_bytes, &w);
+    if ((rc = grid_bin(g, kernels, uvw, reinterpret_cast<const float2*>(vis), weight, V, w, st))) return rc;
+    return grid_run(g, kernels, w, reinterpret_cast<float2*>(grid), stats, st);
+}
+
+int wp_degrid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw, const float* grid,
+              int64_t V, void* workspace, size_t workspace_bytes, float* vis_out, void* stream) {
+    Geom g;
+    int rc = check_grid_args(plan, kernels, uvw, V, workspace, workspace_bytes, &g);
+    if (rc) return rc;
+    if (!grid || (V > 0 && !vis_out)) return WP_ERR_NULL;
+    cudaStream_t st = (cudaStream_t)stream;
+    GridWork w;
+    carve_grid(g, kernels->P, V, workspace, workspace_bytes, &w);
+    if ((rc = grid_bin(g, kernels, uvw, nullptr, nullptr, V, w, st))) return rc;
+    return degrid_run(g, kernels, V, w, reinterpret_cast<const float2*>(grid),
+                      reinterpret_cast<float2*>(vis_out), st);
+}
+
+int wp_dirty_image(const wp_plan* plan, const float* taper, float* grid, double weight_sum, float* image,
+                   void* stream) {
+    Geom g;
+    int rc = make_geom(plan, &g);
+    if (rc) return rc;
+    if (!taper || !grid || !image) return WP_ERR_NULL;
+    if (!(weight_sum > 0.0)) return WP_ERR_SIZE;
+    if ((rc = check_device())) return rc;
+    return image_dirty(g, taper, reinterpret_cast<float2*>(grid), weight_sum, image, (cudaStream_t)stream);
+}
+
+int wp_image_to_grid(const wp_plan* plan, const float* taper, const float* image, double weight_sum,
+                     float* grid, void* stream) {
+    Geom g;
+    int rc = make_geom(plan, &g);
+    if (rc) return rc;
+    if (!taper || !grid || !image) return WP_ERR_NULL;
+    if (!(weight_sum > 0.0)) return WP_ERR_SIZE;
+    if ((rc = check_device())) return rc;
+    return image_to_grid(g, taper, image, weight_sum, reinterpret_cast<float2*>(grid), (cudaStream_t)stream);
+}
+
+}  // extern "C"

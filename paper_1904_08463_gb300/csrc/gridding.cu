@@ -1,0 +1,450 @@
+// Convolutional gridding with w-projection kernels (Alg. 1 / Alg. 2 gridding step) and
+// its adjoint, degridding.
+//
+//   K9  bin      per visibility: nearest |w| plane, conjugation flag (w < 0, Section 4.1),
+//                grid cell + oversampling offset, drop test; all decisions in FP64
+//   --  sort     counting sort by (plane, 64 x 64 centre tile): histogram, exclusive scan,
+//                scatter (uv-sorted binning: consecutive records share a plane and a tile)
+//   --  items    work items (plane, output tile) that some visibility's footprint reaches
+//   K10 grid     persistent blocks pull work items in plane-major order; a block owns one
+//                64 x 64 output tile in registers (warp w owns rows 8w..8w+7, lane l owns
+//                columns l and l+32), streams the visibilities of the neighbouring centre
+//                tiles through shared memory, accumulates tap x visibility with no atomics,
+//                and flushes the tile to the grid once (one float2 atomic per touched cell)
+//   K11 degrid   one warp per visibility gathers conj(tap) x grid over the footprint and
+//                reduces with shuffles
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "wp_internal.cuh"
+
+namespace wp {
+
+namespace {
+constexpr int TILE = 64;           // output / centre tile side (cells)
+constexpr int GRID_WARPS = 8;      // warps per gridding block
+constexpr int ROWS_PER_WARP = TILE / GRID_WARPS;
+constexpr int STAGE = 256;         // visibilities staged per shared-memory round
+constexpr int SCAN_PER_BLOCK = 2048;
+}  // namespace
+
+// =======================================================================================
+// exclusive scan of int32 (n values -> n values; callers append a zero to get the total)
+// =======================================================================================
+__global__ void __launch_bounds__(256) k_scan_block(const int* __restrict__ in, int* __restrict__ out,
+                                                    int64_t n, int* __restrict__ block_sums) {
+    __shared__ int warp_tot[8];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_PER_BLOCK + threadIdx.x * 8;
+    int v[8];
+    int s = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        int64_t i = base + q;
+        v[q] = (i < n) ? in[i] : 0;
+        s += v[q];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    int woff = 0, btot = 0;
+    for (int q = 0; q < 8; ++q) {
+        if (q < wid) woff += warp_tot[q];
+        btot += warp_tot[q];
+    }
+    int run = woff + incl - s;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        int64_t i = base + q;
+        if (i < n) out[i] = run;
+        run += v[q];
+    }
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = btot;
+}
+
+__global__ void k_scan_add(int* __restrict__ out, int64_t n, const int* __restrict__ offs) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_PER_BLOCK;
+    const int add = offs[blockIdx.x];
+    for (int q = threadIdx.x; q < SCAN_PER_BLOCK; q += blockDim.x) {
+        int64_t i = base + q;
+        if (i < n) out[i] += add;
+    }
+}
+
+size_t scan_tmp_ints(int64_t n) {
+    size_t total = 0;
+    while (n > 1) {
+        int64_t nb = (n + SCAN_PER_BLOCK - 1) / SCAN_PER_BLOCK;
+        total += 2 * (size_t)nb + 64;
+        n = nb;
+    }
+    return total + 64;
+}
+
+int exclusive_scan_i32(const int* in, int* out, int64_t n, int* tmp, cudaStream_t st) {
+    if (n <= 0) return WP_OK;
+    int64_t nb = (n + SCAN_PER_BLOCK - 1) / SCAN_PER_BLOCK;
+    int* sums = tmp;
+    int* sums_scan = tmp + nb + 32;
+    k_scan_block<<<(unsigned)nb, 256, 0, st>>>(in, out, n, sums);
+    WP_LAUNCH_CHECK("k_scan_block");
+    if (nb > 1) {
+        int rc = exclusive_scan_i32(sums, sums_scan, nb, tmp + 2 * nb + 64, st);
+        if (rc) return rc;
+        k_scan_add<<<(unsigned)nb, 256, 0, st>>>(out, n, sums_scan);
+        WP_LAUNCH_CHECK("k_scan_add");
+    }
+    return WP_OK;
+}
+
+// =======================================================================================
+// K9: binning.  Record layout (int4): x = iu | iv << 16, y = fu | fv << 8 | conj << 16,
+// z = plane, w = original index.  key = plane * ntiles + (iv / T) * ntx + iu / T, or -1.
+// =======================================================================================
+__global__ void __launch_bounds__(256) k_bin(int64_t V, const float* __restrict__ uvw, int P,
+                                             const double* __restrict__ w_planes,
+                                             const int32_t* __restrict__ support, int s_max, int N,
+                                             double du, int os, int ntx, int ntiles,
+                                             const float* __restrict__ weight,
+                                             int* __restrict__ key, int4* __restrict__ rec,
+                                             int* __restrict__ count, double* __restrict__ red) {
+    extern __shared__ double wps[];
+    __shared__ double red_w[8];
+    __shared__ double red_d[8];
+    for (int i = threadIdx.x; i < P; i += blockDim.x) wps[i] = w_planes[i];
+    __syncthreads();
+    double wsum = 0.0, drops = 0.0;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < V) {
+        double u = (double)uvw[3 * k], v = (double)uvw[3 * k + 1], w = (double)uvw[3 * k + 2];
+        double aw = fabs(w);
+        // lower_bound over the ascending plane values, then nearest of the two neighbours
+        int lo = 0, hi = P;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (wps[mid] < aw) lo = mid + 1; else hi = mid;
+        }
+        int p;
+        if (lo == 0) p = 0;
+        else if (lo == P) p = P - 1;
+        else {
+            double dl_ = fabs(aw - wps[lo - 1]);
+            double dh_ = fabs(aw - wps[lo]);
+            p = (dh_ < dl_) ? lo : lo - 1;          // ties -> lower index
+        }
+        int conj = (w < 0.0) ? 1 : 0;
+        double uc = __dadd_rn(__ddiv_rn(u, du), (double)(N / 2));
+        double vc = __dadd_rn(__ddiv_rn(v, du), (double)(N / 2));
+        double tu = rint(__dmul_rn(uc, (double)os));
+        double tv = rint(__dmul_rn(vc, (double)os));
+        double giu = floor(__ddiv_rn(tu, (double)os));
+        double giv = floor(__ddiv_rn(tv, (double)os));
+        int S = min(max(support[p], 1), s_max);
+        bool ok = (giu - S >= 0.0) && (giu + S <= (double)(N - 1)) && (giv - S >= 0.0) &&
+                  (giv + S <= (double)(N - 1));
+        if (ok) {
+            int iu = (int)giu, iv = (int)giv;
+            int fu = (int)(tu - giu * (double)os);
+            int fv = (int)(tv - giv * (double)os);
+            int kk = p * ntiles + (iv / TILE) * ntx + (iu / TILE);
+            key[k] = kk;
+            rec[k] = make_int4(iu | (iv << 16), fu | (fv << 8) | (conj << 16), p, (int)k);
+            atomicAdd(&count[kk], 1);
+            wsum = weight ? (double)weight[k] : 1.0;
+        } else {
+            key[k] = -1;
+            drops = 1.0;
+        }
+    }
+    // block reduction of the statistics, one double atomic per block
+    for (int o = 16; o; o >>= 1) {
+        wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+        drops += __shfl_xor_sync(0xffffffffu, drops, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { red_w[wid] = wsum; red_d[wid] = drops; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a += red_w[q]; b += red_d[q]; }
+        if (a != 0.0) atomicAdd(&red[0], a);
+        if (b != 0.0) atomicAdd(&red[1], b);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scatter(int64_t V, const int* __restrict__ key,
+                                                 const int4* __restrict__ rec, const float2* __restrict__ vis,
+                                                 const float* __restrict__ weight, const int* __restrict__ start,
+                                                 int* __restrict__ cursor, int4* __restrict__ srec,
+                                                 float2* __restrict__ svis) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= V) return;
+    int kk = key[k];
+    if (kk < 0) return;
+    int pos = start[kk] + atomicAdd(&cursor[kk], 1);
+    srec[pos] = rec[k];
+    if (svis) {
+        float2 v = vis[k];
+        float a = weight ? weight[k] : 1.0f;
+        svis[pos] = make_float2(v.x * a, v.y * a);
+    }
+}
+
+// Work-item flags: item (p, tile) is live if any centre tile within ceil(S_p / T) tiles
+// holds a visibility of plane p (a footprint reaches at most that far).  Bin b's
+// visibilities are [start[b], start[b+1]) of the sorted arrays (start[nbins] = total).
+__global__ void __launch_bounds__(256) k_item_flags(int P, int ntx, int ntiles, int s_max,
+                                                    const int32_t* __restrict__ support,
+                                                    const int* __restrict__ start, int* __restrict__ flags) {
+    const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = (int64_t)P * ntiles;
+    if (it >= n) { if (it == n) flags[n] = 0; return; }
+    int p = (int)(it / ntiles);
+    int t = (int)(it - (int64_t)p * ntiles);
+    int oy = t / ntx, ox = t - oy * ntx;
+    int D = (min(max(support[p], 1), s_max) + TILE - 1) / TILE;
+    // `start` holds the exclusive scan of the per-bin counts, so a run of bins
+    // [a, b] is non-empty iff start[b + 1] > start[a]
+    const int* s = start + (int64_t)p * ntiles;
+    const int cx_lo = max(0, ox - D), cx_hi = min(ntx - 1, ox + D);
+    int any = 0;
+    for (int cy = max(0, oy - D); cy <= min(ntx - 1, oy + D); ++cy)
+        any |= (s[cy * ntx + cx_hi + 1] > s[cy * ntx + cx_lo]);
+    flags[it] = any;
+}
+
+__global__ void __launch_bounds__(256) k_item_write(int64_t n, const int* __restrict__ flags,
+                                                    const int* __restrict__ pos, int* __restrict__ items,
+                                                    int* __restrict__ ctrl) {
+    const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it < n && flags[it]) items[pos[it]] = (int)it;
+    if (it == n - 1) ctrl[1] = pos[it] + flags[it];
+}
+
+int grid_bin(const Geom& g, const wp_wkernels* kern, const float* uvw, const float2* vis,
+             const float* weight, int64_t V, const GridWork& w, cudaStream_t st) {
+    const int P = kern->P;
+    WP_CUDA(cudaMemsetAsync(w.count, 0, sizeof(int) * (size_t)(w.nbins + 1), st));
+    WP_CUDA(cudaMemsetAsync(w.cursor, 0, sizeof(int) * (size_t)w.nbins, st));
+    WP_CUDA(cudaMemsetAsync(w.ctrl, 0, sizeof(int) * 8, st));
+    WP_CUDA(cudaMemsetAsync(w.red, 0, sizeof(double) * 2, st));
+    if (V > 0) {
+        unsigned blocks = (unsigned)((V + 255) / 256);
+        size_t smem = (size_t)P * sizeof(double);
+        if (smem > 48 * 1024)
+            WP_CUDA(cudaFuncSetAttribute(k_bin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_bin<<<blocks, 256, smem, st>>>(V, uvw, P, kern->w_planes, kern->support, g.s_max, g.N, g.du,
+                                         g.os, w.ntx, w.ntiles, weight, w.key, w.rec, w.count, w.red);
+        WP_LAUNCH_CHECK("k_bin");
+    }
+    int rc = exclusive_scan_i32(w.count, w.count, w.nbins + 1, w.scan_tmp, st);
+    if (rc) return rc;
+    if (V > 0) {
+        unsigned blocks = (unsigned)((V + 255) / 256);
+        k_scatter<<<blocks, 256, 0, st>>>(V, w.key, w.rec, vis, weight, w.count, w.cursor, w.srec,
+                                          vis ? w.svis : nullptr);
+        WP_LAUNCH_CHECK("k_scatter");
+    }
+    return WP_OK;
+}
+
+// =======================================================================================
+// K10: gridding
+// =======================================================================================
+__global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(int N, int os, int s_max, int ntx, int ntiles,
+                                                          const int32_t* __restrict__ support,
+                                                          const int64_t* __restrict__ offsets,
+                                                          const float2* __restrict__ cache,
+                                                          const int* __restrict__ start,
+                                                          const int4* __restrict__ srec,
+                                                          const float2* __restrict__ svis,
+                                                          const int* __restrict__ items,
+                                                          int* __restrict__ ctrl, float2* __restrict__ grid) {
+    __shared__ int4 s_rec[STAGE];
+    __shared__ float2 s_vis[STAGE];
+    __shared__ int s_item;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int n_items = ctrl[1];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&ctrl[0], 1);
+        __syncthreads();
+        const int item_idx = s_item;
+        __syncthreads();
+        if (item_idx >= n_items) break;
+        const int item = items[item_idx];
+        const int p = item / ntiles;
+        const int t = item - p * ntiles;
+        const int oy = t / ntx, ox = t - oy * ntx;
+        const int S = min(max(support[p], 1), s_max);
+        const int W = 2 * S + 1;
+        const int W2 = W * W;
+        const int D = (S + TILE - 1) / TILE;
+        const float2* pcache = cache + offsets[p];
+        const int R0 = oy * TILE + wid * ROWS_PER_WARP;
+        const int C0 = ox * TILE + lane;
+        float2 acc[ROWS_PER_WARP][2];
+#pragma unroll
+        for (int r = 0; r < ROWS_PER_WARP; ++r) {
+            acc[r][0] = make_float2(0.f, 0.f);
+            acc[r][1] = make_float2(0.f, 0.f);
+        }
+        const int cx_lo = max(0, ox - D), cx_hi = min(ntx - 1, ox + D);
+        for (int cy = max(0, oy - D); cy <= min(ntx - 1, oy + D); ++cy) {
+            const int kb = p * ntiles + cy * ntx;
+            const int beg = start[kb + cx_lo], end = start[kb + cx_hi + 1];
+            for (int c0 = beg; c0 < end; c0 += STAGE) {
+                const int n = min(STAGE, end - c0);
+                for (int q = threadIdx.x; q < n; q += blockDim.x) {
+                    s_rec[q] = srec[c0 + q];
+                    s_vis[q] = svis[c0 + q];
+                }
+                __syncthreads();
+                for (int q = 0; q < n; ++q) {
+                    const int4 r4 = s_rec[q];
+                    const int iu = r4.x & 0xffff, iv = (r4.x >> 16) & 0xffff;
+                    const int ry0 = iv - S;
+                    if (ry0 > R0 + ROWS_PER_WARP - 1 || ry0 + 2 * S < R0) continue;
+                    const int fu = r4.y & 0xff, fv = (r4.y >> 8) & 0xff;
+                    const float sgn = (r4.y >> 16) ? -1.0f : 1.0f;
+                    const float2 vv = s_vis[q];
+                    const float2* sub = pcache + (int64_t)(fv * os + fu) * W2;
+                    const int jx0 = C0 - (iu - S);
+                    const int jx1 = jx0 + 32;
+                    const bool v0 = (unsigned)jx0 <= (unsigned)(2 * S);
+                    const bool v1 = (unsigned)jx1 <= (unsigned)(2 * S);
+#pragma unroll
+                    for (int r = 0; r < ROWS_PER_WARP; ++r) {
+                        const int jy = R0 + r - ry0;
+                        if ((unsigned)jy <= (unsigned)(2 * S)) {
+                            const float2* row = sub + jy * W;
+                            if (v0) {
+                                float2 tp = __ldg(row + jx0);
+                                float ti = sgn * tp.y;
+                                acc[r][0].x = fmaf(vv.x, tp.x, fmaf(-vv.y, ti, acc[r][0].x));
+                                acc[r][0].y = fmaf(vv.x, ti, fmaf(vv.y, tp.x, acc[r][0].y));
+                            }
+                            if (v1) {
+                                float2 tp = __ldg(row + jx1);
+                                float ti = sgn * tp.y;
+                                acc[r][1].x = fmaf(vv.x, tp.x, fmaf(-vv.y, ti, acc[r][1].x));
+                                acc[r][1].y = fmaf(vv.x, ti, fmaf(vv.y, tp.x, acc[r][1].y));
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // flush the tile: one atomic per touched cell
+#pragma unroll
+        for (int r = 0; r < ROWS_PER_WARP; ++r) {
+            const int row = R0 + r;
+            if (row >= N) continue;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int col = C0 + 32 * c;
+                if (col < N && (acc[r][c].x != 0.0f || acc[r][c].y != 0.0f))
+                    atomicAdd(grid + (int64_t)row * N + col, acc[r][c]);
+            }
+        }
+    }
+}
+
+__global__ void k_add_stats(double* stats, const double* red) {
+    if (threadIdx.x < 2) stats[threadIdx.x] += red[threadIdx.x];
+}
+
+int add_stats(double* stats, const double* red, cudaStream_t st) {
+    k_add_stats<<<1, 32, 0, st>>>(stats, red);
+    WP_LAUNCH_CHECK("k_add_stats");
+    return WP_OK;
+}
+
+int grid_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, float2* grid, double* stats,
+             cudaStream_t st) {
+    const int P = kern->P;
+    const int64_t n = (int64_t)P * w.ntiles;
+    unsigned blocks = (unsigned)((n + 1 + 255) / 256);
+    k_item_flags<<<blocks, 256, 0, st>>>(P, w.ntx, w.ntiles, g.s_max, kern->support, w.count, w.flags);
+    WP_LAUNCH_CHECK("k_item_flags");
+    // the flag scan reuses the cursor array as output (cursor is no longer needed)
+    int rc = exclusive_scan_i32(w.flags, w.cursor, n, w.scan_tmp, st);
+    if (rc) return rc;
+    k_item_write<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, w.flags, w.cursor, w.items, w.ctrl);
+    WP_LAUNCH_CHECK("k_item_write");
+    int dev = 0, sms = 0, per_sm = 0;
+    WP_CUDA(cudaGetDevice(&dev));
+    WP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid, GRID_WARPS * 32, 0));
+    if (per_sm < 1) per_sm = 1;
+    k_grid<<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(g.N, g.os, g.s_max, w.ntx, w.ntiles, kern->support, kern->offsets,
+                                                     reinterpret_cast<const float2*>(kern->cache), w.count,
+                                                     w.srec, w.svis, w.items, w.ctrl, grid);
+    WP_LAUNCH_CHECK("k_grid");
+    if (stats) {
+        rc = add_stats(stats, w.red, st);
+        if (rc) return rc;
+    }
+    return WP_OK;
+}
+
+// =======================================================================================
+// K11: degridding (adjoint).  One warp per binned visibility.
+// =======================================================================================
+__global__ void __launch_bounds__(256) k_degrid(int N, int os, int s_max, int nbins,
+                                                const int32_t* __restrict__ support,
+                                                const int64_t* __restrict__ offsets,
+                                                const float2* __restrict__ cache, const int* __restrict__ start,
+                                                const int4* __restrict__ srec, const float2* __restrict__ grid,
+                                                float2* __restrict__ vis_out, int64_t V) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wpos = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int n_valid = start[nbins];
+    if (wpos >= n_valid || wpos >= V) return;
+    const int4 r4 = srec[wpos];
+    const int iu = r4.x & 0xffff, iv = (r4.x >> 16) & 0xffff;
+    const int fu = r4.y & 0xff, fv = (r4.y >> 8) & 0xff;
+    const float sgn = (r4.y >> 16) ? -1.0f : 1.0f;
+    const int p = r4.z;
+    const int S = min(max(support[p], 1), s_max);
+    const int W = 2 * S + 1;
+    const float2* sub = cache + offsets[p] + (int64_t)(fv * os + fu) * W * W;
+    const float2* g0 = grid + (int64_t)(iv - S) * N + (iu - S);
+    float sr = 0.0f, si = 0.0f;
+    for (int jy = 0; jy < W; ++jy) {
+        const float2* trow = sub + jy * W;
+        const float2* grow = g0 + (int64_t)jy * N;
+        for (int jx = lane; jx < W; jx += 32) {
+            float2 tp = __ldg(trow + jx);
+            float ti = sgn * tp.y;
+            float2 gv = grow[jx];
+            // conj(K) * g
+            sr = fmaf(tp.x, gv.x, fmaf(ti, gv.y, sr));
+            si = fmaf(tp.x, gv.y, fmaf(-ti, gv.x, si));
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) vis_out[r4.w] = make_float2(sr, si);
+}
+
+int degrid_run(const Geom& g, const wp_wkernels* kern, int64_t V, const GridWork& w, const float2* grid,
+               float2* vis_out, cudaStream_t st) {
+    WP_CUDA(cudaMemsetAsync(vis_out, 0, sizeof(float2) * (size_t)V, st));
+    if (V == 0) return WP_OK;
+    int64_t threads = V * 32;
+    unsigned blocks = (unsigned)((threads + 255) / 256);
+    k_degrid<<<blocks, 256, 0, st>>>(g.N, g.os, g.s_max, (int)w.nbins, kern->support, kern->offsets,
+                                     reinterpret_cast<const float2*>(kern->cache), w.count, w.srec, grid,
+                                     vis_out, V);
+    WP_LAUNCH_CHECK("k_degrid");
+    return WP_OK;
+}
+
+}  // namespace wp

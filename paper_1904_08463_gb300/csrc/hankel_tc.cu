@@ -1,0 +1,320 @@
+// Hankel transform on the 5th-generation tensor cores (Section 4.3: the discrete transform
+// is a matrix times a vector; all planes together make one matrix product).
+//
+//   C[m][n] = sum_k H[m][k] F[n][k],  m < K_out (radial output), n < 2 P_pad (re/im of each
+//   plane), k < R_pad (radial input).
+//
+// Precision: TF32 inputs carry 11 significant bits, so each operand is split into
+// hi = rna_tf32(x) and lo = rna_tf32(x - hi); the product is hi*hi' + hi*lo' + lo*hi'
+// (the lo*lo' term is below 2^-22 relative), accumulated in FP32 in tensor memory.
+//
+// Structure (one CTA = one 128 x 128 output tile, optionally one half of K):
+//   warp 0 lane 0   TMA producer: per 32-deep K slice loads A_hi, A_lo, B_hi, B_lo tiles
+//                   (128 rows x 128 B each, 128-byte swizzle) into a 3-stage ring
+//   warp 1 lane 0   MMA issuer: 4 K-steps x 3 products of tcgen05.mma.kind::tf32
+//                   (M = 128, N = 128, K = 8) per slice, commits each stage back to the
+//                   producer and the whole tile to the epilogue
+//   warps 0-3       epilogue: tcgen05.ld of the 128 x 128 FP32 accumulator (warp w reads
+//                   TMEM lanes 32w..32w+31), column pairs (2p, 2p+1) stored as the complex
+//                   radial sample of plane p (coalesced along the radial index)
+// Every mbarrier wait is bounded by a clock budget; on expiry the kernel records
+// WP_ERR_TIMEOUT in `status`, stops issuing, drains what it issued, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "wp_internal.cuh"
+
+namespace wp {
+
+namespace tc {
+
+constexpr int BM = 128, BN = 128, BK = 32;           // BK fp32 = 128 bytes = one swizzle row
+constexpr int STAGES = 3;
+constexpr int TILE_BYTES = BM * BK * 4;              // 16 KB (BN == BM)
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;          // A_hi, A_lo, B_hi, B_lo
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int TMEM_COLS = 128;
+constexpr long long WAIT_BUDGET = 4000000000LL;      // ~2 s of SM clock per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: true when the phase with `parity` completed, false after the budget.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status) {
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > WAIT_BUDGET) {
+            atomicExch(status, WP_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row atoms of
+// 1024 bytes stacked along M/N (stride 1024 B), version field 0b001 at bits 46-48.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);            // start address
+    d |= (uint64_t)1 << 16;                             // leading byte offset (unused, 16 B)
+    d |= (uint64_t)(1024 >> 4) << 32;                   // stride byte offset
+    d |= (uint64_t)1 << 46;                             // fixed 0b001
+    d |= (uint64_t)2 << 61;                             // swizzle: 128 B
+    return d;
+}
+
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(128, 1) k_hankel_tf32x3(const __grid_constant__ CUtensorMap map_a_hi,
+                                                          const __grid_constant__ CUtensorMap map_a_lo,
+                                                          const __grid_constant__ CUtensorMap map_b_hi,
+                                                          const __grid_constant__ CUtensorMap map_b_lo,
+                                                          int M, int K, int k_split, int P,
+                                                          float2* __restrict__ radial, int use_atomic,
+                                                          int* __restrict__ status) {
+    extern __shared__ uint8_t smem_raw[];
+    // 1024-byte aligned stage ring (required by the 128-byte swizzle atoms)
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* gbase = smem_raw + (base - raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * STAGE_BYTES);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
+    const uint32_t bar_full0 = smem_u32(bars);
+    const uint32_t bar_empty0 = smem_u32(bars + STAGES);
+    const uint32_t bar_done = smem_u32(bars + 2 * STAGES);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+    const int kchunk = K / k_split;
+    const int kbeg = blockIdx.z * kchunk;
+    const int nkb = kchunk / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(bar_full0 + 8 * s, 1);
+            mbar_init(bar_empty0 + 8 * s, 1);
+        }
+        mbar_init(bar_done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        int issued = 0;
+        bool ok = true;
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES) ok = mbar_wait(bar_empty0 + 8 * s, ((kb / STAGES) - 1) & 1, status);
+            if (!ok) break;
+            const uint32_t st = base + s * STAGE_BYTES;
+            const uint32_t fb = bar_full0 + 8 * s;
+            mbar_expect_tx(fb, STAGE_BYTES);
+            const int x = kbeg + kb * BK;
+            tma_load_2d(st + 0 * TILE_BYTES, &map_a_hi, x, m0, fb);
+            tma_load_2d(st + 1 * TILE_BYTES, &map_a_lo, x, m0, fb);
+            tma_load_2d(st + 2 * TILE_BYTES, &map_b_hi, x, n0, fb);
+            tma_load_2d(st + 3 * TILE_BYTES, &map_b_lo, x, n0, fb);
+            ++issued;
+        }
+        if (!ok) {
+            // drain: every issued slice must land before the CTA may exit
+            for (int kb = max(0, issued - STAGES); kb < issued; ++kb)
+                mbar_wait(bar_full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, status);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        const uint32_t idesc = idesc_tf32(BM, BN);
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % STAGES;
+            if (!mbar_wait(bar_full0 + 8 * s, (kb / STAGES) & 1, status)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t st = base + s * STAGE_BYTES;
+            const uint64_t a_hi = smem_desc_sw128(st + 0 * TILE_BYTES);
+            const uint64_t a_lo = smem_desc_sw128(st + 1 * TILE_BYTES);
+            const uint64_t b_hi = smem_desc_sw128(st + 2 * TILE_BYTES);
+            const uint64_t b_lo = smem_desc_sw128(st + 3 * TILE_BYTES);
+#pragma unroll
+            for (int j = 0; j < BK / 8; ++j) {
+                const uint64_t adv = (uint64_t)((j * 32) >> 4);   // 8 tf32 = 32 bytes along K
+                mma_tf32(tmem, a_hi + adv, b_hi + adv, idesc, (kb | j) != 0);
+                mma_tf32(tmem, a_hi + adv, b_lo + adv, idesc, 1u);
+                mma_tf32(tmem, a_lo + adv, b_hi + adv, idesc, 1u);
+            }
+            mma_commit(bar_empty0 + 8 * s);
+        }
+        mma_commit(bar_done);   // fires once every issued MMA has completed
+    }
+    __syncwarp();
+
+    // ---------------- epilogue: all four warps ----------------
+    const bool done = mbar_wait(bar_done, 0, status);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (done && *status == 0) {
+        const int m = m0 + warp * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            float v[32];
+            tmem_ld_x32(trow + c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+                const int p = (n0 + c0 + j) >> 1;
+                if (p < P && m < M) {
+                    float2* dst = radial + (int64_t)p * M + m;
+                    if (use_atomic) atomicAdd(dst, make_float2(v[j], v[j + 1]));
+                    else *dst = make_float2(v[j], v[j + 1]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    }
+}
+
+// ------------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 2D row-major FP32 matrix [rows][cols] (cols contiguous), box 32 cols x 128 rows,
+// 128-byte swizzle.  Base must be 16-byte aligned and cols*4 a multiple of 16.
+int make_map(CUtensorMap* map, const float* ptr, int rows, int cols) {
+    auto enc = get_encode();
+    if (!enc) {
+        set_last_error("cuTensorMapEncodeTiled", "driver entry point unavailable");
+        return WP_ERR_CUDA;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_last_error("cuTensorMapEncodeTiled", "encoding failed");
+        return WP_ERR_CUDA;
+    }
+    return WP_OK;
+}
+
+}  // namespace tc
+
+int kg_gemm_tf32x3(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st) {
+    using namespace tc;
+    const int M = g.k_out, N = 2 * p_pad(P), K = g.r_pad;
+    if (M % BM || N % BN || K % BK) {
+        set_last_error("kg_gemm_tf32x3", "shape not tile aligned");
+        return WP_ERR_SIZE;
+    }
+    CUtensorMap ma_hi, ma_lo, mb_hi, mb_lo;
+    int rc;
+    if ((rc = make_map(&ma_hi, w.h_hi, M, K))) return rc;
+    if ((rc = make_map(&ma_lo, w.h_lo, M, K))) return rc;
+    if ((rc = make_map(&mb_hi, w.f_hi, N, K))) return rc;
+    if ((rc = make_map(&mb_lo, w.f_lo, N, K))) return rc;
+    const int tiles = (M / BM) * (N / BN);
+    const int split = (tiles < 152 && (K / 2) % BK == 0) ? 2 : 1;
+    WP_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+    if (split > 1) WP_CUDA(cudaMemsetAsync(radial, 0, (size_t)P * M * sizeof(float2), st));
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(k_hankel_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    });
+    WP_CUDA(attr_err);
+    dim3 grid(N / BN, M / BM, split);
+    k_hankel_tf32x3<<<grid, 128, SMEM_BYTES, st>>>(ma_hi, ma_lo, mb_hi, mb_lo, M, K, split, P, radial,
+                                                   split > 1, status);
+    WP_LAUNCH_CHECK("k_hankel_tf32x3");
+    return WP_OK;
+}
+
+}  // namespace wp

@@ -1,0 +1,425 @@
+// Kernel generation on the radial line (Section 4.3 of the paper, Alg. 2):
+//   K1 j0 matrix   H[k][i] = du^2 2 pi r_i dr J0(2 pi rho_k r_i)   (FP64 evaluation, once)
+//   K2 screen      f_p(r_i) = t(r_i) exp(+2 pi j w_p (sqrt(1 - r_i^2) - 1)) (FP64 phase)
+//   K4 fp32 gemm   C = H F (FP32 SIMT matrix product, the plain comparator)
+//   K5/K6          1 % truncation support and cubic-spline second derivatives
+//   K7 resample    oversampled 2D kernel cache from the radial line
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "wp_internal.cuh"
+
+namespace wp {
+
+// =======================================================================================
+// K1: transform matrix, built once per geometry (Section 4.3: it does not depend on the plane).
+// With du * r_max = 1/2 the argument and weight reduce to integers times constants:
+//   2 pi rho_k r_i = pi k (2i + 1) / (2 os R),   du^2 2 pi r_i dr = pi (2i + 1) / (4 R^2).
+// The TF32 split keeps hi = rna_tf32(h), lo = rna_tf32(h - hi) so that
+// hi*hi' + hi*lo' + lo*hi' reproduces the FP32 product to ~2^-22.
+// =======================================================================================
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__global__ void k_j0_matrix(int k_out, int R, int r_pad, int os, float* __restrict__ h32,
+                            float* __restrict__ h_hi, float* __restrict__ h_lo) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t total = (int64_t)k_out * r_pad;
+    if (idx >= total) return;
+    int k = (int)(idx / r_pad);
+    int i = (int)(idx - (int64_t)k * r_pad);
+    float v = 0.0f;
+    if (i < R) {
+        double two_i1 = (double)(2 * i + 1);
+        double arg = M_PI * ((double)k * two_i1) / (2.0 * (double)os * (double)R);
+        double wgt = M_PI * two_i1 / (4.0 * (double)R * (double)R);
+        v = (float)(wgt * j0(arg));
+    }
+    h32[idx] = v;
+    float hi = to_tf32(v);
+    h_hi[idx] = hi;
+    h_lo[idx] = to_tf32(v - hi);
+}
+
+// Host: band of the inverse of the spline system matrix (rows: [2 1], [1 4 1] ..., [.. 1]).
+// Entries of the inverse decay like (2 - sqrt 3)^|k - j| = 0.268^|k - j|, so a half-width
+// of 32 keeps everything above 1e-18 of the diagonal.
+static void spline_band_host(int K, std::vector<float>& band) {
+    const int HW = 32;
+    band.assign((size_t)K * (2 * HW + 1), 0.0f);
+    std::vector<double> sub(K, 0.0), dia(K, 0.0), sup(K, 0.0), cp(K), x(K), d(K);
+    dia[0] = 2.0; sup[0] = 1.0;
+    for (int k = 1; k < K - 1; ++k) { sub[k] = 1.0; dia[k] = 4.0; sup[k] = 1.0; }
+    dia[K - 1] = 1.0;
+    // forward factor (independent of the right-hand side)
+    cp[0] = sup[0] / dia[0];
+    std::vector<double> den(K);
+    den[0] = dia[0];
+    for (int k = 1; k < K; ++k) {
+        den[k] = dia[k] - sub[k] * cp[k - 1];
+        cp[k] = sup[k] / den[k];
+    }
+    for (int j = 0; j < K; ++j) {
+        // solve A x = e_j
+        for (int k = 0; k < K; ++k) {
+            double rhs = (k == j) ? 1.0 : 0.0;
+            d[k] = (rhs - (k > 0 ? sub[k] * d[k - 1] : 0.0)) / den[k];
+        }
+        x[K - 1] = d[K - 1];
+        for (int k = K - 2; k >= 0; --k) x[k] = d[k] - cp[k] * x[k + 1];
+        for (int k = j - HW; k <= j + HW; ++k) {
+            if (k < 0 || k >= K) continue;
+            band[(size_t)k * (2 * HW + 1) + (j - k + HW)] = (float)x[k];
+        }
+    }
+}
+
+int kg_prepare(const Geom& g, const KgWork& w, cudaStream_t st) {
+    int64_t total = (int64_t)g.k_out * g.r_pad;
+    int threads = 256;
+    int64_t blocks = (total + threads - 1) / threads;
+    k_j0_matrix<<<(unsigned)blocks, threads, 0, st>>>(g.k_out, g.R, g.r_pad, g.os, w.h32, w.h_hi,
+                                                       w.h_lo);
+    WP_LAUNCH_CHECK("k_j0_matrix");
+    std::vector<float> band;
+    spline_band_host(g.k_out, band);
+    WP_CUDA(cudaMemcpyAsync(w.band, band.data(), band.size() * sizeof(float),
+                            cudaMemcpyHostToDevice, st));
+    // the host vector must outlive the copy: pageable copies are staged before return
+    WP_CUDA(cudaStreamSynchronize(st));
+    return WP_OK;
+}
+
+// =======================================================================================
+// K2: image-domain convolution function on the radial line, written transposed
+// (row 2p = real part, row 2p+1 = imaginary part, R contiguous) as the B operand of the
+// K-major matrix product.  The phase w (n - 1) is formed in FP64 with the cancellation-
+// free n - 1 = -r^2 / (1 + sqrt(1 - r^2)), reduced to [-1/2, 1/2] cycles in FP64, and
+// only then handed to the FP32 sincospi.
+// =======================================================================================
+template <bool SPLIT>
+__global__ void k_screen(int R, int r_pad, int P, int P_pad, double r_max,
+                         const float* __restrict__ taper, const double* __restrict__ w_planes,
+                         float* __restrict__ f32, float* __restrict__ f_hi, float* __restrict__ f_lo) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int p = blockIdx.y;
+    if (i >= r_pad) return;
+    float re = 0.0f, im = 0.0f;
+    if (i < R && p < P) {
+        double r = ((double)i + 0.5) * (r_max / (double)R);
+        double r2 = r * r;
+        double nm1 = -r2 / (1.0 + sqrt(1.0 - r2));
+        double cyc = w_planes[p] * nm1;            // phase / (2 pi)
+        double fr = cyc - rint(cyc);               // in [-1/2, 1/2]
+        float s, c;
+        sincospif((float)(2.0 * fr), &s, &c);
+        float t = taper[i];
+        re = t * c;
+        im = t * s;
+    }
+    int64_t row_re = (int64_t)(2 * p) * r_pad + i;
+    int64_t row_im = row_re + r_pad;
+    if (SPLIT) {
+        float hr = to_tf32(re), hi = to_tf32(im);
+        f_hi[row_re] = hr;
+        f_hi[row_im] = hi;
+        f_lo[row_re] = to_tf32(re - hr);
+        f_lo[row_im] = to_tf32(im - hi);
+    } else {
+        f32[row_re] = re;
+        f32[row_im] = im;
+    }
+}
+
+int kg_screen(const Geom& g, const KgWork& w, const float* taper, const double* w_planes, int P,
+              cudaStream_t st) {
+    int Pp = p_pad(P);
+    dim3 grid((g.r_pad + 255) / 256, Pp);
+    if (g.kernelgen == WP_KG_TF32X3)
+        k_screen<true><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, g.r_max, taper, w_planes, w.f32,
+                                             w.f_hi, w.f_lo);
+    else
+        k_screen<false><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, g.r_max, taper, w_planes, w.f32,
+                                              w.f_hi, w.f_lo);
+    WP_LAUNCH_CHECK("k_screen");
+    return WP_OK;
+}
+
+// =======================================================================================
+// K4: plain FP32 SIMT matrix product  D[m][n] = sum_k A[m][k] B[n][k]
+//   A = H [M = k_out][K = r_pad], B = F^T [N = 2 P_pad][K], both K-contiguous.
+// 128 x 128 block tile, 32-deep K slices through shared memory, 8 x 8 register tile per
+// thread.  Output column n = 2p + c is component c of radial[p][m].  With split-K = 2
+// the two halves are combined with atomicAdd into a zeroed output (two addends: the
+// result does not depend on their order).
+// =======================================================================================
+namespace {
+constexpr int GB_M = 128, GB_N = 128, GB_K = 32, GB_PAD = 4;
+}
+
+__global__ void __launch_bounds__(256) k_gemm_fp32(int M, int N, int K, int k_split,
+                                                   const float* __restrict__ A,
+                                                   const float* __restrict__ B, int P,
+                                                   float2* __restrict__ radial, int use_atomic) {
+    __shared__ __align__(16) float As[GB_K][GB_M + GB_PAD];
+    __shared__ __align__(16) float Bs[GB_K][GB_N + GB_PAD];
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
+    const int kchunk = K / k_split;
+    const int kbeg = blockIdx.z * kchunk, kend = kbeg + kchunk;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+
+    for (int k0 = kbeg; k0 < kend; k0 += GB_K) {
+        // 128 rows x 32 k = 1024 float4 per operand, 4 per thread
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int e = tid + q * 256;
+            int row = e / 8, kq = (e % 8) * 4;
+            float4 a = *reinterpret_cast<const float4*>(A + (int64_t)(m0 + row) * K + k0 + kq);
+            float4 b = *reinterpret_cast<const float4*>(B + (int64_t)(n0 + row) * K + k0 + kq);
+            As[kq + 0][row] = a.x; As[kq + 1][row] = a.y; As[kq + 2][row] = a.z; As[kq + 3][row] = a.w;
+            Bs[kq + 0][row] = b.x; Bs[kq + 1][row] = b.y; Bs[kq + 2][row] = b.z; Bs[kq + 3][row] = b.w;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < GB_K; ++kk) {
+            float a[8], b[8];
+            float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
+            float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
+            float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8]);
+            float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8 + 4]);
+            a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w; a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+            b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w; b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        int m = m0 + ty * 8 + i;
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            int n = n0 + tx * 8 + j;
+            int p = n >> 1;
+            if (p < P) {
+                float2* dst = radial + (int64_t)p * M + m;
+                if (use_atomic) {
+                    atomicAdd(&dst->x, acc[i][j]);
+                    atomicAdd(&dst->y, acc[i][j + 1]);
+                } else {
+                    *dst = make_float2(acc[i][j], acc[i][j + 1]);
+                }
+            }
+        }
+    }
+}
+
+int kg_gemm_fp32(const Geom& g, const KgWork& w, int P, float2* radial, cudaStream_t st) {
+    int M = g.k_out, N = 2 * p_pad(P), K = g.r_pad;
+    int tiles = (M / GB_M) * (N / GB_N);
+    int split = (tiles < 152 && (K / 2) % GB_K == 0) ? 2 : 1;
+    if (split > 1) WP_CUDA(cudaMemsetAsync(radial, 0, (size_t)P * M * sizeof(float2), st));
+    dim3 grid(N / GB_N, M / GB_M, split);
+    k_gemm_fp32<<<grid, 256, 0, st>>>(M, N, K, split, w.h32, w.f32, P, radial, split > 1);
+    WP_LAUNCH_CHECK("k_gemm_fp32");
+    return WP_OK;
+}
+
+// =======================================================================================
+// K5 + K6: per plane (one block): 1 % truncation support and spline second derivatives.
+// Support: last k with |C_k| >= tau * max |C|, S = ceil(k / os) clamped to [S_min, S_max].
+// Spline: m = A^-1 rhs with rhs_0 = 6 (y1 - y0), rhs_k = 6 (y_{k+1} - 2 y_k + y_{k-1}),
+// rhs_{K-1} = 0 (zero slope at rho = 0, natural end), using the precomputed band of A^-1.
+// =======================================================================================
+__global__ void __launch_bounds__(256) k_trunc_spline(int K, int os, int s_min, int s_max, float tau,
+                                                      int do_trunc, int do_spline,
+                                                      const float2* __restrict__ radial,
+                                                      const float* __restrict__ band,
+                                                      float2* __restrict__ spline_m,
+                                                      int32_t* __restrict__ support) {
+    extern __shared__ float2 y[];   // [K]
+    __shared__ float red_f[8];
+    __shared__ int red_i[8];
+    const int p = blockIdx.x;
+    const float2* src = radial + (int64_t)p * K;
+    float local_max = 0.0f;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        float2 v = src[k];
+        y[k] = v;
+        local_max = fmaxf(local_max, sqrtf(v.x * v.x + v.y * v.y));
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (do_trunc) {
+        for (int o = 16; o; o >>= 1) local_max = fmaxf(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+        if (lane == 0) red_f[wid] = local_max;
+        __syncthreads();
+        float mx = 0.0f;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) mx = fmaxf(mx, red_f[q]);
+        float thr = tau * mx;
+        int last = 0;
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            float2 v = y[k];
+            if (sqrtf(v.x * v.x + v.y * v.y) >= thr) last = max(last, k);
+        }
+        for (int o = 16; o; o >>= 1) last = max(last, __shfl_xor_sync(0xffffffffu, last, o));
+        if (lane == 0) red_i[wid] = last;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int kl = 0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) kl = max(kl, red_i[q]);
+            int s = (kl + os - 1) / os;
+            s = min(max(s, s_min), s_max);
+            support[p] = s;
+        }
+    }
+    if (do_spline) {
+        float2* dst = spline_m + (int64_t)p * K;
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            const float* b = band + (int64_t)k * 65;
+            float mr = 0.0f, mi = 0.0f;
+            for (int d = -32; d <= 32; ++d) {
+                int j = k + d;
+                if (j < 0 || j >= K) continue;
+                float rr, ri;
+                if (j == 0) {
+                    rr = 6.0f * (y[1].x - y[0].x);
+                    ri = 6.0f * (y[1].y - y[0].y);
+                } else if (j == K - 1) {
+                    rr = 0.0f;
+                    ri = 0.0f;
+                } else {
+                    rr = 6.0f * ((y[j + 1].x - y[j].x) - (y[j].x - y[j - 1].x));
+                    ri = 6.0f * ((y[j + 1].y - y[j].y) - (y[j].y - y[j - 1].y));
+                }
+                float c = b[d + 32];
+                mr = fmaf(c, rr, mr);
+                mi = fmaf(c, ri, mi);
+            }
+            dst[k] = make_float2(mr, mi);
+        }
+    }
+}
+
+int kg_trunc_spline(const Geom& g, const KgWork& w, int P, const float2* radial, float2* spline_m,
+                    int32_t* support, cudaStream_t st) {
+    int do_trunc = (g.tau > 0.0) ? 1 : 0;
+    int do_spline = (g.interp == WP_INTERP_CUBIC) ? 1 : 0;
+    if (!do_trunc && !do_spline) return WP_OK;
+    size_t smem = (size_t)g.k_out * sizeof(float2);
+    if (smem > 48 * 1024)
+        WP_CUDA(cudaFuncSetAttribute(k_trunc_spline, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_trunc_spline<<<P, 256, smem, st>>>(g.k_out, g.os, g.s_min, g.s_max, (float)g.tau, do_trunc,
+                                         do_spline, radial, w.band, spline_m, support);
+    WP_LAUNCH_CHECK("k_trunc_spline");
+    return WP_OK;
+}
+
+// =======================================================================================
+// K7: resample the radial line into the oversampled cache.  One block per (plane, fv):
+// it stages the plane's line (value + second derivative, 16 B per sample) in shared
+// memory and writes the os sub-kernels (fu = 0..os-1) of that fv as one contiguous run
+// of os (2S+1)^2 complex taps, one tap per thread per step, consecutive threads on
+// consecutive taps (coalesced 256 B per warp), streaming stores.  The tap radius squared
+// q = (os (jx - S) - fu)^2 + (os (jy - S) - fv)^2 is an exact integer, so the circular
+// cut q > (os S)^2 and the spline interval floor(sqrt q) are decided exactly.
+// Flat index -> (fu, jy, jx) uses float reciprocals with a half-step offset and one
+// integer correction step, so it is exact for every run length below 2^31.
+// =======================================================================================
+template <bool CUBIC>
+__global__ void __launch_bounds__(256) k_resample(int K, int os, int s_max, const float2* __restrict__ radial,
+                                                  const float2* __restrict__ spline_m,
+                                                  const int32_t* __restrict__ support,
+                                                  const int64_t* __restrict__ offsets,
+                                                  float2* __restrict__ cache) {
+    extern __shared__ float4 line[];   // [n_used] {y.re, y.im, m.re, m.im}
+    const int p = blockIdx.x / os;
+    const int fv = blockIdx.x - p * os;
+    const int S = min(max(support[p], 1), s_max);   // supports outside [1, S_max] are clamped
+    const int W = 2 * S + 1;
+    const int W2 = W * W;
+    const int lim = os * S;
+    const int n_used = min(K, lim + 2);
+    const float2* yl = radial + (int64_t)p * K;
+    const float2* ml = spline_m + (int64_t)p * K;
+    for (int k = threadIdx.x; k < n_used; k += blockDim.x) {
+        float2 a = yl[k];
+        float2 b = CUBIC ? ml[k] : make_float2(0.0f, 0.0f);
+        line[k] = make_float4(a.x, a.y, b.x, b.y);
+    }
+    __syncthreads();
+    const int64_t run = (int64_t)os * W2;
+    float2* dst = cache + offsets[p] + (int64_t)fv * run;
+    const float inv_w2 = 1.0f / (float)W2;
+    const float inv_w = 1.0f / (float)W;
+    const int lim2 = lim * lim;
+    const int dy0 = -os * S - fv;   // os (jy - S) - fv at jy = 0
+    const int dx0 = -os * S;        // os (jx - S) at jx = 0 (fu subtracted below)
+    for (int t = threadIdx.x; t < run; t += blockDim.x) {
+        int fu = (int)(((float)t + 0.5f) * inv_w2);
+        fu -= (fu * W2 > t);            // the estimate is off by at most one: correct it
+        fu += ((fu + 1) * W2 <= t);
+        int r = t - fu * W2;
+        int jy = (int)(((float)r + 0.5f) * inv_w);
+        jy -= (jy * W > r);
+        jy += ((jy + 1) * W <= r);
+        int jx = r - jy * W;
+        int dx = dx0 + os * jx - fu;
+        int dy = dy0 + os * jy;
+        int q = dx * dx + dy * dy;
+        float2 out = make_float2(0.0f, 0.0f);
+        if (q <= lim2) {
+            float x = sqrtf((float)q);
+            int k = min((int)x, K - 2);
+            float a = x - (float)k;
+            float b = 1.0f - a;
+            float4 L0 = line[k];
+            float4 L1 = line[k + 1];
+            out.x = b * L0.x + a * L1.x;
+            out.y = b * L0.y + a * L1.y;
+            if (CUBIC) {
+                float cb = (b * b * b - b) * (1.0f / 6.0f);
+                float ca = (a * a * a - a) * (1.0f / 6.0f);
+                out.x = fmaf(cb, L0.z, fmaf(ca, L1.z, out.x));
+                out.y = fmaf(cb, L0.w, fmaf(ca, L1.w, out.y));
+            }
+        }
+        __stcs(dst + t, out);
+    }
+}
+
+int kg_resample(const Geom& g, int P, const float2* radial, const float2* spline_m,
+                const int32_t* support, const int64_t* offsets, float2* cache, cudaStream_t st) {
+    int n_max = g.os * g.s_max + 2;
+    if (n_max > g.k_out) n_max = g.k_out;
+    size_t smem = (size_t)n_max * sizeof(float4);
+    dim3 grid((unsigned)P * g.os);
+    if (g.interp == WP_INTERP_CUBIC) {
+        if (smem > 48 * 1024)
+            WP_CUDA(cudaFuncSetAttribute(k_resample<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_resample<true><<<grid, 256, smem, st>>>(g.k_out, g.os, g.s_max, radial, spline_m, support, offsets, cache);
+    } else {
+        if (smem > 48 * 1024)
+            WP_CUDA(cudaFuncSetAttribute(k_resample<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_resample<false><<<grid, 256, smem, st>>>(g.k_out, g.os, g.s_max, radial, spline_m, support, offsets, cache);
+    }
+    WP_LAUNCH_CHECK("k_resample");
+    return WP_OK;
+}
+
+}  // namespace wp

@@ -1,0 +1,124 @@
+// Internal declarations of the GB300 w-projection library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/wproj.h"
+
+namespace wp {
+
+// ---------------------------------------------------------------------------------------
+// error reporting
+// ---------------------------------------------------------------------------------------
+void set_last_error(const char* where, const char* what);
+int cuda_fail(const char* where, cudaError_t e);
+
+#define WP_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return ::wp::cuda_fail(#call, e_);       \
+    } while (0)
+
+#define WP_LAUNCH_CHECK(name)                                           \
+    do {                                                                \
+        cudaError_t e_ = cudaGetLastError();                            \
+        if (e_ != cudaSuccess) return ::wp::cuda_fail(name, e_);        \
+    } while (0)
+
+// ---------------------------------------------------------------------------------------
+// derived geometry of a plan
+// ---------------------------------------------------------------------------------------
+struct Geom {
+    int N, os, s_max, s_min, R, r_pad, k_out, interp, kernelgen, fft_m;
+    double dl, du, r_max, tau;
+};
+
+int make_geom(const wp_plan* plan, Geom* g);
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Padded plane count: the matrix product works on 2*P_pad columns, a multiple of 128.
+inline int p_pad(int P) { return (int)round_up(P, 64); }
+
+// ---------------------------------------------------------------------------------------
+// workspace carving: consecutive 256-byte aligned segments
+// ---------------------------------------------------------------------------------------
+struct Carver {
+    char* base;
+    size_t off;
+    size_t cap;
+    explicit Carver(void* b, size_t c) : base((char*)b), off(0), cap(c) {}
+    template <class T>
+    T* take(size_t count) {
+        off = (size_t)round_up((int64_t)off, 256);
+        T* p = base ? (T*)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+    bool fits() const { return off <= cap; }
+};
+
+// Kernel-generation workspace segments.
+struct KgWork {
+    float* h32;        // [k_out][r_pad] FP32 transform matrix
+    float* h_hi;       // [k_out][r_pad] TF32 high part
+    float* h_lo;       // [k_out][r_pad] TF32 low part
+    float* band;       // [k_out][65] spline inverse band
+    float* f32;        // [2 P_pad][r_pad] image-domain functions (FP32 path)
+    float* f_hi;       // [2 P_pad][r_pad]
+    float* f_lo;       // [2 P_pad][r_pad]
+    int*   status;     // [4]
+};
+size_t carve_kg(const Geom& g, int P, void* ws, size_t bytes, KgWork* out);
+
+// Gridding workspace segments.
+struct GridWork {
+    int T, ntx, ntiles;
+    int64_t nbins;
+    int*    count;      // [nbins + 1]   per (plane, centre tile) counts, then exclusive scan
+    int*    cursor;     // [nbins]
+    int*    key;        // [V]           bin key, -1 when dropped
+    int4*   rec;        // [V]           unsorted records
+    int4*   srec;       // [V]           records sorted by bin
+    float2* svis;       // [V]           weighted visibilities sorted by bin
+    int*    flags;      // [nbins + 1]   work-item flags, then exclusive scan
+    int*    items;      // [nbins]       compacted work items (plane * ntiles + tile)
+    int*    scan_tmp;   // scan scratch
+    int*    ctrl;       // [8]  [0] item cursor, [1] item count, [2] status
+    double* red;        // [2]  weight sum, drops (per call)
+};
+size_t carve_grid(const Geom& g, int P, int64_t V, void* ws, size_t bytes, GridWork* out);
+
+// ---------------------------------------------------------------------------------------
+// launchers (return WP_OK or an error code; all asynchronous on `st`)
+// ---------------------------------------------------------------------------------------
+int kg_prepare(const Geom& g, const KgWork& w, cudaStream_t st);
+int kg_screen(const Geom& g, const KgWork& w, const float* taper, const double* w_planes, int P,
+              cudaStream_t st);
+int kg_gemm_fp32(const Geom& g, const KgWork& w, int P, float2* radial, cudaStream_t st);
+int kg_gemm_tf32x3(const Geom& g, const KgWork& w, int P, float2* radial, int* status,
+                   cudaStream_t st);
+int kg_trunc_spline(const Geom& g, const KgWork& w, int P, const float2* radial, float2* spline_m,
+                    int32_t* support, cudaStream_t st);
+int kg_resample(const Geom& g, int P, const float2* radial, const float2* spline_m,
+                const int32_t* support, const int64_t* offsets, float2* cache, cudaStream_t st);
+
+int exclusive_scan_i32(const int* in, int* out, int64_t n, int* tmp, cudaStream_t st);
+size_t scan_tmp_ints(int64_t n);
+
+int grid_bin(const Geom& g, const wp_wkernels* k, const float* uvw, const float2* vis,
+             const float* weight, int64_t V, const GridWork& w, cudaStream_t st);
+int grid_run(const Geom& g, const wp_wkernels* k, const GridWork& w, float2* grid, double* stats,
+             cudaStream_t st);
+int degrid_run(const Geom& g, const wp_wkernels* k, int64_t V, const GridWork& w, const float2* grid,
+               float2* vis_out, cudaStream_t st);
+
+int image_dirty(const Geom& g, const float* taper, float2* grid, double wsum, float* image,
+                cudaStream_t st);
+int image_to_grid(const Geom& g, const float* taper, const float* image, double wsum, float2* grid,
+                  cudaStream_t st);
+void release_fft_plans();
+
+}  // namespace wp

@@ -1,0 +1,95 @@
+"""The C ABI library loads, exports every function declared in include/wproj.h, and its
+host-side logic (plan validation, layouts, argument checks) behaves as documented.
+No device work is requested here."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    from paper_1904_08463_gb300 import _lib, build
+
+    if shutil.which("nvcc") or os.path.exists("/usr/local/cuda/bin/nvcc"):
+        build.build()
+    return _lib, _lib.load()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "wproj.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(wp_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol():
+    _, lib = _lib()
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_plan_geometry():
+    L, lib = _lib()
+    import numpy as np
+
+    p = L.WpPlan(256, float(np.deg2rad(2.0) / 256), 8, 15, 3, 0.01, 512, 0, 0)
+    g = L.WpGeometry()
+    assert lib.wp_plan_geometry(ctypes.byref(p), ctypes.byref(g)) == 0
+    assert g.k_out == 256 and g.r_pad == 512 and g.fft_workspace == 32
+    assert g.du == pytest.approx(1.0 / np.deg2rad(2.0), rel=1e-15)
+    assert g.r_max == pytest.approx(np.deg2rad(1.0), rel=1e-15)
+    p2 = L.WpPlan(4096, float(np.deg2rad(8.0) / 4096), 8, 127, 7, 0.0, 4096, 0, 1)
+    assert lib.wp_plan_geometry(ctypes.byref(p2), ctypes.byref(g)) == 0
+    assert g.k_out == 1152 and g.fft_workspace == 256
+
+
+@pytest.mark.parametrize("field,value", [("image_size", 255), ("image_size", 8), ("cell_size", 0.0),
+                                         ("cell_size", 0.01), ("oversampling", 0), ("oversampling", 17),
+                                         ("max_support", 0), ("max_support", 200), ("min_support", 16),
+                                         ("radial_samples", 4), ("interp", 2), ("kernelgen", 7),
+                                         ("trunc_frac", 1.0)])
+def test_invalid_plans_rejected(field, value):
+    L, lib = _lib()
+    p = L.WpPlan(256, 1e-4, 8, 15, 3, 0.01, 512, 0, 0)
+    setattr(p, field, value)
+    g = L.WpGeometry()
+    assert lib.wp_plan_geometry(ctypes.byref(p), ctypes.byref(g)) == -3
+
+
+def test_layout_and_argument_errors():
+    L, lib = _lib()
+    p = L.WpPlan(256, 1e-4, 8, 15, 3, 0.01, 512, 0, 0)
+    sup = (ctypes.c_int32 * 3)(3, 5, 15)
+    off = (ctypes.c_int64 * 4)()
+    assert lib.wp_kernel_layout(ctypes.byref(p), 3, sup, off) == 0
+    assert list(off) == [0, 64 * 49, 64 * (49 + 121), 64 * (49 + 121 + 961)]
+    bad = (ctypes.c_int32 * 1)(16)
+    assert lib.wp_kernel_layout(ctypes.byref(p), 1, bad, off) == -2
+    assert lib.wp_kernel_layout_max(ctypes.byref(p), 2, off) == 0
+    assert list(off)[:3] == [0, 64 * 961, 2 * 64 * 961]
+    # NULL and size errors are detected on the host before any device work
+    assert lib.wp_hankel_radial(ctypes.byref(p), None, None, 4, None, 0, None, None, None, None) == -1
+    ws = ctypes.c_void_p(256)   # never dereferenced: the size check fails first
+    assert lib.wp_hankel_radial(ctypes.byref(p), ws, ws, 4, ws, 16, ws, ws, ws, None) == -4
+    assert lib.wp_hankel_radial(ctypes.byref(p), ws, ws, 0, ws, 1 << 40, ws, ws, ws, None) == -2
+    assert lib.wp_kernelgen_workspace_bytes(ctypes.byref(p), 16) > 0
+    assert lib.wp_grid_workspace_bytes(ctypes.byref(p), 16, 1000) > 0
+    kern = L.WpWkernels(0, 0, None, None, None, None)
+    assert lib.wp_grid(ctypes.byref(p), ctypes.byref(kern), ws, ws, None, 10, ws, 1 << 40, ws, None, None) == -2
+    assert lib.wp_dirty_image(ctypes.byref(p), ws, ws, 0.0, ws, None) == -2
+    assert lib.wp_strerror(-4) == b"workspace too small or not 256-byte aligned"
+    assert lib.wp_version() >= 100
+
+
+def test_product_path_refuses_to_run_without_library(monkeypatch, tmp_path):
+    from paper_1904_08463_gb300 import _lib as L
+
+    monkeypatch.setattr(L, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(L, "_lib", None)
+    with pytest.raises(ImportError):
+        L.load()

@@ -1,0 +1,126 @@
+"""GPU parity of binning, gridding, degridding and the dirty image against the oracle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import oracle as o
+from tests.common import IMAGE_TOL, f32, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _wp():
+    import paper_1904_08463_gb300 as wp
+
+    return wp
+
+
+def _setup(N, dl, os_, s_max, R, planes, supports, sigma=0.3):
+    wp = _wp()
+    dev = torch.device("cuda")
+    plan = wp.Plan(N, dl, os_, s_max, 1, 0.0, R, "cubic", "fp32")
+    g = o.Geometry(N, dl, os_, s_max, 1, 0.0, R)
+    taper = synth.gaussian_taper_samples(N, dl, R, sigma)
+    tap_d = torch.tensor(taper, dtype=torch.float32, device=dev)
+    wk = wp.make_wkernels(plan, tap_d, planes, supports=supports)
+    ks = o.wkernels(g, f32(taper), planes, supports=supports)
+    return wp, dev, plan, g, taper, tap_d, wk, ks
+
+
+def test_small_imaging_grid_and_dirty_image():
+    """20k visibilities, 5 point sources, 16 planes; grid vs oracle grid, and the dirty
+    image vs the oracle's dirty image inside the circle (<= 1e-4 of the peak)."""
+    d = synth.small_imaging()
+    N, dl = d["N"], d["cell_size"]
+    planes = np.linspace(0.0, 500.0, 16)
+    sup = np.full(16, 5)
+    wp, dev, plan, g, taper, tap_d, wk, ks = _setup(N, dl, 8, 15, 512, planes, sup)
+    uvw, vis = d["uvw"], d["vis"]
+    G, stats = wp.grid(plan, wk, torch.tensor(uvw, device=dev), torch.tensor(vis, device=dev),
+                       torch.tensor(d["weight"], device=dev))
+    Gh = G.cpu().numpy()
+    b = o.bin_vis(g, uvw, planes, sup)
+    Go = o.grid(g, ks, b, vis, d["weight"])
+    assert np.abs(Gh - Go).max() < 1e-5 * np.abs(Go).max()
+    st = stats.cpu().numpy()
+    assert st[1] == (b.drop != 0).sum()
+    assert st[0] == pytest.approx(float(d["weight"][b.drop == 0].sum()))
+    img = wp.dirty_image(plan, tap_d, G, float(st[0])).cpu().numpy()
+    ref = o.dirty_image(g, Go, f32(taper), float(st[0]))
+    assert np.abs(img - ref).max() < IMAGE_TOL * np.abs(ref).max()
+    assert np.all(img[~o.disc_mask(g)] == 0)
+
+
+@pytest.mark.parametrize("V,seed", [(0, 1), (1, 2), (37, 3), (5000, 4)])
+def test_grid_edges_and_conjugation(V, seed):
+    """Empty input, one visibility, ragged counts; visibilities on and past the grid edge
+    (dropped), negative w (conjugated kernels), a plane count off every tile size."""
+    N, dl = 96, np.deg2rad(3.0) / 96
+    planes = np.array([0.0, 40.0, 130.0, 300.0, 800.0])
+    sup = np.array([1, 3, 6, 9, 12])
+    wp, dev, plan, g, taper, tap_d, wk, ks = _setup(N, dl, 4, 12, 128, planes, sup)
+    rng = np.random.default_rng(seed)
+    du = g.du
+    uvw = np.stack([rng.uniform(-N / 2 - 2, N / 2 + 2, V) * du, rng.uniform(-N / 2 - 2, N / 2 + 2, V) * du,
+                    rng.uniform(-900, 900, V)], 1).astype(np.float32).reshape(V, 3)
+    vis = (rng.normal(size=V) + 1j * rng.normal(size=V)).astype(np.complex64)
+    wt = rng.uniform(0.5, 2.0, V).astype(np.float32)
+    G, stats = wp.grid(plan, wk, torch.tensor(uvw, device=dev).reshape(-1), torch.tensor(vis, device=dev),
+                       torch.tensor(wt, device=dev))
+    b = o.bin_vis(g, uvw, planes, sup)
+    Go = o.grid(g, ks, b, vis, wt)
+    scale = max(np.abs(Go).max(), 1e-30)
+    assert np.abs(G.cpu().numpy() - Go).max() <= 1e-5 * scale
+    assert stats[1].item() == (b.drop != 0).sum()
+    # degridding of a random grid
+    X = (rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))).astype(np.complex64)
+    Vd = wp.degrid(plan, wk, torch.tensor(uvw, device=dev).reshape(-1), torch.tensor(X, device=dev))
+    Vo = o.degrid(g, ks, b, X.astype(np.complex128))
+    if V:
+        assert np.abs(Vd.cpu().numpy() - Vo).max() <= 2e-5 * max(np.abs(Vo).max(), 1e-30)
+
+
+def test_grid_degrid_adjoint_on_gpu():
+    """<grid(V), X> = <V, degrid(X)> for the GPU operators (unit weights)."""
+    N, dl = 128, np.deg2rad(4.0) / 128
+    planes = np.linspace(0, 1000, 9)
+    sup = np.arange(2, 11)
+    wp, dev, plan, g, taper, tap_d, wk, ks = _setup(N, dl, 8, 12, 256, planes, sup)
+    rng = np.random.default_rng(9)
+    V = 20000
+    uvw = synth.uniform_disc_uvw(V, (N / 2 - 14) * g.du, 1000.0, 10)
+    vis = (rng.normal(size=V) + 1j * rng.normal(size=V)).astype(np.complex64)
+    X = (rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))).astype(np.complex64)
+    u_d = torch.tensor(uvw, device=dev).reshape(-1)
+    G, _ = wp.grid(plan, wk, u_d, torch.tensor(vis, device=dev))
+    Vd = wp.degrid(plan, wk, u_d, torch.tensor(X, device=dev))
+    lhs = np.vdot(G.cpu().numpy().astype(np.complex128), X.astype(np.complex128))
+    rhs = np.vdot(vis.astype(np.complex128), Vd.cpu().numpy().astype(np.complex128))
+    assert abs(lhs - rhs) < 1e-5 * abs(lhs)
+
+
+def test_dirty_image_and_adjoint_on_synthetic_grids():
+    """The image stage alone on seeded synthetic grids (sizes 64 and 1024): vs the oracle's
+    numpy transform, and image_to_grid as the adjoint of the linear part of dirty_image."""
+    wp = _wp()
+    dev = torch.device("cuda")
+    for N, seed in ((64, 1), (1024, 2)):
+        dl = np.deg2rad(4.0) / N
+        R = 512
+        plan = wp.Plan(N, dl, 8, 15, 3, 0.01, R)
+        g = o.Geometry(N, dl, 8, 15, 3, 0.01, R)
+        taper = synth.gaussian_taper_samples(N, dl, R, 0.25)
+        rng = np.random.default_rng(seed)
+        X = (rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))).astype(np.complex64)
+        tap_d = torch.tensor(taper, dtype=torch.float32, device=dev)
+        img = wp.dirty_image(plan, tap_d, torch.tensor(X, device=dev), 3.5).cpu().numpy()
+        ref = o.dirty_image(g, X.astype(np.complex128), f32(taper), 3.5)
+        assert np.abs(img - ref).max() < 1e-5 * np.abs(ref).max()
+        Y = rng.normal(size=(N, N)).astype(np.float32)
+        Gy = wp.image_to_grid(plan, tap_d, torch.tensor(Y, device=dev), 3.5).cpu().numpy().astype(np.complex128)
+        # <Re A X, Y> = Re <X, A^H Y>
+        lhs = float(np.sum(ref * Y))
+        rhs = float(np.real(np.vdot(Gy, X.astype(np.complex128))))
+        assert abs(lhs - rhs) < 1e-4 * abs(lhs) + 1e-6
