@@ -163,6 +163,10 @@ def run_gpu(args):
 
         dist.init_process_group("nccl")
     kb = kernel_batch()
+    if args.plane_stride > 1:
+        for key in ("w_abs", "support"):
+            kb[key] = kb[key][::args.plane_stride]
+        kb["w_signed"] = kb["w_signed"][::args.plane_stride]
     P = len(kb["w_abs"])
     plan = wp.Plan(N_IMG, kb["cell_size"], OS, 127, 7, 0.0, R_KG, "cubic", args.kernelgen)
     g = plan.geometry()
@@ -176,7 +180,7 @@ def run_gpu(args):
     wp.kernelgen_prepare(plan, P, ws)
     radial = torch.empty((P, g.k_out), dtype=torch.complex64, device=dev)
     spline_m = torch.empty_like(radial)
-    cache = torch.empty(off_host[-1], dtype=torch.complex64, device=dev)
+    cache = torch.empty(1 if args.hankel_only else off_host[-1], dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream()
     lib = _lib.load()
     cplan = plan.c()
@@ -189,6 +193,10 @@ def run_gpu(args):
             ctypes.c_void_p(spline_m.data_ptr()), None, ctypes.c_void_p(stream.cuda_stream)))
         if ev is not None:
             ev[0].record(stream)
+        if args.hankel_only:
+            if ev is not None:
+                ev[1].record(stream)
+            return
         _lib.check("wp_resample", lib.wp_resample(
             ctypes.byref(cplan), ctypes.c_void_p(radial.data_ptr()), ctypes.c_void_p(spline_m.data_ptr()), P,
             ctypes.c_void_p(sup_d.data_ptr()), ctypes.c_void_p(off_d.data_ptr()),
@@ -212,7 +220,14 @@ def run_gpu(args):
         step(evs[k])
     t_end.record(stream)
     torch.cuda.synchronize()
+    # keep the same load on for about a second so that the clock sampler sees it
+    t_soak = time.perf_counter()
+    while time.perf_counter() - t_soak < 1.0:
+        for _ in range(20):
+            step()
+        torch.cuda.synchronize()
     clk = clocks.stop()
+    clk["note"] = "sampled every 200 ms over the timed steps plus ~1 s of the same steps right after"
     ms_total = t_start.elapsed_time(t_end)
     if world > 1:
         tt = torch.tensor([ms_total], device=dev)
@@ -230,6 +245,82 @@ def run_gpu(args):
     achieved = alg_bytes / (resample_ms * 1e-3) / 1e9
 
     # ---- end to end through the C ABI with host buffers -----------------------------
+    e2e = None
+    if args.e2e:
+        e2e = measure_e2e(args, world, P, kb, sup_host, off_host, cache, taper_d, wpl_d, sup_d, off_d, step, stream)
+    out = build_line(args, world, P, kb, ms_step, resample_ms, bytes_cache, alg_bytes, hbm, src, achieved,
+                     e2e, clk)
+    if args.routes and not args.hankel_only:
+        out["routes"] = time_routes(args, kb, plan, taper_d, wpl_d, sup_host, ws, radial, spline_m, cache,
+                                    sup_d, off_d, ms_step)
+    if args.imaging and rank == 0:
+        out["imaging"] = run_imaging(args, dev)
+    if rank == 0 and args.cpu_baseline:
+        rate, thr, sample = oracle_kernel_rate()
+        out["cpu_baseline"] = {"value": rate, "unit": "w-kernels/s", "cores": thr, "kind": "oracle",
+                               "sample": sample}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def time_routes(args, kb, plan, taper_d, wpl_d, sup_host, ws, radial, spline_m, cache, sup_d, off_d,
+                headline_ms):
+    """The same batch through the other kernel-generation routes on the same GPU: the plain
+    FP32 SIMT Hankel product and the standard 2D-FFT route (Alg. 1 with workspace
+    undersampling, M = 256, 2048^2 transforms, circular support)."""
+    import torch
+
+    import paper_1904_08463_gb300 as wp
+
+    P = len(kb["w_abs"])
+    res = {args.kernelgen + "_hankel": {"ms_per_step": headline_ms, "w_kernels_per_s": P / (headline_ms * 1e-3)}}
+
+    def timeit(fn, n):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    other = "fp32" if args.kernelgen == "tf32x3" else "tf32x3"
+    p2 = plan.replace(kernelgen=other)
+
+    def hankel_other():
+        wp.hankel_radial(p2, taper_d, wpl_d, ws, radial, spline_m)
+        wp.resample(p2, radial, spline_m, sup_d, off_d, cache)
+
+    ms = timeit(hankel_other, max(3, min(args.steps, 10)))
+    res[other + "_hankel"] = {"ms_per_step": ms, "w_kernels_per_s": P / (ms * 1e-3)}
+    fws = wp.workspace(int(wp._lib.load().wp_fft_workspace_bytes(__import__("ctypes").byref(plan.c()), P)))
+    import ctypes
+
+    lib = wp._lib.load()
+
+    def fft_route():
+        wp._lib.check("wp_fft_wkernels", lib.wp_fft_wkernels(
+            ctypes.byref(plan.c()), ctypes.c_void_p(taper_d.data_ptr()), ctypes.c_void_p(wpl_d.data_ptr()), P,
+            ctypes.c_void_p(sup_d.data_ptr()), ctypes.c_void_p(off_d.data_ptr()), 1,
+            ctypes.c_void_p(fws.data_ptr()), fws.numel(), ctypes.c_void_p(cache.data_ptr()),
+            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+
+    ms = timeit(fft_route, 2)
+    res["fft2d"] = {"ms_per_step": ms, "w_kernels_per_s": P / (ms * 1e-3),
+                    "workspace": "M=256 -> 2048^2 complex64 per plane, batched cuFFT C2C"}
+    res["speedup_hankel_vs_fft2d"] = ms / headline_ms
+    del fws
+    return res
+
+
+def measure_e2e(args, world, P, kb, sup_host, off_host, cache, taper_d, wpl_d, sup_d, off_d, step, stream):
+    import torch
+
     pin_cache = torch.empty(off_host[-1], dtype=torch.complex64, pin_memory=True)
     h_taper = torch.tensor(kb["taper"], dtype=torch.float32).pin_memory()
     h_wpl = torch.tensor(kb["w_abs"], dtype=torch.float64).pin_memory()
@@ -256,8 +347,13 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / n_e2e
+    return {"value": world * P / (e2e_ms * 1e-3), "unit": "w-kernels/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
 
-    out = {
+
+def build_line(args, world, P, kb, ms_step, resample_ms, bytes_cache, alg_bytes, hbm, src, achieved, e2e, clk):
+    value = world * P / (ms_step * 1e-3)
+    return {
         "metric": METRIC,
         "value": value,
         "unit": "w-kernels/s",
@@ -295,27 +391,10 @@ def run_gpu(args):
             "launch_ms": resample_ms,
             "share_of_step": resample_ms / ms_step,
         },
-        "e2e": {
-            "value": world * P / (e2e_ms * 1e-3),
-            "unit": "w-kernels/s",
-            "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h,
-            "ms_per_step": e2e_ms,
-        },
+        "e2e": e2e,
         "gpu_launches": 4 * args.steps,
         "clocks": clk,
     }
-    del pin_cache
-    if args.imaging and rank == 0:
-        out["imaging"] = run_imaging(args, dev)
-    if rank == 0 and args.cpu_baseline:
-        rate, thr, sample = oracle_kernel_rate()
-        out["cpu_baseline"] = {"value": rate, "unit": "w-kernels/s", "cores": thr, "kind": "oracle",
-                               "sample": sample}
-    if rank == 0:
-        print(json.dumps(out))
-    if world > 1:
-        torch.distributed.destroy_process_group()
 
 
 def log(msg):
@@ -338,7 +417,7 @@ def run_imaging(args, dev):
     noise = torch.randn(vis.numel(), 2, generator=g, dtype=torch.float64) * d["noise_sigma"]
     vis = vis + torch.complex(noise[:, 0], noise[:, 1]).to(torch.complex64).to(dev)
     V = vis.numel()
-    P = 512
+    P = args.imaging_planes
     planes = np.sort(np.abs(d["uvw"][:, 2].astype(np.float64)))
     planes = np.array([c.mean() for c in np.array_split(planes, P)])
     plan = wp.Plan(N, dl, OS, 127, 3, 0.01, 512, "cubic", args.kernelgen)
@@ -399,7 +478,7 @@ def run_imaging(args, dev):
     st = stats.cpu().numpy()
     return {
         "workload": f"full imaging: {V} visibilities (64-antenna 8 h track, dec -30, 1.4 GHz, uvw x "
-                    f"{d['scale']:.3f}), 200 sources + 1 mJy noise, 512 |w|-planes (mean of "
+                    f"{d['scale']:.3f}), 200 sources + 1 mJy noise, {P} |w|-planes (mean of "
                     f"equal-count chunks), 1% truncation, S_max 127, os 8, R 512, 4096^2 grid, 8 deg",
         "value": V / (ms * 1e-3) / 1e6,
         "unit": "Mvis/s",
@@ -449,10 +528,18 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--kernelgen", default="fp32", choices=["fp32", "tf32x3"])
+    ap.add_argument("--kernelgen", default="tf32x3", choices=["fp32", "tf32x3"])
     ap.add_argument("--no-imaging", dest="imaging", action="store_false")
     ap.add_argument("--imaging-vis", type=int, default=1 << 23)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-routes", dest="routes", action="store_false",
+                    help="skip timing the other kernel-generation routes (FP32 Hankel, 2D FFT)")
+    ap.add_argument("--imaging-planes", type=int, default=512)
+    ap.add_argument("--hankel-only", action="store_true",
+                    help="profiling aid: time only screen + Hankel product + spline (no cache)")
+    ap.add_argument("--plane-stride", type=int, default=1,
+                    help="use every n-th |w| plane of the batch (small cases for profiling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

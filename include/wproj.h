@@ -166,7 +166,8 @@ int wp_hankel_radial(const wp_plan* plan, const float* taper, const double* w_pl
  * line at radius x = sqrt((os (jx - S) - fu)^2 + (os (jy - S) - fv)^2) samples, and 0 when
  * x > os S (the truncated line rotated about rho = 0 has circular support).
  *   radial, spline_m  as written by wp_hankel_radial (spline_m unused for linear)
- *   support [P] int32, offsets [P+1] int64 (device), cache out.
+ *   support [P] int32 (values outside [1, S_max] are clamped), offsets [P+1] int64 (device),
+ *   cache out, 8-byte aligned (WP_ERR_SIZE otherwise).
  */
 int wp_resample(const wp_plan* plan, const float* radial, const float* spline_m, int32_t P,
                 const int32_t* support, const int64_t* offsets, float* cache, void* stream);
@@ -180,6 +181,29 @@ int wp_make_wkernels(const wp_plan* plan, const float* taper, const double* w_pl
                      int32_t P, int32_t* support, const int64_t* offsets, void* workspace,
                      size_t workspace_bytes, float* radial, float* spline_m, float* cache,
                      void* stream);
+
+/* ---- standard kernel generation by 2D FFT (the comparator; Alg. 1, Section 4.2) ------ */
+
+/* Bytes of scratch for wp_fft_wkernels: a batch of zero-padded (M os)^2 complex workspaces
+   (as many planes as fit in 1 GiB, at least one) and an M^2 table. */
+size_t wp_fft_workspace_bytes(const wp_plan* plan, int32_t P);
+
+/*
+ * Kernel cache by the standard route: per plane the image-domain product taper x w-screen
+ * t(r) exp(+2 pi j w (sqrt(1 - r^2) - 1)) is sampled on the M x M workspace spanning the
+ * field of view (M = power of two >= 2 S_max + 1, Section 4.2; t linearly interpolated
+ * between the radial nodes, 0 outside r_max), zero padded to (M os)^2 (Alg. 1, oversampling
+ * by padding), transformed (cuFFT C2C forward, batched), scaled by (FOV/M)^2 du^2, and tap
+ * (jx, jy) of sub-kernel (fu, fv) is read at fine offset (os (jx - S) - fu, os (jy - S) - fv).
+ * With circular != 0 taps beyond radius S are zeroed (the Hankel route's support shape).
+ * Same cache layout as wp_resample; supports are inputs (no truncation in this route).
+ *   taper [R] float, w_planes [P] double, support [P] int32, offsets [P+1] int64 (device);
+ *   workspace wp_fft_workspace_bytes(plan, P) bytes, 256-byte aligned; cache out.
+ * Uses cached batched cuFFT plans (freed by wp_release).
+ */
+int wp_fft_wkernels(const wp_plan* plan, const float* taper, const double* w_planes, int32_t P,
+                    const int32_t* support, const int64_t* offsets, int32_t circular,
+                    void* workspace, size_t workspace_bytes, float* cache, void* stream);
 
 /* ---- gridding (Alg. 1 / Alg. 2 gridding step) and its adjoint ----------------------- */
 
@@ -212,6 +236,50 @@ int wp_grid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw,
 int wp_degrid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw,
               const float* grid, int64_t V, void* workspace, size_t workspace_bytes,
               float* vis_out, void* stream);
+
+/* ---- differentiation of the visibility prediction ----------------------------------
+ * Model: V = wp_degrid(K(t), wp_image_to_grid(I; t)) for a model image I and the radial
+ * taper t, where the kernels K(t) come from wp_hankel_radial + wp_resample (supports and
+ * plane values fixed).  For a real loss L the incoming gradient is g = dL/dRe V + j dL/dIm V
+ * and complex gradients are returned in the same form (dL = Re(conj(gz) dz)).  The image
+ * gradient is wp_dirty_image of wp_grid(g) (unit weights); the taper gradient is the sum of
+ * wp_hankel_adjoint (kernels) and wp_image_adjoint (the division by t in the image step).
+ */
+
+/* Bytes of scratch for wp_grad_radial (the gridding workspace plus work-item lists). */
+size_t wp_grad_workspace_bytes(const wp_plan* plan, int32_t P, int64_t V);
+
+/*
+ * Gradient of L with respect to the radial lines and their spline second derivatives:
+ * for every visibility and every tap inside the support, Q = conj(g) G(cell) (w >= 0) or
+ * g conj(G(cell)) (w < 0), spread onto the radial samples through the resample weights.
+ *   grad_vis [V] complex (g), grid [N][N] complex (the grid that was degridded);
+ *   grad_radial, grad_spline_m [P][K_out] complex out (overwritten; grad_spline_m may be
+ *   NULL for linear interpolation).
+ */
+int wp_grad_radial(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw,
+                   const float* grad_vis, const float* grid, int64_t V, void* workspace,
+                   size_t workspace_bytes, float* grad_radial, float* grad_spline_m, void* stream);
+
+/*
+ * Adjoint of kernel generation back to the taper (Section 4.3's transform is linear, so its
+ * adjoint is the same matrix transposed): spline adjoint, dF = dC H, then
+ * grad_taper[i] += sum_p Re(conj(dF_p,i) exp(+2 pi j w_p (n_i - 1))).
+ *   workspace: the kernel-generation workspace prepared by wp_kernelgen_prepare;
+ *   grad_taper [R] float, ACCUMULATED into.
+ */
+int wp_hankel_adjoint(const wp_plan* plan, const double* w_planes, int32_t P, void* workspace,
+                      size_t workspace_bytes, const float* grad_radial, const float* grad_spline_m,
+                      float* grad_taper, void* stream);
+
+/*
+ * Image-side adjoint: with U = Re(centred inverse transform of grid_g) (grid_g = wp_grid of g
+ * with unit weights; transformed in place), inside the circle
+ *   grad_image = U / (t(r) weight_sum),  grad_taper += spread of -U I / (t(r)^2 weight_sum)
+ * onto the taper nodes by the linear-interpolation weights; grad_image = 0 outside.
+ */
+int wp_image_adjoint(const wp_plan* plan, const float* taper, const float* image, float* grid_g,
+                     double weight_sum, float* grad_image, float* grad_taper, void* stream);
 
 /* ---- image <-> grid (Section 3: inverse transform and anti-aliasing correction) ----- */
 

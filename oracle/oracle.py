@@ -315,7 +315,9 @@ def fft_wkernel(geom: Geometry, taper: np.ndarray, w: float, S: int, circular: b
     l = j * dlw
     L, Mm = np.meshgrid(l, l, indexing="xy")      # [m][l]
     r = np.hypot(L, Mm)
-    t = taper_at(geom, taper, r)
+    # inside the disc r <= r_max = (M/2) dlw, decided on the integer pixel offsets
+    inside = (j[None, :] ** 2 + j[:, None] ** 2) <= (M // 2) ** 2
+    t = np.where(inside, taper_at(geom, taper, np.minimum(r, geom.r_max)), 0.0)
     n = np.sqrt(1.0 - r * r)
     f = t * np.exp(2j * np.pi * w * (n - 1.0))
     X = np.zeros((Lp, Lp), dtype=np.complex128)
@@ -449,3 +451,26 @@ def mean_w_planes(w: np.ndarray, P: int) -> np.ndarray:
     aw = np.sort(np.abs(np.asarray(w, dtype=np.float64)))
     chunks = np.array_split(aw, P)
     return np.array([c.mean() for c in chunks], dtype=np.float64)
+
+
+# --------------------------------------------------------------------------------------
+# Visibility prediction from a model image (the forward model whose gradients the CUDA
+# path differentiates): the adjoint pair of the dirty image and of gridding.
+# --------------------------------------------------------------------------------------
+def image_to_grid(geom: Geometry, image: np.ndarray, taper: np.ndarray, weight_sum: float = 1.0) -> np.ndarray:
+    """grid[v][u] = sum over pixels inside the circle of I / (t(r) wsum)
+    exp(-2 pi j ((u - N/2)(l - N/2) + (v - N/2)(m - N/2)) / N): the adjoint of the linear part
+    of dirty_image (Section 3)."""
+    t = taper_at(geom, taper, pixel_radius(geom))
+    inside = disc_mask(geom)
+    X = np.zeros_like(np.asarray(image, dtype=np.float64))
+    X[inside] = np.asarray(image, dtype=np.float64)[inside] / (t[inside] * weight_sum)
+    return np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(X)))
+
+
+def predict_vis(geom: Geometry, image: np.ndarray, taper: np.ndarray, w_planes, supports, uvw: np.ndarray,
+                weight_sum: float = 1.0) -> np.ndarray:
+    """V = degrid(kernels(taper), image_to_grid(image; taper)), all in FP64."""
+    ks = wkernels(geom, taper, w_planes, supports=supports)
+    b = bin_vis(geom, uvw, w_planes, ks.support)
+    return degrid(geom, ks, b, image_to_grid(geom, image, taper, weight_sum))

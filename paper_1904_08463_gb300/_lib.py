@@ -89,11 +89,21 @@ _SIGS = {
                               c_void_p, c_void_p]),
     "wp_make_wkernels": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_int32, c_void_p, c_void_p,
                                    c_void_p, c_size_t, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "wp_fft_workspace_bytes": (c_size_t, [P_(WpPlan), c_int32]),
+    "wp_fft_wkernels": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_int32,
+                                  c_void_p, c_size_t, c_void_p, c_void_p]),
     "wp_grid_workspace_bytes": (c_size_t, [P_(WpPlan), c_int32, c_int64]),
     "wp_grid": (c_int32, [P_(WpPlan), P_(WpWkernels), c_void_p, c_void_p, c_void_p, c_int64,
                           c_void_p, c_size_t, c_void_p, c_void_p, c_void_p]),
     "wp_degrid": (c_int32, [P_(WpPlan), P_(WpWkernels), c_void_p, c_void_p, c_int64, c_void_p,
                             c_size_t, c_void_p, c_void_p]),
+    "wp_grad_workspace_bytes": (c_size_t, [P_(WpPlan), c_int32, c_int64]),
+    "wp_grad_radial": (c_int32, [P_(WpPlan), P_(WpWkernels), c_void_p, c_void_p, c_void_p, c_int64, c_void_p,
+                                 c_size_t, c_void_p, c_void_p, c_void_p]),
+    "wp_hankel_adjoint": (c_int32, [P_(WpPlan), c_void_p, c_int32, c_void_p, c_size_t, c_void_p, c_void_p,
+                                    c_void_p, c_void_p]),
+    "wp_image_adjoint": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p,
+                                   c_void_p]),
     "wp_dirty_image": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
     "wp_image_to_grid": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
 }

@@ -198,6 +198,26 @@ def make_wkernels(plan: Plan, taper: torch.Tensor, w_planes, supports=None,
     return WKernels(w_planes, sup, off, cache, radial, spline_m)
 
 
+def fft_wkernels(plan: Plan, taper: torch.Tensor, w_planes, supports, circular: bool = True,
+                 ws: torch.Tensor | None = None, stream=None) -> WKernels:
+    """Kernel cache by the standard 2D-FFT route (Alg. 1 with workspace undersampling),
+    for comparison with the Hankel route; supports are given."""
+    dev = taper.device
+    _need(taper, torch.float32, "taper", plan.radial_samples)
+    w_planes = torch.as_tensor(w_planes, dtype=torch.float64, device=dev).contiguous()
+    P = int(w_planes.numel())
+    sup_host = [int(s) for s in supports]
+    off = torch.tensor(kernel_layout(plan, sup_host), dtype=torch.int64, device=dev)
+    sup = torch.tensor(sup_host, dtype=torch.int32, device=dev)
+    if ws is None:
+        ws = workspace(int(_lib.load().wp_fft_workspace_bytes(ctypes.byref(plan.c()), P)), dev)
+    cache = torch.empty(int(off[-1].item()), dtype=torch.complex64, device=dev)
+    _lib.check("wp_fft_wkernels", _lib.load().wp_fft_wkernels(
+        ctypes.byref(plan.c()), _ptr(taper), _ptr(w_planes), P, _ptr(sup), _ptr(off), int(bool(circular)),
+        _ptr(ws), ws.numel(), _ptr(cache), _stream(stream)))
+    return WKernels(w_planes, sup, off, cache)
+
+
 # ----------------------------------------------------------------------------- gridding
 def grid_workspace_bytes(plan: Plan, P: int, V: int) -> int:
     return int(_lib.load().wp_grid_workspace_bytes(ctypes.byref(plan.c()), P, V))

@@ -64,9 +64,11 @@ size_t carve_kg(const Geom& g, int P, void* ws, size_t bytes, KgWork* out) {
     w.h_hi = c.take<float>(hk);
     w.h_lo = c.take<float>(hk);
     w.band = c.take<float>((size_t)g.k_out * 65);
+    w.nm1 = c.take<double>((size_t)g.r_pad);
     w.f32 = c.take<float>(fk);
     w.f_hi = c.take<float>(fk);
     w.f_lo = c.take<float>(fk);
+    w.gct = c.take<float>((size_t)2 * p_pad(P) * g.k_out);
     w.status = c.take<int>(64);
     if (out) *out = w;
     return (size_t)round_up((int64_t)c.off, 256);
@@ -111,6 +113,8 @@ static int check_device() {
 
 static bool aligned256(const void* p) { return ((uintptr_t)p & 255u) == 0; }
 
+int check_device_public() { return check_device(); }
+
 }  // namespace wp
 
 using namespace wp;
@@ -136,7 +140,10 @@ const char* wp_strerror(int code) {
     }
 }
 
-void wp_release(void) { release_fft_plans(); }
+void wp_release(void) {
+    release_fft_plans();
+    release_fft_kernelgen_plans();
+}
 
 int wp_plan_geometry(const wp_plan* plan, wp_geometry* geom) {
     if (!plan || !geom) return WP_ERR_NULL;
@@ -232,6 +239,7 @@ int wp_resample(const wp_plan* plan, const float* radial, const float* spline_m,
     if (P < 1 || P > 65536) return WP_ERR_SIZE;
     if (!radial || !support || !offsets || !cache) return WP_ERR_NULL;
     if (g.interp == WP_INTERP_CUBIC && !spline_m) return WP_ERR_NULL;
+    if ((uintptr_t)cache & 7u) return WP_ERR_SIZE;    // complex64 taps
     if ((rc = check_device())) return rc;
     return kg_resample(g, P, reinterpret_cast<const float2*>(radial),
                        reinterpret_cast<const float2*>(spline_m), support, offsets,
@@ -246,6 +254,27 @@ int wp_make_wkernels(const wp_plan* plan, const float* taper, const double* w_pl
                               support, stream);
     if (rc) return rc;
     return wp_resample(plan, radial, spline_m, P, support, offsets, cache, stream);
+}
+
+size_t wp_fft_workspace_bytes(const wp_plan* plan, int32_t P) {
+    Geom g;
+    if (make_geom(plan, &g) || P < 1) return 0;
+    return fft_workspace_bytes(g, P);
+}
+
+int wp_fft_wkernels(const wp_plan* plan, const float* taper, const double* w_planes, int32_t P,
+                    const int32_t* support, const int64_t* offsets, int32_t circular, void* workspace,
+                    size_t workspace_bytes, float* cache, void* stream) {
+    Geom g;
+    int rc = make_geom(plan, &g);
+    if (rc) return rc;
+    if (P < 1 || P > 65536) return WP_ERR_SIZE;
+    if (!taper || !w_planes || !support || !offsets || !workspace || !cache) return WP_ERR_NULL;
+    if (!aligned256(workspace) || workspace_bytes < fft_workspace_bytes(g, P)) return WP_ERR_WORKSPACE;
+    if ((int64_t)g.fft_m * g.os > 32768) return WP_ERR_SIZE;
+    if ((rc = check_device())) return rc;
+    return fft_wkernels(g, taper, w_planes, P, support, offsets, circular, workspace, workspace_bytes,
+                        reinterpret_cast<float2*>(cache), (cudaStream_t)stream);
 }
 
 size_t wp_grid_workspace_bytes(const wp_plan* plan, int32_t P, int64_t V) {
@@ -295,6 +324,61 @@ int wp_degrid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw,
     if ((rc = grid_bin(g, kernels, uvw, nullptr, nullptr, V, w, st))) return rc;
     return degrid_run(g, kernels, V, w, reinterpret_cast<const float2*>(grid),
                       reinterpret_cast<float2*>(vis_out), st);
+}
+
+size_t wp_grad_workspace_bytes(const wp_plan* plan, int32_t P, int64_t V) {
+    Geom g;
+    if (make_geom(plan, &g) || P < 1 || V < 0) return 0;
+    return carve_grid(g, P, V, nullptr, 0, nullptr) + (size_t)round_up(2 * sizeof(int) * grad_extra_ints(P, V) + 512, 256);
+}
+
+int wp_grad_radial(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw, const float* grad_vis,
+                   const float* grid, int64_t V, void* workspace, size_t workspace_bytes, float* grad_radial,
+                   float* grad_spline_m, void* stream) {
+    Geom g;
+    int rc = check_grid_args(plan, kernels, uvw, V, workspace, workspace_bytes, &g);
+    if (rc) return rc;
+    if (!grid || !grad_radial || (V > 0 && !grad_vis)) return WP_ERR_NULL;
+    if (g.interp == WP_INTERP_CUBIC && !grad_spline_m) return WP_ERR_NULL;
+    if (workspace_bytes < wp_grad_workspace_bytes(plan, kernels->P, V)) return WP_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    GridWork w;
+    const size_t gb = carve_grid(g, kernels->P, V, workspace, workspace_bytes, &w);
+    int* items = reinterpret_cast<int*>(static_cast<char*>(workspace) + gb);
+    const size_t n_extra = grad_extra_ints(kernels->P, V);
+    if ((rc = grid_bin(g, kernels, uvw, nullptr, nullptr, V, w, st))) return rc;
+    return grad_radial_run(g, kernels, w, items, items + n_extra, reinterpret_cast<const float2*>(grad_vis),
+                           reinterpret_cast<const float2*>(grid), reinterpret_cast<float2*>(grad_radial),
+                           reinterpret_cast<float2*>(grad_spline_m), st);
+}
+
+int wp_hankel_adjoint(const wp_plan* plan, const double* w_planes, int32_t P, void* workspace,
+                      size_t workspace_bytes, const float* grad_radial, const float* grad_spline_m,
+                      float* grad_taper, void* stream) {
+    Geom g;
+    int rc = make_geom(plan, &g);
+    if (rc) return rc;
+    if (P < 1 || P > 65536) return WP_ERR_SIZE;
+    if (!w_planes || !workspace || !grad_radial || !grad_taper) return WP_ERR_NULL;
+    if (g.interp == WP_INTERP_CUBIC && !grad_spline_m) return WP_ERR_NULL;
+    if (!aligned256(workspace) || workspace_bytes < carve_kg(g, P, nullptr, 0, nullptr)) return WP_ERR_WORKSPACE;
+    if ((rc = check_device())) return rc;
+    KgWork w;
+    carve_kg(g, P, workspace, workspace_bytes, &w);
+    return hankel_adjoint_run(g, w, P, w_planes, reinterpret_cast<const float2*>(grad_radial),
+                              reinterpret_cast<const float2*>(grad_spline_m), grad_taper, (cudaStream_t)stream);
+}
+
+int wp_image_adjoint(const wp_plan* plan, const float* taper, const float* image, float* grid_g,
+                     double weight_sum, float* grad_image, float* grad_taper, void* stream) {
+    Geom g;
+    int rc = make_geom(plan, &g);
+    if (rc) return rc;
+    if (!taper || !image || !grid_g || !grad_image || !grad_taper) return WP_ERR_NULL;
+    if (!(weight_sum > 0.0)) return WP_ERR_SIZE;
+    if ((rc = check_device())) return rc;
+    return image_adjoint(g, taper, image, reinterpret_cast<float2*>(grid_g), weight_sum, grad_image, grad_taper,
+                         (cudaStream_t)stream);
 }
 
 int wp_dirty_image(const wp_plan* plan, const float* taper, float* grid, double weight_sum, float* image,

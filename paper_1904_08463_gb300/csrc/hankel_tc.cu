@@ -12,11 +12,13 @@
 //   warp 0 lane 0   TMA producer: per 32-deep K slice loads A_hi, A_lo, B_hi, B_lo tiles
 //                   (128 rows x 128 B each, 128-byte swizzle) into a 3-stage ring
 //   warp 1 lane 0   MMA issuer: 4 K-steps x 3 products of tcgen05.mma.kind::tf32
-//                   (M = 128, N = 128, K = 8) per slice, commits each stage back to the
-//                   producer and the whole tile to the epilogue
-//   warps 0-3       epilogue: tcgen05.ld of the 128 x 128 FP32 accumulator (warp w reads
-//                   TMEM lanes 32w..32w+31), column pairs (2p, 2p+1) stored as the complex
-//                   radial sample of plane p (coalesced along the radial index)
+//                   (M = 128, N = 128, K = 8) per slice into one of two TMEM buffers,
+//                   commits each stage back to the producer and each group of slices
+//                   to the accumulation warps
+//   warps 2-5       accumulation: tcgen05.ld of each finished partial (warp w reads TMEM
+//                   lanes 32 (w % 4) ..) into FP32 registers; epilogue: column pairs
+//                   (2p, 2p+1) stored as the complex radial sample of plane p (coalesced
+//                   along the radial index)
 // Every mbarrier wait is bounded by a clock budget; on expiry the kernel records
 // WP_ERR_TIMEOUT in `status`, stops issuing, drains what it issued, frees TMEM and returns.
 #include <cuda.h>
@@ -37,7 +39,8 @@ constexpr int STAGES = 3;
 constexpr int TILE_BYTES = BM * BK * 4;              // 16 KB (BN == BM)
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;          // A_hi, A_lo, B_hi, B_lo
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int TMEM_COLS = 128;
+constexpr int TMEM_COLS = 2 * BN;                   // two accumulator buffers
+constexpr int GROUP = 2;                             // K-slices per TMEM partial sum
 constexpr long long WAIT_BUDGET = 4000000000LL;      // ~2 s of SM clock per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -128,7 +131,30 @@ __device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(128, 1) k_hankel_tf32x3(const __grid_constant__ CUtensorMap map_a_hi,
+__device__ __forceinline__ void tmem_ld_x32_nowait(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Six warps: 0 = TMA producer, 1 = MMA issuer (and TMEM owner), 2..5 = accumulation and
+// epilogue (warp w reads TMEM lanes 32 (w % 4) .. +31, i.e. output rows of that quarter).
+// The tensor core's FP32 accumulation does not round to nearest: its error grows with the
+// number of MMA steps folded into one accumulator (about 2^-25 of the running sum per
+// step, one-signed).  So the MMA issuer accumulates only GROUP K-slices into one of two
+// TMEM buffers; the accumulation warps move each finished partial into FP32 registers
+// (IEEE adds) while the next group runs into the other buffer.
+__global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant__ CUtensorMap map_a_hi,
                                                           const __grid_constant__ CUtensorMap map_a_lo,
                                                           const __grid_constant__ CUtensorMap map_b_hi,
                                                           const __grid_constant__ CUtensorMap map_b_lo,
@@ -136,32 +162,39 @@ __global__ void __launch_bounds__(128, 1) k_hankel_tf32x3(const __grid_constant_
                                                           float2* __restrict__ radial, int use_atomic,
                                                           int* __restrict__ status) {
     extern __shared__ uint8_t smem_raw[];
-    // 1024-byte aligned stage ring (required by the 128-byte swizzle atoms)
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* gbase = smem_raw + (base - raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * STAGE_BYTES);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
+    // bars: full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], done
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
     const uint32_t bar_full0 = smem_u32(bars);
     const uint32_t bar_empty0 = smem_u32(bars + STAGES);
-    const uint32_t bar_done = smem_u32(bars + 2 * STAGES);
+    const uint32_t bar_accf0 = smem_u32(bars + 2 * STAGES);
+    const uint32_t bar_acce0 = smem_u32(bars + 2 * STAGES + 2);
+    const uint32_t bar_done = smem_u32(bars + 2 * STAGES + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
     const int kchunk = K / k_split;
     const int kbeg = blockIdx.z * kchunk;
     const int nkb = kchunk / BK;
+    const int ngroups = (nkb + GROUP - 1) / GROUP;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(bar_full0 + 8 * s, 1);
             mbar_init(bar_empty0 + 8 * s, 1);
         }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bar_accf0 + 8 * b, 1);
+            mbar_init(bar_acce0 + 8 * b, 4);     // one arrival per accumulation warp
+        }
         mbar_init(bar_done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(smem_u32(tmem_slot)), "r"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -171,78 +204,110 @@ __global__ void __launch_bounds__(128, 1) k_hankel_tf32x3(const __grid_constant_
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer ----------------
-        int issued = 0;
-        bool ok = true;
-        for (int kb = 0; kb < nkb && ok; ++kb) {
-            const int s = kb % STAGES;
-            if (kb >= STAGES) ok = mbar_wait(bar_empty0 + 8 * s, ((kb / STAGES) - 1) & 1, status);
-            if (!ok) break;
-            const uint32_t st = base + s * STAGE_BYTES;
-            const uint32_t fb = bar_full0 + 8 * s;
-            mbar_expect_tx(fb, STAGE_BYTES);
-            const int x = kbeg + kb * BK;
-            tma_load_2d(st + 0 * TILE_BYTES, &map_a_hi, x, m0, fb);
-            tma_load_2d(st + 1 * TILE_BYTES, &map_a_lo, x, m0, fb);
-            tma_load_2d(st + 2 * TILE_BYTES, &map_b_hi, x, n0, fb);
-            tma_load_2d(st + 3 * TILE_BYTES, &map_b_lo, x, n0, fb);
-            ++issued;
-        }
-        if (!ok) {
-            // drain: every issued slice must land before the CTA may exit
-            for (int kb = max(0, issued - STAGES); kb < issued; ++kb)
-                mbar_wait(bar_full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, status);
-        }
-    } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer ----------------
-        const uint32_t idesc = idesc_tf32(BM, BN);
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % STAGES;
-            if (!mbar_wait(bar_full0 + 8 * s, (kb / STAGES) & 1, status)) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t st = base + s * STAGE_BYTES;
-            const uint64_t a_hi = smem_desc_sw128(st + 0 * TILE_BYTES);
-            const uint64_t a_lo = smem_desc_sw128(st + 1 * TILE_BYTES);
-            const uint64_t b_hi = smem_desc_sw128(st + 2 * TILE_BYTES);
-            const uint64_t b_lo = smem_desc_sw128(st + 3 * TILE_BYTES);
-#pragma unroll
-            for (int j = 0; j < BK / 8; ++j) {
-                const uint64_t adv = (uint64_t)((j * 32) >> 4);   // 8 tf32 = 32 bytes along K
-                mma_tf32(tmem, a_hi + adv, b_hi + adv, idesc, (kb | j) != 0);
-                mma_tf32(tmem, a_hi + adv, b_lo + adv, idesc, 1u);
-                mma_tf32(tmem, a_lo + adv, b_hi + adv, idesc, 1u);
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            int issued = 0;
+            bool ok = true;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % STAGES;
+                if (kb >= STAGES) ok = mbar_wait(bar_empty0 + 8 * s, ((kb / STAGES) - 1) & 1, status);
+                if (!ok) break;
+                const uint32_t st = base + s * STAGE_BYTES;
+                const uint32_t fb = bar_full0 + 8 * s;
+                mbar_expect_tx(fb, STAGE_BYTES);
+                const int x = kbeg + kb * BK;
+                tma_load_2d(st + 0 * TILE_BYTES, &map_a_hi, x, m0, fb);
+                tma_load_2d(st + 1 * TILE_BYTES, &map_a_lo, x, m0, fb);
+                tma_load_2d(st + 2 * TILE_BYTES, &map_b_hi, x, n0, fb);
+                tma_load_2d(st + 3 * TILE_BYTES, &map_b_lo, x, n0, fb);
+                ++issued;
             }
-            mma_commit(bar_empty0 + 8 * s);
+            if (!ok) {
+                // every issued slice must land before the CTA may exit
+                for (int kb = max(0, issued - STAGES); kb < issued; ++kb)
+                    mbar_wait(bar_full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, status);
+            }
         }
-        mma_commit(bar_done);   // fires once every issued MMA has completed
-    }
-    __syncwarp();
-
-    // ---------------- epilogue: all four warps ----------------
-    const bool done = mbar_wait(bar_done, 0, status);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (done && *status == 0) {
-        const int m = m0 + warp * 32 + lane;
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-            float v[32];
-            tmem_ld_x32(trow + c0, v);
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            const uint32_t idesc = idesc_tf32(BM, BN);
+            bool ok = true;
+            for (int g = 0; g < ngroups && ok; ++g) {
+                const int b = g & 1;
+                if (g >= 2) ok = mbar_wait(bar_acce0 + 8 * b, ((g >> 1) - 1) & 1, status);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t dacc = tmem + (uint32_t)(b * BN);
+                const int kb_end = min(nkb, (g + 1) * GROUP);
+                for (int kb = g * GROUP; kb < kb_end; ++kb) {
+                    const int s = kb % STAGES;
+                    if (!mbar_wait(bar_full0 + 8 * s, (kb / STAGES) & 1, status)) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t st = base + s * STAGE_BYTES;
+                    const uint64_t a_hi = smem_desc_sw128(st + 0 * TILE_BYTES);
+                    const uint64_t a_lo = smem_desc_sw128(st + 1 * TILE_BYTES);
+                    const uint64_t b_hi = smem_desc_sw128(st + 2 * TILE_BYTES);
+                    const uint64_t b_lo = smem_desc_sw128(st + 3 * TILE_BYTES);
+                    const uint32_t first = (kb == g * GROUP) ? 1u : 0u;
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-                const int p = (n0 + c0 + j) >> 1;
+                    for (int j = 0; j < BK / 8; ++j) {
+                        const uint64_t adv = (uint64_t)((j * 32) >> 4);   // 8 tf32 = 32 bytes along K
+                        mma_tf32(dacc, a_hi + adv, b_lo + adv, idesc, (first && j == 0) ? 0u : 1u);
+                        mma_tf32(dacc, a_lo + adv, b_hi + adv, idesc, 1u);
+                        mma_tf32(dacc, a_hi + adv, b_hi + adv, idesc, 1u);
+                    }
+                    mma_commit(bar_empty0 + 8 * s);
+                }
+                if (ok) mma_commit(bar_accf0 + 8 * b);
+            }
+            mma_commit(bar_done);   // fires once every issued MMA has completed
+        }
+    } else {
+        // ---------------- accumulation + epilogue (warps 2..5) ----------------
+        const int q = warp & 3;                         // TMEM lane quarter
+        float acc[BN];
+#pragma unroll
+        for (int i = 0; i < BN; ++i) acc[i] = 0.0f;
+        bool ok = true;
+        for (int g = 0; g < ngroups; ++g) {
+            const int b = g & 1;
+            // warp-uniform decision: every lane polls, the warp proceeds only if all saw it
+            if (!__all_sync(0xffffffffu, mbar_wait(bar_accf0 + 8 * b, (g >> 1) & 1, status))) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
+#pragma unroll
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld_x32_nowait(trow + c0, r);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int i = 0; i < 32; ++i) acc[c0 + i] += __uint_as_float(r[i]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_acce0 + 8 * b);
+        }
+        if (ok && *status == 0) {
+            const int m = m0 + q * 32 + lane;
+#pragma unroll
+            for (int j = 0; j < BN; j += 2) {
+                const int p = (n0 + j) >> 1;
                 if (p < P && m < M) {
                     float2* dst = radial + (int64_t)p * M + m;
-                    if (use_atomic) atomicAdd(dst, make_float2(v[j], v[j + 1]));
-                    else *dst = make_float2(v[j], v[j + 1]);
+                    if (use_atomic) atomicAdd(dst, make_float2(acc[j], acc[j + 1]));
+                    else *dst = make_float2(acc[j], acc[j + 1]);
                 }
             }
         }
     }
+    __syncwarp();
+    // no MMA may still write TMEM when it is freed
+    if (warp == 1) mbar_wait(bar_done, 0, status);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
     }
@@ -311,7 +376,7 @@ int kg_gemm_tf32x3(const Geom& g, const KgWork& w, int P, float2* radial, int* s
     });
     WP_CUDA(attr_err);
     dim3 grid(N / BN, M / BM, split);
-    k_hankel_tf32x3<<<grid, 128, SMEM_BYTES, st>>>(ma_hi, ma_lo, mb_hi, mb_lo, M, K, split, P, radial,
+    k_hankel_tf32x3<<<grid, 192, SMEM_BYTES, st>>>(ma_hi, ma_lo, mb_hi, mb_lo, M, K, split, P, radial,
                                                    split > 1, status);
     WP_LAUNCH_CHECK("k_hankel_tf32x3");
     return WP_OK;

@@ -142,4 +142,11 @@ int image_to_grid(const Geom& g, const float* taper, const float* image, double 
     return WP_OK;
 }
 
+int image_adjoint(const Geom& g, const float* taper, const float* image, float2* grid_g, double wsum,
+                  float* grad_image, float* grad_taper, cudaStream_t st) {
+    int rc = exec_fft(g.N, grid_g, CUFFT_INVERSE, st);
+    if (rc) return rc;
+    return launch_image_adjoint(g, taper, image, grid_g, wsum, grad_image, grad_taper, st);
+}
+
 }  // namespace wp

@@ -48,7 +48,8 @@ __global__ void k_j0_matrix(int k_out, int R, int r_pad, int os, float* __restri
     h_lo[idx] = to_tf32(v - hi);
 }
 
-// Host: band of the inverse of the spline system matrix (rows: [2 1], [1 4 1] ..., [.. 1]).
+// Host: band of the inverse of the spline system matrix (rows: [2 1], [1 4 1] ..., [.. 1]),
+// stored diagonal-major: band[d][k] = A^-1[k][k + d - 32] (consecutive k contiguous).
 // Entries of the inverse decay like (2 - sqrt 3)^|k - j| = 0.268^|k - j|, so a half-width
 // of 32 keeps everything above 1e-18 of the diagonal.
 static void spline_band_host(int K, std::vector<float>& band) {
@@ -76,12 +77,27 @@ static void spline_band_host(int K, std::vector<float>& band) {
         for (int k = K - 2; k >= 0; --k) x[k] = d[k] - cp[k] * x[k + 1];
         for (int k = j - HW; k <= j + HW; ++k) {
             if (k < 0 || k >= K) continue;
-            band[(size_t)k * (2 * HW + 1) + (j - k + HW)] = (float)x[k];
+            band[(size_t)(j - k + HW) * K + k] = (float)x[k];
         }
     }
 }
 
+// n - 1 at the radial nodes, in FP64, without cancellation: -r^2 / (1 + sqrt(1 - r^2)).
+__global__ void k_nm1(int R, int r_pad, double r_max, double* __restrict__ nm1) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= r_pad) return;
+    double v = 0.0;
+    if (i < R) {
+        double r = ((double)i + 0.5) * (r_max / (double)R);
+        double r2 = r * r;
+        v = -r2 / (1.0 + sqrt(1.0 - r2));
+    }
+    nm1[i] = v;
+}
+
 int kg_prepare(const Geom& g, const KgWork& w, cudaStream_t st) {
+    k_nm1<<<(g.r_pad + 255) / 256, 256, 0, st>>>(g.R, g.r_pad, g.r_max, w.nm1);
+    WP_LAUNCH_CHECK("k_nm1");
     int64_t total = (int64_t)g.k_out * g.r_pad;
     int threads = 256;
     int64_t blocks = (total + threads - 1) / threads;
@@ -100,12 +116,13 @@ int kg_prepare(const Geom& g, const KgWork& w, cudaStream_t st) {
 // =======================================================================================
 // K2: image-domain convolution function on the radial line, written transposed
 // (row 2p = real part, row 2p+1 = imaginary part, R contiguous) as the B operand of the
-// K-major matrix product.  The phase w (n - 1) is formed in FP64 with the cancellation-
-// free n - 1 = -r^2 / (1 + sqrt(1 - r^2)), reduced to [-1/2, 1/2] cycles in FP64, and
-// only then handed to the FP32 sincospi.
+// K-major matrix product.  The phase in cycles, w (n - 1), is one FP64 product of the
+// plane's w and the node's n - 1 (precomputed once per geometry in FP64 without
+// cancellation), reduced to [-1/2, 1/2] cycles in FP64, and only then handed to the FP32
+// sincospi -- so |w| up to 1e5 keeps FP32 phase accuracy.
 // =======================================================================================
 template <bool SPLIT>
-__global__ void k_screen(int R, int r_pad, int P, int P_pad, double r_max,
+__global__ void k_screen(int R, int r_pad, int P, int P_pad, const double* __restrict__ nm1,
                          const float* __restrict__ taper, const double* __restrict__ w_planes,
                          float* __restrict__ f32, float* __restrict__ f_hi, float* __restrict__ f_lo) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -113,10 +130,7 @@ __global__ void k_screen(int R, int r_pad, int P, int P_pad, double r_max,
     if (i >= r_pad) return;
     float re = 0.0f, im = 0.0f;
     if (i < R && p < P) {
-        double r = ((double)i + 0.5) * (r_max / (double)R);
-        double r2 = r * r;
-        double nm1 = -r2 / (1.0 + sqrt(1.0 - r2));
-        double cyc = w_planes[p] * nm1;            // phase / (2 pi)
+        double cyc = w_planes[p] * nm1[i];         // phase / (2 pi)
         double fr = cyc - rint(cyc);               // in [-1/2, 1/2]
         float s, c;
         sincospif((float)(2.0 * fr), &s, &c);
@@ -143,11 +157,9 @@ int kg_screen(const Geom& g, const KgWork& w, const float* taper, const double* 
     int Pp = p_pad(P);
     dim3 grid((g.r_pad + 255) / 256, Pp);
     if (g.kernelgen == WP_KG_TF32X3)
-        k_screen<true><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, g.r_max, taper, w_planes, w.f32,
-                                             w.f_hi, w.f_lo);
+        k_screen<true><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1, taper, w_planes, w.f32, w.f_hi, w.f_lo);
     else
-        k_screen<false><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, g.r_max, taper, w_planes, w.f32,
-                                              w.f_hi, w.f_lo);
+        k_screen<false><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1, taper, w_planes, w.f32, w.f_hi, w.f_lo);
     WP_LAUNCH_CHECK("k_screen");
     return WP_OK;
 }
@@ -252,7 +264,9 @@ __global__ void __launch_bounds__(256) k_trunc_spline(int K, int os, int s_min, 
                                                       const float* __restrict__ band,
                                                       float2* __restrict__ spline_m,
                                                       int32_t* __restrict__ support) {
-    extern __shared__ float2 y[];   // [K]
+    extern __shared__ float2 sm[];   // y[K], rhs[K + 64] (rhs padded by 32 zeros on each side)
+    float2* y = sm;
+    float2* rhs = sm + K + 32;
     __shared__ float red_f[8];
     __shared__ int red_i[8];
     const int p = blockIdx.x;
@@ -262,6 +276,10 @@ __global__ void __launch_bounds__(256) k_trunc_spline(int K, int os, int s_min, 
         float2 v = src[k];
         y[k] = v;
         local_max = fmaxf(local_max, sqrtf(v.x * v.x + v.y * v.y));
+    }
+    for (int k = threadIdx.x; k < 32; k += blockDim.x) {
+        rhs[k - 32] = make_float2(0.0f, 0.0f);
+        rhs[K + k] = make_float2(0.0f, 0.0f);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -289,27 +307,28 @@ __global__ void __launch_bounds__(256) k_trunc_spline(int K, int os, int s_min, 
         }
     }
     if (do_spline) {
+        for (int j = threadIdx.x; j < K; j += blockDim.x) {
+            float2 r;
+            if (j == 0) {
+                r = make_float2(6.0f * (y[1].x - y[0].x), 6.0f * (y[1].y - y[0].y));
+            } else if (j == K - 1) {
+                r = make_float2(0.0f, 0.0f);
+            } else {
+                r = make_float2(6.0f * ((y[j + 1].x - y[j].x) - (y[j].x - y[j - 1].x)),
+                                6.0f * ((y[j + 1].y - y[j].y) - (y[j].y - y[j - 1].y)));
+            }
+            rhs[j] = r;
+        }
+        __syncthreads();
         float2* dst = spline_m + (int64_t)p * K;
         for (int k = threadIdx.x; k < K; k += blockDim.x) {
-            const float* b = band + (int64_t)k * 65;
             float mr = 0.0f, mi = 0.0f;
-            for (int d = -32; d <= 32; ++d) {
-                int j = k + d;
-                if (j < 0 || j >= K) continue;
-                float rr, ri;
-                if (j == 0) {
-                    rr = 6.0f * (y[1].x - y[0].x);
-                    ri = 6.0f * (y[1].y - y[0].y);
-                } else if (j == K - 1) {
-                    rr = 0.0f;
-                    ri = 0.0f;
-                } else {
-                    rr = 6.0f * ((y[j + 1].x - y[j].x) - (y[j].x - y[j - 1].x));
-                    ri = 6.0f * ((y[j + 1].y - y[j].y) - (y[j].y - y[j - 1].y));
-                }
-                float c = b[d + 32];
-                mr = fmaf(c, rr, mr);
-                mi = fmaf(c, ri, mi);
+#pragma unroll 13
+            for (int d = 0; d < 65; ++d) {
+                const float c = band[(int64_t)d * K + k];    // zero where k + d - 32 is outside
+                const float2 r = rhs[k + d - 32];
+                mr = fmaf(c, r.x, mr);
+                mi = fmaf(c, r.y, mi);
             }
             dst[k] = make_float2(mr, mi);
         }
@@ -321,7 +340,7 @@ int kg_trunc_spline(const Geom& g, const KgWork& w, int P, const float2* radial,
     int do_trunc = (g.tau > 0.0) ? 1 : 0;
     int do_spline = (g.interp == WP_INTERP_CUBIC) ? 1 : 0;
     if (!do_trunc && !do_spline) return WP_OK;
-    size_t smem = (size_t)g.k_out * sizeof(float2);
+    size_t smem = (size_t)(2 * g.k_out + 64) * sizeof(float2);
     if (smem > 48 * 1024)
         WP_CUDA(cudaFuncSetAttribute(k_trunc_spline, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_trunc_spline<<<P, 256, smem, st>>>(g.k_out, g.os, g.s_min, g.s_max, (float)g.tau, do_trunc,
@@ -331,25 +350,69 @@ int kg_trunc_spline(const Geom& g, const KgWork& w, int P, const float2* radial,
 }
 
 // =======================================================================================
-// K7: resample the radial line into the oversampled cache.  One block per (plane, fv):
-// it stages the plane's line (value + second derivative, 16 B per sample) in shared
-// memory and writes the os sub-kernels (fu = 0..os-1) of that fv as one contiguous run
-// of os (2S+1)^2 complex taps, one tap per thread per step, consecutive threads on
-// consecutive taps (coalesced 256 B per warp), streaming stores.  The tap radius squared
-// q = (os (jx - S) - fu)^2 + (os (jy - S) - fv)^2 is an exact integer, so the circular
-// cut q > (os S)^2 and the spline interval floor(sqrt q) are decided exactly.
-// Flat index -> (fu, jy, jx) uses float reciprocals with a half-step offset and one
-// integer correction step, so it is exact for every run length below 2^31.
+// K7: resample the radial line into the oversampled cache.
+//
+// Every tap of every sub-kernel samples one radially symmetric 2D function on the fine
+// grid (spacing du/os): tap (jx, jy) of sub-kernel (fu, fv) sits at fine offset
+// (os (jx - S) - fu, os (jy - S) - fv).  Mirroring x maps sub-kernel fu > 0 onto os - fu
+// with jx -> 2S + 1 - jx (fu = 0 maps onto itself); y likewise.  So only the sub-kernels
+// with fu, fv <= os/2 are evaluated -- (os/2 + 1)^2 of os^2 -- and each evaluated tap is
+// stored to up to four sub-kernels straight from registers.  The column / row of a
+// mirrored sub-kernel that has no pre-image (jx = 0 for fu > 0) lies beyond the support
+// radius and is written as zeros.
+//
+// One block per (plane, representative), issued from the last plane backwards (supports
+// grow with |w|: the largest blocks start first).  Consecutive threads take consecutive
+// taps of the flattened (2S+1)^2 representative, so each of the (up to) four stores of a
+// warp covers one contiguous run (ascending or descending) of the cache.
+//
+// Tap values: the plane's line (value + spline second derivative, 16 B per sample) sits
+// in shared memory with a one-slot skew every 8 samples (neighbouring taps are up to os
+// samples apart on the line; the skew spreads them over the banks).  The radius test
+// q = dx^2 + dy^2 <= (os S)^2 is an exact integer test; x = sqrt(q) only picks the spline
+// interval and its weights, which are continuous across interval ends.
 // =======================================================================================
+__device__ __forceinline__ int skew(int k) { return k + (k >> 3); }
+
 template <bool CUBIC>
-__global__ void __launch_bounds__(256) k_resample(int K, int os, int s_max, const float2* __restrict__ radial,
+__device__ __forceinline__ float2 resample_tap(const float4* __restrict__ line, int dx, int dy, int lim2) {
+    const int q = dx * dx + dy * dy;
+    float2 out = make_float2(0.0f, 0.0f);
+    if (q <= lim2) {
+        const float qf = (float)q;
+        const float x = (q > 0) ? qf * rsqrtf(qf) : 0.0f;
+        // round(x - 1/2) through the float mantissa (1.5 * 2^23): the interval index
+        const float tt = (x - 0.5f) + 12582912.0f;
+        const int k = __float_as_int(tt) - 0x4B400000;
+        const float a = x - (tt - 12582912.0f);
+        const float b = 1.0f - a;
+        const float4 L0 = line[skew(k)];
+        const float4 L1 = line[skew(k + 1)];
+        out.x = fmaf(b, L0.x, a * L1.x);
+        out.y = fmaf(b, L0.y, a * L1.y);
+        if (CUBIC) {
+            const float cb = (b * b - 1.0f) * b * (1.0f / 6.0f);
+            const float ca = (a * a - 1.0f) * a * (1.0f / 6.0f);
+            out.x = fmaf(cb, L0.z, fmaf(ca, L1.z, out.x));
+            out.y = fmaf(cb, L0.w, fmaf(ca, L1.w, out.y));
+        }
+    }
+    return out;
+}
+
+template <bool CUBIC>
+__global__ void __launch_bounds__(256) k_resample(int K, int os, int s_max, int nrep, int n_items,
+                                                  const float2* __restrict__ radial,
                                                   const float2* __restrict__ spline_m,
                                                   const int32_t* __restrict__ support,
                                                   const int64_t* __restrict__ offsets,
                                                   float2* __restrict__ cache) {
-    extern __shared__ float4 line[];   // [n_used] {y.re, y.im, m.re, m.im}
-    const int p = blockIdx.x / os;
-    const int fv = blockIdx.x - p * os;
+    extern __shared__ float4 line[];   // skew(n_used) entries {y.re, y.im, m.re, m.im}
+    const int item = n_items - 1 - (int)blockIdx.x;
+    const int p = item / nrep;
+    const int rep = item - p * nrep;
+    const int h = os / 2;
+    const int fv = rep / (h + 1), fu = rep - fv * (h + 1);   // 0 <= fu, fv <= os / 2
     const int S = min(max(support[p], 1), s_max);   // supports outside [1, S_max] are clamped
     const int W = 2 * S + 1;
     const int W2 = W * W;
@@ -360,46 +423,41 @@ __global__ void __launch_bounds__(256) k_resample(int K, int os, int s_max, cons
     for (int k = threadIdx.x; k < n_used; k += blockDim.x) {
         float2 a = yl[k];
         float2 b = CUBIC ? ml[k] : make_float2(0.0f, 0.0f);
-        line[k] = make_float4(a.x, a.y, b.x, b.y);
+        line[skew(k)] = make_float4(a.x, a.y, b.x, b.y);
+    }
+    // mirror images of this representative (a mirror of 0, or one landing on itself, adds
+    // nothing): x -> os - fu, y -> os - fv
+    const bool mx = (fu != 0) && (os - fu != fu);
+    const bool my = (fv != 0) && (os - fv != fv);
+    float2* const base = cache + offsets[p];
+    float2* const d00 = base + (int64_t)(fv * os + fu) * W2;
+    float2* const d10 = base + (int64_t)(fv * os + (os - fu)) * W2;          // x-mirrored
+    float2* const d01 = base + (int64_t)((os - fv) * os + fu) * W2;          // y-mirrored
+    float2* const d11 = base + (int64_t)((os - fv) * os + (os - fu)) * W2;   // both
+    const float2 zero = make_float2(0.0f, 0.0f);
+    // zero column / row of mirrored sub-kernels
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        if (mx) { __stcs(d10 + (int64_t)i * W, zero); if (my) __stcs(d11 + (int64_t)i * W, zero); }
+        if (my) { __stcs(d01 + i, zero); if (mx) __stcs(d11 + i, zero); }
     }
     __syncthreads();
-    const int64_t run = (int64_t)os * W2;
-    float2* dst = cache + offsets[p] + (int64_t)fv * run;
-    const float inv_w2 = 1.0f / (float)W2;
     const float inv_w = 1.0f / (float)W;
     const int lim2 = lim * lim;
     const int dy0 = -os * S - fv;   // os (jy - S) - fv at jy = 0
-    const int dx0 = -os * S;        // os (jx - S) at jx = 0 (fu subtracted below)
-    for (int t = threadIdx.x; t < run; t += blockDim.x) {
-        int fu = (int)(((float)t + 0.5f) * inv_w2);
-        fu -= (fu * W2 > t);            // the estimate is off by at most one: correct it
-        fu += ((fu + 1) * W2 <= t);
-        int r = t - fu * W2;
-        int jy = (int)(((float)r + 0.5f) * inv_w);
-        jy -= (jy * W > r);
-        jy += ((jy + 1) * W <= r);
-        int jx = r - jy * W;
-        int dx = dx0 + os * jx - fu;
-        int dy = dy0 + os * jy;
-        int q = dx * dx + dy * dy;
-        float2 out = make_float2(0.0f, 0.0f);
-        if (q <= lim2) {
-            float x = sqrtf((float)q);
-            int k = min((int)x, K - 2);
-            float a = x - (float)k;
-            float b = 1.0f - a;
-            float4 L0 = line[k];
-            float4 L1 = line[k + 1];
-            out.x = b * L0.x + a * L1.x;
-            out.y = b * L0.y + a * L1.y;
-            if (CUBIC) {
-                float cb = (b * b * b - b) * (1.0f / 6.0f);
-                float ca = (a * a * a - a) * (1.0f / 6.0f);
-                out.x = fmaf(cb, L0.z, fmaf(ca, L1.z, out.x));
-                out.y = fmaf(cb, L0.w, fmaf(ca, L1.w, out.y));
-            }
-        }
-        __stcs(dst + t, out);
+    const int dx0 = -os * S - fu;   // os (jx - S) - fu at jx = 0
+    const int m1 = 2 * S + 1;       // mirror: j -> 2S + 1 - j
+    for (int t = threadIdx.x; t < W2; t += blockDim.x) {
+        int jy = (int)(((float)t + 0.5f) * inv_w);
+        jy -= (jy * W > t);                              // the estimate is off by at most one
+        jy += ((jy + 1) * W <= t);
+        const int jx = t - jy * W;
+        const float2 v = resample_tap<CUBIC>(line, dx0 + os * jx, dy0 + os * jy, lim2);
+        __stcs(d00 + t, v);
+        const bool xin = mx && jx > 0;                   // pre-image of column 2S+1-jx exists
+        const bool yin = my && jy > 0;
+        if (xin) __stcs(d10 + (jy * W + (m1 - jx)), v);
+        if (yin) __stcs(d01 + ((m1 - jy) * W + jx), v);
+        if (xin && yin) __stcs(d11 + ((m1 - jy) * W + (m1 - jx)), v);
     }
 }
 
@@ -407,16 +465,21 @@ int kg_resample(const Geom& g, int P, const float2* radial, const float2* spline
                 const int32_t* support, const int64_t* offsets, float2* cache, cudaStream_t st) {
     int n_max = g.os * g.s_max + 2;
     if (n_max > g.k_out) n_max = g.k_out;
-    size_t smem = (size_t)n_max * sizeof(float4);
-    dim3 grid((unsigned)P * g.os);
+    size_t smem = (size_t)(n_max + (n_max >> 3) + 1) * sizeof(float4);
+    const int h = g.os / 2;
+    const int nrep = (h + 1) * (h + 1);
+    const int n_items = P * nrep;
+    dim3 grid((unsigned)n_items);
     if (g.interp == WP_INTERP_CUBIC) {
         if (smem > 48 * 1024)
             WP_CUDA(cudaFuncSetAttribute(k_resample<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_resample<true><<<grid, 256, smem, st>>>(g.k_out, g.os, g.s_max, radial, spline_m, support, offsets, cache);
+        k_resample<true><<<grid, 256, smem, st>>>(g.k_out, g.os, g.s_max, nrep, n_items, radial, spline_m, support,
+                                                  offsets, cache);
     } else {
         if (smem > 48 * 1024)
             WP_CUDA(cudaFuncSetAttribute(k_resample<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_resample<false><<<grid, 256, smem, st>>>(g.k_out, g.os, g.s_max, radial, spline_m, support, offsets, cache);
+        k_resample<false><<<grid, 256, smem, st>>>(g.k_out, g.os, g.s_max, nrep, n_items, radial, spline_m, support,
+                                                   offsets, cache);
     }
     WP_LAUNCH_CHECK("k_resample");
     return WP_OK;

@@ -36,6 +36,7 @@ struct Geom {
 };
 
 int make_geom(const wp_plan* plan, Geom* g);
+int check_device_public();   // WP_OK when the current device is sm_103
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
@@ -65,10 +66,12 @@ struct KgWork {
     float* h32;        // [k_out][r_pad] FP32 transform matrix
     float* h_hi;       // [k_out][r_pad] TF32 high part
     float* h_lo;       // [k_out][r_pad] TF32 low part
-    float* band;       // [k_out][65] spline inverse band
+    float* band;       // [65][k_out] spline inverse band (row d holds A^-1[k][k + d - 32])
+    double* nm1;       // [R] n - 1 = sqrt(1 - r_i^2) - 1 at the radial nodes
     float* f32;        // [2 P_pad][r_pad] image-domain functions (FP32 path)
     float* f_hi;       // [2 P_pad][r_pad]
     float* f_lo;       // [2 P_pad][r_pad]
+    float* gct;        // [2 P_pad][k_out] radial-line gradient rows (re, im) for the adjoint
     int*   status;     // [4]
 };
 size_t carve_kg(const Geom& g, int P, void* ws, size_t bytes, KgWork* out);
@@ -120,5 +123,22 @@ int image_dirty(const Geom& g, const float* taper, float2* grid, double wsum, fl
 int image_to_grid(const Geom& g, const float* taper, const float* image, double wsum, float2* grid,
                   cudaStream_t st);
 void release_fft_plans();
+
+size_t fft_workspace_bytes(const Geom& g, int P);
+int fft_wkernels(const Geom& g, const float* taper, const double* w_planes, int P, const int32_t* support,
+                 const int64_t* offsets, int circular, void* ws, size_t ws_bytes, float2* cache,
+                 cudaStream_t st);
+void release_fft_kernelgen_plans();
+
+// differentiation (grad.cu)
+size_t grad_extra_ints(int P, int64_t V);
+int grad_radial_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, int* item_plane, int* item_chunk,
+                    const float2* gvis, const float2* grid, float2* gC, float2* gM, cudaStream_t st);
+int hankel_adjoint_run(const Geom& g, const KgWork& w, int P, const double* w_planes, const float2* gC,
+                       const float2* gM, float* grad_taper, cudaStream_t st);
+int launch_image_adjoint(const Geom& g, const float* taper, const float* image, const float2* F, double wsum,
+                         float* grad_image, float* grad_taper, cudaStream_t st);
+int image_adjoint(const Geom& g, const float* taper, const float* image, float2* grid_g, double wsum,
+                  float* grad_image, float* grad_taper, cudaStream_t st);
 
 }  // namespace wp

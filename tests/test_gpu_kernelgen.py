@@ -46,28 +46,31 @@ def _compare(g, wk, ks, tol=KERNEL_TOL):
         assert e < tol, f"plane {p}: cache rel. L2 {e:.3e}"
 
 
-def test_small_imaging_kernels_fp32():
+@pytest.mark.parametrize("kernelgen", ["fp32", "tf32x3"])
+def test_small_imaging_kernels(kernelgen):
     """256^2, 2 deg FOV, 16 |w|-planes <= 500, os 8, R 512, S_max 15, 1 % truncation."""
     N, dl = 256, np.deg2rad(2.0) / 256
     planes = np.linspace(0.0, 500.0, 16)
-    plan, g, wk, ks = _run(N, dl, 8, 15, 3, 0.01, 512, "cubic", "fp32", planes)
+    plan, g, wk, ks = _run(N, dl, 8, 15, 3, 0.01, 512, "cubic", kernelgen, planes)
     _compare(g, wk, ks)
 
 
+@pytest.mark.parametrize("kernelgen", ["fp32", "tf32x3"])
 @pytest.mark.parametrize("os_,R,P,interp", [(1, 300, 5, "cubic"), (4, 97, 3, "linear"),
                                             (16, 256, 70, "cubic"), (8, 2048, 130, "linear")])
-def test_kernels_ragged_shapes_fp32(os_, R, P, interp):
+def test_kernels_ragged_shapes(os_, R, P, interp, kernelgen):
     """Plane counts off the 64-column tile, R off the 32-deep slice, os 1 and 16, both
     interpolations, supports fixed by the caller (including the minimum 1)."""
     N, dl = 128, np.deg2rad(4.0) / 128
     planes = np.linspace(0.0, 1500.0, P)
     rng = np.random.default_rng(P)
     sup = rng.integers(1, 13, P)
-    plan, g, wk, ks = _run(N, dl, os_, 12, 1, 0.0, R, interp, "fp32", planes, supports=sup)
+    plan, g, wk, ks = _run(N, dl, os_, 12, 1, 0.0, R, interp, kernelgen, planes, supports=sup)
     _compare(g, wk, ks)
 
 
-def test_large_w_kernels_fp32_sampled():
+@pytest.mark.parametrize("kernelgen", ["fp32", "tf32x3"])
+def test_large_w_kernels_sampled(kernelgen):
     """1024 signed planes linspace[-20000, 20000] (512 distinct |w|), R 4096, os 8,
     supports 7..127 growing with |w|, 8 degree FOV on 4096^2: every plane is generated
     on the GPU; 6 planes spread over |w| are checked against the oracle."""
@@ -75,7 +78,7 @@ def test_large_w_kernels_fp32_sampled():
     dev = torch.device("cuda")
     N, dl, R = 4096, np.deg2rad(8.0) / 4096, 4096
     _, aw, sup = synth.kernel_batch_planes()
-    plan = wp.Plan(N, dl, 8, 127, 7, 0.0, R, "cubic", "fp32")
+    plan = wp.Plan(N, dl, 8, 127, 7, 0.0, R, "cubic", kernelgen)
     taper = synth.gaussian_taper_samples(N, dl, R)
     wk = wp.make_wkernels(plan, torch.tensor(taper, dtype=torch.float32, device=dev), aw, supports=sup)
     torch.cuda.synchronize()
@@ -90,3 +93,22 @@ def test_large_w_kernels_fp32_sampled():
         c = wk.cache[int(off[p]):int(off[p + 1])].cpu().numpy()
         e = rel_l2(c, ks.cache[ks.offsets[j]:ks.offsets[j + 1]])
         assert e < KERNEL_TOL, f"|w| = {aw[p]:.1f}: cache rel. L2 {e:.3e}"
+
+
+def test_tensor_core_route_matches_fp32_route_on_every_plane():
+    """All 512 planes of the large-|w| batch: the tcgen05 TF32x3 radial lines agree with the
+    FP32 SIMT ones to well inside the kernel tolerance (both are ~1e-7 from FP64)."""
+    wp = _wp()
+    dev = torch.device("cuda")
+    N, dl, R = 4096, np.deg2rad(8.0) / 4096, 4096
+    _, aw, sup = synth.kernel_batch_planes()
+    taper = torch.tensor(synth.gaussian_taper_samples(N, dl, R), dtype=torch.float32, device=dev)
+    w = torch.tensor(aw, dtype=torch.float64, device=dev)
+    out = {}
+    for kg in ("fp32", "tf32x3"):
+        plan = wp.Plan(N, dl, 8, 127, 7, 0.0, R, "cubic", kg)
+        ws = wp.kernelgen_prepare(plan, len(aw))
+        out[kg] = wp.hankel_radial(plan, taper, w, ws)[0].cpu().numpy()
+    num = np.linalg.norm(out["fp32"] - out["tf32x3"], axis=1)
+    den = np.linalg.norm(out["fp32"], axis=1)
+    assert (num / den).max() < 2e-6
