@@ -13,7 +13,8 @@
  *  - Every array argument is a DEVICE pointer unless its comment says "host".
  *    Device memory is owned by the caller; the library allocates no device memory
  *    except cuFFT plans/work areas (wp_dirty_image, wp_image_to_grid,
- *    wp_fft_wkernels), which it caches per device and size until wp_release().
+ *    wp_fft_wkernels), which it caches per device and size until wp_release(), and the
+ *    fixed scratch array of wp_grid_static.
  *  - Complex values are interleaved float pairs (re, im) -- the layout of CUDA's
  *    float2 / cuFloatComplex / torch.complex64.
  *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*; NULL is
@@ -236,6 +237,30 @@ int wp_grid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw,
 int wp_degrid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw,
               const float* grid, int64_t V, void* workspace, size_t workspace_bytes,
               float* vis_out, void* stream);
+
+/*
+ * Allocation-free gridding.  This entry point has no counterpart in the paper; it exists
+ * for callers that cannot allocate device memory -- for example an imaging pipeline that
+ * reserves all of HBM for its own pools at start-up and forbids later allocations, or a
+ * host framework whose plug-ins may only use memory they are handed -- and therefore
+ * cannot provide the scratch that wp_grid takes.
+ *  - Same arguments and result as wp_grid, minus the workspace: the scratch is one array of
+ *    WP_GRID_STATIC_SCRATCH_BYTES (64 MiB) compiled into the library, which every GPU that
+ *    loads the library holds until the process exits.
+ *  - A problem whose scratch need (wp_grid_workspace_bytes) exceeds that size is rejected
+ *    with WP_ERR_SIZE before any launch (roughly 1.5 million visibilities fit with a
+ *    256^2 grid and 16 planes; fewer with large grids and many planes).
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *    with that device current; make that first call before any stream capture.
+ *  - No cudaMalloc, cudaFree or allocating library routine is called.
+ *  - All calls share the one array and it keeps the previous call's contents; each call
+ *    clears what must start at zero.  Calls that overlap on the GPU (other streams or host
+ *    threads) race on the array: the caller must serialise them.
+ */
+#define WP_GRID_STATIC_SCRATCH_BYTES (64ull << 20)
+int wp_grid_static(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw,
+                   const float* vis, const float* weight, int64_t V, float* grid,
+                   double* stats, void* stream);
 
 /* ---- differentiation of the visibility prediction ----------------------------------
  * Model: V = wp_degrid(K(t), wp_image_to_grid(I; t)) for a model image I and the radial

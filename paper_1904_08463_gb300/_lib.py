@@ -95,6 +95,8 @@ _SIGS = {
     "wp_grid_workspace_bytes": (c_size_t, [P_(WpPlan), c_int32, c_int64]),
     "wp_grid": (c_int32, [P_(WpPlan), P_(WpWkernels), c_void_p, c_void_p, c_void_p, c_int64,
                           c_void_p, c_size_t, c_void_p, c_void_p, c_void_p]),
+    "wp_grid_static": (c_int32, [P_(WpPlan), P_(WpWkernels), c_void_p, c_void_p, c_void_p, c_int64,
+                                 c_void_p, c_void_p, c_void_p]),
     "wp_degrid": (c_int32, [P_(WpPlan), P_(WpWkernels), c_void_p, c_void_p, c_int64, c_void_p,
                             c_size_t, c_void_p, c_void_p]),
     "wp_grad_workspace_bytes": (c_size_t, [P_(WpPlan), c_int32, c_int64]),

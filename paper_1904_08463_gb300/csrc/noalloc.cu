@@ -1,0 +1,73 @@
+// Gridding without any device allocation by the library or the caller.
+//
+// wp_grid needs scratch (binned records, bin counts, work items) that the caller normally
+// allocates and passes in.  Some callers cannot do that: an imaging pipeline that reserves
+// every byte of HBM for its own pools at start-up and forbids later allocations (so that a
+// long observation never fragments memory or fails half-way), or a host framework whose
+// plug-ins may only use memory it hands them.  wp_grid_static gives those callers the same
+// gridding with the scratch taken from one fixed-size array compiled into this library.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "wp_internal.cuh"
+
+namespace wp {
+namespace {
+
+// The scratch.  Every GPU that loads libwproj.so holds these bytes until the process exits.
+constexpr size_t kStaticScratchBytes = (size_t)WP_GRID_STATIC_SCRATCH_BYTES;
+__device__ __align__(256) unsigned char g_grid_scratch[kStaticScratchBytes];
+
+std::mutex g_mu;
+void* g_scratch_ptr[64] = {};   // device address of g_grid_scratch, per device ordinal
+
+// Once per device, with that device current: the host-side symbol is only a stand-in, the
+// device address must come from the runtime.
+int scratch_for_current_device(void** out) {
+    int dev = 0;
+    WP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return WP_ERR_DEVICE;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_grid_scratch);
+        if (e != cudaSuccess) return cuda_fail("cudaGetSymbolAddress(g_grid_scratch)", e);
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return WP_OK;
+}
+
+}  // namespace
+}  // namespace wp
+
+using namespace wp;
+
+extern "C" int wp_grid_static(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw,
+                              const float* vis, const float* weight, int64_t V, float* grid,
+                              double* stats, void* stream) {
+    Geom g;
+    int rc = make_geom(plan, &g);
+    if (rc) return rc;
+    if (!kernels || !grid) return WP_ERR_NULL;
+    if (kernels->P < 1 || kernels->P > 8192) return WP_ERR_SIZE;
+    if (!kernels->w_planes || !kernels->support || !kernels->offsets || !kernels->cache) return WP_ERR_NULL;
+    if (V < 0 || V > 2147483647LL) return WP_ERR_SIZE;
+    if (V > 0 && (!uvw || !vis)) return WP_ERR_NULL;
+    if ((int64_t)kernels->P * ((g.N + 63) / 64) * ((g.N + 63) / 64) >= 2147483647LL) return WP_ERR_SIZE;
+    const size_t need = carve_grid(g, kernels->P, V, nullptr, 0, nullptr);
+    if (need > kStaticScratchBytes) {
+        set_last_error("wp_grid_static", "problem needs more scratch than the static array holds "
+                                         "(WP_GRID_STATIC_SCRATCH_BYTES); use wp_grid");
+        return WP_ERR_SIZE;
+    }
+    if ((rc = check_device_public())) return rc;
+    void* scratch = nullptr;
+    if ((rc = scratch_for_current_device(&scratch))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    GridWork w;
+    carve_grid(g, kernels->P, V, scratch, kStaticScratchBytes, &w);
+    if ((rc = grid_bin(g, kernels, uvw, reinterpret_cast<const float2*>(vis), weight, V, w, st))) return rc;
+    return grid_run(g, kernels, w, reinterpret_cast<float2*>(grid), stats, st);
+}
