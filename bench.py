@@ -32,6 +32,11 @@ if ROOT not in sys.path:
 
 import synth  # noqa: E402
 
+# DRAM read + write bytes of one k_resample launch on the 512-plane batch, from the ncu capture
+# summarised in profiles/k_resample_kernel_batch.md (every-8th-plane case, scaled by the ratio
+# of algorithmic bytes).  Reported only while the kernel source is the one it was measured on.
+RESAMPLE_TRAFFIC = {"bytes_per_launch": 5.71e9, "source_sha1": "bc410a2014ed"}
+
 METRIC = "w-kernels/s (Hankel vs 2D-FFT) and Mvis/s gridded, 1 GB300, at stated FP64 error"
 N_IMG, FOV_DEG, R_KG, OS = 4096, 8.0, 4096, 8
 
@@ -44,6 +49,31 @@ def _peaks():
         return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
     except Exception:
         return 6800.0, 1900.0, "fallback"
+
+
+def max_over_ranks(ms: float, device, world: int) -> float:
+    """Replicas only (every rank runs the whole workload on its own GPU): the job's time is the
+    slowest rank's, so value = ranks x work / max time."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def resample_traffic():
+    import hashlib
+
+    path = os.path.join(ROOT, "paper_1904_08463_gb300", "csrc", "kernelgen.cu")
+    try:
+        h = hashlib.sha1(open(path, "rb").read()).hexdigest()[:12]
+    except OSError:
+        return None
+    return RESAMPLE_TRAFFIC["bytes_per_launch"] if h == RESAMPLE_TRAFFIC["source_sha1"] else None
 
 
 class Clocks:
@@ -228,12 +258,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
     clk = clocks.stop()
     clk["note"] = "sampled every 200 ms over the timed steps plus ~1 s of the same steps right after"
-    ms_total = t_start.elapsed_time(t_end)
-    if world > 1:
-        tt = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(tt.item())
-        torch.distributed.barrier()
+    ms_total = max_over_ranks(t_start.elapsed_time(t_end), dev, world)
     ms_step = ms_total / args.steps
     resample_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
     value = world * P / (ms_step * 1e-3)
@@ -255,6 +280,10 @@ def run_gpu(args):
                                     sup_d, off_d, ms_step)
     if args.imaging and rank == 0:
         out["imaging"] = run_imaging(args, dev)
+    if args.batch and rank == 0:
+        out["batched"] = run_batch(args, dev)
+    if args.grad and rank == 0:
+        out["differentiation"] = run_grad(args, dev)
     if rank == 0 and args.cpu_baseline:
         rate, thr, sample = oracle_kernel_rate()
         out["cpu_baseline"] = {"value": rate, "unit": "w-kernels/s", "cores": thr, "kind": "oracle",
@@ -386,7 +415,7 @@ def build_line(args, world, P, kb, ms_step, resample_ms, bytes_cache, alg_bytes,
             "peak_source": f"{src} hbm_gbs (burst copy)",
             "unit": "GB/s",
             "frac": achieved / hbm,
-            "traffic": None,
+            "traffic": resample_traffic(),
             "alg_bytes_per_launch": alg_bytes,
             "launch_ms": resample_ms,
             "share_of_step": resample_ms / ms_step,
@@ -418,8 +447,7 @@ def run_imaging(args, dev):
     vis = vis + torch.complex(noise[:, 0], noise[:, 1]).to(torch.complex64).to(dev)
     V = vis.numel()
     P = args.imaging_planes
-    planes = np.sort(np.abs(d["uvw"][:, 2].astype(np.float64)))
-    planes = np.array([c.mean() for c in np.array_split(planes, P)])
+    planes = wp.plane_values(uvw.reshape(-1), P).cpu().numpy()   # Alg. 2 steps 1-3 on the GPU
     plan = wp.Plan(N, dl, OS, 127, 3, 0.01, 512, "cubic", args.kernelgen)
     taper = torch.tensor(synth.gaussian_taper_samples(N, dl, 512), dtype=torch.float32, device=dev)
     wpl = torch.tensor(planes, dtype=torch.float64, device=dev)
@@ -428,13 +456,25 @@ def run_imaging(args, dev):
     off = torch.tensor(wp.kernel_layout_max(plan, P), dtype=torch.int64, device=dev)
     cache = torch.empty(int(off[-1].item()), dtype=torch.complex64, device=dev)
     sup = torch.empty(P, dtype=torch.int32, device=dev)
-    gws = wp.workspace(wp.grid_workspace_bytes(plan, P, V), dev)
+    gws = wp.workspace(max(wp.grid_workspace_bytes(plan.replace(grid_tile=t), P, V) for t in (32, 64)), dev)
     G = torch.zeros((N, N), dtype=torch.complex64, device=dev)
     img = torch.empty((N, N), dtype=torch.float32, device=dev)
     stats = torch.zeros(2, dtype=torch.float64, device=dev)
     radial = torch.empty((P, plan.geometry().k_out), dtype=torch.complex64, device=dev)
     spl = torch.empty_like(radial)
     wk = wp.WKernels(wpl, sup, off, cache)
+    # the gridder's launch shape (method x tile) is picked by the autotuner on this problem
+    from paper_1904_08463_gb300.autotune import GRID_CHOICES, Autotuner
+
+    wp.hankel_radial(plan, taper, wpl, ws, radial, spl, sup)
+    wp.resample(plan, radial, spl, sup, off, cache)
+    tuner = Autotuner()
+    mt = tuner.choose(Autotuner.key("grid", N, P, 127, V), [list(c) for c in GRID_CHOICES],
+                      lambda c: wp.grid(plan.replace(grid_method=int(c[0]), grid_tile=int(c[1])), wk,
+                                        uvw.reshape(-1), vis, None, G, gws, stats))
+    plan = plan.replace(grid_method=int(mt[0]), grid_tile=int(mt[1]))
+    gws_need = wp.grid_workspace_bytes(plan, P, V)
+    assert gws.numel() >= gws_need
 
     def step(ev=None):
         wp.hankel_radial(plan, taper, wpl, ws, radial, spl, sup)
@@ -487,6 +527,8 @@ def run_imaging(args, dev):
         "gridding_mvis_per_s": V / (grid_ms * 1e-3) / 1e6,
         "supports": {"min": int(sup_h.min()), "max": int(sup_h.max()), "mean": float(sup_h.mean())},
         "taps_per_vis": taps / V,
+        "grid_launch_shape": {"method": ["register tile", "shared-memory tile"][plan.grid_method],
+                              "tile": plan.grid_tile or 64, "chosen_by": "autotuner", "ms": tuner.table},
         "dropped": float(st[1]),
         "roofline": {"kernel": "k_grid", "bound": "alu", "achieved": flops / (grid_ms * 1e-3) / 1e12,
                      "peak": fp32_peak, "unit": "TFLOP/s",
@@ -494,6 +536,105 @@ def run_imaging(args, dev):
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                      "hbm_frac": (V * 24 + 2 * N * N * 8) / (grid_ms * 1e-3) / 1e9 / _peaks()[0]},
     }
+
+
+def run_batch(args, dev):
+    """Independent imaging problems of uneven size (grid 512..4096, 32..512 planes, 1e5..4e6
+    visibilities, per-problem seeds) in one CUDA-graph launch after autotuning, against the
+    same steps issued one problem at a time."""
+    import torch
+
+    import paper_1904_08463_gb300 as wp
+    from paper_1904_08463_gb300.autotune import Autotuner
+    from paper_1904_08463_gb300.batch import BatchImager, Problem
+
+    log("batch: generating problems")
+    specs = synth.batch_problems(n=args.batch_problems)
+    pbs = []
+    for d in specs:
+        R = 512
+        plan = wp.Plan(d["N"], d["cell_size"], OS, d["max_support"], 3, 0.01, R, "cubic", "tf32x3")
+        taper = torch.tensor(synth.gaussian_taper_samples(d["N"], d["cell_size"], R), dtype=torch.float32,
+                             device=dev)
+        vis = synth.predict_torch(d["uvw"], d["sky"], dev)
+        pbs.append(Problem(plan, taper, torch.tensor(d["uvw"], device=dev).reshape(-1), vis, d["P"]))
+    log("batch: set-up and autotuning")
+    tuner = Autotuner()
+    b = BatchImager(pbs, n_streams=4, tuner=tuner)
+    V = b.total_visibilities()
+
+    def timeit(fn, n=3):
+        fn()
+        torch.cuda.synchronize()
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        c.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(c) / n
+
+    log("batch: timing")
+    ms_seq = timeit(b.run_sequential)
+    b.capture()
+    ms_graph = timeit(b.replay)
+    choices = {}
+    for k, v in tuner.table.items():
+        choices[str(v["best"])] = choices.get(str(v["best"]), 0) + 1
+    return {"workload": f"{len(pbs)} independent problems, grids {sorted(set(d['N'] for d in specs))}, "
+                        f"planes {min(d['P'] for d in specs)}..{max(d['P'] for d in specs)}, "
+                        f"{min(len(d['uvw']) for d in specs)}..{max(len(d['uvw']) for d in specs)} visibilities, "
+                        "1% truncation, os 8, R 512",
+            "visibilities": V, "ms_graph": ms_graph, "ms_sequential": ms_seq,
+            "mvis_per_s_graph": V / (ms_graph * 1e-3) / 1e6, "mvis_per_s_sequential": V / (ms_seq * 1e-3) / 1e6,
+            "speedup_graph_vs_sequential": ms_seq / ms_graph, "tuned_choices": choices, "dropped": b.dropped()}
+
+
+def run_grad(args, dev):
+    """Differentiation workload: the full-imaging geometry (4096^2, 512 planes) with 2M
+    visibilities; one forward prediction from a 4096^2 float32 model image and a 512-sample
+    taper, chi-squared loss, and the hand-written backward to both."""
+    import torch
+
+    import paper_1904_08463_gb300 as wp
+    from paper_1904_08463_gb300.autograd import Predictor, chi2
+
+    log("grad: inputs")
+    d = synth.full_imaging(V=2 * 1024 * 1024)
+    N, dl, R, P = d["N"], d["cell_size"], 512, 512
+    uvw = torch.tensor(d["uvw"], device=dev).reshape(-1)
+    vobs = synth.predict_torch(d["uvw"], d["sky"], dev)
+    planes = wp.plane_values(uvw, P)
+    plan0 = wp.Plan(N, dl, OS, 127, 3, 0.01, R, "cubic", "tf32x3")
+    taper0 = torch.tensor(synth.gaussian_taper_samples(N, dl, R), dtype=torch.float32, device=dev)
+    ws = wp.kernelgen_prepare(plan0, P)
+    _, _, sup = wp.hankel_radial(plan0, taper0, planes, ws)
+    pr = Predictor(plan0.replace(trunc_frac=0.0), planes.cpu().numpy(), sup.cpu().tolist(), uvw)
+    image = torch.zeros((N, N), dtype=torch.float32, device=dev, requires_grad=True)
+    taper = taper0.clone().requires_grad_(True)
+
+    def step():
+        image.grad = None
+        taper.grad = None
+        loss = chi2(pr(image, taper), vobs)
+        loss.backward()
+        return loss
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 3
+    a.record()
+    for _ in range(n):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / n
+    V = vobs.numel()
+    return {"workload": f"{V} visibilities, 4096^2 float32 model image, 512 planes, 512-sample taper, chi^2",
+            "ms_per_forward_backward": ms, "mvis_per_s": V / (ms * 1e-3) / 1e6,
+            "grad_image_norm": float(image.grad.norm()), "grad_taper_norm": float(taper.grad.norm())}
 
 
 def run_reference(args):
@@ -536,6 +677,9 @@ def main():
     ap.add_argument("--no-routes", dest="routes", action="store_false",
                     help="skip timing the other kernel-generation routes (FP32 Hankel, 2D FFT)")
     ap.add_argument("--imaging-planes", type=int, default=512)
+    ap.add_argument("--batch", action="store_true", help="also time the batched uneven-problem workload")
+    ap.add_argument("--grad", action="store_true", help="also time forward + backward of the prediction")
+    ap.add_argument("--batch-problems", type=int, default=48)
     ap.add_argument("--hankel-only", action="store_true",
                     help="profiling aid: time only screen + Hankel product + spline (no cache)")
     ap.add_argument("--plane-stride", type=int, default=1,

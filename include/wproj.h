@@ -80,6 +80,10 @@ typedef struct wp_plan {
     int32_t radial_samples; /* R, 8 <= R <= 65536                                      */
     int32_t interp;         /* WP_INTERP_CUBIC | WP_INTERP_LINEAR                      */
     int32_t kernelgen;      /* WP_KG_FP32 | WP_KG_TF32X3                               */
+    int32_t grid_tile;      /* gridding tile side in cells: 0 (default, 64), 32 or 64    */
+    int32_t grid_method;    /* 0 (default): register tile, lanes own grid cells;
+                               1: shared-memory tile, footprint spread over the lanes.
+                               grid_tile and grid_method are tuning choices only       */
 } wp_plan;
 
 /* Derived sizes of a plan (host struct filled by wp_plan_geometry). */
@@ -205,6 +209,20 @@ size_t wp_fft_workspace_bytes(const wp_plan* plan, int32_t P);
 int wp_fft_wkernels(const wp_plan* plan, const float* taper, const double* w_planes, int32_t P,
                     const int32_t* support, const int64_t* offsets, int32_t circular,
                     void* workspace, size_t workspace_bytes, float* cache, void* stream);
+
+/* ---- w-plane values (Alg. 1 / Alg. 2 steps 1-3) ------------------------------------- */
+
+/* Bytes of scratch for wp_plane_values with V visibilities. */
+size_t wp_plane_values_workspace_bytes(int64_t V);
+
+/*
+ * Plane values as the paper's default: sort |w| of all V visibilities, cut the sorted list
+ * into P equal-count chunks (the first V mod P chunks hold one more) and take each chunk's
+ * mean (FP64 sums of the float32 |w|).  Result ascending, ready for wp_wkernels.w_planes.
+ *   uvw [V][3] float; w_planes [P] double out; 1 <= P <= V.
+ */
+int wp_plane_values(const float* uvw, int64_t V, int32_t P, void* workspace,
+                    size_t workspace_bytes, double* w_planes, void* stream);
 
 /* ---- gridding (Alg. 1 / Alg. 2 gridding step) and its adjoint ----------------------- */
 

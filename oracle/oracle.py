@@ -77,6 +77,7 @@ def _load():
             lib.or_grid.argtypes = [L, P, P, P, P, P, P, P, P, P, P, P, P, I, I, P]
             lib.or_degrid.argtypes = [L, P, P, P, P, P, P, P, P, P, P, I, I, P, P]
             lib.or_dft_image.argtypes = [L, P, P, P, I, D, I, P, P, P]
+            lib.or_grid_cells.argtypes = [L, P, P, P, P, P, P, P, P, P, P, I, P, P, I, I, I, P, P, P]
             _lib = lib
     return _lib
 
@@ -279,8 +280,9 @@ def layout(geom: Geometry, support_arr) -> np.ndarray:
     return np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
 
 
-def wkernels(geom: Geometry, taper: np.ndarray, w_planes, supports=None) -> KernelSet:
-    """Hankel w-kernels for every plane: screen, transform, truncate, spline, resample."""
+def wkernels(geom: Geometry, taper: np.ndarray, w_planes, supports=None, with_cache: bool = True) -> KernelSet:
+    """Hankel w-kernels for every plane: screen, transform, truncate, spline, resample.
+    with_cache=False stops after the radial lines and supports (cache left empty)."""
     w_planes = _f64(w_planes)
     radial = np.stack([radial_kernel(geom, taper, w) for w in w_planes])
     if supports is None:
@@ -288,6 +290,8 @@ def wkernels(geom: Geometry, taper: np.ndarray, w_planes, supports=None) -> Kern
     else:
         sup = np.asarray(supports, dtype=np.int32)
     off = layout(geom, sup)
+    if not with_cache:
+        return KernelSet(w_planes, radial, sup, off, np.empty(0, dtype=np.complex128))
     cache = np.empty(int(off[-1]), dtype=np.complex128)
     for p in range(len(w_planes)):
         cache[off[p]:off[p + 1]] = resample(geom, radial[p], int(sup[p])).ravel()
@@ -474,3 +478,24 @@ def predict_vis(geom: Geometry, image: np.ndarray, taper: np.ndarray, w_planes, 
     ks = wkernels(geom, taper, w_planes, supports=supports)
     b = bin_vis(geom, uvw, w_planes, ks.support)
     return degrid(geom, ks, b, image_to_grid(geom, image, taper, weight_sum))
+
+
+def grid_cells(geom: Geometry, ks: KernelSet, bins: Bins, vis: np.ndarray, cells_u, cells_v, wt=None) -> np.ndarray:
+    """Gridded values at the listed cells, taps evaluated from the radial lines directly."""
+    vis = np.ascontiguousarray(vis, dtype=np.complex64).view(np.float32)
+    wtp = None
+    if wt is not None:
+        wt = np.ascontiguousarray(wt, dtype=np.float32)
+        wtp = _p(wt)
+    radial = _c128(ks.radial)
+    m = np.stack([spline_m(r) for r in radial]) if geom.interp == 0 else np.zeros_like(radial)
+    m = _c128(m)
+    cu = np.ascontiguousarray(cells_u, dtype=np.int32)
+    cv = np.ascontiguousarray(cells_v, dtype=np.int32)
+    sup = np.ascontiguousarray(ks.support, dtype=np.int32)
+    out = np.empty(cu.size, dtype=np.complex128)
+    _load().or_grid_cells(bins.plane.size, _p(bins.plane), _p(bins.conj), _p(bins.iu), _p(bins.iv), _p(bins.fu),
+                          _p(bins.fv), _p(bins.drop), _p(vis), wtp, _p(sup), radial.shape[1],
+                          _p(radial.view(np.float64)), _p(m.view(np.float64)), int(geom.interp), geom.oversampling,
+                          cu.size, _p(cu), _p(cv), _p(out.view(np.float64)))
+    return out

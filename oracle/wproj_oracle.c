@@ -411,3 +411,41 @@ void or_dft_image(int64_t V, const float *uvw, const float *vis, const float *wt
         out[q] = s / wsum;
     }
 }
+
+/*
+ * Gridded value at selected cells only (the gridding sum of Alg. 1 / Alg. 2 evaluated cell by
+ * cell, for checks at sizes where the full oracle grid is too slow):
+ *   out[c] = sum over visibilities k whose footprint covers cell c of wt_k V_k K_k(cell),
+ * with the tap K evaluated directly from plane p's radial line (spline or linear, as
+ * or_resample: zero beyond the support radius, conjugated for w < 0).
+ *   radial, spline_m: [P][K] complex lines; cells: (cu[c], cv[c]) grid column / row.
+ */
+void or_grid_cells(int64_t V, const int *plane, const int *conj, const int *iu, const int *iv,
+                   const int *fu, const int *fv, const int *drop, const float *vis, const float *wt,
+                   const int *support, int K, const double *radial, const double *spline_m, int interp,
+                   int os, int ncells, const int *cu, const int *cv, double *out)
+{
+    for (int c = 0; c < ncells; ++c) out[2 * c] = out[2 * c + 1] = 0.0;
+    for (int64_t k = 0; k < V; ++k) {
+        if (drop[k]) continue;
+        int p = plane[k], S = support[p];
+        int64_t lim = (int64_t)os * S;
+        lim = lim * lim;
+        double a = wt ? (double)wt[k] : 1.0;
+        double vr = a * (double)vis[2 * k], vi = a * (double)vis[2 * k + 1];
+        for (int c = 0; c < ncells; ++c) {
+            int jx = cu[c] - (iu[k] - S), jy = cv[c] - (iv[k] - S);
+            if (jx < 0 || jx > 2 * S || jy < 0 || jy > 2 * S) continue;
+            int64_t dx = (int64_t)os * (jx - S) - fu[k];
+            int64_t dy = (int64_t)os * (jy - S) - fv[k];
+            int64_t q = dx * dx + dy * dy;
+            if (q > lim) continue;
+            double kr, ki;
+            spline_eval(K, radial + (int64_t)2 * p * K, spline_m + (int64_t)2 * p * K, 1.0, interp,
+                        sqrt((double)q), &kr, &ki);
+            if (conj[k]) ki = -ki;
+            out[2 * c] += vr * kr - vi * ki;
+            out[2 * c + 1] += vr * ki + vi * kr;
+        }
+    }
+}

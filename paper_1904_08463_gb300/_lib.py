@@ -38,6 +38,8 @@ class WpPlan(ctypes.Structure):
         ("radial_samples", c_int32),
         ("interp", c_int32),
         ("kernelgen", c_int32),
+        ("grid_tile", c_int32),
+        ("grid_method", c_int32),
     ]
 
 
@@ -92,6 +94,8 @@ _SIGS = {
     "wp_fft_workspace_bytes": (c_size_t, [P_(WpPlan), c_int32]),
     "wp_fft_wkernels": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_int32,
                                   c_void_p, c_size_t, c_void_p, c_void_p]),
+    "wp_plane_values_workspace_bytes": (c_size_t, [c_int64]),
+    "wp_plane_values": (c_int32, [c_void_p, c_int64, c_int32, c_void_p, c_size_t, c_void_p, c_void_p]),
     "wp_grid_workspace_bytes": (c_size_t, [P_(WpPlan), c_int32, c_int64]),
     "wp_grid": (c_int32, [P_(WpPlan), P_(WpWkernels), c_void_p, c_void_p, c_void_p, c_int64,
                           c_void_p, c_size_t, c_void_p, c_void_p, c_void_p]),

@@ -52,11 +52,14 @@ class Plan:
     radial_samples: int = 512
     interp: str = "cubic"
     kernelgen: str = "fp32"
+    grid_tile: int = 0          # gridding tile side (0 = default 64; 32 or 64): tuning only
+    grid_method: int = 0        # 0 register tile (default), 1 shared-memory tile: tuning only
 
     def c(self) -> _lib.WpPlan:
         return _lib.WpPlan(self.image_size, self.cell_size, self.oversampling, self.max_support,
                            self.min_support, self.trunc_frac, self.radial_samples,
-                           _lib.INTERP[self.interp], _lib.KERNELGEN[self.kernelgen])
+                           _lib.INTERP[self.interp], _lib.KERNELGEN[self.kernelgen], self.grid_tile,
+                           self.grid_method)
 
     def geometry(self) -> _lib.WpGeometry:
         g = _lib.WpGeometry()
@@ -216,6 +219,17 @@ def fft_wkernels(plan: Plan, taper: torch.Tensor, w_planes, supports, circular: 
         ctypes.byref(plan.c()), _ptr(taper), _ptr(w_planes), P, _ptr(sup), _ptr(off), int(bool(circular)),
         _ptr(ws), ws.numel(), _ptr(cache), _stream(stream)))
     return WKernels(w_planes, sup, off, cache)
+
+
+def plane_values(uvw: torch.Tensor, P: int, stream=None) -> torch.Tensor:
+    """|w|-plane values: means of P equal-count chunks of the sorted |w| (Alg. 2 steps 1-3)."""
+    V = int(uvw.numel() // 3)
+    _need(uvw, torch.float32, "uvw", 3 * V)
+    ws = workspace(int(_lib.load().wp_plane_values_workspace_bytes(V)), uvw.device)
+    out = torch.empty(P, dtype=torch.float64, device=uvw.device)
+    _lib.check("wp_plane_values", _lib.load().wp_plane_values(
+        _ptr(uvw), V, P, _ptr(ws), ws.numel(), _ptr(out), _stream(stream)))
+    return out
 
 
 # ----------------------------------------------------------------------------- gridding

@@ -36,6 +36,8 @@ int make_geom(const wp_plan* plan, Geom* g) {
     if (plan->radial_samples < 8 || plan->radial_samples > 65536) return WP_ERR_PLAN;
     if (plan->interp != WP_INTERP_CUBIC && plan->interp != WP_INTERP_LINEAR) return WP_ERR_PLAN;
     if (plan->kernelgen != WP_KG_FP32 && plan->kernelgen != WP_KG_TF32X3) return WP_ERR_PLAN;
+    if (plan->grid_tile != 0 && plan->grid_tile != 32 && plan->grid_tile != 64) return WP_ERR_PLAN;
+    if (plan->grid_method != 0 && plan->grid_method != 1) return WP_ERR_PLAN;
     g->N = N;
     g->dl = plan->cell_size;
     g->du = 1.0 / ((double)N * plan->cell_size);
@@ -49,6 +51,8 @@ int make_geom(const wp_plan* plan, Geom* g) {
     g->k_out = (int)round_up((int64_t)plan->oversampling * (plan->max_support + 2), 128);
     g->interp = plan->interp;
     g->kernelgen = plan->kernelgen;
+    g->grid_tile = plan->grid_tile ? plan->grid_tile : 64;
+    g->grid_method = plan->grid_method;
     int m = 1;
     while (m < 2 * plan->max_support + 1) m *= 2;
     g->fft_m = m;
@@ -77,7 +81,7 @@ size_t carve_kg(const Geom& g, int P, void* ws, size_t bytes, KgWork* out) {
 size_t carve_grid(const Geom& g, int P, int64_t V, void* ws, size_t bytes, GridWork* out) {
     Carver c(ws, bytes);
     GridWork w;
-    w.T = 64;
+    w.T = g.grid_tile;
     w.ntx = (g.N + w.T - 1) / w.T;
     w.ntiles = w.ntx * w.ntx;
     w.nbins = (int64_t)P * w.ntiles;
@@ -275,6 +279,21 @@ int wp_fft_wkernels(const wp_plan* plan, const float* taper, const double* w_pla
     if ((rc = check_device())) return rc;
     return fft_wkernels(g, taper, w_planes, P, support, offsets, circular, workspace, workspace_bytes,
                         reinterpret_cast<float2*>(cache), (cudaStream_t)stream);
+}
+
+size_t wp_plane_values_workspace_bytes(int64_t V) {
+    if (V < 1 || V > 2147483647LL) return 0;
+    return plane_values_workspace_bytes(V);
+}
+
+int wp_plane_values(const float* uvw, int64_t V, int32_t P, void* workspace, size_t workspace_bytes,
+                    double* w_planes, void* stream) {
+    if (!uvw || !workspace || !w_planes) return WP_ERR_NULL;
+    if (V < 1 || V > 2147483647LL || P < 1 || P > V) return WP_ERR_SIZE;
+    if (!aligned256(workspace) || workspace_bytes < plane_values_workspace_bytes(V)) return WP_ERR_WORKSPACE;
+    int rc = check_device();
+    if (rc) return rc;
+    return plane_values(uvw, V, P, workspace, workspace_bytes, w_planes, (cudaStream_t)stream);
 }
 
 size_t wp_grid_workspace_bytes(const wp_plan* plan, int32_t P, int64_t V) {

@@ -3,14 +3,16 @@
 //
 //   K9  bin      per visibility: nearest |w| plane, conjugation flag (w < 0, Section 4.1),
 //                grid cell + oversampling offset, drop test; all decisions in FP64
-//   --  sort     counting sort by (plane, 64 x 64 centre tile): histogram, exclusive scan,
+//   --  sort     counting sort by (plane, T x T centre tile; T = 64 or 32): histogram, scan,
 //                scatter (uv-sorted binning: consecutive records share a plane and a tile)
 //   --  items    work items (plane, output tile) that some visibility's footprint reaches
 //   K10 grid     persistent blocks pull work items in plane-major order; a block owns one
-//                64 x 64 output tile in registers (warp w owns rows 8w..8w+7, lane l owns
-//                columns l and l+32), streams the visibilities of the neighbouring centre
-//                tiles through shared memory, accumulates tap x visibility with no atomics,
-//                and flushes the tile to the grid once (one float2 atomic per touched cell)
+//                T x T output tile in registers (warp w owns rows (T/8) w .. , lane l owns
+//                columns l, l + 32, ..); each warp walks the binned visibilities of the
+//                neighbouring centre tiles on its own (no block barrier inside an item),
+//                two at a time with all 32 tap loads issued before the FMAs, accumulates
+//                tap x visibility with no atomics, and flushes the tile to the grid once
+//                (one float2 atomic per touched cell)
 //   K11 degrid   one warp per visibility gathers conj(tap) x grid over the footprint and
 //                reduces with shuffles
 #include <cuda_runtime.h>
@@ -21,10 +23,7 @@
 namespace wp {
 
 namespace {
-constexpr int TILE = 64;           // output / centre tile side (cells)
 constexpr int GRID_WARPS = 8;      // warps per gridding block
-constexpr int ROWS_PER_WARP = TILE / GRID_WARPS;
-constexpr int STAGE = 256;         // visibilities staged per shared-memory round
 constexpr int SCAN_PER_BLOCK = 2048;
 }  // namespace
 
@@ -108,7 +107,7 @@ int exclusive_scan_i32(const int* in, int* out, int64_t n, int* tmp, cudaStream_
 __global__ void __launch_bounds__(256) k_bin(int64_t V, const float* __restrict__ uvw, int P,
                                              const double* __restrict__ w_planes,
                                              const int32_t* __restrict__ support, int s_max, int N,
-                                             double du, int os, int ntx, int ntiles,
+                                             double du, int os, int T, int ntx, int ntiles,
                                              const float* __restrict__ weight,
                                              int* __restrict__ key, int4* __restrict__ rec,
                                              int* __restrict__ count, double* __restrict__ red) {
@@ -150,7 +149,7 @@ __global__ void __launch_bounds__(256) k_bin(int64_t V, const float* __restrict_
             int iu = (int)giu, iv = (int)giv;
             int fu = (int)(tu - giu * (double)os);
             int fv = (int)(tv - giv * (double)os);
-            int kk = p * ntiles + (iv / TILE) * ntx + (iu / TILE);
+            int kk = p * ntiles + (iv / T) * ntx + (iu / T);
             key[k] = kk;
             rec[k] = make_int4(iu | (iv << 16), fu | (fv << 8) | (conj << 16), p, (int)k);
             atomicAdd(&count[kk], 1);
@@ -197,7 +196,7 @@ __global__ void __launch_bounds__(256) k_scatter(int64_t V, const int* __restric
 // Work-item flags: item (p, tile) is live if any centre tile within ceil(S_p / T) tiles
 // holds a visibility of plane p (a footprint reaches at most that far).  Bin b's
 // visibilities are [start[b], start[b+1]) of the sorted arrays (start[nbins] = total).
-__global__ void __launch_bounds__(256) k_item_flags(int P, int ntx, int ntiles, int s_max,
+__global__ void __launch_bounds__(256) k_item_flags(int P, int T, int ntx, int ntiles, int s_max,
                                                     const int32_t* __restrict__ support,
                                                     const int* __restrict__ start, int* __restrict__ flags) {
     const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -206,7 +205,7 @@ __global__ void __launch_bounds__(256) k_item_flags(int P, int ntx, int ntiles, 
     int p = (int)(it / ntiles);
     int t = (int)(it - (int64_t)p * ntiles);
     int oy = t / ntx, ox = t - oy * ntx;
-    int D = (min(max(support[p], 1), s_max) + TILE - 1) / TILE;
+    int D = (min(max(support[p], 1), s_max) + T - 1) / T;
     // `start` holds the exclusive scan of the per-bin counts, so a run of bins
     // [a, b] is non-empty iff start[b + 1] > start[a]
     const int* s = start + (int64_t)p * ntiles;
@@ -238,7 +237,7 @@ int grid_bin(const Geom& g, const wp_wkernels* kern, const float* uvw, const flo
         if (smem > 48 * 1024)
             WP_CUDA(cudaFuncSetAttribute(k_bin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_bin<<<blocks, 256, smem, st>>>(V, uvw, P, kern->w_planes, kern->support, g.s_max, g.N, g.du,
-                                         g.os, w.ntx, w.ntiles, weight, w.key, w.rec, w.count, w.red);
+                                         g.os, w.T, w.ntx, w.ntiles, weight, w.key, w.rec, w.count, w.red);
         WP_LAUNCH_CHECK("k_bin");
     }
     int rc = exclusive_scan_i32(w.count, w.count, w.nbins + 1, w.scan_tmp, st);
@@ -255,7 +254,46 @@ int grid_bin(const Geom& g, const wp_wkernels* kern, const float* uvw, const flo
 // =======================================================================================
 // K10: gridding
 // =======================================================================================
-__global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(int N, int os, int s_max, int ntx, int ntiles,
+// One visibility's contribution to the warp's ROWS rows x COLS column groups.
+template <int ROWS, int COLS>
+__device__ __forceinline__ void grid_one(const int4 r4, const float2 vv, const float2* __restrict__ pcache,
+                                         int os, int S, int W, int W2, int R0, int C0,
+                                         float2 (&acc)[ROWS][COLS]) {
+    const int iu = r4.x & 0xffff, iv = (r4.x >> 16) & 0xffff;
+    const int ry0 = iv - S;
+    if (ry0 > R0 + ROWS - 1 || ry0 + 2 * S < R0) return;
+    const int fu = r4.y & 0xff, fv = (r4.y >> 8) & 0xff;
+    const float sgn = (r4.y >> 16) ? -1.0f : 1.0f;
+    const float2* sub = pcache + (int64_t)(fv * os + fu) * W2;
+    int jx[COLS];
+    bool vc[COLS];
+#pragma unroll
+    for (int c = 0; c < COLS; ++c) {
+        jx[c] = C0 + 32 * c - (iu - S);
+        vc[c] = (unsigned)jx[c] <= (unsigned)(2 * S);
+    }
+    float2 tp[ROWS][COLS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {                   // all loads first
+        const int jy = R0 + r - ry0;
+        const bool rv = (unsigned)jy <= (unsigned)(2 * S);
+        const float2* row = sub + jy * W;
+#pragma unroll
+        for (int c = 0; c < COLS; ++c)
+            tp[r][c] = (rv && vc[c]) ? __ldg(row + jx[c]) : make_float2(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+        for (int c = 0; c < COLS; ++c) {
+            const float ti = sgn * tp[r][c].y;
+            acc[r][c].x = fmaf(vv.x, tp[r][c].x, fmaf(-vv.y, ti, acc[r][c].x));
+            acc[r][c].y = fmaf(vv.x, ti, fmaf(vv.y, tp[r][c].x, acc[r][c].y));
+        }
+}
+
+template <int TILE>
+__global__ void __launch_bounds__(GRID_WARPS * 32, 3) k_grid(int N, int os, int s_max, int ntx, int ntiles,
                                                           const int32_t* __restrict__ support,
                                                           const int64_t* __restrict__ offsets,
                                                           const float2* __restrict__ cache,
@@ -264,8 +302,7 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(int N, int os, int s_m
                                                           const float2* __restrict__ svis,
                                                           const int* __restrict__ items,
                                                           int* __restrict__ ctrl, float2* __restrict__ grid) {
-    __shared__ int4 s_rec[STAGE];
-    __shared__ float2 s_vis[STAGE];
+    constexpr int ROWS = TILE / GRID_WARPS, COLS = TILE / 32;
     __shared__ int s_item;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int n_items = ctrl[1];
@@ -284,71 +321,129 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(int N, int os, int s_m
         const int W2 = W * W;
         const int D = (S + TILE - 1) / TILE;
         const float2* pcache = cache + offsets[p];
-        const int R0 = oy * TILE + wid * ROWS_PER_WARP;
+        const int R0 = oy * TILE + wid * ROWS;
         const int C0 = ox * TILE + lane;
-        float2 acc[ROWS_PER_WARP][2];
+        float2 acc[ROWS][COLS];
 #pragma unroll
-        for (int r = 0; r < ROWS_PER_WARP; ++r) {
-            acc[r][0] = make_float2(0.f, 0.f);
-            acc[r][1] = make_float2(0.f, 0.f);
-        }
+        for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+            for (int c = 0; c < COLS; ++c) acc[r][c] = make_float2(0.f, 0.f);
+        // every warp walks the same visibility list independently (records are read by all
+        // lanes at once: one broadcast load each), so no block barrier inside the item
         const int cx_lo = max(0, ox - D), cx_hi = min(ntx - 1, ox + D);
         for (int cy = max(0, oy - D); cy <= min(ntx - 1, oy + D); ++cy) {
             const int kb = p * ntiles + cy * ntx;
             const int beg = start[kb + cx_lo], end = start[kb + cx_hi + 1];
-            for (int c0 = beg; c0 < end; c0 += STAGE) {
-                const int n = min(STAGE, end - c0);
-                for (int q = threadIdx.x; q < n; q += blockDim.x) {
-                    s_rec[q] = srec[c0 + q];
-                    s_vis[q] = svis[c0 + q];
-                }
-                __syncthreads();
-                for (int q = 0; q < n; ++q) {
-                    const int4 r4 = s_rec[q];
-                    const int iu = r4.x & 0xffff, iv = (r4.x >> 16) & 0xffff;
-                    const int ry0 = iv - S;
-                    if (ry0 > R0 + ROWS_PER_WARP - 1 || ry0 + 2 * S < R0) continue;
-                    const int fu = r4.y & 0xff, fv = (r4.y >> 8) & 0xff;
-                    const float sgn = (r4.y >> 16) ? -1.0f : 1.0f;
-                    const float2 vv = s_vis[q];
-                    const float2* sub = pcache + (int64_t)(fv * os + fu) * W2;
-                    const int jx0 = C0 - (iu - S);
-                    const int jx1 = jx0 + 32;
-                    const bool v0 = (unsigned)jx0 <= (unsigned)(2 * S);
-                    const bool v1 = (unsigned)jx1 <= (unsigned)(2 * S);
-#pragma unroll
-                    for (int r = 0; r < ROWS_PER_WARP; ++r) {
-                        const int jy = R0 + r - ry0;
-                        if ((unsigned)jy <= (unsigned)(2 * S)) {
-                            const float2* row = sub + jy * W;
-                            if (v0) {
-                                float2 tp = __ldg(row + jx0);
-                                float ti = sgn * tp.y;
-                                acc[r][0].x = fmaf(vv.x, tp.x, fmaf(-vv.y, ti, acc[r][0].x));
-                                acc[r][0].y = fmaf(vv.x, ti, fmaf(vv.y, tp.x, acc[r][0].y));
-                            }
-                            if (v1) {
-                                float2 tp = __ldg(row + jx1);
-                                float ti = sgn * tp.y;
-                                acc[r][1].x = fmaf(vv.x, tp.x, fmaf(-vv.y, ti, acc[r][1].x));
-                                acc[r][1].y = fmaf(vv.x, ti, fmaf(vv.y, tp.x, acc[r][1].y));
-                            }
-                        }
-                    }
-                }
-                __syncthreads();
+            int q = beg;
+            for (; q + 1 < end; q += 2) {
+                const int4 ra = __ldg(srec + q);
+                const int4 rb = __ldg(srec + q + 1);
+                const float2 va = __ldg(svis + q);
+                const float2 vb = __ldg(svis + q + 1);
+                grid_one<ROWS, COLS>(ra, va, pcache, os, S, W, W2, R0, C0, acc);
+                grid_one<ROWS, COLS>(rb, vb, pcache, os, S, W, W2, R0, C0, acc);
             }
+            if (q < end) grid_one<ROWS, COLS>(__ldg(srec + q), __ldg(svis + q), pcache, os, S, W, W2, R0, C0, acc);
         }
         // flush the tile: one atomic per touched cell
 #pragma unroll
-        for (int r = 0; r < ROWS_PER_WARP; ++r) {
+        for (int r = 0; r < ROWS; ++r) {
             const int row = R0 + r;
             if (row >= N) continue;
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
+            for (int c = 0; c < COLS; ++c) {
                 const int col = C0 + 32 * c;
                 if (col < N && (acc[r][c].x != 0.0f || acc[r][c].y != 0.0f))
                     atomicAdd(grid + (int64_t)row * N + col, acc[r][c]);
+            }
+        }
+    }
+}
+
+// Footprint-major variant: the block's T x T output tile lives in shared memory; each warp
+// takes whole visibilities (round robin over the item's list) and spreads the footprint's
+// intersection with the tile over its 32 lanes as one flat index range, so every lane does
+// a useful tap whatever the support; contributions from different warps meet in shared
+// memory through float atomics, and the tile is flushed once per item.
+template <int TILE>
+__global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_fm(int N, int os, int s_max, int ntx, int ntiles,
+                                                             const int32_t* __restrict__ support,
+                                                             const int64_t* __restrict__ offsets,
+                                                             const float2* __restrict__ cache,
+                                                             const int* __restrict__ start,
+                                                             const int4* __restrict__ srec,
+                                                             const float2* __restrict__ svis,
+                                                             const int* __restrict__ items,
+                                                             int* __restrict__ ctrl, float2* __restrict__ grid) {
+    constexpr int TP = TILE + 1;                  // padded row: row wraps land on other banks
+    __shared__ float tre[TILE * TP];              // real and imaginary parts in separate planes:
+    __shared__ float tim[TILE * TP];              // consecutive lanes hit consecutive banks
+    __shared__ int s_item;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int n_items = ctrl[1];
+    for (int i = threadIdx.x; i < TILE * TP; i += blockDim.x) { tre[i] = 0.0f; tim[i] = 0.0f; }
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&ctrl[0], 1);
+        __syncthreads();
+        const int item_idx = s_item;
+        __syncthreads();
+        if (item_idx >= n_items) break;
+        const int item = items[item_idx];
+        const int p = item / ntiles;
+        const int t = item - p * ntiles;
+        const int oy = t / ntx, ox = t - oy * ntx;
+        const int S = min(max(support[p], 1), s_max);
+        const int W = 2 * S + 1;
+        const int W2 = W * W;
+        const int D = (S + TILE - 1) / TILE;
+        const float2* pcache = cache + offsets[p];
+        const int ty0 = oy * TILE, tx0 = ox * TILE;
+        const int cx_lo = max(0, ox - D), cx_hi = min(ntx - 1, ox + D);
+        int seq = 0;   // position in the item's visibility list (same on every warp)
+        for (int cy = max(0, oy - D); cy <= min(ntx - 1, oy + D); ++cy) {
+            const int kb = p * ntiles + cy * ntx;
+            const int beg = start[kb + cx_lo], end = start[kb + cx_hi + 1];
+            const int first = beg + ((wid - seq) % GRID_WARPS + GRID_WARPS) % GRID_WARPS;
+            seq += end - beg;
+            for (int q = first; q < end; q += GRID_WARPS) {
+                const int4 r4 = __ldg(srec + q);
+                const float2 vv = __ldg(svis + q);
+                const int iu = r4.x & 0xffff, iv = (r4.x >> 16) & 0xffff;
+                // intersection of the footprint [iu-S, iu+S] x [iv-S, iv+S] with the tile
+                const int c0 = max(iu - S, tx0), c1 = min(iu + S, tx0 + TILE - 1);
+                const int r0 = max(iv - S, ty0), r1 = min(iv + S, ty0 + TILE - 1);
+                if (c0 > c1 || r0 > r1) continue;
+                const int w = c1 - c0 + 1, h = r1 - r0 + 1;
+                const int fu = r4.y & 0xff, fv = (r4.y >> 8) & 0xff;
+                const float sgn = (r4.y >> 16) ? -1.0f : 1.0f;
+                const float2* sub = pcache + (int64_t)(fv * os + fu) * W2 + (r0 - (iv - S)) * W + (c0 - (iu - S));
+                const int tbase = (r0 - ty0) * TP + (c0 - tx0);
+                // lane-strided walk over the h x w rectangle, rows followed incrementally
+                const int step_r = 32 / w, step_c = 32 - step_r * w;
+                int row = lane / w, col = lane - (lane / w) * w;
+                for (int i = lane; i < h * w; i += 32) {
+                    const float2 tp = __ldg(sub + row * W + col);
+                    const float ti = sgn * tp.y;
+                    const int cell = tbase + row * TP + col;
+                    atomicAdd(tre + cell, fmaf(vv.x, tp.x, -vv.y * ti));
+                    atomicAdd(tim + cell, fmaf(vv.x, ti, vv.y * tp.x));
+                    col += step_c;
+                    row += step_r;
+                    if (col >= w) { col -= w; ++row; }
+                }
+            }
+        }
+        __syncthreads();
+        // flush the tile (one atomic per touched cell) and clear it for the next item
+        for (int i = threadIdx.x; i < TILE * TILE; i += blockDim.x) {
+            const int ry = i / TILE, rx = i - ry * TILE;
+            const int c = ry * TP + rx;
+            const float2 a = make_float2(tre[c], tim[c]);
+            if (a.x != 0.0f || a.y != 0.0f) {
+                const int gy = ty0 + ry, gx = tx0 + rx;
+                if (gy < N && gx < N) atomicAdd(grid + (int64_t)gy * N + gx, a);
+                tre[c] = 0.0f;
+                tim[c] = 0.0f;
             }
         }
     }
@@ -369,7 +464,7 @@ int grid_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, float2* 
     const int P = kern->P;
     const int64_t n = (int64_t)P * w.ntiles;
     unsigned blocks = (unsigned)((n + 1 + 255) / 256);
-    k_item_flags<<<blocks, 256, 0, st>>>(P, w.ntx, w.ntiles, g.s_max, kern->support, w.count, w.flags);
+    k_item_flags<<<blocks, 256, 0, st>>>(P, w.T, w.ntx, w.ntiles, g.s_max, kern->support, w.count, w.flags);
     WP_LAUNCH_CHECK("k_item_flags");
     // the flag scan reuses the cursor array as output (cursor is no longer needed)
     int rc = exclusive_scan_i32(w.flags, w.cursor, n, w.scan_tmp, st);
@@ -379,11 +474,34 @@ int grid_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, float2* 
     int dev = 0, sms = 0, per_sm = 0;
     WP_CUDA(cudaGetDevice(&dev));
     WP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid, GRID_WARPS * 32, 0));
-    if (per_sm < 1) per_sm = 1;
-    k_grid<<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(g.N, g.os, g.s_max, w.ntx, w.ntiles, kern->support, kern->offsets,
-                                                     reinterpret_cast<const float2*>(kern->cache), w.count,
-                                                     w.srec, w.svis, w.items, w.ctrl, grid);
+    const float2* c2 = reinterpret_cast<const float2*>(kern->cache);
+    if (g.grid_method == 1) {
+        if (w.T == 32) {
+            WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_fm<32>, GRID_WARPS * 32, 0));
+            if (per_sm < 1) per_sm = 1;
+            k_grid_fm<32><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(g.N, g.os, g.s_max, w.ntx, w.ntiles,
+                                                                    kern->support, kern->offsets, c2, w.count,
+                                                                    w.srec, w.svis, w.items, w.ctrl, grid);
+        } else {
+            WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_fm<64>, GRID_WARPS * 32, 0));
+            if (per_sm < 1) per_sm = 1;
+            k_grid_fm<64><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(g.N, g.os, g.s_max, w.ntx, w.ntiles,
+                                                                    kern->support, kern->offsets, c2, w.count,
+                                                                    w.srec, w.svis, w.items, w.ctrl, grid);
+        }
+    } else if (w.T == 32) {
+        WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid<32>, GRID_WARPS * 32, 0));
+        if (per_sm < 1) per_sm = 1;
+        k_grid<32><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(g.N, g.os, g.s_max, w.ntx, w.ntiles, kern->support,
+                                                             kern->offsets, c2, w.count, w.srec, w.svis, w.items,
+                                                             w.ctrl, grid);
+    } else {
+        WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid<64>, GRID_WARPS * 32, 0));
+        if (per_sm < 1) per_sm = 1;
+        k_grid<64><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(g.N, g.os, g.s_max, w.ntx, w.ntiles, kern->support,
+                                                             kern->offsets, c2, w.count, w.srec, w.svis, w.items,
+                                                             w.ctrl, grid);
+    }
     WP_LAUNCH_CHECK("k_grid");
     if (stats) {
         rc = add_stats(stats, w.red, st);

@@ -1,0 +1,65 @@
+// w-plane values (Alg. 1 / Alg. 2 steps 1-3 of the paper): sort the visibilities' |w|,
+// cut the sorted list into P equal-count chunks (the first V mod P chunks one longer) and
+// take each chunk's mean -- the paper's default of average w per plane.  The sort is a
+// radix sort of the float bit patterns (non-negative floats order like their bits); the
+// chunk means are FP64 sums, one block per chunk.
+#include <cuda_runtime.h>
+#include <cub/device/device_radix_sort.cuh>
+
+#include "wp_internal.cuh"
+
+namespace wp {
+
+__global__ void k_abs_w_keys(int64_t V, const float* __restrict__ uvw, unsigned* __restrict__ keys) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < V) keys[k] = __float_as_uint(fabsf(uvw[3 * k + 2]));
+}
+
+__global__ void __launch_bounds__(256) k_chunk_means(int64_t V, int P, const unsigned* __restrict__ sorted,
+                                                     double* __restrict__ out) {
+    __shared__ double red[8];
+    const int c = blockIdx.x;
+    const int64_t q = V / P, r = V % P;
+    const int64_t beg = (int64_t)c * q + (c < r ? c : r);
+    const int64_t n = q + (c < r ? 1 : 0);
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)__uint_as_float(sorted[beg + i]);
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        out[c] = t / (double)n;
+    }
+}
+
+static size_t sort_temp_bytes(int64_t V) {
+    size_t bytes = 0;
+    cub::DeviceRadixSort::SortKeys(nullptr, bytes, (const unsigned*)nullptr, (unsigned*)nullptr, (int)V, 0, 31);
+    return bytes;
+}
+
+size_t plane_values_workspace_bytes(int64_t V) {
+    Carver c(nullptr, 0);
+    c.take<unsigned>((size_t)V);
+    c.take<unsigned>((size_t)V);
+    c.take<char>(sort_temp_bytes(V));
+    return (size_t)round_up((int64_t)c.off, 256);
+}
+
+int plane_values(const float* uvw, int64_t V, int P, void* ws, size_t bytes, double* out, cudaStream_t st) {
+    Carver c(ws, bytes);
+    unsigned* keys = c.take<unsigned>((size_t)V);
+    unsigned* sorted = c.take<unsigned>((size_t)V);
+    size_t tb = sort_temp_bytes(V);
+    void* tmp = c.take<char>(tb);
+    k_abs_w_keys<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(V, uvw, keys);
+    WP_LAUNCH_CHECK("k_abs_w_keys");
+    WP_CUDA(cub::DeviceRadixSort::SortKeys(tmp, tb, keys, sorted, (int)V, 0, 31, st));
+    k_chunk_means<<<P, 256, 0, st>>>(V, P, sorted, out);
+    WP_LAUNCH_CHECK("k_chunk_means");
+    return WP_OK;
+}
+
+}  // namespace wp

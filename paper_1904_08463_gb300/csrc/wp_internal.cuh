@@ -31,7 +31,7 @@ int cuda_fail(const char* where, cudaError_t e);
 // derived geometry of a plan
 // ---------------------------------------------------------------------------------------
 struct Geom {
-    int N, os, s_max, s_min, R, r_pad, k_out, interp, kernelgen, fft_m;
+    int N, os, s_max, s_min, R, r_pad, k_out, interp, kernelgen, fft_m, grid_tile, grid_method;
     double dl, du, r_max, tau;
 };
 
@@ -129,6 +129,10 @@ int fft_wkernels(const Geom& g, const float* taper, const double* w_planes, int 
                  const int64_t* offsets, int circular, void* ws, size_t ws_bytes, float2* cache,
                  cudaStream_t st);
 void release_fft_kernelgen_plans();
+
+// plane values (planes.cu)
+size_t plane_values_workspace_bytes(int64_t V);
+int plane_values(const float* uvw, int64_t V, int P, void* ws, size_t bytes, double* out, cudaStream_t st);
 
 // differentiation (grad.cu)
 size_t grad_extra_ints(int P, int64_t V);

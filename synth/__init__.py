@@ -189,3 +189,26 @@ def full_imaging(V: int = 1 << 23, seed: int = 3, n_sources: int = 200, noise_si
     sky = sources_in_disc(n_sources, np.deg2rad(fov_deg / 2), seed + 1, 1e-3, 1.0, log_uniform=True)
     return dict(N=N, cell_size=dl, uvw=uvw, sky=sky, scale=s, noise_sigma=noise_sigma,
                 noise_seed=seed + 2)
+
+
+def batch_problems(n: int = 48, seed: int = 100, sizes=(512, 1024, 2048, 4096), planes=(32, 512),
+                   vis=(100_000, 4_000_000), fov_deg: float = 8.0, n_sources: int = 20):
+    """Independent imaging problems of uneven size: grid side drawn from `sizes`, plane count
+    log-uniform in `planes`, visibility count log-uniform in `vis`; each generated like the
+    full-imaging workload (64-antenna track at dec -30, uvw scaled to fit the grid) with its
+    own seed.  Returns a list of dicts with N, cell_size, P, max_support, uvw, sky."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        N = int(rng.choice(sizes))
+        P = int(round(np.exp(rng.uniform(np.log(planes[0]), np.log(planes[1])))))
+        V = int(round(np.exp(rng.uniform(np.log(vis[0]), np.log(vis[1])))))
+        s_max = min(127, N // 8 - 1)
+        dl = np.deg2rad(fov_deg) / N
+        du = 1.0 / (N * dl)
+        n_dumps = -(-V // (64 * 63 // 2))
+        uvw = track_uvw(n_dumps=n_dumps, seed=seed + 7 * i + 1, max_vis=V)
+        uvw, s = scale_to_grid(uvw, (N / 2 - (s_max + 2)) * du)
+        sky = sources_in_disc(n_sources, np.deg2rad(fov_deg / 2), seed + 7 * i + 2, 1e-3, 1.0, log_uniform=True)
+        out.append(dict(N=N, cell_size=dl, P=min(P, V), max_support=s_max, uvw=uvw, sky=sky, scale=s))
+    return out

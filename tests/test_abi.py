@@ -37,13 +37,13 @@ def test_plan_geometry():
     L, lib = _lib()
     import numpy as np
 
-    p = L.WpPlan(256, float(np.deg2rad(2.0) / 256), 8, 15, 3, 0.01, 512, 0, 0)
+    p = L.WpPlan(256, float(np.deg2rad(2.0) / 256), 8, 15, 3, 0.01, 512, 0, 0, 0, 0)
     g = L.WpGeometry()
     assert lib.wp_plan_geometry(ctypes.byref(p), ctypes.byref(g)) == 0
     assert g.k_out == 256 and g.r_pad == 512 and g.fft_workspace == 32
     assert g.du == pytest.approx(1.0 / np.deg2rad(2.0), rel=1e-15)
     assert g.r_max == pytest.approx(np.deg2rad(1.0), rel=1e-15)
-    p2 = L.WpPlan(4096, float(np.deg2rad(8.0) / 4096), 8, 127, 7, 0.0, 4096, 0, 1)
+    p2 = L.WpPlan(4096, float(np.deg2rad(8.0) / 4096), 8, 127, 7, 0.0, 4096, 0, 1, 32, 1)
     assert lib.wp_plan_geometry(ctypes.byref(p2), ctypes.byref(g)) == 0
     assert g.k_out == 1152 and g.fft_workspace == 256
 
@@ -52,10 +52,11 @@ def test_plan_geometry():
                                          ("cell_size", 0.01), ("oversampling", 0), ("oversampling", 17),
                                          ("max_support", 0), ("max_support", 200), ("min_support", 16),
                                          ("radial_samples", 4), ("interp", 2), ("kernelgen", 7),
-                                         ("trunc_frac", 1.0)])
+                                         ("trunc_frac", 1.0), ("grid_tile", 48),
+                                         ("grid_method", 2)])
 def test_invalid_plans_rejected(field, value):
     L, lib = _lib()
-    p = L.WpPlan(256, 1e-4, 8, 15, 3, 0.01, 512, 0, 0)
+    p = L.WpPlan(256, 1e-4, 8, 15, 3, 0.01, 512, 0, 0, 0, 0)
     setattr(p, field, value)
     g = L.WpGeometry()
     assert lib.wp_plan_geometry(ctypes.byref(p), ctypes.byref(g)) == -3
@@ -63,7 +64,7 @@ def test_invalid_plans_rejected(field, value):
 
 def test_layout_and_argument_errors():
     L, lib = _lib()
-    p = L.WpPlan(256, 1e-4, 8, 15, 3, 0.01, 512, 0, 0)
+    p = L.WpPlan(256, 1e-4, 8, 15, 3, 0.01, 512, 0, 0, 0, 0)
     sup = (ctypes.c_int32 * 3)(3, 5, 15)
     off = (ctypes.c_int64 * 4)()
     assert lib.wp_kernel_layout(ctypes.byref(p), 3, sup, off) == 0

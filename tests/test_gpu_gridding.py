@@ -17,10 +17,10 @@ def _wp():
     return wp
 
 
-def _setup(N, dl, os_, s_max, R, planes, supports, sigma=0.3):
+def _setup(N, dl, os_, s_max, R, planes, supports, sigma=0.3, grid_tile=0, grid_method=0):
     wp = _wp()
     dev = torch.device("cuda")
-    plan = wp.Plan(N, dl, os_, s_max, 1, 0.0, R, "cubic", "fp32")
+    plan = wp.Plan(N, dl, os_, s_max, 1, 0.0, R, "cubic", "fp32", grid_tile, grid_method)
     g = o.Geometry(N, dl, os_, s_max, 1, 0.0, R)
     taper = synth.gaussian_taper_samples(N, dl, R, sigma)
     tap_d = torch.tensor(taper, dtype=torch.float32, device=dev)
@@ -53,14 +53,17 @@ def test_small_imaging_grid_and_dirty_image():
     assert np.all(img[~o.disc_mask(g)] == 0)
 
 
+@pytest.mark.parametrize("grid_method", [0, 1])
+@pytest.mark.parametrize("grid_tile", [32, 64])
 @pytest.mark.parametrize("V,seed", [(0, 1), (1, 2), (37, 3), (5000, 4)])
-def test_grid_edges_and_conjugation(V, seed):
+def test_grid_edges_and_conjugation(V, seed, grid_tile, grid_method):
     """Empty input, one visibility, ragged counts; visibilities on and past the grid edge
     (dropped), negative w (conjugated kernels), a plane count off every tile size."""
     N, dl = 96, np.deg2rad(3.0) / 96
     planes = np.array([0.0, 40.0, 130.0, 300.0, 800.0])
     sup = np.array([1, 3, 6, 9, 12])
-    wp, dev, plan, g, taper, tap_d, wk, ks = _setup(N, dl, 4, 12, 128, planes, sup)
+    wp, dev, plan, g, taper, tap_d, wk, ks = _setup(N, dl, 4, 12, 128, planes, sup, grid_tile=grid_tile,
+                                                    grid_method=grid_method)
     rng = np.random.default_rng(seed)
     du = g.du
     uvw = np.stack([rng.uniform(-N / 2 - 2, N / 2 + 2, V) * du, rng.uniform(-N / 2 - 2, N / 2 + 2, V) * du,
@@ -124,3 +127,14 @@ def test_dirty_image_and_adjoint_on_synthetic_grids():
         lhs = float(np.sum(ref * Y))
         rhs = float(np.real(np.vdot(Gy, X.astype(np.complex128))))
         assert abs(lhs - rhs) < 1e-4 * abs(lhs) + 1e-6
+
+
+@pytest.mark.parametrize("V,P,seed", [(20000, 16, 1), (1001, 7, 2), (64, 64, 3), (5, 1, 4)])
+def test_plane_values_are_means_of_equal_count_chunks(V, P, seed):
+    """Alg. 2 steps 1-3: sort |w|, P equal-count chunks (first V mod P one longer), means."""
+    wp = _wp()
+    uvw = synth.uniform_disc_uvw(V, 1000.0, 700.0, seed)
+    got = wp.plane_values(torch.tensor(uvw, device="cuda").reshape(-1), P).cpu().numpy()
+    ref = o.mean_w_planes(uvw[:, 2].astype(np.float64), P)
+    assert np.allclose(got, ref, rtol=1e-13, atol=0)
+    assert np.all(np.diff(got) >= 0)

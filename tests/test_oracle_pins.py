@@ -382,3 +382,13 @@ def test_point_source_at_phase_centre_peak_equals_flux():
     # the gridded kernel sums to t(0) = 1 up to the 0.1 % truncation -> peak = flux
     assert img[N // 2, N // 2] == pytest.approx(0.7, rel=3e-3)
     assert img.max() == img[N // 2, N // 2]
+
+
+def test_cellwise_gridding_equals_full_oracle_grid():
+    """The cell-by-cell form (taps evaluated from the radial lines) reproduces the full
+    oracle grid exactly at every sampled cell, conjugated kernels included."""
+    g, tap, ks, b, uvw, vis = _random_problem(1, 400)
+    G = o.grid(g, ks, b, vis)
+    cu = np.arange(5, 60, 2)
+    cv = (cu * 7) % 64
+    assert np.array_equal(o.grid_cells(g, ks, b, vis, cu, cv), G[cv, cu])
