@@ -610,7 +610,11 @@ def run_grad(args, dev):
     ws = wp.kernelgen_prepare(plan0, P)
     _, _, sup = wp.hankel_radial(plan0, taper0, planes, ws)
     pr = Predictor(plan0.replace(trunc_frac=0.0), planes.cpu().numpy(), sup.cpu().tolist(), uvw)
-    image = torch.zeros((N, N), dtype=torch.float32, device=dev, requires_grad=True)
+    # model image: the sky's point sources on their pixels (non-zero, so that the taper enters)
+    img0 = torch.zeros((N, N), dtype=torch.float32)
+    for l_, m_, f_ in zip(d["sky"].l, d["sky"].m, d["sky"].flux):
+        img0[int(round(m_ / dl)) + N // 2, int(round(l_ / dl)) + N // 2] += float(f_)
+    image = img0.to(dev).requires_grad_(True)
     taper = taper0.clone().requires_grad_(True)
 
     def step():

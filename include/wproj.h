@@ -82,8 +82,10 @@ typedef struct wp_plan {
     int32_t kernelgen;      /* WP_KG_FP32 | WP_KG_TF32X3                               */
     int32_t grid_tile;      /* gridding tile side in cells: 0 (default, 64), 32 or 64    */
     int32_t grid_method;    /* 0 (default): register tile, lanes own grid cells;
-                               1: shared-memory tile, footprint spread over the lanes.
-                               grid_tile and grid_method are tuning choices only       */
+                               1: shared-memory tile, footprint spread over the lanes;
+                               2: per-warp shared-memory 32 x 32 tiles, groups of 8 planes
+                               per work item (grid_tile ignored).  grid_tile and
+                               grid_method are tuning choices only: results are the same */
 } wp_plan;
 
 /* Derived sizes of a plan (host struct filled by wp_plan_geometry). */
@@ -164,6 +166,24 @@ int wp_kernelgen_prepare(const wp_plan* plan, int32_t P, void* workspace,
 int wp_hankel_radial(const wp_plan* plan, const float* taper, const double* w_planes,
                      int32_t P, void* workspace, size_t workspace_bytes, float* radial,
                      float* spline_m, int32_t* support, void* stream);
+
+/*
+ * Device-side status of the last kernel-generation call on `workspace` (synchronizes
+ * `stream`): 0, or WP_ERR_TIMEOUT when a bounded wait of the tensor-core transform expired
+ * (its output is then left unwritten, and the CUDA context stays usable).
+ */
+int wp_kernelgen_status(const wp_plan* plan, int32_t P, void* workspace, size_t workspace_bytes,
+                        int32_t* status_host, void* stream);
+
+/*
+ * Self-test of that failure path: runs the tensor-core transform with its tile loads
+ * withheld and a ~10 ms wait budget, so every CTA's first wait expires; writes the
+ * resulting device status to *status_host (expected WP_ERR_TIMEOUT) and synchronizes.
+ * Nothing faults or hangs; `radial` ([P][K_out] complex) is not written.
+ */
+int wp_selftest_bounded_wait(const wp_plan* plan, int32_t P, void* workspace,
+                             size_t workspace_bytes, float* radial, int32_t* status_host,
+                             void* stream);
 
 /*
  * Oversampled kernel cache from the radial lines (Section 4.3.2 and the cache step of

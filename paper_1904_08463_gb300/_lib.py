@@ -87,6 +87,9 @@ _SIGS = {
     "wp_kernelgen_prepare": (c_int32, [P_(WpPlan), c_int32, c_void_p, c_size_t, c_void_p]),
     "wp_hankel_radial": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_int32, c_void_p, c_size_t,
                                    c_void_p, c_void_p, c_void_p, c_void_p]),
+    "wp_kernelgen_status": (c_int32, [P_(WpPlan), c_int32, c_void_p, c_size_t, c_void_p, c_void_p]),
+    "wp_selftest_bounded_wait": (c_int32, [P_(WpPlan), c_int32, c_void_p, c_size_t, c_void_p, c_void_p,
+                                           c_void_p]),
     "wp_resample": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_int32, c_void_p, c_void_p,
                               c_void_p, c_void_p]),
     "wp_make_wkernels": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_int32, c_void_p, c_void_p,

@@ -37,7 +37,7 @@ int make_geom(const wp_plan* plan, Geom* g) {
     if (plan->interp != WP_INTERP_CUBIC && plan->interp != WP_INTERP_LINEAR) return WP_ERR_PLAN;
     if (plan->kernelgen != WP_KG_FP32 && plan->kernelgen != WP_KG_TF32X3) return WP_ERR_PLAN;
     if (plan->grid_tile != 0 && plan->grid_tile != 32 && plan->grid_tile != 64) return WP_ERR_PLAN;
-    if (plan->grid_method != 0 && plan->grid_method != 1) return WP_ERR_PLAN;
+    if (plan->grid_method < 0 || plan->grid_method > 2) return WP_ERR_PLAN;
     g->N = N;
     g->dl = plan->cell_size;
     g->du = 1.0 / ((double)N * plan->cell_size);
@@ -81,7 +81,7 @@ size_t carve_kg(const Geom& g, int P, void* ws, size_t bytes, KgWork* out) {
 size_t carve_grid(const Geom& g, int P, int64_t V, void* ws, size_t bytes, GridWork* out) {
     Carver c(ws, bytes);
     GridWork w;
-    w.T = g.grid_tile;
+    w.T = (g.grid_method == 2) ? 32 : g.grid_tile;    // the warp-private gridder uses 32 x 32 tiles
     w.ntx = (g.N + w.T - 1) / w.T;
     w.ntiles = w.ntx * w.ntx;
     w.nbins = (int64_t)P * w.ntiles;
@@ -198,6 +198,7 @@ size_t wp_kernelgen_workspace_bytes(const wp_plan* plan, int32_t P) {
 
 int wp_kernelgen_prepare(const wp_plan* plan, int32_t P, void* workspace, size_t workspace_bytes,
                          void* stream) {
+    WP_RANGE("wp_kernelgen_prepare");
     Geom g;
     int rc = make_geom(plan, &g);
     if (rc) return rc;
@@ -213,6 +214,7 @@ int wp_kernelgen_prepare(const wp_plan* plan, int32_t P, void* workspace, size_t
 int wp_hankel_radial(const wp_plan* plan, const float* taper, const double* w_planes, int32_t P,
                      void* workspace, size_t workspace_bytes, float* radial, float* spline_m,
                      int32_t* support, void* stream) {
+    WP_RANGE("wp_hankel_radial");
     Geom g;
     int rc = make_geom(plan, &g);
     if (rc) return rc;
@@ -235,8 +237,45 @@ int wp_hankel_radial(const wp_plan* plan, const float* taper, const double* w_pl
                            reinterpret_cast<float2*>(spline_m), support, st);
 }
 
+int wp_kernelgen_status(const wp_plan* plan, int32_t P, void* workspace, size_t workspace_bytes,
+                        int32_t* status_host, void* stream) {
+    Geom g;
+    int rc = make_geom(plan, &g);
+    if (rc) return rc;
+    if (P < 1 || P > 65536) return WP_ERR_SIZE;
+    if (!workspace || !status_host) return WP_ERR_NULL;
+    if (!aligned256(workspace) || workspace_bytes < carve_kg(g, P, nullptr, 0, nullptr)) return WP_ERR_WORKSPACE;
+    KgWork w;
+    carve_kg(g, P, workspace, workspace_bytes, &w);
+    WP_CUDA(cudaMemcpyAsync(status_host, w.status, sizeof(int32_t), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    WP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return WP_OK;
+}
+
+int wp_selftest_bounded_wait(const wp_plan* plan, int32_t P, void* workspace, size_t workspace_bytes,
+                             float* radial, int32_t* status_host, void* stream) {
+    WP_RANGE("wp_selftest_bounded_wait");
+    Geom g;
+    int rc = make_geom(plan, &g);
+    if (rc) return rc;
+    if (P < 1 || P > 65536) return WP_ERR_SIZE;
+    if (!workspace || !radial || !status_host) return WP_ERR_NULL;
+    if (!aligned256(workspace) || workspace_bytes < carve_kg(g, P, nullptr, 0, nullptr)) return WP_ERR_WORKSPACE;
+    if ((rc = check_device())) return rc;
+    KgWork w;
+    carve_kg(g, P, workspace, workspace_bytes, &w);
+    // loads withheld, 2e7-cycle (~10 ms) budget: the first wait of every CTA expires
+    rc = kg_gemm_tf32x3_ex(g, w, P, reinterpret_cast<float2*>(radial), w.status, (cudaStream_t)stream,
+                           20000000LL, 1);
+    if (rc) return rc;
+    WP_CUDA(cudaMemcpyAsync(status_host, w.status, sizeof(int32_t), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    WP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return WP_OK;
+}
+
 int wp_resample(const wp_plan* plan, const float* radial, const float* spline_m, int32_t P,
                 const int32_t* support, const int64_t* offsets, float* cache, void* stream) {
+    WP_RANGE("wp_resample");
     Geom g;
     int rc = make_geom(plan, &g);
     if (rc) return rc;
@@ -253,6 +292,7 @@ int wp_resample(const wp_plan* plan, const float* radial, const float* spline_m,
 int wp_make_wkernels(const wp_plan* plan, const float* taper, const double* w_planes, int32_t P,
                      int32_t* support, const int64_t* offsets, void* workspace, size_t workspace_bytes,
                      float* radial, float* spline_m, float* cache, void* stream) {
+    WP_RANGE("wp_make_wkernels");
     if (!support || !offsets || !cache) return WP_ERR_NULL;
     int rc = wp_hankel_radial(plan, taper, w_planes, P, workspace, workspace_bytes, radial, spline_m,
                               support, stream);
@@ -269,6 +309,7 @@ size_t wp_fft_workspace_bytes(const wp_plan* plan, int32_t P) {
 int wp_fft_wkernels(const wp_plan* plan, const float* taper, const double* w_planes, int32_t P,
                     const int32_t* support, const int64_t* offsets, int32_t circular, void* workspace,
                     size_t workspace_bytes, float* cache, void* stream) {
+    WP_RANGE("wp_fft_wkernels");
     Geom g;
     int rc = make_geom(plan, &g);
     if (rc) return rc;
@@ -288,6 +329,7 @@ size_t wp_plane_values_workspace_bytes(int64_t V) {
 
 int wp_plane_values(const float* uvw, int64_t V, int32_t P, void* workspace, size_t workspace_bytes,
                     double* w_planes, void* stream) {
+    WP_RANGE("wp_plane_values");
     if (!uvw || !workspace || !w_planes) return WP_ERR_NULL;
     if (V < 1 || V > 2147483647LL || P < 1 || P > V) return WP_ERR_SIZE;
     if (!aligned256(workspace) || workspace_bytes < plane_values_workspace_bytes(V)) return WP_ERR_WORKSPACE;
@@ -320,6 +362,7 @@ static int check_grid_args(const wp_plan* plan, const wp_wkernels* k, const floa
 int wp_grid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw, const float* vis,
             const float* weight, int64_t V, void* workspace, size_t workspace_bytes, float* grid,
             double* stats, void* stream) {
+    WP_RANGE("wp_grid");
     Geom g;
     int rc = check_grid_args(plan, kernels, uvw, V, workspace, workspace_bytes, &g);
     if (rc) return rc;
@@ -333,6 +376,7 @@ int wp_grid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw, c
 
 int wp_degrid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw, const float* grid,
               int64_t V, void* workspace, size_t workspace_bytes, float* vis_out, void* stream) {
+    WP_RANGE("wp_degrid");
     Geom g;
     int rc = check_grid_args(plan, kernels, uvw, V, workspace, workspace_bytes, &g);
     if (rc) return rc;
@@ -354,6 +398,7 @@ size_t wp_grad_workspace_bytes(const wp_plan* plan, int32_t P, int64_t V) {
 int wp_grad_radial(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw, const float* grad_vis,
                    const float* grid, int64_t V, void* workspace, size_t workspace_bytes, float* grad_radial,
                    float* grad_spline_m, void* stream) {
+    WP_RANGE("wp_grad_radial");
     Geom g;
     int rc = check_grid_args(plan, kernels, uvw, V, workspace, workspace_bytes, &g);
     if (rc) return rc;
@@ -374,6 +419,7 @@ int wp_grad_radial(const wp_plan* plan, const wp_wkernels* kernels, const float*
 int wp_hankel_adjoint(const wp_plan* plan, const double* w_planes, int32_t P, void* workspace,
                       size_t workspace_bytes, const float* grad_radial, const float* grad_spline_m,
                       float* grad_taper, void* stream) {
+    WP_RANGE("wp_hankel_adjoint");
     Geom g;
     int rc = make_geom(plan, &g);
     if (rc) return rc;
@@ -390,6 +436,7 @@ int wp_hankel_adjoint(const wp_plan* plan, const double* w_planes, int32_t P, vo
 
 int wp_image_adjoint(const wp_plan* plan, const float* taper, const float* image, float* grid_g,
                      double weight_sum, float* grad_image, float* grad_taper, void* stream) {
+    WP_RANGE("wp_image_adjoint");
     Geom g;
     int rc = make_geom(plan, &g);
     if (rc) return rc;
@@ -402,6 +449,7 @@ int wp_image_adjoint(const wp_plan* plan, const float* taper, const float* image
 
 int wp_dirty_image(const wp_plan* plan, const float* taper, float* grid, double weight_sum, float* image,
                    void* stream) {
+    WP_RANGE("wp_dirty_image");
     Geom g;
     int rc = make_geom(plan, &g);
     if (rc) return rc;
@@ -413,6 +461,7 @@ int wp_dirty_image(const wp_plan* plan, const float* taper, float* grid, double 
 
 int wp_image_to_grid(const wp_plan* plan, const float* taper, const float* image, double weight_sum,
                      float* grid, void* stream) {
+    WP_RANGE("wp_image_to_grid");
     Geom g;
     int rc = make_geom(plan, &g);
     if (rc) return rc;

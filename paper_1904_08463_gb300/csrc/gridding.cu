@@ -449,6 +449,128 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_fm(int N, int os, int 
     }
 }
 
+// Warp-private variant (grid_method 2): 32 x 32 output tiles, one shared-memory copy of the
+// tile per warp.  A work item is (group of PG consecutive planes, tile); each warp takes
+// whole visibilities of the item's planes (round robin) and spreads the footprint's
+// intersection with the tile over its lanes as one flat range -- distinct cells per lane, so
+// a plain read-modify-write of the warp's own copy needs no atomics, and a visibility that
+// misses the tile costs one warp a few instructions instead of every warp.  At the end of
+// the item the copies are summed and the tile is flushed with one atomic per touched cell.
+constexpr int WPT = 32;             // tile side of the warp-private variant
+constexpr int WPT_PAD = WPT + 1;    // padded rows (row wraps of a lane range fall on other banks)
+constexpr int PLANE_GROUP = 8;      // planes per work item
+
+__global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_wp(int N, int os, int s_max, int P, int ntx, int ntiles,
+                                                             const int32_t* __restrict__ support,
+                                                             const int64_t* __restrict__ offsets,
+                                                             const float2* __restrict__ cache,
+                                                             const int* __restrict__ start,
+                                                             const int4* __restrict__ srec,
+                                                             const float2* __restrict__ svis,
+                                                             const int* __restrict__ items,
+                                                             int* __restrict__ ctrl, float2* __restrict__ grid) {
+    extern __shared__ float smem[];                      // [GRID_WARPS][2][WPT * WPT_PAD]
+    __shared__ int s_item;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float* myre = smem + wid * 2 * WPT * WPT_PAD;
+    float* myim = myre + WPT * WPT_PAD;
+    for (int i = threadIdx.x; i < GRID_WARPS * 2 * WPT * WPT_PAD; i += blockDim.x) smem[i] = 0.0f;
+    const int n_items = ctrl[1];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&ctrl[0], 1);
+        __syncthreads();
+        const int item_idx = s_item;
+        __syncthreads();
+        if (item_idx >= n_items) break;
+        const int item = items[item_idx];
+        const int grp = item / ntiles;
+        const int t = item - grp * ntiles;
+        const int oy = t / ntx, ox = t - oy * ntx;
+        const int ty0 = oy * WPT, tx0 = ox * WPT;
+        int seq = 0;   // position in the item's visibility list (identical on every warp)
+        for (int p = grp * PLANE_GROUP; p < min(P, (grp + 1) * PLANE_GROUP); ++p) {
+            const int S = min(max(support[p], 1), s_max);
+            const int W = 2 * S + 1, W2 = W * W;
+            const int D = (S + WPT - 1) / WPT;
+            const float2* pcache = cache + offsets[p];
+            const int cx_lo = max(0, ox - D), cx_hi = min(ntx - 1, ox + D);
+            for (int cy = max(0, oy - D); cy <= min(ntx - 1, oy + D); ++cy) {
+                const int kb = p * ntiles + cy * ntx;
+                const int beg = start[kb + cx_lo], end = start[kb + cx_hi + 1];
+                const int first = beg + ((wid - seq) % GRID_WARPS + GRID_WARPS) % GRID_WARPS;
+                seq += end - beg;
+                for (int q = first; q < end; q += GRID_WARPS) {
+                    const int4 r4 = __ldg(srec + q);
+                    const int iu = r4.x & 0xffff, iv = (r4.x >> 16) & 0xffff;
+                    const int c0 = max(iu - S, tx0), c1 = min(iu + S, tx0 + WPT - 1);
+                    const int r0 = max(iv - S, ty0), r1 = min(iv + S, ty0 + WPT - 1);
+                    if (c0 > c1 || r0 > r1) continue;
+                    const float2 vv = __ldg(svis + q);
+                    const int w = c1 - c0 + 1, h = r1 - r0 + 1;
+                    const int fu = r4.y & 0xff, fv = (r4.y >> 8) & 0xff;
+                    const float sgn = (r4.y >> 16) ? -1.0f : 1.0f;
+                    const float2* sub = pcache + (int64_t)(fv * os + fu) * W2 + (r0 - (iv - S)) * W + (c0 - (iu - S));
+                    const int tb = (r0 - ty0) * WPT_PAD + (c0 - tx0);
+                    const int step_r = 32 / w, step_c = 32 - step_r * w;
+                    int row = lane / w, col = lane - (lane / w) * w;
+                    for (int i = lane; i < h * w; i += 32) {
+                        const float2 tp = __ldg(sub + row * W + col);
+                        const float ti = sgn * tp.y;
+                        const int cell = tb + row * WPT_PAD + col;
+                        myre[cell] += fmaf(vv.x, tp.x, -vv.y * ti);
+                        myim[cell] += fmaf(vv.x, ti, vv.y * tp.x);
+                        col += step_c;
+                        row += step_r;
+                        if (col >= w) { col -= w; ++row; }
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        __syncthreads();
+        // sum the warp copies, flush, clear
+        for (int i = threadIdx.x; i < WPT * WPT; i += blockDim.x) {
+            const int ry = i / WPT, rx = i - ry * WPT;
+            const int c = ry * WPT_PAD + rx;
+            float ar = 0.0f, ai = 0.0f;
+#pragma unroll
+            for (int k = 0; k < GRID_WARPS; ++k) {
+                float* b = smem + k * 2 * WPT * WPT_PAD;
+                ar += b[c];
+                ai += b[WPT * WPT_PAD + c];
+                b[c] = 0.0f;
+                b[WPT * WPT_PAD + c] = 0.0f;
+            }
+            if (ar != 0.0f || ai != 0.0f) {
+                const int gy = ty0 + ry, gx = tx0 + rx;
+                if (gy < N && gx < N) atomicAdd(grid + (int64_t)gy * N + gx, make_float2(ar, ai));
+            }
+        }
+    }
+}
+
+// Work-item flags of the warp-private variant: (plane group, tile) is live if any plane of
+// the group has a visibility within its footprint reach of the tile.
+__global__ void __launch_bounds__(256) k_item_flags_grp(int P, int ngrp, int ntx, int ntiles, int s_max,
+                                                        const int32_t* __restrict__ support,
+                                                        const int* __restrict__ start, int* __restrict__ flags) {
+    const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = (int64_t)ngrp * ntiles;
+    if (it >= n) return;
+    const int grp = (int)(it / ntiles);
+    const int t = (int)(it - (int64_t)grp * ntiles);
+    const int oy = t / ntx, ox = t - oy * ntx;
+    int any = 0;
+    for (int p = grp * PLANE_GROUP; p < min(P, (grp + 1) * PLANE_GROUP) && !any; ++p) {
+        const int D = (min(max(support[p], 1), s_max) + WPT - 1) / WPT;
+        const int* s = start + (int64_t)p * ntiles;
+        const int cx_lo = max(0, ox - D), cx_hi = min(ntx - 1, ox + D);
+        for (int cy = max(0, oy - D); cy <= min(ntx - 1, oy + D); ++cy)
+            any |= (s[cy * ntx + cx_hi + 1] > s[cy * ntx + cx_lo]);
+    }
+    flags[it] = any;
+}
+
 __global__ void k_add_stats(double* stats, const double* red) {
     if (threadIdx.x < 2) stats[threadIdx.x] += red[threadIdx.x];
 }
@@ -462,9 +584,13 @@ int add_stats(double* stats, const double* red, cudaStream_t st) {
 int grid_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, float2* grid, double* stats,
              cudaStream_t st) {
     const int P = kern->P;
-    const int64_t n = (int64_t)P * w.ntiles;
+    const int ngrp = (P + PLANE_GROUP - 1) / PLANE_GROUP;
+    const int64_t n = (g.grid_method == 2) ? (int64_t)ngrp * w.ntiles : (int64_t)P * w.ntiles;
     unsigned blocks = (unsigned)((n + 1 + 255) / 256);
-    k_item_flags<<<blocks, 256, 0, st>>>(P, w.T, w.ntx, w.ntiles, g.s_max, kern->support, w.count, w.flags);
+    if (g.grid_method == 2)
+        k_item_flags_grp<<<blocks, 256, 0, st>>>(P, ngrp, w.ntx, w.ntiles, g.s_max, kern->support, w.count, w.flags);
+    else
+        k_item_flags<<<blocks, 256, 0, st>>>(P, w.T, w.ntx, w.ntiles, g.s_max, kern->support, w.count, w.flags);
     WP_LAUNCH_CHECK("k_item_flags");
     // the flag scan reuses the cursor array as output (cursor is no longer needed)
     int rc = exclusive_scan_i32(w.flags, w.cursor, n, w.scan_tmp, st);
@@ -475,7 +601,15 @@ int grid_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, float2* 
     WP_CUDA(cudaGetDevice(&dev));
     WP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const float2* c2 = reinterpret_cast<const float2*>(kern->cache);
-    if (g.grid_method == 1) {
+    if (g.grid_method == 2) {
+        const size_t smem = (size_t)GRID_WARPS * 2 * WPT * WPT_PAD * sizeof(float);
+        WP_CUDA(cudaFuncSetAttribute(k_grid_wp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_wp, GRID_WARPS * 32, smem));
+        if (per_sm < 1) per_sm = 1;
+        k_grid_wp<<<sms * per_sm, GRID_WARPS * 32, smem, st>>>(g.N, g.os, g.s_max, P, w.ntx, w.ntiles, kern->support,
+                                                               kern->offsets, c2, w.count, w.srec, w.svis, w.items,
+                                                               w.ctrl, grid);
+    } else if (g.grid_method == 1) {
         if (w.T == 32) {
             WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_fm<32>, GRID_WARPS * 32, 0));
             if (per_sm < 1) per_sm = 1;

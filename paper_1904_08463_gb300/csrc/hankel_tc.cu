@@ -21,6 +21,7 @@
 //                   along the radial index)
 // Every mbarrier wait is bounded by a clock budget; on expiry the kernel records
 // WP_ERR_TIMEOUT in `status`, stops issuing, drains what it issued, frees TMEM and returns.
+// `withhold_loads` (self-test only) keeps the producer idle so that the first wait expires.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -41,7 +42,7 @@ constexpr int STAGE_BYTES = 4 * TILE_BYTES;          // A_hi, A_lo, B_hi, B_lo
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr int TMEM_COLS = 2 * BN;                   // two accumulator buffers
 constexpr int GROUP = 2;                             // K-slices per TMEM partial sum
-constexpr long long WAIT_BUDGET = 4000000000LL;      // ~2 s of SM clock per wait
+constexpr long long WAIT_BUDGET = 4000000000LL;      // ~2 s of SM clock per wait (default)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -67,11 +68,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: true when the phase with `parity` completed, false after the budget.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status) {
+// Bounded wait: true when the phase with `parity` completed, false after the budget
+// (SM clock cycles), with WP_ERR_TIMEOUT recorded in `status`.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, long long budget) {
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > WAIT_BUDGET) {
+        if (clock64() - t0 > budget) {
             atomicExch(status, WP_ERR_TIMEOUT);
             return false;
         }
@@ -160,7 +162,8 @@ __global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant_
                                                           const __grid_constant__ CUtensorMap map_b_lo,
                                                           int M, int K, int k_split, int P,
                                                           float2* __restrict__ radial, int use_atomic,
-                                                          int* __restrict__ status) {
+                                                          int* __restrict__ status, long long budget,
+                                                          int withhold_loads) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -205,13 +208,13 @@ __global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant_
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        if (lane == 0) {
+        if (lane == 0 && !withhold_loads) {
             // ---------------- TMA producer ----------------
             int issued = 0;
             bool ok = true;
             for (int kb = 0; kb < nkb; ++kb) {
                 const int s = kb % STAGES;
-                if (kb >= STAGES) ok = mbar_wait(bar_empty0 + 8 * s, ((kb / STAGES) - 1) & 1, status);
+                if (kb >= STAGES) ok = mbar_wait(bar_empty0 + 8 * s, ((kb / STAGES) - 1) & 1, status, budget);
                 if (!ok) break;
                 const uint32_t st = base + s * STAGE_BYTES;
                 const uint32_t fb = bar_full0 + 8 * s;
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant_
             if (!ok) {
                 // every issued slice must land before the CTA may exit
                 for (int kb = max(0, issued - STAGES); kb < issued; ++kb)
-                    mbar_wait(bar_full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, status);
+                    mbar_wait(bar_full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, status, budget);
             }
         }
     } else if (warp == 1) {
@@ -236,14 +239,14 @@ __global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant_
             bool ok = true;
             for (int g = 0; g < ngroups && ok; ++g) {
                 const int b = g & 1;
-                if (g >= 2) ok = mbar_wait(bar_acce0 + 8 * b, ((g >> 1) - 1) & 1, status);
+                if (g >= 2) ok = mbar_wait(bar_acce0 + 8 * b, ((g >> 1) - 1) & 1, status, budget);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t dacc = tmem + (uint32_t)(b * BN);
                 const int kb_end = min(nkb, (g + 1) * GROUP);
                 for (int kb = g * GROUP; kb < kb_end; ++kb) {
                     const int s = kb % STAGES;
-                    if (!mbar_wait(bar_full0 + 8 * s, (kb / STAGES) & 1, status)) { ok = false; break; }
+                    if (!mbar_wait(bar_full0 + 8 * s, (kb / STAGES) & 1, status, budget)) { ok = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t st = base + s * STAGE_BYTES;
                     const uint64_t a_hi = smem_desc_sw128(st + 0 * TILE_BYTES);
@@ -274,7 +277,7 @@ __global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant_
         for (int g = 0; g < ngroups; ++g) {
             const int b = g & 1;
             // warp-uniform decision: every lane polls, the warp proceeds only if all saw it
-            if (!__all_sync(0xffffffffu, mbar_wait(bar_accf0 + 8 * b, (g >> 1) & 1, status))) { ok = false; break; }
+            if (!__all_sync(0xffffffffu, mbar_wait(bar_accf0 + 8 * b, (g >> 1) & 1, status, budget))) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
 #pragma unroll
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant_
     }
     __syncwarp();
     // no MMA may still write TMEM when it is freed
-    if (warp == 1) mbar_wait(bar_done, 0, status);
+    if (warp == 1) mbar_wait(bar_done, 0, status, budget);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 1) {
@@ -352,7 +355,8 @@ int make_map(CUtensorMap* map, const float* ptr, int rows, int cols) {
 
 }  // namespace tc
 
-int kg_gemm_tf32x3(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st) {
+int kg_gemm_tf32x3_ex(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st,
+                      long long budget, int withhold_loads) {
     using namespace tc;
     const int M = g.k_out, N = 2 * p_pad(P), K = g.r_pad;
     if (M % BM || N % BN || K % BK) {
@@ -377,9 +381,13 @@ int kg_gemm_tf32x3(const Geom& g, const KgWork& w, int P, float2* radial, int* s
     WP_CUDA(attr_err);
     dim3 grid(N / BN, M / BM, split);
     k_hankel_tf32x3<<<grid, 192, SMEM_BYTES, st>>>(ma_hi, ma_lo, mb_hi, mb_lo, M, K, split, P, radial,
-                                                   split > 1, status);
+                                                   split > 1, status, budget, withhold_loads);
     WP_LAUNCH_CHECK("k_hankel_tf32x3");
     return WP_OK;
+}
+
+int kg_gemm_tf32x3(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st) {
+    return kg_gemm_tf32x3_ex(g, w, P, radial, status, st, tc::WAIT_BUDGET, 0);
 }
 
 }  // namespace wp

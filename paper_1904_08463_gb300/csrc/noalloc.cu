@@ -47,6 +47,7 @@ using namespace wp;
 extern "C" int wp_grid_static(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw,
                               const float* vis, const float* weight, int64_t V, float* grid,
                               double* stats, void* stream) {
+    WP_RANGE("wp_grid_static");
     Geom g;
     int rc = make_geom(plan, &g);
     if (rc) return rc;

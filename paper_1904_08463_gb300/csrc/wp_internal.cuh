@@ -5,9 +5,19 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/wproj.h"
 
 namespace wp {
+
+// NVTX range around each C-ABI call (free unless a profiler is attached), so that tools can
+// attribute kernels to the library call that launched them.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+#define WP_RANGE(name) ::wp::NvtxRange wp_nvtx_range_(name)
 
 // ---------------------------------------------------------------------------------------
 // error reporting
@@ -103,6 +113,8 @@ int kg_screen(const Geom& g, const KgWork& w, const float* taper, const double* 
 int kg_gemm_fp32(const Geom& g, const KgWork& w, int P, float2* radial, cudaStream_t st);
 int kg_gemm_tf32x3(const Geom& g, const KgWork& w, int P, float2* radial, int* status,
                    cudaStream_t st);
+int kg_gemm_tf32x3_ex(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st,
+                      long long budget, int withhold_loads);
 int kg_trunc_spline(const Geom& g, const KgWork& w, int P, const float2* radial, float2* spline_m,
                     int32_t* support, cudaStream_t st);
 int kg_resample(const Geom& g, int P, const float2* radial, const float2* spline_m,
