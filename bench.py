@@ -216,7 +216,7 @@ def run_gpu(args):
     cplan = plan.c()
     import ctypes
 
-    def step(ev=None):
+    def step(ev=None, cache_ptr=None):
         _lib.check("wp_hankel_radial", lib.wp_hankel_radial(
             ctypes.byref(cplan), ctypes.c_void_p(taper_d.data_ptr()), ctypes.c_void_p(wpl_d.data_ptr()), P,
             ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(radial.data_ptr()),
@@ -230,7 +230,8 @@ def run_gpu(args):
         _lib.check("wp_resample", lib.wp_resample(
             ctypes.byref(cplan), ctypes.c_void_p(radial.data_ptr()), ctypes.c_void_p(spline_m.data_ptr()), P,
             ctypes.c_void_p(sup_d.data_ptr()), ctypes.c_void_p(off_d.data_ptr()),
-            ctypes.c_void_p(cache.data_ptr()), ctypes.c_void_p(stream.cuda_stream)))
+            ctypes.c_void_p(cache_ptr if cache_ptr is not None else cache.data_ptr()),
+            ctypes.c_void_p(stream.cuda_stream)))
         if ev is not None:
             ev[1].record(stream)
 
@@ -366,18 +367,36 @@ def measure_e2e(args, world, P, kb, sup_host, off_host, cache, taper_d, wpl_d, s
         step()
         pin_cache.copy_(cache, non_blocking=True)
 
-    e2e_step()
-    torch.cuda.synchronize()
+    def direct_step():
+        # same C-ABI calls, the cache written by the resample kernel straight into the pinned
+        # host buffer across the CPU-GPU link (no separate device-to-host copy)
+        taper_d.copy_(h_taper, non_blocking=True)
+        wpl_d.copy_(h_wpl, non_blocking=True)
+        sup_d.copy_(h_sup, non_blocking=True)
+        off_d.copy_(h_off, non_blocking=True)
+        step(cache_ptr=pin_cache.data_ptr())
+
     n_e2e = max(2, min(args.steps, 5))
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(n_e2e):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / n_e2e
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_e2e):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n_e2e
+
+    ms_copy = timed(e2e_step)
+    ms_direct = timed(direct_step)
+    e2e_ms = min(ms_copy, ms_direct)
     return {"value": world * P / (e2e_ms * 1e-3), "unit": "w-kernels/s", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+            "method": "cache written directly into pinned host memory" if ms_direct <= ms_copy
+                      else "device cache + cudaMemcpyAsync to pinned host memory",
+            "ms_copy": ms_copy, "ms_direct": ms_direct}
 
 
 def build_line(args, world, P, kb, ms_step, resample_ms, bytes_cache, alg_bytes, hbm, src, achieved, e2e, clk):

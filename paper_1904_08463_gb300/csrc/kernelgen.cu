@@ -367,12 +367,12 @@ int kg_trunc_spline(const Geom& g, const KgWork& w, int P, const float2* radial,
 // warp covers one contiguous run (ascending or descending) of the cache.
 //
 // Tap values: the plane's line (value + spline second derivative, 16 B per sample) sits
-// in shared memory with a one-slot skew every 8 samples (neighbouring taps are up to os
-// samples apart on the line; the skew spreads them over the banks).  The radius test
+// in shared memory with an XOR swizzle of the slot within each group of 8 (neighbouring
+// taps are up to os samples apart on the line; the swizzle spreads them over the banks).  The radius test
 // q = dx^2 + dy^2 <= (os S)^2 is an exact integer test; x = sqrt(q) only picks the spline
 // interval and its weights, which are continuous across interval ends.
 // =======================================================================================
-__device__ __forceinline__ int skew(int k) { return k + (k >> 3); }
+__device__ __forceinline__ int skew(int k) { return k ^ ((k >> 3) & 7); }
 
 template <bool CUBIC>
 __device__ __forceinline__ float2 resample_tap(const float4* __restrict__ line, int dx, int dy, int lim2) {
@@ -441,16 +441,14 @@ __global__ void __launch_bounds__(256) k_resample(int K, int os, int s_max, int 
         if (my) { __stcs(d01 + i, zero); if (mx) __stcs(d11 + i, zero); }
     }
     __syncthreads();
-    const float inv_w = 1.0f / (float)W;
     const int lim2 = lim * lim;
     const int dy0 = -os * S - fv;   // os (jy - S) - fv at jy = 0
     const int dx0 = -os * S - fu;   // os (jx - S) - fu at jx = 0
     const int m1 = 2 * S + 1;       // mirror: j -> 2S + 1 - j
+    // thread's tap t = threadIdx.x + i * blockDim.x, followed as (jy, jx) without division
+    const int step_r = (int)blockDim.x / W, step_c = (int)blockDim.x - step_r * W;
+    int jy = (int)threadIdx.x / W, jx = (int)threadIdx.x - jy * W;
     for (int t = threadIdx.x; t < W2; t += blockDim.x) {
-        int jy = (int)(((float)t + 0.5f) * inv_w);
-        jy -= (jy * W > t);                              // the estimate is off by at most one
-        jy += ((jy + 1) * W <= t);
-        const int jx = t - jy * W;
         const float2 v = resample_tap<CUBIC>(line, dx0 + os * jx, dy0 + os * jy, lim2);
         __stcs(d00 + t, v);
         const bool xin = mx && jx > 0;                   // pre-image of column 2S+1-jx exists
@@ -458,6 +456,9 @@ __global__ void __launch_bounds__(256) k_resample(int K, int os, int s_max, int 
         if (xin) __stcs(d10 + (jy * W + (m1 - jx)), v);
         if (yin) __stcs(d01 + ((m1 - jy) * W + jx), v);
         if (xin && yin) __stcs(d11 + ((m1 - jy) * W + (m1 - jx)), v);
+        jx += step_c;
+        jy += step_r;
+        if (jx >= W) { jx -= W; ++jy; }
     }
 }
 
@@ -465,7 +466,7 @@ int kg_resample(const Geom& g, int P, const float2* radial, const float2* spline
                 const int32_t* support, const int64_t* offsets, float2* cache, cudaStream_t st) {
     int n_max = g.os * g.s_max + 2;
     if (n_max > g.k_out) n_max = g.k_out;
-    size_t smem = (size_t)(n_max + (n_max >> 3) + 1) * sizeof(float4);
+    size_t smem = (size_t)round_up(n_max, 8) * sizeof(float4);
     const int h = g.os / 2;
     const int nrep = (h + 1) * (h + 1);
     const int n_items = P * nrep;
