@@ -192,8 +192,7 @@ int wp_selftest_bounded_wait(const wp_plan* plan, int32_t P, void* workspace,
  * x > os S (the truncated line rotated about rho = 0 has circular support).
  *   radial, spline_m  as written by wp_hankel_radial (spline_m unused for linear)
  *   support [P] int32 (values outside [1, S_max] are clamped), offsets [P+1] int64 (device),
- *   cache out, 8-byte aligned (WP_ERR_SIZE otherwise); any memory the device can write,
- *   e.g. pinned host memory (the kernel then writes across the CPU-GPU link).
+ *   cache out (device memory), 8-byte aligned (WP_ERR_SIZE otherwise).
  */
 int wp_resample(const wp_plan* plan, const float* radial, const float* spline_m, int32_t P,
                 const int32_t* support, const int64_t* offsets, float* cache, void* stream);

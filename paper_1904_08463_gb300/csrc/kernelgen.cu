@@ -354,23 +354,28 @@ int kg_trunc_spline(const Geom& g, const KgWork& w, int P, const float2* radial,
 //
 // Every tap of every sub-kernel samples one radially symmetric 2D function on the fine
 // grid (spacing du/os): tap (jx, jy) of sub-kernel (fu, fv) sits at fine offset
-// (os (jx - S) - fu, os (jy - S) - fv).  Mirroring x maps sub-kernel fu > 0 onto os - fu
-// with jx -> 2S + 1 - jx (fu = 0 maps onto itself); y likewise.  So only the sub-kernels
-// with fu, fv <= os/2 are evaluated -- (os/2 + 1)^2 of os^2 -- and each evaluated tap is
-// stored to up to four sub-kernels straight from registers.  The column / row of a
-// mirrored sub-kernel that has no pre-image (jx = 0 for fu > 0) lies beyond the support
-// radius and is written as zeros.
+// (dx, dy) = (os (jx - S) - fu, os (jy - S) - fv) and its value depends only on
+// q = dx^2 + dy^2.  Negating dx maps sub-kernel fu onto fu' = (os - fu) mod os:
+//   fu = 0    jx -> 2S - jx        (onto itself)
+//   fu > 0    jx -> 2S + 1 - jx    (onto fu'; fu' = fu when 2 fu = os)
+// and column jx = 0 of a sub-kernel with fu > 0 lies beyond the support radius
+// (|dx| > os S): it is zero, and it is the image of column 0 of fu.  Likewise for y.
 //
-// One block per (plane, representative), issued from the last plane backwards (supports
-// grow with |w|: the largest blocks start first).  Consecutive threads take consecutive
-// taps of the flattened (2S+1)^2 representative, so each of the (up to) four stores of a
-// warp covers one contiguous run (ascending or descending) of the cache.
+// One block per (plane, representative fu, fv <= os/2) evaluates each axis only over the
+// part its mirror does not cover -- [0, S] when the sub-kernel is its own mirror
+// (fu = 0 or 2 fu = os), [0, 2S] otherwise -- and stores every evaluated tap to four cache
+// entries (neither, x, y, both mirrored); entries that coincide (centre lines, the zero
+// line of 2 fu = os) receive the same bits twice, since the value is a function of q.
+// For os = 8 that is (8S + 5)^2 evaluations for 64 (2S + 1)^2 cache entries.  Blocks are
+// issued from the last plane backwards (supports grow with |w|: the largest blocks start
+// first); consecutive threads take consecutive taps of the flattened evaluation domain, so
+// each of the four stores of a warp covers contiguous runs of the cache.
 //
 // Tap values: the plane's line (value + spline second derivative, 16 B per sample) sits
 // in shared memory with an XOR swizzle of the slot within each group of 8 (neighbouring
-// taps are up to os samples apart on the line; the swizzle spreads them over the banks).  The radius test
-// q = dx^2 + dy^2 <= (os S)^2 is an exact integer test; x = sqrt(q) only picks the spline
-// interval and its weights, which are continuous across interval ends.
+// taps are up to os samples apart on the line; the swizzle spreads them over the banks).
+// The radius test q <= (os S)^2 is an exact integer test; x = sqrt(q) only picks the
+// spline interval and its weights, which are continuous across interval ends.
 // =======================================================================================
 __device__ __forceinline__ int skew(int k) { return k ^ ((k >> 3) & 7); }
 
@@ -380,7 +385,7 @@ __device__ __forceinline__ float2 resample_tap(const float4* __restrict__ line, 
     float2 out = make_float2(0.0f, 0.0f);
     if (q <= lim2) {
         const float qf = (float)q;
-        const float x = (q > 0) ? qf * rsqrtf(qf) : 0.0f;
+        const float x = qf * rsqrtf(fmaxf(qf, 1.0f));   // q = 0 gives 0, else sqrt(q)
         // round(x - 1/2) through the float mantissa (1.5 * 2^23): the interval index
         const float tt = (x - 0.5f) + 12582912.0f;
         const int k = __float_as_int(tt) - 0x4B400000;
@@ -400,14 +405,40 @@ __device__ __forceinline__ float2 resample_tap(const float4* __restrict__ line, 
     return out;
 }
 
+// Bulk (TMA) store from shared memory: a byte range, 16-byte aligned on both sides and a
+// multiple of 16 bytes long, written by the copy engine in whole cache lines.
+__device__ __forceinline__ void bulk_store(float2* gdst, uint32_t saddr, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                 ::"l"(gdst), "r"(saddr), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ int parity8(const float2* g) { return (int)(((uintptr_t)g >> 3) & 1); }
+
+constexpr int RS_THREADS = 384;
+
+// Staged output: every chunk of whole evaluated rows [r0, r1) lands in at most four contiguous
+// cache ranges -- rows [r0, r1) of the sub-kernel itself (F) and of its x-mirror (X), the
+// mirrored rows of the y-mirror (Y) and of the xy-mirror (XY); when the sub-kernel is its own
+// x-mirror, X and XY fold into F and Y.  Each range is assembled in shared memory, placed so
+// that shared and global addresses agree modulo 16 bytes, and written by the copy engine
+// (cp.async.bulk) in whole cache lines; an odd head / tail element goes through a plain store.
+// Plain warp stores of these ranges would start 8 bytes off the 16-byte grid for every other
+// sub-kernel and row, and run in reverse for the mirrors, which costs about a third of the
+// write bandwidth.  Two buffer sets alternate with one barrier per chunk: before it, the
+// threads that issued the copies of chunk c - 1 wait until those have read their set, which
+// chunk c + 1 overwrites.
 template <bool CUBIC>
-__global__ void __launch_bounds__(256) k_resample(int K, int os, int s_max, int nrep, int n_items,
-                                                  const float2* __restrict__ radial,
-                                                  const float2* __restrict__ spline_m,
-                                                  const int32_t* __restrict__ support,
-                                                  const int64_t* __restrict__ offsets,
-                                                  float2* __restrict__ cache) {
-    extern __shared__ float4 line[];   // skew(n_used) entries {y.re, y.im, m.re, m.im}
+__global__ void __launch_bounds__(RS_THREADS) k_resample(int K, int os, int s_max, int nrep, int n_items,
+                                                         int n_line, int slot,
+                                                         const float2* __restrict__ radial,
+                                                         const float2* __restrict__ spline_m,
+                                                         const int32_t* __restrict__ support,
+                                                         const int64_t* __restrict__ offsets,
+                                                         float2* __restrict__ cache) {
+    extern __shared__ float4 line[];   // skew(n_used) entries {y.re, y.im, m.re, m.im}, then
+                                       // 2 buffer sets x 4 regions x slot float2
+    float2* const stage = reinterpret_cast<float2*>(line + n_line);
+    const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(stage);
     const int item = n_items - 1 - (int)blockIdx.x;
     const int p = item / nrep;
     const int rep = item - p * nrep;
@@ -425,62 +456,122 @@ __global__ void __launch_bounds__(256) k_resample(int K, int os, int s_max, int 
         float2 b = CUBIC ? ml[k] : make_float2(0.0f, 0.0f);
         line[skew(k)] = make_float4(a.x, a.y, b.x, b.y);
     }
-    // mirror images of this representative (a mirror of 0, or one landing on itself, adds
-    // nothing): x -> os - fu, y -> os - fv
-    const bool mx = (fu != 0) && (os - fu != fu);
-    const bool my = (fv != 0) && (os - fv != fv);
+    // per axis: mirror sub-kernel, evaluated extent, mirror centre
+    const int fu2 = fu ? os - fu : 0, fv2 = fv ? os - fv : 0;
+    const bool xself = (fu2 == fu);
+    const int nx = xself ? S + 1 : W, ny = (fv2 == fv) ? S + 1 : W;
+    const int cx = fu ? W : W - 1, cy = fv ? W : W - 1;   // j -> c - j (j = 0 with f > 0: -> 0)
     float2* const base = cache + offsets[p];
     float2* const d00 = base + (int64_t)(fv * os + fu) * W2;
-    float2* const d10 = base + (int64_t)(fv * os + (os - fu)) * W2;          // x-mirrored
-    float2* const d01 = base + (int64_t)((os - fv) * os + fu) * W2;          // y-mirrored
-    float2* const d11 = base + (int64_t)((os - fv) * os + (os - fu)) * W2;   // both
+    float2* const d10 = base + (int64_t)(fv * os + fu2) * W2;    // x-mirrored
+    float2* const d01 = base + (int64_t)(fv2 * os + fu) * W2;    // y-mirrored
+    float2* const d11 = base + (int64_t)(fv2 * os + fu2) * W2;   // both
     const float2 zero = make_float2(0.0f, 0.0f);
-    // zero column / row of mirrored sub-kernels
-    for (int i = threadIdx.x; i < W; i += blockDim.x) {
-        if (mx) { __stcs(d10 + (int64_t)i * W, zero); if (my) __stcs(d11 + (int64_t)i * W, zero); }
-        if (my) { __stcs(d01 + i, zero); if (mx) __stcs(d11 + i, zero); }
-    }
-    __syncthreads();
+    if (fv2 != fv)   // row 0 of the y-mirrored sub-kernels has no pre-image: zero
+        for (int i = threadIdx.x; i < W; i += blockDim.x) {
+            __stcs(d01 + i, zero);
+            if (!xself) __stcs(d11 + i, zero);
+        }
     const int lim2 = lim * lim;
     const int dy0 = -os * S - fv;   // os (jy - S) - fv at jy = 0
     const int dx0 = -os * S - fu;   // os (jx - S) - fu at jx = 0
-    const int m1 = 2 * S + 1;       // mirror: j -> 2S + 1 - j
-    // thread's tap t = threadIdx.x + i * blockDim.x, followed as (jy, jx) without division
-    const int step_r = (int)blockDim.x / W, step_c = (int)blockDim.x - step_r * W;
-    int jy = (int)threadIdx.x / W, jx = (int)threadIdx.x - jy * W;
-    for (int t = threadIdx.x; t < W2; t += blockDim.x) {
-        const float2 v = resample_tap<CUBIC>(line, dx0 + os * jx, dy0 + os * jy, lim2);
-        __stcs(d00 + t, v);
-        const bool xin = mx && jx > 0;                   // pre-image of column 2S+1-jx exists
-        const bool yin = my && jy > 0;
-        if (xin) __stcs(d10 + (jy * W + (m1 - jx)), v);
-        if (yin) __stcs(d01 + ((m1 - jy) * W + jx), v);
-        if (xin && yin) __stcs(d11 + ((m1 - jy) * W + (m1 - jx)), v);
-        jx += step_c;
-        jy += step_r;
-        if (jx >= W) { jx -= W; ++jy; }
+    const int rpc = max(1, (slot - 2) / W);   // rows per chunk
+    const int step_r = (int)blockDim.x / nx, step_c = (int)blockDim.x - step_r * nx;
+    const int jy_t = (int)threadIdx.x / nx, jx_t = (int)threadIdx.x - jy_t * nx;
+    __syncthreads();   // line staged
+    int so = 0;        // offset of the current buffer set
+    for (int r0 = 0, chunk = 0; r0 < ny; r0 += rpc, ++chunk) {
+        const int r1 = min(ny, r0 + rpc);
+        const int ya = (fv && r0 == 0) ? 1 : r0;   // rows with a y-mirror: [ya, r1)
+        const int ylo = cy - (r1 - 1);              // lowest mirrored row
+        float2* const gF = d00 + r0 * W;
+        float2* const gX = d10 + r0 * W;
+        float2* const gY = d01 + ylo * W;
+        float2* const gXY = d11 + ylo * W;
+        const int oF = so + parity8(gF);
+        const int oX = xself ? oF : so + slot + parity8(gX);
+        const int oY = so + 2 * slot + parity8(gY);
+        const int oXY = xself ? oY : so + 3 * slot + parity8(gXY);
+        int jy = r0 + jy_t, jx = jx_t;
+        const int n_eval = (r1 - r0) * nx;
+        for (int t = threadIdx.x; t < n_eval; t += blockDim.x) {
+            const float2 v = resample_tap<CUBIC>(line, dx0 + os * jx, dy0 + os * jy, lim2);
+            const int mj = (jx == 0 && fu) ? 0 : cx - jx;
+            const int lf = (jy - r0) * W;
+            // mirrored row cy - jy relative to ylo; the row jy = 0 without a mirror (fv > 0)
+            // lands past the Y range's end and is never copied out
+            const int lm = (r1 - 1 - jy) * W;
+            stage[oF + lf + jx] = v;
+            stage[oX + lf + mj] = v;
+            stage[oY + lm + jx] = v;
+            stage[oXY + lm + mj] = v;
+            jx += step_c;
+            jy += step_r;
+            if (jx >= nx) { jx -= nx; ++jy; }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        // threads 0..3 own one region's copies each; chunk - 1's must have read the other set
+        if (threadIdx.x < 4 && chunk >= 1) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            const int k = threadIdx.x;
+            const int nF = (r1 - r0) * W, nY = (r1 - ya) * W;
+            float2* const g = k == 0 ? gF : k == 1 ? gX : k == 2 ? gY : gXY;
+            const int o = k == 0 ? oF : k == 1 ? oX : k == 2 ? oY : oXY;
+            const int n = k == 0 ? nF : k == 1 ? (xself ? 0 : nF) : k == 2 ? nY : (xself ? 0 : nY);
+            if (n > 0) {
+                const int sh = parity8(g);          // odd head element
+                const int nb = (n - sh) & ~1;       // aligned body
+                if (nb > 0) bulk_store(g + sh, stage_s + 8u * (uint32_t)(o + sh), (uint32_t)nb * 8u);
+                if (sh) __stcs(g, stage[o]);
+                if ((n - sh) & 1) __stcs(g + (n - 1), stage[o + n - 1]);
+            }
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+        so = so ? 0 : 4 * slot;
     }
+    // bulk copies must finish reading shared memory before the block exits
+    if (threadIdx.x < 4) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 int kg_resample(const Geom& g, int P, const float2* radial, const float2* spline_m,
                 const int32_t* support, const int64_t* offsets, float2* cache, cudaStream_t st) {
     int n_max = g.os * g.s_max + 2;
     if (n_max > g.k_out) n_max = g.k_out;
-    size_t smem = (size_t)round_up(n_max, 8) * sizeof(float4);
+    const int n_line = (int)round_up(n_max, 8);
+    const size_t line_bytes = (size_t)n_line * sizeof(float4);
+    // staging capacity per region (elements, even): up to 1536 -- about four taps per thread
+    // per chunk -- while two blocks still fit on an SM; never below one row of the largest
+    // support
+    int dev = 0, smem_sm = 0, smem_block = 0, reserved = 0;
+    WP_CUDA(cudaGetDevice(&dev));
+    WP_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    WP_CUDA(cudaDeviceGetAttribute(&smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    WP_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    const int w_max = 2 * g.s_max + 1;
+    const long two_per_sm = (long)smem_sm / 2 - reserved - (long)line_bytes;
+    int cap = (int)(two_per_sm / (8 * (long)sizeof(float2))) - 2;
+    cap = cap > 1536 ? 1536 : cap;
+    cap &= ~1;
+    if (cap < w_max + 1) cap = w_max + 1;   // even, >= one row
+    const int slot = cap + 2;
+    const size_t smem = line_bytes + (size_t)8 * slot * sizeof(float2);
+    if (smem > (size_t)smem_block) {
+        set_last_error("wp_resample", "staging for this support and oversampling exceeds shared memory");
+        return WP_ERR_UNSUPPORTED;
+    }
     const int h = g.os / 2;
     const int nrep = (h + 1) * (h + 1);
     const int n_items = P * nrep;
     dim3 grid((unsigned)n_items);
     if (g.interp == WP_INTERP_CUBIC) {
-        if (smem > 48 * 1024)
-            WP_CUDA(cudaFuncSetAttribute(k_resample<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_resample<true><<<grid, 256, smem, st>>>(g.k_out, g.os, g.s_max, nrep, n_items, radial, spline_m, support,
-                                                  offsets, cache);
+        WP_CUDA(cudaFuncSetAttribute(k_resample<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_resample<true><<<grid, RS_THREADS, smem, st>>>(g.k_out, g.os, g.s_max, nrep, n_items, n_line, slot,
+                                                         radial, spline_m, support, offsets, cache);
     } else {
-        if (smem > 48 * 1024)
-            WP_CUDA(cudaFuncSetAttribute(k_resample<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_resample<false><<<grid, 256, smem, st>>>(g.k_out, g.os, g.s_max, nrep, n_items, radial, spline_m, support,
-                                                   offsets, cache);
+        WP_CUDA(cudaFuncSetAttribute(k_resample<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_resample<false><<<grid, RS_THREADS, smem, st>>>(g.k_out, g.os, g.s_max, nrep, n_items, n_line, slot,
+                                                          radial, spline_m, support, offsets, cache);
     }
     WP_LAUNCH_CHECK("k_resample");
     return WP_OK;

@@ -112,3 +112,46 @@ def test_tensor_core_route_matches_fp32_route_on_every_plane():
     num = np.linalg.norm(out["fp32"] - out["tf32x3"], axis=1)
     den = np.linalg.norm(out["fp32"], axis=1)
     assert (num / den).max() < 2e-6
+
+
+@pytest.mark.parametrize("os_,interp", [(3, "cubic"), (5, "linear"), (8, "cubic")])
+def test_resample_staged_rows_odd_os_unaligned_cache(os_, interp):
+    """Supports up to 60 (121-wide rows: several staged chunks per sub-kernel), odd and even
+    oversampling, and a cache that starts 8 bytes past a 16-byte boundary: every plane
+    against the oracle, and the mirror identities of the cache hold bit for bit
+    (tap (jx, jy) of sub-kernel fu equals tap (2S + [fu > 0] - jx, jy) of (os - fu) mod os)."""
+    wp = _wp()
+    dev = torch.device("cuda")
+    N, dl, R, s_max = 256, np.deg2rad(3.0) / 256, 512, 60
+    planes = np.array([0.0, 150.0, 400.0, 900.0, 1400.0, 2000.0])
+    sup = np.array([1, 2, 17, 33, 60, 59])
+    plan = wp.Plan(N, dl, os_, s_max, 1, 0.0, R, interp, "tf32x3")
+    taper = synth.gaussian_taper_samples(N, dl, R)
+    w = torch.tensor(planes, dtype=torch.float64, device=dev)
+    ws = wp.kernelgen_prepare(plan, len(planes))
+    radial, spline_m, _ = wp.hankel_radial(plan, torch.tensor(taper, dtype=torch.float32, device=dev), w, ws)
+    off = wp.kernel_layout(plan, sup.tolist())
+    store = torch.full((off[-1] + 2,), float("nan"), dtype=torch.complex64, device=dev)
+    cache = store[1:off[-1] + 1]
+    assert cache.data_ptr() % 16 == 8
+    wp.resample(plan, radial, spline_m, torch.tensor(sup, dtype=torch.int32, device=dev),
+                torch.tensor(off, dtype=torch.int64, device=dev), cache)
+    torch.cuda.synchronize()
+    got = store.cpu().numpy()
+    assert np.isnan(got[0].real) and np.isnan(got[-1].real), "wrote outside the cache"
+    got = got[1:-1]
+    g = o.Geometry(N, dl, os_, s_max, 1, 0.0, R, 0 if interp == "cubic" else 1)
+    ks = o.wkernels(g, f32(taper), planes, supports=sup)
+    for p, S in enumerate(sup):
+        c = got[off[p]:off[p + 1]]
+        e = rel_l2(c, ks.cache[ks.offsets[p]:ks.offsets[p + 1]])
+        assert e < KERNEL_TOL, f"plane {p} (S = {S}): cache rel. L2 {e:.3e}"
+        Wd = 2 * S + 1
+        k = c.reshape(os_, os_, Wd, Wd)           # [fv][fu][jy][jx]
+        for fu in range(os_):
+            fu2, sh = ((os_ - fu) % os_, 1 if fu else 0)
+            jx = np.arange(sh, Wd)
+            mj = 2 * S + sh - jx
+            assert np.array_equal(k[:, fu][..., jx].view(np.uint64), k[:, fu2][..., mj].view(np.uint64))
+            if fu:
+                assert not np.any(k[:, fu][..., 0])
