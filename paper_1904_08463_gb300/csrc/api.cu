@@ -69,6 +69,7 @@ size_t carve_kg(const Geom& g, int P, void* ws, size_t bytes, KgWork* out) {
     w.h_lo = c.take<float>(hk);
     w.band = c.take<float>((size_t)g.k_out * 65);
     w.nm1 = c.take<double>((size_t)g.r_pad);
+    w.nm1f = c.take<float2>((size_t)g.r_pad);
     w.f32 = c.take<float>(fk);
     w.f_hi = c.take<float>(fk);
     w.f_lo = c.take<float>(fk);

@@ -82,8 +82,9 @@ static void spline_band_host(int K, std::vector<float>& band) {
     }
 }
 
-// n - 1 at the radial nodes, in FP64, without cancellation: -r^2 / (1 + sqrt(1 - r^2)).
-__global__ void k_nm1(int R, int r_pad, double r_max, double* __restrict__ nm1) {
+// n - 1 at the radial nodes, in FP64, without cancellation: -r^2 / (1 + sqrt(1 - r^2)); also
+// split into a float pair hi + lo (hi = the nearest float, lo = the nearest float to the rest).
+__global__ void k_nm1(int R, int r_pad, double r_max, double* __restrict__ nm1, float2* __restrict__ nm1f) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= r_pad) return;
     double v = 0.0;
@@ -93,10 +94,12 @@ __global__ void k_nm1(int R, int r_pad, double r_max, double* __restrict__ nm1) 
         v = -r2 / (1.0 + sqrt(1.0 - r2));
     }
     nm1[i] = v;
+    const float hi = (float)v;
+    nm1f[i] = make_float2(hi, (float)(v - (double)hi));
 }
 
 int kg_prepare(const Geom& g, const KgWork& w, cudaStream_t st) {
-    k_nm1<<<(g.r_pad + 255) / 256, 256, 0, st>>>(g.R, g.r_pad, g.r_max, w.nm1);
+    k_nm1<<<(g.r_pad + 255) / 256, 256, 0, st>>>(g.R, g.r_pad, g.r_max, w.nm1, w.nm1f);
     WP_LAUNCH_CHECK("k_nm1");
     int64_t total = (int64_t)g.k_out * g.r_pad;
     int threads = 256;
@@ -116,24 +119,38 @@ int kg_prepare(const Geom& g, const KgWork& w, cudaStream_t st) {
 // =======================================================================================
 // K2: image-domain convolution function on the radial line, written transposed
 // (row 2p = real part, row 2p+1 = imaginary part, R contiguous) as the B operand of the
-// K-major matrix product.  The phase in cycles, w (n - 1), is one FP64 product of the
-// plane's w and the node's n - 1 (precomputed once per geometry in FP64 without
-// cancellation), reduced to [-1/2, 1/2] cycles in FP64, and only then handed to the FP32
-// sincospi -- so |w| up to 1e5 keeps FP32 phase accuracy.
+// K-major matrix product.  The phase in cycles, w (n - 1), must keep FP32 accuracy after
+// reduction to [-1/2, 1/2] even for |w| ~ 1e5 (hundreds of cycles).  It is formed from the
+// float pairs w = w_hi + w_lo and n - 1 = n_hi + n_lo (the latter precomputed once per
+// geometry from FP64): p = w_hi n_hi rounded, its exact rounding error fma(w_hi, n_hi, -p),
+// plus the cross terms (w_lo n_lo, ~2^-48 of the phase, is dropped); subtracting rint(p) from
+// p is exact, and one final rounding gives the reduced phase -- as accurate as the FP64
+// product rounded to float, on the FP32 units (FP64 throughput is low on this part).
 // =======================================================================================
 template <bool SPLIT>
-__global__ void k_screen(int R, int r_pad, int P, int P_pad, const double* __restrict__ nm1,
+__global__ void k_screen(int R, int r_pad, int P, int P_pad, const float2* __restrict__ nm1f,
                          const float* __restrict__ taper, const double* __restrict__ w_planes,
                          float* __restrict__ f32, float* __restrict__ f_hi, float* __restrict__ f_lo) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int p = blockIdx.y;
+    __shared__ float2 wsplit;
+    const int p = blockIdx.y;
+    if (threadIdx.x == 0) {
+        const double wd = (p < P) ? w_planes[p] : 0.0;
+        const float hi = (float)wd;
+        wsplit = make_float2(hi, (float)(wd - (double)hi));
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= r_pad) return;
     float re = 0.0f, im = 0.0f;
     if (i < R && p < P) {
-        double cyc = w_planes[p] * nm1[i];         // phase / (2 pi)
-        double fr = cyc - rint(cyc);               // in [-1/2, 1/2]
+        const float2 n = nm1f[i];
+        const float2 w = wsplit;
+        const float ph = w.x * n.x;
+        float pl = fmaf(w.x, n.x, -ph);               // exact error of the high product
+        pl = fmaf(w.x, n.y, fmaf(w.y, n.x, pl));      // cross terms
+        const float fr = (ph - rintf(ph)) + pl;       // phase / (2 pi), reduced
         float s, c;
-        sincospif((float)(2.0 * fr), &s, &c);
+        sincospif(2.0f * fr, &s, &c);
         float t = taper[i];
         re = t * c;
         im = t * s;
@@ -157,9 +174,9 @@ int kg_screen(const Geom& g, const KgWork& w, const float* taper, const double* 
     int Pp = p_pad(P);
     dim3 grid((g.r_pad + 255) / 256, Pp);
     if (g.kernelgen == WP_KG_TF32X3)
-        k_screen<true><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1, taper, w_planes, w.f32, w.f_hi, w.f_lo);
+        k_screen<true><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo);
     else
-        k_screen<false><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1, taper, w_planes, w.f32, w.f_hi, w.f_lo);
+        k_screen<false><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo);
     WP_LAUNCH_CHECK("k_screen");
     return WP_OK;
 }
@@ -269,7 +286,9 @@ __global__ void __launch_bounds__(256) k_trunc_spline(int K, int os, int s_min, 
     float2* rhs = sm + K + 32;
     __shared__ float red_f[8];
     __shared__ int red_i[8];
+    __shared__ float toe[65];        // one interior row of the band (Toeplitz coefficients)
     const int p = blockIdx.x;
+    if (do_spline && threadIdx.x < 65) toe[threadIdx.x] = band[(int64_t)threadIdx.x * K + K / 2];
     const float2* src = radial + (int64_t)p * K;
     float local_max = 0.0f;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
@@ -323,12 +342,23 @@ __global__ void __launch_bounds__(256) k_trunc_spline(int K, int os, int s_min, 
         float2* dst = spline_m + (int64_t)p * K;
         for (int k = threadIdx.x; k < K; k += blockDim.x) {
             float mr = 0.0f, mi = 0.0f;
+            if (k >= 32 && k < K - 32) {
+                // interior rows: A^-1 is Toeplitz there (the end conditions reach row k only
+                // through terms ~0.268^min(k, K-1-k), below FP32 resolution at distance 32)
 #pragma unroll 13
-            for (int d = 0; d < 65; ++d) {
-                const float c = band[(int64_t)d * K + k];    // zero where k + d - 32 is outside
-                const float2 r = rhs[k + d - 32];
-                mr = fmaf(c, r.x, mr);
-                mi = fmaf(c, r.y, mi);
+                for (int d = 0; d < 65; ++d) {
+                    const float2 r = rhs[k + d - 32];
+                    mr = fmaf(toe[d], r.x, mr);
+                    mi = fmaf(toe[d], r.y, mi);
+                }
+            } else {
+#pragma unroll 13
+                for (int d = 0; d < 65; ++d) {
+                    const float c = band[(int64_t)d * K + k];    // zero where k + d - 32 is outside
+                    const float2 r = rhs[k + d - 32];
+                    mr = fmaf(c, r.x, mr);
+                    mi = fmaf(c, r.y, mi);
+                }
             }
             dst[k] = make_float2(mr, mi);
         }

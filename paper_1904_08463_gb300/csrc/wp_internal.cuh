@@ -78,6 +78,7 @@ struct KgWork {
     float* h_lo;       // [k_out][r_pad] TF32 low part
     float* band;       // [65][k_out] spline inverse band (row d holds A^-1[k][k + d - 32])
     double* nm1;       // [R] n - 1 = sqrt(1 - r_i^2) - 1 at the radial nodes
+    float2* nm1f;      // [R] the same as an unevaluated float pair (hi, lo)
     float* f32;        // [2 P_pad][r_pad] image-domain functions (FP32 path)
     float* f_hi;       // [2 P_pad][r_pad]
     float* f_lo;       // [2 P_pad][r_pad]
