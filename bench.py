@@ -37,6 +37,9 @@ import synth  # noqa: E402
 # of algorithmic bytes).  Reported only while the kernel source is the one it was measured on.
 RESAMPLE_TRAFFIC = {"bytes_per_launch": 5.931e9, "source_sha1": "3dd5bb084d0e"}
 
+GRID_METHOD_NAMES = {0: "register tile", 1: "shared-memory tile, footprint over the lanes (atomics)",
+                     2: "warp-private shared-memory tiles", 3: "shared-memory tile, rows owned by warps"}
+
 METRIC = "w-kernels/s (Hankel vs 2D-FFT) and Mvis/s gridded, 1 GB300, at stated FP64 error"
 N_IMG, FOV_DEG, R_KG, OS = 4096, 8.0, 4096, 8
 
@@ -500,7 +503,10 @@ def run_imaging(args, dev):
     wp.hankel_radial(plan, taper, wpl, ws, radial, spl, sup)
     wp.resample(plan, radial, spl, sup, off, cache)
     tuner = Autotuner()
-    mt = tuner.choose(Autotuner.key("grid", N, P, 127, V), [list(c) for c in GRID_CHOICES],
+    choices = [list(c) for c in GRID_CHOICES]
+    if args.grid_shape:
+        choices = [[int(x) for x in args.grid_shape.split(",")]]
+    mt = tuner.choose(Autotuner.key("grid", N, P, 127, V), choices,
                       lambda c: wp.grid(plan.replace(grid_method=int(c[0]), grid_tile=int(c[1])), wk,
                                         uvw.reshape(-1), vis, None, G, gws, stats))
     plan = plan.replace(grid_method=int(mt[0]), grid_tile=int(mt[1]))
@@ -558,7 +564,7 @@ def run_imaging(args, dev):
         "gridding_mvis_per_s": V / (grid_ms * 1e-3) / 1e6,
         "supports": {"min": int(sup_h.min()), "max": int(sup_h.max()), "mean": float(sup_h.mean())},
         "taps_per_vis": taps / V,
-        "grid_launch_shape": {"method": ["register tile", "shared-memory tile"][plan.grid_method],
+        "grid_launch_shape": {"method": GRID_METHOD_NAMES[plan.grid_method],
                               "tile": plan.grid_tile or 64, "chosen_by": "autotuner", "ms": tuner.table},
         "dropped": float(st[1]),
         "roofline": {"kernel": "k_grid", "bound": "alu", "achieved": flops / (grid_ms * 1e-3) / 1e12,
@@ -712,6 +718,8 @@ def main():
     ap.add_argument("--no-routes", dest="routes", action="store_false",
                     help="skip timing the other kernel-generation routes (FP32 Hankel, 2D FFT)")
     ap.add_argument("--imaging-planes", type=int, default=512)
+    ap.add_argument("--grid-shape", default="",
+                    help="gridder 'method,tile' for the imaging workload instead of the autotuner's pick")
     ap.add_argument("--batch", action="store_true", help="also time the batched uneven-problem workload")
     ap.add_argument("--grad", action="store_true", help="also time forward + backward of the prediction")
     ap.add_argument("--batch-problems", type=int, default=48)

@@ -84,8 +84,11 @@ typedef struct wp_plan {
     int32_t grid_method;    /* 0 (default): register tile, lanes own grid cells;
                                1: shared-memory tile, footprint spread over the lanes;
                                2: per-warp shared-memory 32 x 32 tiles, groups of 8 planes
-                               per work item (grid_tile ignored).  grid_tile and
-                               grid_method are tuning choices only: results are the same */
+                               per work item (grid_tile ignored);
+                               3: shared-memory tile, each warp owning every 8th row, lanes
+                               across the footprint's columns (no atomics in the tile).
+                               grid_tile and grid_method are tuning choices only: the
+                               results agree to FP32 rounding order                      */
 } wp_plan;
 
 /* Derived sizes of a plan (host struct filled by wp_plan_geometry). */

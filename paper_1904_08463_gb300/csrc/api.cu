@@ -37,7 +37,7 @@ int make_geom(const wp_plan* plan, Geom* g) {
     if (plan->interp != WP_INTERP_CUBIC && plan->interp != WP_INTERP_LINEAR) return WP_ERR_PLAN;
     if (plan->kernelgen != WP_KG_FP32 && plan->kernelgen != WP_KG_TF32X3) return WP_ERR_PLAN;
     if (plan->grid_tile != 0 && plan->grid_tile != 32 && plan->grid_tile != 64) return WP_ERR_PLAN;
-    if (plan->grid_method < 0 || plan->grid_method > 2) return WP_ERR_PLAN;
+    if (plan->grid_method < 0 || plan->grid_method > 3) return WP_ERR_PLAN;
     g->N = N;
     g->dl = plan->cell_size;
     g->du = 1.0 / ((double)N * plan->cell_size);

@@ -53,7 +53,7 @@ def test_small_imaging_grid_and_dirty_image():
     assert np.all(img[~o.disc_mask(g)] == 0)
 
 
-@pytest.mark.parametrize("grid_method", [0, 1, 2])
+@pytest.mark.parametrize("grid_method", [0, 1, 2, 3])
 @pytest.mark.parametrize("grid_tile", [32, 64])
 @pytest.mark.parametrize("V,seed", [(0, 1), (1, 2), (37, 3), (5000, 4)])
 def test_grid_edges_and_conjugation(V, seed, grid_tile, grid_method):
