@@ -53,7 +53,7 @@ class Plan:
     interp: str = "cubic"
     kernelgen: str = "fp32"
     grid_tile: int = 0          # gridding tile side (0 = default 64; 32 or 64): tuning only
-    grid_method: int = 0        # 0 register tile (default), 1/2/3 shared-memory tiles: tuning only
+    grid_method: int = 3        # 3 row-owned shared tile (fastest measured), 0 register tile, 1/2: tuning only
 
     def c(self) -> _lib.WpPlan:
         return _lib.WpPlan(self.image_size, self.cell_size, self.oversampling, self.max_support,

@@ -393,7 +393,7 @@ int wp_degrid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw,
 size_t wp_grad_workspace_bytes(const wp_plan* plan, int32_t P, int64_t V) {
     Geom g;
     if (make_geom(plan, &g) || P < 1 || V < 0) return 0;
-    return carve_grid(g, P, V, nullptr, 0, nullptr) + (size_t)round_up(2 * sizeof(int) * grad_extra_ints(P, V) + 512, 256);
+    return carve_grid(g, P, V, nullptr, 0, nullptr) + carve_grad(g, P, V, nullptr, 0, nullptr);
 }
 
 int wp_grad_radial(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw, const float* grad_vis,
@@ -409,10 +409,10 @@ int wp_grad_radial(const wp_plan* plan, const wp_wkernels* kernels, const float*
     cudaStream_t st = (cudaStream_t)stream;
     GridWork w;
     const size_t gb = carve_grid(g, kernels->P, V, workspace, workspace_bytes, &w);
-    int* items = reinterpret_cast<int*>(static_cast<char*>(workspace) + gb);
-    const size_t n_extra = grad_extra_ints(kernels->P, V);
+    GradWork gw;
+    carve_grad(g, kernels->P, V, static_cast<char*>(workspace) + gb, workspace_bytes - gb, &gw);
     if ((rc = grid_bin(g, kernels, uvw, nullptr, nullptr, V, w, st))) return rc;
-    return grad_radial_run(g, kernels, w, items, items + n_extra, reinterpret_cast<const float2*>(grad_vis),
+    return grad_radial_run(g, kernels, w, gw, reinterpret_cast<const float2*>(grad_vis),
                            reinterpret_cast<const float2*>(grid), reinterpret_cast<float2*>(grad_radial),
                            reinterpret_cast<float2*>(grad_spline_m), st);
 }

@@ -6,12 +6,16 @@
 // g = dL/dRe(V) + j dL/dIm(V); the gradient of a complex parameter z is returned in the
 // same form, so that dL = Re(conj(g_z) dz).
 //
-//   k_grad_items     per-plane chunks of the binned visibilities (work items)
-//   k_grad_radial    per visibility and tap: Q = conj(g) G(cell) (w >= 0) or g conj(G(cell))
-//                    (w < 0, the kernel there is conjugated), scattered onto the radial line
-//                    through the resample interpolation weights: d/dC_k gets b Q, d/dC_k+1
-//                    gets a Q, and the spline second derivatives get the cubic weights;
-//                    accumulated per plane in shared memory, flushed once per work item
+//   k_sub_count,     the binned visibilities regrouped by (plane, sub-kernel fv, fu), each
+//   k_sub_scatter    with its cell and g, s g (s = -1 for w < 0)
+//   k_grad_taps      per (plane, representative sub-kernel): every thread owns one tap of the
+//                    quadrant that the x/y mirrors do not cover (as in the resample), and sums
+//                    Q = conj(g) G(cell) (w >= 0) or g conj(G(cell)) (w < 0) in registers over
+//                    the visibilities of the (up to four) mirror sub-kernels at the tap's
+//                    mirror positions -- all at the same radius -- then scatters the sum onto
+//                    the radial line through the resample interpolation weights (d/dC_k gets
+//                    b Q, d/dC_k+1 gets a Q, the spline second derivatives the cubic weights),
+//                    accumulated per block in shared memory and flushed once
 //   k_spline_adjoint dC += D^T 6 A^-T dM (the spline system's adjoint, banded inverse),
 //                    written as real/imaginary rows for the transposed product
 //   k_gemm_nn        dF = dC H  (the Hankel transform's adjoint: the same matrix, transposed)
@@ -28,107 +32,145 @@
 namespace wp {
 
 namespace {
-constexpr int GCH = 256;           // visibilities per gradient work item
 constexpr int GG_M = 128, GG_N = 128, GG_K = 32;
 }  // namespace
 
-// Work items: for plane p, ceil(n_p / GCH) chunks of its binned visibilities.
-__global__ void k_grad_items(int P, int ntiles, const int* __restrict__ start, int* __restrict__ item_plane,
-                             int* __restrict__ item_chunk, int* __restrict__ ctrl) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int n = 0;
-    for (int p = 0; p < P; ++p) {
-        const int cnt = start[(p + 1) * ntiles] - start[p * ntiles];
-        const int ch = (cnt + GCH - 1) / GCH;
-        for (int c = 0; c < ch; ++c) {
-            item_plane[n] = p;
-            item_chunk[n] = c;
-            ++n;
-        }
+// ---- visibilities regrouped by (plane, sub-kernel): key = p os^2 + fv os + fu ----------
+__global__ void k_sub_count(const int* __restrict__ n_valid, const int4* __restrict__ srec, int os,
+                            int* __restrict__ count2) {
+    const int n = *n_valid;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const int4 r4 = srec[r];
+        atomicAdd(count2 + r4.z * os * os + ((r4.y >> 8) & 0xff) * os + (r4.y & 0xff), 1);
     }
-    ctrl[0] = 0;   // item cursor
-    ctrl[1] = n;   // item count
 }
 
-__global__ void __launch_bounds__(256) k_grad_radial(int N, int os, int s_max, int K, int ntiles,
-                                                     const int32_t* __restrict__ support,
-                                                     const int* __restrict__ start,
-                                                     const int4* __restrict__ srec,
-                                                     const float2* __restrict__ gvis,
-                                                     const float2* __restrict__ grid,
-                                                     const int* __restrict__ item_plane,
-                                                     const int* __restrict__ item_chunk,
-                                                     int* __restrict__ ctrl, float2* __restrict__ gC,
-                                                     float2* __restrict__ gM, int cubic) {
-    extern __shared__ float2 acc[];    // [2][K]: d/dC then d/dM of the current plane
-    __shared__ int s_item;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int n_items = ctrl[1];
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&ctrl[0], 1);
-        __syncthreads();
-        const int it = s_item;
-        __syncthreads();
-        if (it >= n_items) break;
-        const int p = item_plane[it];
-        const int S = min(max(support[p], 1), s_max);
-        const int W = 2 * S + 1, W2 = W * W;
-        const int lim = os * S, lim2 = lim * lim;
-        const int ku = min(K, lim + 2);
-        for (int k = threadIdx.x; k < 2 * ku; k += blockDim.x) acc[k] = make_float2(0.0f, 0.0f);
-        __syncthreads();
-        const int pb = start[p * ntiles], pe = start[(p + 1) * ntiles];
-        const int r0 = pb + item_chunk[it] * GCH;
-        const int r1 = min(pe, r0 + GCH);
-        const float inv_w = 1.0f / (float)W;
-        for (int r = r0 + wid; r < r1; r += 8) {
-            const int4 r4 = srec[r];
-            const int iu = r4.x & 0xffff, iv = (r4.x >> 16) & 0xffff;
-            const int fu = r4.y & 0xff, fv = (r4.y >> 8) & 0xff;
-            const bool neg = (r4.y >> 16) & 1;
-            const float2 g = gvis[r4.w];
-            const float2* g0 = grid + (int64_t)(iv - S) * N + (iu - S);
-            for (int t = lane; t < W2; t += 32) {
-                int jy = (int)(((float)t + 0.5f) * inv_w);
-                jy -= (jy * W > t);
-                jy += ((jy + 1) * W <= t);
-                const int jx = t - jy * W;
-                const int dx = os * (jx - S) - fu, dy = os * (jy - S) - fv;
-                const int q = dx * dx + dy * dy;
-                if (q > lim2) continue;                       // tap forced to zero: no gradient
-                const float2 G = g0[(int64_t)jy * N + jx];
-                float2 Q;
-                if (!neg) Q = make_float2(g.x * G.x + g.y * G.y, g.x * G.y - g.y * G.x);   // conj(g) G
-                else      Q = make_float2(g.x * G.x + g.y * G.y, g.y * G.x - g.x * G.y);   // g conj(G)
-                const float x = sqrtf((float)q);
-                const int k = min((int)x, K - 2);
-                const float a = x - (float)k, b = 1.0f - a;
-                atomicAdd(&acc[k].x, b * Q.x);
-                atomicAdd(&acc[k].y, b * Q.y);
-                atomicAdd(&acc[k + 1].x, a * Q.x);
-                atomicAdd(&acc[k + 1].y, a * Q.y);
-                if (cubic) {
-                    const float cb = (b * b * b - b) * (1.0f / 6.0f);
-                    const float ca = (a * a * a - a) * (1.0f / 6.0f);
-                    atomicAdd(&acc[ku + k].x, cb * Q.x);
-                    atomicAdd(&acc[ku + k].y, cb * Q.y);
-                    atomicAdd(&acc[ku + k + 1].x, ca * Q.x);
-                    atomicAdd(&acc[ku + k + 1].y, ca * Q.y);
-                }
+__global__ void k_sub_scatter(const int* __restrict__ n_valid, const int4* __restrict__ srec,
+                              const float2* __restrict__ gvis, int os, const int* __restrict__ start2,
+                              int* __restrict__ cursor2, int* __restrict__ uv2, float4* __restrict__ g4) {
+    const int n = *n_valid;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const int4 r4 = srec[r];
+        const int key = r4.z * os * os + ((r4.y >> 8) & 0xff) * os + (r4.y & 0xff);
+        const int pos = start2[key] + atomicAdd(cursor2 + key, 1);
+        const float2 g = gvis[r4.w];
+        const float sg = ((r4.y >> 16) & 1) ? -1.0f : 1.0f;
+        uv2[pos] = r4.x;
+        g4[pos] = make_float4(g.x, g.y, sg * g.x, sg * g.y);
+    }
+}
+
+// Sum of Q over the visibilities [vb, ve) of one sub-kernel at up to two columns (ca, and cb
+// when two_c) and two rows (ra, and rb when two_r) of the footprint.
+__device__ __forceinline__ void tap_sum(int vb, int ve, bool on, int N, int S, const int* __restrict__ uv2,
+                                        const float4* __restrict__ g4, const float2* __restrict__ grid,
+                                        int ca, int cb, bool two_c, int ra, int rb, bool two_r,
+                                        float& qr, float& qi) {
+    for (int v = vb; v < ve; ++v) {
+        const int uv = uv2[v];
+        const float4 gg = g4[v];
+        if (!on) continue;
+        const int iu = uv & 0xffff, iv = (uv >> 16) & 0xffff;
+        const float2* g0 = grid + (int64_t)(iv - S) * N + (iu - S);
+        float2 G = g0[(int64_t)ra * N + ca];
+        qr = fmaf(gg.x, G.x, fmaf(gg.y, G.y, qr));
+        qi = fmaf(gg.z, G.y, fmaf(-gg.w, G.x, qi));
+        if (two_c) {
+            G = g0[(int64_t)ra * N + cb];
+            qr = fmaf(gg.x, G.x, fmaf(gg.y, G.y, qr));
+            qi = fmaf(gg.z, G.y, fmaf(-gg.w, G.x, qi));
+        }
+        if (two_r) {
+            G = g0[(int64_t)rb * N + ca];
+            qr = fmaf(gg.x, G.x, fmaf(gg.y, G.y, qr));
+            qi = fmaf(gg.z, G.y, fmaf(-gg.w, G.x, qi));
+            if (two_c) {
+                G = g0[(int64_t)rb * N + cb];
+                qr = fmaf(gg.x, G.x, fmaf(gg.y, G.y, qr));
+                qi = fmaf(gg.z, G.y, fmaf(-gg.w, G.x, qi));
             }
         }
-        __syncthreads();
-        float2* dC = gC + (int64_t)p * K;
-        float2* dM = gM + (int64_t)p * K;
-        for (int k = threadIdx.x; k < ku; k += blockDim.x) {
-            const float2 c = acc[k];
-            if (c.x != 0.0f || c.y != 0.0f) atomicAdd(dC + k, c);
-            if (cubic) {
-                const float2 m = acc[ku + k];
-                if (m.x != 0.0f || m.y != 0.0f) atomicAdd(dM + k, m);
+    }
+}
+
+template <bool CUBIC>
+__global__ void __launch_bounds__(256) k_grad_taps(int N, int os, int s_max, int K, int nrep, int n_items,
+                                                   const int32_t* __restrict__ support,
+                                                   const int* __restrict__ start2, const int* __restrict__ uv2,
+                                                   const float4* __restrict__ g4, const float2* __restrict__ grid,
+                                                   float2* __restrict__ gC, float2* __restrict__ gM) {
+    extern __shared__ float2 acc[];    // [ku] d/dC, then [ku] d/dM
+    const int item = n_items - 1 - (int)blockIdx.x;   // largest supports first
+    const int p = item / nrep;
+    const int rep = item - p * nrep;
+    const int h = os / 2;
+    const int fv = rep / (h + 1), fu = rep - fv * (h + 1);
+    const int S = min(max(support[p], 1), s_max);
+    const int W = 2 * S + 1;
+    const int lim = os * S, lim2 = lim * lim;
+    const int ku = min(K, lim + 2);
+    for (int k = threadIdx.x; k < (CUBIC ? 2 : 1) * ku; k += blockDim.x) acc[k] = make_float2(0.0f, 0.0f);
+    // the quadrant and the mirror maps of the resample
+    const int fu2 = fu ? os - fu : 0, fv2 = fv ? os - fv : 0;
+    const bool xself = (fu2 == fu), yself = (fv2 == fv);
+    const int nx = xself ? S + 1 : W, ny = yself ? S + 1 : W;
+    const int cx = fu ? W : W - 1, cy = fv ? W : W - 1;
+    const int os2 = os * os;
+    const int* s00 = start2 + p * os2 + fv * os + fu;
+    const int* s10 = start2 + p * os2 + fv * os + fu2;
+    const int* s01 = start2 + p * os2 + fv2 * os + fu;
+    const int* s11 = start2 + p * os2 + fv2 * os + fu2;
+    const int v00 = s00[0], e00 = s00[1], v10 = s10[0], e10 = s10[1];
+    const int v01 = s01[0], e01 = s01[1], v11 = s11[0], e11 = s11[1];
+    __syncthreads();
+    const int n_eval = nx * ny;
+    for (int t0 = 0; t0 < n_eval; t0 += blockDim.x) {
+        const int t = t0 + (int)threadIdx.x;
+        const int jy = t / nx, jx = t - (t / nx) * nx;
+        const int dx = os * (jx - S) - fu, dy = os * (jy - S) - fv;
+        const int q = dx * dx + dy * dy;
+        const bool on = (t < n_eval) && (q <= lim2);
+        const int mj = (jx == 0 && fu) ? 0 : cx - jx;
+        const int mjy = (jy == 0 && fv) ? 0 : cy - jy;
+        // a sub-kernel that is its own mirror holds the tap at both positions (once if equal)
+        const bool x2 = xself && mj != jx, y2 = yself && mjy != jy;
+        float qr = 0.0f, qi = 0.0f;
+        tap_sum(v00, e00, on, N, S, uv2, g4, grid, jx, mj, x2, jy, mjy, y2, qr, qi);
+        if (!xself) tap_sum(v10, e10, on, N, S, uv2, g4, grid, mj, mj, false, jy, mjy, y2, qr, qi);
+        if (!yself) tap_sum(v01, e01, on, N, S, uv2, g4, grid, jx, mj, x2, mjy, mjy, false, qr, qi);
+        if (!xself && !yself) tap_sum(v11, e11, on, N, S, uv2, g4, grid, mj, mj, false, mjy, mjy, false, qr, qi);
+        if (on && (qr != 0.0f || qi != 0.0f)) {
+            // the resample's interpolation interval and weights at this radius
+            const float qf = (float)q;
+            const float x = qf * rsqrtf(fmaxf(qf, 1.0f));
+            const float tt = (x - 0.5f) + 12582912.0f;
+            const int k = __float_as_int(tt) - 0x4B400000;
+            const float a = x - (tt - 12582912.0f);
+            const float b = 1.0f - a;
+            atomicAdd(&acc[k].x, b * qr);
+            atomicAdd(&acc[k].y, b * qi);
+            atomicAdd(&acc[k + 1].x, a * qr);
+            atomicAdd(&acc[k + 1].y, a * qi);
+            if (CUBIC) {
+                const float cb = (b * b - 1.0f) * b * (1.0f / 6.0f);
+                const float ca = (a * a - 1.0f) * a * (1.0f / 6.0f);
+                atomicAdd(&acc[ku + k].x, cb * qr);
+                atomicAdd(&acc[ku + k].y, cb * qi);
+                atomicAdd(&acc[ku + k + 1].x, ca * qr);
+                atomicAdd(&acc[ku + k + 1].y, ca * qi);
             }
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    float2* dC = gC + (int64_t)p * K;
+    float2* dM = gM + (int64_t)p * K;
+    for (int k = threadIdx.x; k < ku; k += blockDim.x) {
+        const float2 c = acc[k];
+        if (c.x != 0.0f || c.y != 0.0f) atomicAdd(dC + k, c);
+        if (CUBIC) {
+            const float2 m = acc[ku + k];
+            if (m.x != 0.0f || m.y != 0.0f) atomicAdd(dM + k, m);
+        }
     }
 }
 
@@ -289,26 +331,55 @@ __global__ void __launch_bounds__(256) k_image_adjoint(int N, int R, const float
 }
 
 // ------------------------------------------------------------------------------ launchers
-size_t grad_extra_ints(int P, int64_t V) { return (size_t)(P + V / GCH + 2); }
+size_t carve_grad(const Geom& g, int P, int64_t V, void* ws, size_t bytes, GradWork* out) {
+    Carver c(ws, bytes);
+    GradWork w;
+    const int64_t nb2 = (int64_t)P * g.os * g.os;
+    w.count2 = c.take<int>((size_t)nb2 + 1);
+    w.cursor2 = c.take<int>((size_t)nb2 + 1);
+    w.uv2 = c.take<int>((size_t)(V > 0 ? V : 1));
+    w.g4 = c.take<float4>((size_t)(V > 0 ? V : 1));
+    w.scan_tmp = c.take<int>(scan_tmp_ints(nb2 + 1));
+    if (out) *out = w;
+    return (size_t)round_up((int64_t)c.off, 256);
+}
 
-int grad_radial_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, int* item_plane, int* item_chunk,
+int grad_radial_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, const GradWork& gw,
                     const float2* gvis, const float2* grid, float2* gC, float2* gM, cudaStream_t st) {
     const int P = kern->P;
+    const bool cubic = (g.interp == WP_INTERP_CUBIC);
     WP_CUDA(cudaMemsetAsync(gC, 0, sizeof(float2) * (size_t)P * g.k_out, st));
-    if (g.interp == WP_INTERP_CUBIC) WP_CUDA(cudaMemsetAsync(gM, 0, sizeof(float2) * (size_t)P * g.k_out, st));
-    k_grad_items<<<1, 32, 0, st>>>(P, w.ntiles, w.count, item_plane, item_chunk, w.ctrl);
-    WP_LAUNCH_CHECK("k_grad_items");
+    if (cubic) WP_CUDA(cudaMemsetAsync(gM, 0, sizeof(float2) * (size_t)P * g.k_out, st));
+    const int64_t nb2 = (int64_t)P * g.os * g.os;
+    WP_CUDA(cudaMemsetAsync(gw.count2, 0, sizeof(int) * (size_t)(nb2 + 1), st));
+    WP_CUDA(cudaMemsetAsync(gw.cursor2, 0, sizeof(int) * (size_t)(nb2 + 1), st));
     int dev = 0, sms = 0;
     WP_CUDA(cudaGetDevice(&dev));
     WP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int* n_valid = w.count + w.nbins;   // binned (not dropped) visibilities
+    k_sub_count<<<sms * 4, 256, 0, st>>>(n_valid, w.srec, g.os, gw.count2);
+    WP_LAUNCH_CHECK("k_sub_count");
+    int rc = exclusive_scan_i32(gw.count2, gw.count2, nb2 + 1, gw.scan_tmp, st);
+    if (rc) return rc;
+    k_sub_scatter<<<sms * 4, 256, 0, st>>>(n_valid, w.srec, gvis, g.os, gw.count2, gw.cursor2, gw.uv2, gw.g4);
+    WP_LAUNCH_CHECK("k_sub_scatter");
+    const int h = g.os / 2;
+    const int nrep = (h + 1) * (h + 1);
+    const int n_items = P * nrep;
     const int ku = g.os * g.s_max + 2 < g.k_out ? g.os * g.s_max + 2 : g.k_out;
-    const size_t smem = (size_t)2 * ku * sizeof(float2);
-    if (smem > 48 * 1024)
-        WP_CUDA(cudaFuncSetAttribute(k_grad_radial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_grad_radial<<<sms * 4, 256, smem, st>>>(g.N, g.os, g.s_max, g.k_out, w.ntiles, kern->support, w.count, w.srec,
-                                              gvis, grid, item_plane, item_chunk, w.ctrl, gC, gM,
-                                              g.interp == WP_INTERP_CUBIC);
-    WP_LAUNCH_CHECK("k_grad_radial");
+    const size_t smem = (size_t)(cubic ? 2 : 1) * ku * sizeof(float2);
+    if (cubic) {
+        if (smem > 48 * 1024)
+            WP_CUDA(cudaFuncSetAttribute(k_grad_taps<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_grad_taps<true><<<n_items, 256, smem, st>>>(g.N, g.os, g.s_max, g.k_out, nrep, n_items, kern->support,
+                                                      gw.count2, gw.uv2, gw.g4, grid, gC, gM);
+    } else {
+        if (smem > 48 * 1024)
+            WP_CUDA(cudaFuncSetAttribute(k_grad_taps<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_grad_taps<false><<<n_items, 256, smem, st>>>(g.N, g.os, g.s_max, g.k_out, nrep, n_items, kern->support,
+                                                       gw.count2, gw.uv2, gw.g4, grid, gC, gM);
+    }
+    WP_LAUNCH_CHECK("k_grad_taps");
     return WP_OK;
 }
 

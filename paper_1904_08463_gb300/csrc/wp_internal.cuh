@@ -148,8 +148,15 @@ size_t plane_values_workspace_bytes(int64_t V);
 int plane_values(const float* uvw, int64_t V, int P, void* ws, size_t bytes, double* out, cudaStream_t st);
 
 // differentiation (grad.cu)
-size_t grad_extra_ints(int P, int64_t V);
-int grad_radial_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, int* item_plane, int* item_chunk,
+struct GradWork {
+    int*    count2;     // [P os^2 + 1] visibilities per (plane, sub-kernel), then exclusive scan
+    int*    cursor2;    // [P os^2 + 1]
+    int*    uv2;        // [V] cell (iu | iv << 16) of each regrouped visibility
+    float4* g4;         // [V] (g, s g), s = -1 for w < 0
+    int*    scan_tmp;
+};
+size_t carve_grad(const Geom& g, int P, int64_t V, void* ws, size_t bytes, GradWork* out);
+int grad_radial_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, const GradWork& gw,
                     const float2* gvis, const float2* grid, float2* gC, float2* gM, cudaStream_t st);
 int hankel_adjoint_run(const Geom& g, const KgWork& w, int P, const double* w_planes, const float2* gC,
                        const float2* gM, float* grad_taper, cudaStream_t st);
