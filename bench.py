@@ -337,6 +337,20 @@ def time_routes(args, kb, plan, taper_d, wpl_d, sup_host, ws, radial, spline_m, 
 
     ms = timeit(hankel_other, max(3, min(args.steps, 10)))
     res[other + "_hankel"] = {"ms_per_step": ms, "w_kernels_per_s": P / (ms * 1e-3)}
+    # the projection-slice realisation of the Hankel transform (the variant the paper timed):
+    # workspace image summed over one axis, zero-padded by os, batched 1D cuFFT
+    p3 = plan.replace(kernelgen="projslice")
+    ws3 = wp.workspace(wp.kernelgen_workspace_bytes(p3, P))
+    wp.kernelgen_prepare(p3, P, ws3)
+
+    def projslice():
+        wp.hankel_radial(p3, taper_d, wpl_d, ws3, radial, spline_m)
+        wp.resample(p3, radial, spline_m, sup_d, off_d, cache)
+
+    ms = timeit(projslice, max(3, min(args.steps, 10)))
+    res["projslice_hankel"] = {"ms_per_step": ms, "w_kernels_per_s": P / (ms * 1e-3),
+                               "line": "M=256 workspace projected, 2048-point 1D cuFFT per plane"}
+    del ws3
     fws = wp.workspace(int(wp._lib.load().wp_fft_workspace_bytes(__import__("ctypes").byref(plan.c()), P)))
     import ctypes
 

@@ -63,6 +63,11 @@ extern "C" {
 #define WP_KG_FP32         0   /* Hankel transform as FP32 SIMT matrix product          */
 #define WP_KG_TF32X3       1   /* Hankel transform on tcgen05 tensor cores, TF32 hi/lo
                                   split (3 products), FP32 accumulation in TMEM          */
+#define WP_KG_PROJSLICE    2   /* Hankel transform by the projection-slice theorem
+                                  (Section 4.3.1, Alg. 2 steps 4-12): the taper x screen
+                                  on the undersampled M x M workspace (Section 4.2) summed
+                                  over one axis, zero-padded by os, 1D FFT; the radial
+                                  line is the v = 0 slice of the 2D-FFT route's transform */
 
 /*
  * Imager settings (Section 5: image size, cell size, oversampling, maximum support,
@@ -79,7 +84,7 @@ typedef struct wp_plan {
                                (Section 3.1, default 0.01); <= 0: supports are given   */
     int32_t radial_samples; /* R, 8 <= R <= 65536                                      */
     int32_t interp;         /* WP_INTERP_CUBIC | WP_INTERP_LINEAR                      */
-    int32_t kernelgen;      /* WP_KG_FP32 | WP_KG_TF32X3                               */
+    int32_t kernelgen;      /* WP_KG_FP32 | WP_KG_TF32X3 | WP_KG_PROJSLICE             */
     int32_t grid_tile;      /* gridding tile side in cells: 0 (default, 64), 32 or 64    */
     int32_t grid_method;    /* 0 (default): register tile, lanes own grid cells;
                                1: shared-memory tile, footprint spread over the lanes;

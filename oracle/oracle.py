@@ -280,11 +280,15 @@ def layout(geom: Geometry, support_arr) -> np.ndarray:
     return np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
 
 
-def wkernels(geom: Geometry, taper: np.ndarray, w_planes, supports=None, with_cache: bool = True) -> KernelSet:
-    """Hankel w-kernels for every plane: screen, transform, truncate, spline, resample.
+def wkernels(geom: Geometry, taper: np.ndarray, w_planes, supports=None, with_cache: bool = True,
+             route: str = "hankel") -> KernelSet:
+    """w-kernels for every plane: radial line, truncate, spline, resample.  The radial line
+    comes from the matrix Hankel transform (route="hankel", Section 4.3) or from the
+    projection-slice theorem on the undersampled workspace (route="projslice", Section 4.3.1).
     with_cache=False stops after the radial lines and supports (cache left empty)."""
     w_planes = _f64(w_planes)
-    radial = np.stack([radial_kernel(geom, taper, w) for w in w_planes])
+    line = radial_kernel if route == "hankel" else projslice_radial
+    radial = np.stack([line(geom, taper, w) for w in w_planes])
     if supports is None:
         sup = np.array([support(geom, radial[p]) for p in range(len(w_planes))], dtype=np.int32)
     else:
@@ -301,6 +305,36 @@ def wkernels(geom: Geometry, taper: np.ndarray, w_planes, supports=None, with_ca
 # --------------------------------------------------------------------------------------
 # Standard w-projection kernels by 2D FFT (Alg. 1 steps 4-11, workspace undersampling)
 # --------------------------------------------------------------------------------------
+def workspace_image(geom: Geometry, taper: np.ndarray, w: float):
+    """Image-domain convolution function on the undersampled M x M workspace (Section 4.2;
+    Alg. 1 steps 5-8, Alg. 2 steps 4-8): taper x w-screen at the pixel centres l = j FOV/M,
+    j = -M/2 .. M/2-1, zero outside the disc r <= r_max = (M/2) FOV/M (decided on the integer
+    offsets).  Returns (f [m][l], j, pixel size)."""
+    M = workspace_size(geom.max_support)
+    dlw = geom.fov / M
+    j = np.arange(M) - M // 2
+    l = j * dlw
+    L, Mm = np.meshgrid(l, l, indexing="xy")      # [m][l]
+    r = np.hypot(L, Mm)
+    inside = (j[None, :] ** 2 + j[:, None] ** 2) <= (M // 2) ** 2
+    t = np.where(inside, taper_at(geom, taper, np.minimum(r, geom.r_max)), 0.0)
+    n = np.sqrt(1.0 - r * r)
+    return t * np.exp(2j * np.pi * w * (n - 1.0)), j, dlw
+
+
+def projslice_radial(geom: Geometry, taper: np.ndarray, w: float) -> np.ndarray:
+    """Radial kernel line by the projection-slice theorem (Section 4.3.1, Alg. 2 steps 9-12):
+    the workspace image is projected onto the l axis (summed over m), zero padded to M*os and
+    transformed by a 1D FFT; sample k sits at uv offset k du/os on the v = 0 slice.  Scaled
+    like the 2D route: (FOV/M)^2 du^2.  Samples k >= M*os wrap periodically."""
+    f, j, dlw = workspace_image(geom, taper, w)
+    Lp = f.shape[0] * geom.oversampling
+    X = np.zeros(Lp, dtype=np.complex128)
+    X[j % Lp] = f.sum(axis=0)
+    Y = np.fft.fft(X) * (dlw ** 2) * geom.du ** 2
+    return Y[np.arange(geom.k_out) % Lp]
+
+
 def fft_wkernel(geom: Geometry, taper: np.ndarray, w: float, S: int, circular: bool = True) -> np.ndarray:
     """Kernel cache of one plane by the 2D FFT route (Alg. 1 with Section 4.2).
 
@@ -311,19 +345,10 @@ def fft_wkernel(geom: Geometry, taper: np.ndarray, w: float, S: int, circular: b
     The image-domain function is zero outside the disc r <= r_max so that the two
     routes transform the same function; with circular=True taps beyond radius S are
     zeroed as in the Hankel route."""
-    M = workspace_size(geom.max_support)
+    f, j, dlw = workspace_image(geom, taper, w)
+    M = f.shape[0]
     os_ = geom.oversampling
     Lp = M * os_
-    dlw = geom.fov / M
-    j = np.arange(M) - M // 2
-    l = j * dlw
-    L, Mm = np.meshgrid(l, l, indexing="xy")      # [m][l]
-    r = np.hypot(L, Mm)
-    # inside the disc r <= r_max = (M/2) dlw, decided on the integer pixel offsets
-    inside = (j[None, :] ** 2 + j[:, None] ** 2) <= (M // 2) ** 2
-    t = np.where(inside, taper_at(geom, taper, np.minimum(r, geom.r_max)), 0.0)
-    n = np.sqrt(1.0 - r * r)
-    f = t * np.exp(2j * np.pi * w * (n - 1.0))
     X = np.zeros((Lp, Lp), dtype=np.complex128)
     X[np.ix_(j % Lp, j % Lp)] = f
     Y = np.fft.fft2(X) * (dlw ** 2) * geom.du ** 2

@@ -35,7 +35,8 @@ int make_geom(const wp_plan* plan, Geom* g) {
     if (!(plan->trunc_frac < 1.0)) return WP_ERR_PLAN;
     if (plan->radial_samples < 8 || plan->radial_samples > 65536) return WP_ERR_PLAN;
     if (plan->interp != WP_INTERP_CUBIC && plan->interp != WP_INTERP_LINEAR) return WP_ERR_PLAN;
-    if (plan->kernelgen != WP_KG_FP32 && plan->kernelgen != WP_KG_TF32X3) return WP_ERR_PLAN;
+    if (plan->kernelgen != WP_KG_FP32 && plan->kernelgen != WP_KG_TF32X3 && plan->kernelgen != WP_KG_PROJSLICE)
+        return WP_ERR_PLAN;
     if (plan->grid_tile != 0 && plan->grid_tile != 32 && plan->grid_tile != 64) return WP_ERR_PLAN;
     if (plan->grid_method < 0 || plan->grid_method > 3) return WP_ERR_PLAN;
     g->N = N;
@@ -70,6 +71,9 @@ size_t carve_kg(const Geom& g, int P, void* ws, size_t bytes, KgWork* out) {
     w.band = c.take<float>((size_t)g.k_out * 65);
     w.nm1 = c.take<double>((size_t)g.r_pad);
     w.nm1f = c.take<float2>((size_t)g.r_pad);
+    const bool ps = (g.kernelgen == WP_KG_PROJSLICE);
+    w.ps_nm1 = c.take<float2>(ps ? (size_t)g.fft_m * g.fft_m : 0);
+    w.ps_x = c.take<float2>(ps ? (size_t)P * g.fft_m * g.os : 0);
     w.f32 = c.take<float>(fk);
     w.f_hi = c.take<float>(fk);
     w.f_lo = c.take<float>(fk);
@@ -148,6 +152,7 @@ const char* wp_strerror(int code) {
 void wp_release(void) {
     release_fft_plans();
     release_fft_kernelgen_plans();
+    release_ps_plans();
 }
 
 int wp_plan_geometry(const wp_plan* plan, wp_geometry* geom) {
@@ -228,11 +233,15 @@ int wp_hankel_radial(const wp_plan* plan, const float* taper, const double* w_pl
     cudaStream_t st = (cudaStream_t)stream;
     KgWork w;
     carve_kg(g, P, workspace, workspace_bytes, &w);
-    if ((rc = kg_screen(g, w, taper, w_planes, P, st))) return rc;
-    if (g.kernelgen == WP_KG_TF32X3)
-        rc = kg_gemm_tf32x3(g, w, P, reinterpret_cast<float2*>(radial), w.status, st);
-    else
-        rc = kg_gemm_fp32(g, w, P, reinterpret_cast<float2*>(radial), st);
+    if (g.kernelgen == WP_KG_PROJSLICE) {
+        rc = kg_projslice(g, w, taper, w_planes, P, reinterpret_cast<float2*>(radial), st);
+    } else {
+        if ((rc = kg_screen(g, w, taper, w_planes, P, st))) return rc;
+        if (g.kernelgen == WP_KG_TF32X3)
+            rc = kg_gemm_tf32x3(g, w, P, reinterpret_cast<float2*>(radial), w.status, st);
+        else
+            rc = kg_gemm_fp32(g, w, P, reinterpret_cast<float2*>(radial), st);
+    }
     if (rc) return rc;
     return kg_trunc_spline(g, w, P, reinterpret_cast<const float2*>(radial),
                            reinterpret_cast<float2*>(spline_m), support, st);
@@ -427,6 +436,7 @@ int wp_hankel_adjoint(const wp_plan* plan, const double* w_planes, int32_t P, vo
     if (P < 1 || P > 65536) return WP_ERR_SIZE;
     if (!w_planes || !workspace || !grad_radial || !grad_taper) return WP_ERR_NULL;
     if (g.interp == WP_INTERP_CUBIC && !grad_spline_m) return WP_ERR_NULL;
+    if (g.kernelgen == WP_KG_PROJSLICE) return WP_ERR_UNSUPPORTED;   // the adjoint is the matrix route's
     if (!aligned256(workspace) || workspace_bytes < carve_kg(g, P, nullptr, 0, nullptr)) return WP_ERR_WORKSPACE;
     if ((rc = check_device())) return rc;
     KgWork w;

@@ -79,6 +79,8 @@ struct KgWork {
     float* band;       // [65][k_out] spline inverse band (row d holds A^-1[k][k + d - 32])
     double* nm1;       // [R] n - 1 = sqrt(1 - r_i^2) - 1 at the radial nodes
     float2* nm1f;      // [R] the same as an unevaluated float pair (hi, lo)
+    float2* ps_nm1;    // [M * M] n - 1 at the workspace pixels as float pairs (projection route)
+    float2* ps_x;      // [P][M os] projected, zero-padded lines, transformed in place (projection route)
     float* f32;        // [2 P_pad][r_pad] image-domain functions (FP32 path)
     float* f_hi;       // [2 P_pad][r_pad]
     float* f_lo;       // [2 P_pad][r_pad]
@@ -116,6 +118,9 @@ int kg_gemm_tf32x3(const Geom& g, const KgWork& w, int P, float2* radial, int* s
                    cudaStream_t st);
 int kg_gemm_tf32x3_ex(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st,
                       long long budget, int withhold_loads);
+int kg_ps_prepare(const Geom& g, const KgWork& w, cudaStream_t st);
+int kg_projslice(const Geom& g, const KgWork& w, const float* taper, const double* w_planes, int P,
+                 float2* radial, cudaStream_t st);
 int kg_trunc_spline(const Geom& g, const KgWork& w, int P, const float2* radial, float2* spline_m,
                     int32_t* support, cudaStream_t st);
 int kg_resample(const Geom& g, int P, const float2* radial, const float2* spline_m,
@@ -142,6 +147,7 @@ int fft_wkernels(const Geom& g, const float* taper, const double* w_planes, int 
                  const int64_t* offsets, int circular, void* ws, size_t ws_bytes, float2* cache,
                  cudaStream_t st);
 void release_fft_kernelgen_plans();
+void release_ps_plans();
 
 // plane values (planes.cu)
 size_t plane_values_workspace_bytes(int64_t V);

@@ -87,6 +87,21 @@ def test_layout_and_argument_errors():
     assert lib.wp_version() >= 100
 
 
+def test_projection_route_plan_and_workspace():
+    """The projection-slice route is a valid kernelgen value; its workspace holds the
+    workspace-pixel n - 1 table and the padded lines (more than the matrix route at a small
+    R), and the Hankel adjoint (the matrix route's) refuses it before any device work."""
+    L, lib = _lib()
+    ps = L.WpPlan(256, 1e-4, 8, 15, 3, 0.01, 512, 0, L.KERNELGEN["projslice"], 0, 0)
+    g = L.WpGeometry()
+    assert lib.wp_plan_geometry(ctypes.byref(ps), ctypes.byref(g)) == 0
+    mx = L.WpPlan(256, 1e-4, 8, 15, 3, 0.01, 512, 0, L.KERNELGEN["tf32x3"], 0, 0)
+    assert lib.wp_kernelgen_workspace_bytes(ctypes.byref(ps), 1000) > \
+        lib.wp_kernelgen_workspace_bytes(ctypes.byref(mx), 1000) - 3 * 256 * 512 * 4
+    ws = ctypes.c_void_p(256)
+    assert lib.wp_hankel_adjoint(ctypes.byref(ps), ws, 4, ws, 1 << 40, ws, ws, ws, None) == -8
+
+
 def test_product_path_refuses_to_run_without_library(monkeypatch, tmp_path):
     from paper_1904_08463_gb300 import _lib as L
 

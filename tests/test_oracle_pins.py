@@ -238,6 +238,49 @@ def test_fft_route_agrees_with_hankel_route():
         assert np.linalg.norm(hk - fk) / np.linalg.norm(hk) < 5e-6
 
 
+def test_projslice_line_is_v0_slice_of_2d_route():
+    """Section 4.3.1: the 1D transform of the workspace image projected onto l is the v = 0
+    slice of its 2D transform -- exactly, for the discrete transforms.  Sample k of the
+    projection route's line is tap (jx, S) of sub-kernel (fu, 0) of the 2D-FFT route with
+    os (jx - S) - fu = k, here at w = 0 and at a w whose screen wraps many turns."""
+    g = o.Geometry(96, np.deg2rad(3.0) / 96, 4, 12, 1, 0.0, 512)
+    tap = o.gaussian_taper(g)
+    S, os_ = g.max_support, g.oversampling
+    for w in (0.0, 700.0):
+        line = o.projslice_radial(g, tap, w)
+        full = o.fft_wkernel(g, tap, w, S, circular=False)        # [fv][fu][jy][jx]
+        k = np.arange(os_ * S + 1)
+        m = -(-k // os_)                                          # ceil(k / os)
+        fu = os_ * m - k
+        ref = full[0, fu, S, S + m]
+        assert np.abs(line[k] - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_projslice_gaussian_closed_form():
+    """A Gaussian taper exp(-r^2 / (2 s^2)) at w = 0 transforms to 2 pi s^2 exp(-2 pi^2 s^2 rho^2);
+    with 12.8 workspace pixels per s and the disc edge at 10 s, the projection route's line
+    (in tap units, times du^2) matches it to the taper's linear interpolation (~1e-6)."""
+    g = o.Geometry(256, np.deg2rad(2.0) / 256, 2, 127, 1, 0.0, 4096)
+    s_ = 0.05 * g.fov
+    tap = np.exp(-g.r_nodes() ** 2 / (2 * s_ * s_))
+    line = o.projslice_radial(g, tap, 0.0)
+    rho = g.rho()
+    ref = 2 * np.pi * s_ ** 2 * np.exp(-2 * np.pi ** 2 * s_ ** 2 * rho ** 2) * g.du ** 2
+    n = 2 * g.oversampling * 10                  # out to 10 uv cells (the kernel is ~1e-30 there)
+    assert np.abs(line[:n] - ref[:n]).max() < 2e-6 * ref[0]
+    assert np.abs(line[:n].imag).max() < 1e-12 * ref[0]
+
+
+def test_projslice_route_agrees_with_hankel_route():
+    """Both routes approximate the same 2D transform of a radially symmetric function: for a
+    taper that vanishes smoothly inside the disc their caches agree to discretisation error."""
+    g, a, tap = _paraxial_geometry(4096)
+    for w in (0.0, 20000.0):
+        hk = o.resample(g, o.radial_kernel(g, tap, w), 10)
+        pk = o.resample(g, o.projslice_radial(g, tap, w), 10)
+        assert np.linalg.norm(hk - pk) / np.linalg.norm(hk) < 5e-6
+
+
 # ------------------------------------------------------------------------------ binning
 def test_binning_rules():
     N, dl, os_ = 64, 1e-3, 8
