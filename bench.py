@@ -39,7 +39,8 @@ import synth  # noqa: E402
 RESAMPLE_TRAFFIC = {"bytes_per_launch": 5.931e9, "source_sha1": "8fe9f3a2b9c0"}
 
 GRID_METHOD_NAMES = {0: "register tile", 1: "shared-memory tile, footprint over the lanes (atomics)",
-                     2: "warp-private shared-memory tiles", 3: "shared-memory tile, rows owned by warps"}
+                     2: "warp-private shared-memory tiles", 3: "shared-memory tile, rows owned by warps",
+                     4: "rows owned by warps, taps interpolated from the radial line"}
 
 METRIC = "w-kernels/s (Hankel vs 2D-FFT) and Mvis/s gridded, 1 GB300, at stated FP64 error"
 N_IMG, FOV_DEG, R_KG, OS = 4096, 8.0, 4096, 8
@@ -516,7 +517,7 @@ def run_imaging(args, dev):
     stats = torch.zeros(2, dtype=torch.float64, device=dev)
     radial = torch.empty((P, plan.geometry().k_out), dtype=torch.complex64, device=dev)
     spl = torch.empty_like(radial)
-    wk = wp.WKernels(wpl, sup, off, cache)
+    wk = wp.WKernels(wpl, sup, off, cache, radial, spl)
     # the gridder's launch shape (method x tile) is picked by the autotuner on this problem
     from paper_1904_08463_gb300.autotune import GRID_CHOICES, Autotuner
 

@@ -91,7 +91,10 @@ typedef struct wp_plan {
                                2: per-warp shared-memory 32 x 32 tiles, groups of 8 planes
                                per work item (grid_tile ignored);
                                3: shared-memory tile, each warp owning every 8th row, lanes
-                               across the footprint's columns (no atomics in the tile).
+                               across the footprint's columns (no atomics in the tile);
+                               4: as 3, each tap interpolated on the fly from the plane's
+                               radial line (wp_wkernels.radial / spline_m) instead of
+                               read from the cache.
                                grid_tile and grid_method are tuning choices only: the
                                results agree to FP32 rounding order                      */
 } wp_plan;
@@ -121,6 +124,10 @@ typedef struct wp_wkernels {
     const int32_t* support;   /* [P] support S_p, min_support <= S_p <= max_support    */
     const int64_t* offsets;   /* [P+1] complex-element offsets into cache              */
     const float*   cache;     /* interleaved complex taps                              */
+    const float*   radial;    /* [P][K_out] complex radial lines (wp_hankel_radial);
+                                 read only by gridding with grid_method 4, which then
+                                 needs no cache (cache may be NULL)                     */
+    const float*   spline_m;  /* [P][K_out] spline second derivatives (cubic, method 4) */
 } wp_wkernels;
 
 /* ---- plan helpers (host only, no device work) -------------------------------------- */

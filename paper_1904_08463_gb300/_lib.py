@@ -62,6 +62,8 @@ class WpWkernels(ctypes.Structure):
         ("support", c_void_p),
         ("offsets", c_void_p),
         ("cache", c_void_p),
+        ("radial", c_void_p),
+        ("spline_m", c_void_p),
     ]
 
 

@@ -53,7 +53,7 @@ class Plan:
     interp: str = "cubic"
     kernelgen: str = "fp32"
     grid_tile: int = 0          # gridding tile side (0 = default 64; 32 or 64): tuning only
-    grid_method: int = 3        # 3 row-owned shared tile (fastest measured), 0 register tile, 1/2: tuning only
+    grid_method: int = 3        # 3 row-owned shared tile (fastest measured), 0 register tile, 1/2/4: tuning only
 
     def c(self) -> _lib.WpPlan:
         return _lib.WpPlan(self.image_size, self.cell_size, self.oversampling, self.max_support,
@@ -87,7 +87,10 @@ class WKernels:
 
     def c(self) -> _lib.WpWkernels:
         return _lib.WpWkernels(self.P, 0, self.w_planes.data_ptr(), self.support.data_ptr(),
-                               self.offsets.data_ptr(), self.cache.data_ptr())
+                               self.offsets.data_ptr(),
+                               self.cache.data_ptr() if self.cache is not None else None,
+                               self.radial.data_ptr() if self.radial is not None else None,
+                               self.spline_m.data_ptr() if self.spline_m is not None else None)
 
     def subkernel(self, p: int, os_: int, support_host=None) -> torch.Tensor:
         s = int(self.support[p]) if support_host is None else int(support_host[p])

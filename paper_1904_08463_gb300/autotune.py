@@ -2,8 +2,9 @@
 
 Three choices do not change results, only speed: the kernel-generation route of the Hankel
 transform (FP32 SIMT or tcgen05 TF32x3 matrix product -- both meet the kernel tolerance),
-and the gridder's method (register tile with lanes owning cells, or shared-memory tile with
-the footprint spread over the lanes) and tile side (32 or 64 cells).  For a problem class -- grid size, plane
+and the gridder's method (register tile; shared-memory tiles with the footprint spread over
+the lanes, per-warp copies, or warp-owned rows; warp-owned rows with taps interpolated from
+the radial line) and tile side (32 or 64 cells).  For a problem class -- grid size, plane
 count, maximum support, visibility count, each bucketed -- the tuner times every
 candidate on the problem itself with CUDA events and keeps the fastest; the table can be
 saved as JSON and reloaded so that a tuned class is never timed again.
@@ -19,7 +20,7 @@ import torch
 
 KERNELGEN_CHOICES = ("fp32", "tf32x3")
 TILE_CHOICES = (32, 64)
-GRID_CHOICES = tuple((m, t) for m in (0, 1, 3) for t in TILE_CHOICES) + ((2, 32),)   # (grid_method, grid_tile)
+GRID_CHOICES = tuple((m, t) for m in (0, 1, 3, 4) for t in TILE_CHOICES) + ((2, 32),)   # (grid_method, grid_tile)
 
 
 def _bucket(x: int) -> int:

@@ -38,7 +38,7 @@ int make_geom(const wp_plan* plan, Geom* g) {
     if (plan->kernelgen != WP_KG_FP32 && plan->kernelgen != WP_KG_TF32X3 && plan->kernelgen != WP_KG_PROJSLICE)
         return WP_ERR_PLAN;
     if (plan->grid_tile != 0 && plan->grid_tile != 32 && plan->grid_tile != 64) return WP_ERR_PLAN;
-    if (plan->grid_method < 0 || plan->grid_method > 3) return WP_ERR_PLAN;
+    if (plan->grid_method < 0 || plan->grid_method > 4) return WP_ERR_PLAN;
     g->N = N;
     g->dl = plan->cell_size;
     g->du = 1.0 / ((double)N * plan->cell_size);
@@ -355,12 +355,17 @@ size_t wp_grid_workspace_bytes(const wp_plan* plan, int32_t P, int64_t V) {
 }
 
 static int check_grid_args(const wp_plan* plan, const wp_wkernels* k, const float* uvw, int64_t V,
-                           void* workspace, size_t workspace_bytes, Geom* g) {
+                           void* workspace, size_t workspace_bytes, Geom* g, bool gridding = false) {
     int rc = make_geom(plan, g);
     if (rc) return rc;
     if (!k || !workspace) return WP_ERR_NULL;
     if (k->P < 1 || k->P > 8192) return WP_ERR_SIZE;
-    if (!k->w_planes || !k->support || !k->offsets || !k->cache) return WP_ERR_NULL;
+    if (!k->w_planes || !k->support || !k->offsets) return WP_ERR_NULL;
+    if (gridding && g->grid_method == 4) {      // taps from the radial lines, no cache
+        if (!k->radial || (g->interp == WP_INTERP_CUBIC && !k->spline_m)) return WP_ERR_NULL;
+    } else if (!k->cache) {
+        return WP_ERR_NULL;
+    }
     if (V < 0 || V > 2147483647LL) return WP_ERR_SIZE;
     if (V > 0 && !uvw) return WP_ERR_NULL;
     if ((int64_t)k->P * ((g->N + 63) / 64) * ((g->N + 63) / 64) >= 2147483647LL) return WP_ERR_SIZE;
@@ -374,7 +379,7 @@ int wp_grid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw, c
             double* stats, void* stream) {
     WP_RANGE("wp_grid");
     Geom g;
-    int rc = check_grid_args(plan, kernels, uvw, V, workspace, workspace_bytes, &g);
+    int rc = check_grid_args(plan, kernels, uvw, V, workspace, workspace_bytes, &g, true);
     if (rc) return rc;
     if (!grid || (V > 0 && !vis)) return WP_ERR_NULL;
     cudaStream_t st = (cudaStream_t)stream;

@@ -571,6 +571,131 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_ro(int N, int os, int 
     }
 }
 
+// On-the-fly taps (grid_method 4): the row-owned tile of method 3, but each tap is
+// interpolated from the plane's radial line in shared memory (the resample's own evaluation,
+// so the values are the cache's bits) instead of being read from the cache.  The line is
+// staged once per run of consecutive items of the same plane.
+template <int TILE, bool CUBIC>
+__global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_otf(int N, int os, int s_max, int K, int ntx, int ntiles,
+                                                              const int32_t* __restrict__ support,
+                                                              const float2* __restrict__ radial,
+                                                              const float2* __restrict__ spline_m,
+                                                              const int* __restrict__ start,
+                                                              const int4* __restrict__ srec,
+                                                              const float2* __restrict__ svis,
+                                                              const int* __restrict__ items,
+                                                              int* __restrict__ ctrl, float2* __restrict__ grid) {
+    constexpr int CH = TILE / 32;
+    extern __shared__ float4 line[];              // skew(n_used) entries {y.re, y.im, m.re, m.im}
+    __shared__ float2 tile[TILE * TILE];
+    __shared__ int l_j[RO_LIST];                  // first footprint column | first row << 16
+    __shared__ int l_f[RO_LIST];                  // fu | fv << 8
+    __shared__ uint32_t l_geo[RO_LIST];           // r0 | r1 << 8 | c0 << 16 | (w - 1) << 24 | conj << 31
+    __shared__ float2 l_vv[RO_LIST];
+    __shared__ int s_item, s_n;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int n_items = ctrl[1];
+    int line_p = -1;
+    for (int i = threadIdx.x; i < TILE * TILE; i += blockDim.x) tile[i] = make_float2(0.0f, 0.0f);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&ctrl[0], 1);
+        __syncthreads();
+        const int item_idx = s_item;
+        __syncthreads();
+        if (item_idx >= n_items) break;
+        const int item = items[item_idx];
+        const int p = item / ntiles;
+        const int t = item - p * ntiles;
+        const int oy = t / ntx, ox = t - oy * ntx;
+        const int S = min(max(support[p], 1), s_max);
+        const int lim = os * S, lim2 = lim * lim;
+        if (p != line_p) {                        // block-uniform: every thread saw the same item
+            const int n_used = min(K, lim + 2);
+            const float2* yl = radial + (int64_t)p * K;
+            const float2* ml = spline_m + (int64_t)p * K;
+            for (int k = threadIdx.x; k < n_used; k += blockDim.x) {
+                const float2 a = yl[k];
+                const float2 b = CUBIC ? ml[k] : make_float2(0.0f, 0.0f);
+                line[skew(k)] = make_float4(a.x, a.y, b.x, b.y);
+            }
+            line_p = p;
+            __syncthreads();
+        }
+        const int D = (S + TILE - 1) / TILE;
+        const int ty0 = oy * TILE, tx0 = ox * TILE;
+        const int cx_lo = max(0, ox - D), cx_hi = min(ntx - 1, ox + D);
+        for (int cy = max(0, oy - D); cy <= min(ntx - 1, oy + D); ++cy) {
+            const int kb = p * ntiles + cy * ntx;
+            const int beg = start[kb + cx_lo], end = start[kb + cx_hi + 1];
+            for (int base = beg; base < end; base += RO_LIST) {
+                if (threadIdx.x == 0) s_n = 0;
+                __syncthreads();
+                const int q = base + (int)threadIdx.x;
+                if (q < end) {
+                    const int4 r4 = __ldg(srec + q);
+                    const int iu = r4.x & 0xffff, iv = (r4.x >> 16) & 0xffff;
+                    const int c0 = max(iu - S, tx0), c1 = min(iu + S, tx0 + TILE - 1);
+                    const int r0 = max(iv - S, ty0), r1 = min(iv + S, ty0 + TILE - 1);
+                    if (c0 <= c1 && r0 <= r1) {
+                        const int slot = atomicAdd(&s_n, 1);
+                        l_j[slot] = (c0 - (iu - S)) | ((r0 - (iv - S)) << 16);
+                        l_f[slot] = r4.y & 0xffff;
+                        l_geo[slot] = (uint32_t)(r0 - ty0) | ((uint32_t)(r1 - ty0) << 8) |
+                                      ((uint32_t)(c0 - tx0) << 16) | ((uint32_t)(c1 - c0) << 24) |
+                                      ((uint32_t)((r4.y >> 16) & 1) << 31);
+                        l_vv[slot] = __ldg(svis + q);
+                    }
+                }
+                __syncthreads();
+                const int n = s_n;
+                for (int e = 0; e < n; ++e) {
+                    const uint32_t geo = l_geo[e];
+                    const int r0 = (int)(geo & 0xff), r1 = (int)((geo >> 8) & 0xff);
+                    const int rw = r0 + ((wid - r0) & (GRID_WARPS - 1));   // first owned row
+                    if (rw > r1) continue;
+                    const int c0 = (int)((geo >> 16) & 0xff), w = (int)((geo >> 24) & 0x7f) + 1;
+                    const float sgn = (geo >> 31) ? -1.0f : 1.0f;
+                    const float2 vv = l_vv[e];
+                    const int jx0 = l_j[e] & 0xffff, jy0 = l_j[e] >> 16;
+                    const int fu = l_f[e] & 0xff, fv = l_f[e] >> 8;
+                    // fine offsets of the first tap of the intersection's first owned row
+                    const int dx0 = os * (jx0 - S) - fu;
+                    int dy = os * (jy0 + (rw - r0) - S) - fv;
+                    float2* trow = tile + rw * TILE + c0;
+                    for (int r = rw; r <= r1; r += GRID_WARPS) {
+#pragma unroll
+                        for (int k = 0; k < CH; ++k) {
+                            const int c = lane + 32 * k;
+                            if (c < w) {
+                                const float2 tp = resample_tap<CUBIC>(line, dx0 + os * c, dy, lim2);
+                                const float ti = sgn * tp.y;
+                                float2 a = trow[c];
+                                a.x = fmaf(vv.x, tp.x, fmaf(-vv.y, ti, a.x));
+                                a.y = fmaf(vv.x, ti, fmaf(vv.y, tp.x, a.y));
+                                trow[c] = a;
+                            }
+                        }
+                        dy += os * GRID_WARPS;
+                        trow += GRID_WARPS * TILE;
+                    }
+                    __syncwarp();   // the next entry may touch this one's cells from other lanes
+                }
+                __syncthreads();   // the list is rebuilt for the next round
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < TILE * TILE; i += blockDim.x) {
+            const float2 a = tile[i];
+            if (a.x != 0.0f || a.y != 0.0f) {
+                const int gy = ty0 + i / TILE, gx = tx0 + (i & (TILE - 1));
+                if (gy < N && gx < N) atomicAdd(grid + (int64_t)gy * N + gx, a);
+                tile[i] = make_float2(0.0f, 0.0f);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Warp-private variant (grid_method 2): 32 x 32 output tiles, one shared-memory copy of the
 // tile per warp.  A work item is (group of PG consecutive planes, tile); each warp takes
 // whole visibilities of the item's planes (round robin) and spreads the footprint's
@@ -731,6 +856,28 @@ int grid_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, float2* 
         k_grid_wp<<<sms * per_sm, GRID_WARPS * 32, smem, st>>>(g.N, g.os, g.s_max, P, w.ntx, w.ntiles, kern->support,
                                                                kern->offsets, c2, w.count, w.srec, w.svis, w.items,
                                                                w.ctrl, grid);
+    } else if (g.grid_method == 4) {
+        int n_line = g.os * g.s_max + 2;
+        if (n_line > g.k_out) n_line = g.k_out;
+        n_line = (n_line + 7) / 8 * 8;
+        const size_t smem = (size_t)n_line * sizeof(float4);
+        const float2* rad = reinterpret_cast<const float2*>(kern->radial);
+        const float2* spl = reinterpret_cast<const float2*>(kern->spline_m);
+        const bool cubic = (g.interp == WP_INTERP_CUBIC);
+#define WP_LAUNCH_OTF(T, C)                                                                                     \
+        do {                                                                                                    \
+            WP_CUDA(cudaFuncSetAttribute(k_grid_otf<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+            WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_otf<T, C>, GRID_WARPS * 32, smem)); \
+            if (per_sm < 1) per_sm = 1;                                                                         \
+            k_grid_otf<T, C><<<sms * per_sm, GRID_WARPS * 32, smem, st>>>(g.N, g.os, g.s_max, g.k_out, w.ntx,   \
+                w.ntiles, kern->support, rad, spl, w.count, w.srec, w.svis, w.items, w.ctrl, grid);            \
+        } while (0)
+        if (w.T == 32) {
+            if (cubic) WP_LAUNCH_OTF(32, true); else WP_LAUNCH_OTF(32, false);
+        } else {
+            if (cubic) WP_LAUNCH_OTF(64, true); else WP_LAUNCH_OTF(64, false);
+        }
+#undef WP_LAUNCH_OTF
     } else if (g.grid_method == 3) {
         if (w.T == 32) {
             WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_ro<32>, GRID_WARPS * 32, 0));

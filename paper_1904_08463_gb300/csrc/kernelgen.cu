@@ -412,33 +412,7 @@ int kg_trunc_spline(const Geom& g, const KgWork& w, int P, const float2* radial,
 // The radius test q <= (os S)^2 is an exact integer test; x = sqrt(q) only picks the
 // spline interval and its weights, which are continuous across interval ends.
 // =======================================================================================
-__device__ __forceinline__ int skew(int k) { return k ^ ((k >> 3) & 7); }
-
-template <bool CUBIC>
-__device__ __forceinline__ float2 resample_tap(const float4* __restrict__ line, int dx, int dy, int lim2) {
-    const int q = dx * dx + dy * dy;
-    float2 out = make_float2(0.0f, 0.0f);
-    if (q <= lim2) {
-        const float qf = (float)q;
-        const float x = qf * rsqrtf(fmaxf(qf, 1.0f));   // q = 0 gives 0, else sqrt(q)
-        // round(x - 1/2) through the float mantissa (1.5 * 2^23): the interval index
-        const float tt = (x - 0.5f) + 12582912.0f;
-        const int k = __float_as_int(tt) - 0x4B400000;
-        const float a = x - (tt - 12582912.0f);
-        const float b = 1.0f - a;
-        const float4 L0 = line[skew(k)];
-        const float4 L1 = line[skew(k + 1)];
-        out.x = fmaf(b, L0.x, a * L1.x);
-        out.y = fmaf(b, L0.y, a * L1.y);
-        if (CUBIC) {
-            const float cb = (b * b - 1.0f) * b * (1.0f / 6.0f);
-            const float ca = (a * a - 1.0f) * a * (1.0f / 6.0f);
-            out.x = fmaf(cb, L0.z, fmaf(ca, L1.z, out.x));
-            out.y = fmaf(cb, L0.w, fmaf(ca, L1.w, out.y));
-        }
-    }
-    return out;
-}
+// skew() and resample_tap() live in wp_internal.cuh (the on-the-fly gridder uses them too).
 
 // Bulk (TMA) store from shared memory: a byte range, 16-byte aligned on both sides and a
 // multiple of 16 bytes long, written by the copy engine in whole cache lines.

@@ -53,7 +53,12 @@ extern "C" int wp_grid_static(const wp_plan* plan, const wp_wkernels* kernels, c
     if (rc) return rc;
     if (!kernels || !grid) return WP_ERR_NULL;
     if (kernels->P < 1 || kernels->P > 8192) return WP_ERR_SIZE;
-    if (!kernels->w_planes || !kernels->support || !kernels->offsets || !kernels->cache) return WP_ERR_NULL;
+    if (!kernels->w_planes || !kernels->support || !kernels->offsets) return WP_ERR_NULL;
+    if (g.grid_method == 4) {           // taps from the radial lines, no cache
+        if (!kernels->radial || (g.interp == WP_INTERP_CUBIC && !kernels->spline_m)) return WP_ERR_NULL;
+    } else if (!kernels->cache) {
+        return WP_ERR_NULL;
+    }
     if (V < 0 || V > 2147483647LL) return WP_ERR_SIZE;
     if (V > 0 && (!uvw || !vis)) return WP_ERR_NULL;
     if ((int64_t)kernels->P * ((g.N + 63) / 64) * ((g.N + 63) / 64) >= 2147483647LL) return WP_ERR_SIZE;

@@ -110,6 +110,44 @@ size_t carve_grid(const Geom& g, int P, int64_t V, void* ws, size_t bytes, GridW
 // ---------------------------------------------------------------------------------------
 // launchers (return WP_OK or an error code; all asynchronous on `st`)
 // ---------------------------------------------------------------------------------------
+// The kernel tap at fine offset (dx, dy) (units du/os) from the plane's radial line staged in
+// shared memory as {y.re, y.im, m.re, m.im} per sample, slot k at skew(k) (XOR swizzle within
+// each group of 8: neighbouring taps are up to os samples apart on the line).  The radius test
+// q = dx^2 + dy^2 <= lim2 = (os S)^2 is exact on integers; x = sqrt(q) only picks the spline
+// interval and its weights, which are continuous across interval ends.  Shared by the
+// resample (cache) and the on-the-fly gridder, so both produce the same bits.
+// ---------------------------------------------------------------------------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ int skew(int k) { return k ^ ((k >> 3) & 7); }
+
+template <bool CUBIC>
+__device__ __forceinline__ float2 resample_tap(const float4* __restrict__ line, int dx, int dy, int lim2) {
+    const int q = dx * dx + dy * dy;
+    float2 out = make_float2(0.0f, 0.0f);
+    if (q <= lim2) {
+        const float qf = (float)q;
+        const float x = qf * rsqrtf(fmaxf(qf, 1.0f));   // q = 0 gives 0, else sqrt(q)
+        // round(x - 1/2) through the float mantissa (1.5 * 2^23): the interval index
+        const float tt = (x - 0.5f) + 12582912.0f;
+        const int k = __float_as_int(tt) - 0x4B400000;
+        const float a = x - (tt - 12582912.0f);
+        const float b = 1.0f - a;
+        const float4 L0 = line[skew(k)];
+        const float4 L1 = line[skew(k + 1)];
+        out.x = fmaf(b, L0.x, a * L1.x);
+        out.y = fmaf(b, L0.y, a * L1.y);
+        if (CUBIC) {
+            const float cb = (b * b - 1.0f) * b * (1.0f / 6.0f);
+            const float ca = (a * a - 1.0f) * a * (1.0f / 6.0f);
+            out.x = fmaf(cb, L0.z, fmaf(ca, L1.z, out.x));
+            out.y = fmaf(cb, L0.w, fmaf(ca, L1.w, out.y));
+        }
+    }
+    return out;
+}
+#endif
+
+// ---------------------------------------------------------------------------------------
 int kg_prepare(const Geom& g, const KgWork& w, cudaStream_t st);
 int kg_screen(const Geom& g, const KgWork& w, const float* taper, const double* w_planes, int P,
               cudaStream_t st);

@@ -53,7 +53,7 @@ def test_small_imaging_grid_and_dirty_image():
     assert np.all(img[~o.disc_mask(g)] == 0)
 
 
-@pytest.mark.parametrize("grid_method", [0, 1, 2, 3])
+@pytest.mark.parametrize("grid_method", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("grid_tile", [32, 64])
 @pytest.mark.parametrize("V,seed", [(0, 1), (1, 2), (37, 3), (5000, 4)])
 def test_grid_edges_and_conjugation(V, seed, grid_tile, grid_method):
@@ -138,3 +138,35 @@ def test_plane_values_are_means_of_equal_count_chunks(V, P, seed):
     ref = o.mean_w_planes(uvw[:, 2].astype(np.float64), P)
     assert np.allclose(got, ref, rtol=1e-13, atol=0)
     assert np.all(np.diff(got) >= 0)
+
+
+@pytest.mark.parametrize("interp", ["cubic", "linear"])
+def test_on_the_fly_taps_need_no_cache_and_match_the_cache_gridder(interp):
+    """grid_method 4 interpolates every tap from the plane's radial line in shared memory with
+    the resample's own evaluation: with the cache pointer left NULL it grids the same values as
+    the cache-reading method 3 (to FP32 accumulation order) and as the oracle."""
+    import paper_1904_08463_gb300 as wp
+
+    dev = torch.device("cuda")
+    N, dl = 128, np.deg2rad(3.0) / 128
+    planes = np.array([0.0, 90.0, 260.0, 700.0])
+    sup = np.array([2, 5, 9, 14])
+    plan = wp.Plan(N, dl, 8, 14, 1, 0.0, 256, interp, "fp32", 64, 3)
+    taper = synth.gaussian_taper_samples(N, dl, 256)
+    wk = wp.make_wkernels(plan, torch.tensor(taper, dtype=torch.float32, device=dev), planes, supports=sup)
+    rng = np.random.default_rng(11)
+    V = 3000
+    uvw = np.stack([rng.uniform(-N / 2 + 16, N / 2 - 16, V) / (N * dl), rng.uniform(-N / 2 + 16, N / 2 - 16, V) / (N * dl),
+                    rng.uniform(-800, 800, V)], 1).astype(np.float32)
+    vis = (rng.normal(size=V) + 1j * rng.normal(size=V)).astype(np.complex64)
+    u_d, v_d = torch.tensor(uvw, device=dev).reshape(-1), torch.tensor(vis, device=dev)
+    G3, _ = wp.grid(plan, wk, u_d, v_d)
+    wk_nocache = wp.WKernels(wk.w_planes, wk.support, wk.offsets, None, wk.radial, wk.spline_m)
+    G4, _ = wp.grid(plan.replace(grid_method=4), wk_nocache, u_d, v_d)
+    G3, G4 = G3.cpu().numpy(), G4.cpu().numpy()
+    assert np.abs(G4 - G3).max() <= 2e-6 * np.abs(G3).max()
+    g = o.Geometry(N, dl, 8, 14, 1, 0.0, 256, 0 if interp == "cubic" else 1)
+    ks = o.wkernels(g, f32(taper), planes, supports=sup)
+    b = o.bin_vis(g, uvw, planes, sup)
+    Go = o.grid(g, ks, b, vis.astype(np.complex128))
+    assert rel_l2(G4, Go) < 1e-5
