@@ -725,6 +725,88 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_sweep(args):
+    """Kernel-generation cost along the paper's scaling axes (its Figs. 3-7: number of
+    w-planes, kernel support, oversampling) on the headline geometry (4096^2, 8 deg, R 4096,
+    Gaussian taper, |w| linspace[0, 20000], every plane at the sweep's support), for the
+    matrix Hankel route (TF32x3), the projection-slice Hankel route and the standard 2D-FFT
+    route.  Each route's time covers the radial line (or the 2D transform) and the
+    oversampled cache of every plane.  Prints one JSON line with the table."""
+    import ctypes
+
+    import torch
+
+    import paper_1904_08463_gb300 as wp
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    dl = np.deg2rad(FOV_DEG) / N_IMG
+    taper_d = torch.tensor(synth.gaussian_taper_samples(N_IMG, dl, R_KG), dtype=torch.float32, device=dev)
+    lib = wp._lib.load()
+
+    def timeit(fn, n):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    def point(P, S, os_):
+        plan = wp.Plan(N_IMG, dl, os_, S, 1, 0.0, R_KG, "cubic", "tf32x3")
+        wpl = torch.tensor(np.linspace(0.0, 20000.0, P), dtype=torch.float64, device=dev)
+        sup_h = [S] * P
+        sup = torch.tensor(sup_h, dtype=torch.int32, device=dev)
+        off_h = wp.kernel_layout(plan, sup_h)
+        off = torch.tensor(off_h, dtype=torch.int64, device=dev)
+        cache = torch.empty(off_h[-1], dtype=torch.complex64, device=dev)
+        g = plan.geometry()
+        radial = torch.empty((P, g.k_out), dtype=torch.complex64, device=dev)
+        spl = torch.empty_like(radial)
+        out = {"planes": P, "support": S, "oversampling": os_, "cache_gb": off_h[-1] * 8 / 1e9}
+        for route in ("tf32x3", "projslice"):
+            pr = plan.replace(kernelgen=route)
+            ws = wp.workspace(wp.kernelgen_workspace_bytes(pr, P), dev)
+            wp.kernelgen_prepare(pr, P, ws)
+
+            def run(pr=pr, ws=ws):
+                wp.hankel_radial(pr, taper_d, wpl, ws, radial, spl)
+                wp.resample(pr, radial, spl, sup, off, cache)
+
+            out[route + "_ms"] = timeit(run, 5)
+            del ws
+        fws = wp.workspace(int(lib.wp_fft_workspace_bytes(ctypes.byref(plan.c()), P)), dev)
+
+        def fft():
+            wp._lib.check("wp_fft_wkernels", lib.wp_fft_wkernels(
+                ctypes.byref(plan.c()), ctypes.c_void_p(taper_d.data_ptr()), ctypes.c_void_p(wpl.data_ptr()), P,
+                ctypes.c_void_p(sup.data_ptr()), ctypes.c_void_p(off.data_ptr()), 1,
+                ctypes.c_void_p(fws.data_ptr()), fws.numel(), ctypes.c_void_p(cache.data_ptr()),
+                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+
+        out["fft2d_ms"] = timeit(fft, 2)
+        out["fft2d_over_tf32x3"] = out["fft2d_ms"] / out["tf32x3_ms"]
+        out["fft2d_over_projslice"] = out["fft2d_ms"] / out["projslice_ms"]
+        del fws, cache
+        torch.cuda.empty_cache()
+        log(f"sweep {out}")
+        return out
+
+    rows = []
+    for P in (16, 64, 256, 1024):
+        rows.append(dict(axis="planes", **point(P, 127, 8)))
+    for S in (31, 63, 255, 511):
+        rows.append(dict(axis="support", **point(64, S, 8)))
+    for os_ in (1, 2, 4, 16):
+        rows.append(dict(axis="oversampling", **point(64, 127, os_)))
+    print(json.dumps({"sweep": "kernel generation: matrix Hankel (TF32x3), projection-slice Hankel, 2D FFT",
+                      "geometry": "4096^2, 8 deg, R 4096, Gaussian taper, |w| linspace[0, 20000], all planes "
+                                  "at the listed support", "rows": rows}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -748,10 +830,14 @@ def main():
                     help="profiling aid: time only screen + Hankel product + spline (no cache)")
     ap.add_argument("--plane-stride", type=int, default=1,
                     help="use every n-th |w| plane of the batch (small cases for profiling)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="kernel-generation cost over planes / support / oversampling for the three routes")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3
-    if args.impl == "reference":
+    if args.sweep:
+        run_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
