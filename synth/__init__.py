@@ -38,6 +38,20 @@ def gaussian_taper_samples(image_size: int, cell_size: float, radial_samples: in
     return np.exp(-0.5 * (r / s) ** 2)
 
 
+def pswf_taper_samples(image_size: int, cell_size: float, radial_samples: int,
+                       c: float = 3.0 * np.pi) -> np.ndarray:
+    """Radially symmetric prolate spheroidal anti-aliasing function: the order-0 angular
+    prolate spheroidal function psi(c, x) (scipy's pro_ang1, normalised to psi(0) = 1) taken
+    along the radius, x = r / r_max, sampled at the radial nodes r_i = (i + 1/2) r_max / R.
+    Its transform is concentrated within about c / pi uv cells; c = 3 pi matches the
+    classic six-cell-wide gridding function."""
+    import scipy.special as sp
+
+    x = (np.arange(radial_samples, dtype=np.float64) + 0.5) / radial_samples
+    psi = sp.pro_ang1(0, 0, c, x)[0]
+    return psi / sp.pro_ang1(0, 0, c, 0.0)[0]
+
+
 def uniform_disc_uvw(V: int, uv_radius: float, w_max: float, seed: int) -> np.ndarray:
     """(u, v) uniform in a disc of radius uv_radius, w uniform in [-w_max, w_max]."""
     rng = np.random.default_rng(seed)

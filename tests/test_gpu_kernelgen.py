@@ -155,3 +155,21 @@ def test_resample_staged_rows_odd_os_unaligned_cache(os_, interp):
             assert np.array_equal(k[:, fu][..., jx].view(np.uint64), k[:, fu2][..., mj].view(np.uint64))
             if fu:
                 assert not np.any(k[:, fu][..., 0])
+
+
+@pytest.mark.parametrize("kernelgen", ["tf32x3", "projslice"])
+def test_prolate_taper_kernels(kernelgen):
+    """The radially symmetric prolate spheroidal taper (c = 3 pi) instead of the Gaussian:
+    the small imaging geometry's kernels against the oracle, by both Hankel routes."""
+    pytest.importorskip("scipy.special")
+    wp = _wp()
+    dev = torch.device("cuda")
+    N, dl, R = 256, np.deg2rad(2.0) / 256, 512
+    planes = np.linspace(0.0, 500.0, 16)
+    plan = wp.Plan(N, dl, 8, 15, 3, 0.01, R, "cubic", kernelgen)
+    g = o.Geometry(N, dl, 8, 15, 3, 0.01, R)
+    taper = synth.pswf_taper_samples(N, dl, R)
+    wk = wp.make_wkernels(plan, torch.tensor(taper, dtype=torch.float32, device=dev), planes)
+    torch.cuda.synchronize()
+    ks = o.wkernels(g, f32(taper), planes, route="hankel" if kernelgen != "projslice" else "projslice")
+    _compare(g, wk, ks)
