@@ -173,3 +173,25 @@ def test_prolate_taper_kernels(kernelgen):
     torch.cuda.synchronize()
     ks = o.wkernels(g, f32(taper), planes, route="hankel" if kernelgen != "projslice" else "projslice")
     _compare(g, wk, ks)
+
+
+def test_resample_largest_support():
+    """Support 511 at os 8, the largest the plan allows: the staged line (64 KB) and four
+    regions of one 1023-tap row leave room for one resample block per SM, one row per chunk
+    -- the cache against the oracle."""
+    wp = _wp()
+    dev = torch.device("cuda")
+    N, dl, R = 1024, np.deg2rad(4.0) / 1024, 1024
+    planes = np.array([0.0, 3000.0])
+    sup = np.array([511, 200])
+    plan = wp.Plan(N, dl, 8, 511, 1, 0.0, R, "cubic", "tf32x3")
+    taper = synth.gaussian_taper_samples(N, dl, R)
+    wk = wp.make_wkernels(plan, torch.tensor(taper, dtype=torch.float32, device=dev), planes, supports=sup)
+    torch.cuda.synchronize()
+    g = o.Geometry(N, dl, 8, 511, 1, 0.0, R)
+    ks = o.wkernels(g, f32(taper), planes, supports=sup)
+    off = wk.offsets.cpu().numpy()
+    for p in range(len(planes)):
+        c = wk.cache[int(off[p]):int(off[p + 1])].cpu().numpy()
+        e = rel_l2(c, ks.cache[ks.offsets[p]:ks.offsets[p + 1]])
+        assert e < KERNEL_TOL, f"plane {p} (S = {sup[p]}): cache rel. L2 {e:.3e}"
