@@ -154,9 +154,11 @@ size_t wp_kernelgen_workspace_bytes(const wp_plan* plan, int32_t P);
  * Once per plan geometry (Section 4.3: the transform matrix does not depend on the plane, so it is built once):
  * builds in `workspace` the K_out x R transform matrix H[k][i] = du^2 2 pi r_i dr
  * J0(2 pi rho_k r_i) (J0 evaluated in FP64 on the device, stored as FP32 and as a TF32
- * hi/lo pair) and the band of the inverse of the spline system.  Must precede
- * wp_hankel_radial / wp_make_wkernels on that workspace; they then accept any P' whose
- * workspace size still fits.  Synchronizes `stream` (a small host table is uploaded).
+ * hi/lo pair) and the band of the inverse of the spline system.  With kernelgen ==
+ * WP_KG_PROJSLICE it builds instead the table of n - 1 at the M x M workspace pixels (FP64,
+ * stored as float pairs).  Must precede wp_hankel_radial / wp_make_wkernels on that
+ * workspace; they then accept any P' whose workspace size still fits.  Synchronizes
+ * `stream` (a small host table is uploaded).
  */
 int wp_kernelgen_prepare(const wp_plan* plan, int32_t P, void* workspace,
                          size_t workspace_bytes, void* stream);
@@ -165,7 +167,11 @@ int wp_kernelgen_prepare(const wp_plan* plan, int32_t P, void* workspace,
  * Radial kernel lines of P planes: for each plane p (|w| = w_planes[p]):
  *   f_p(r_i) = taper[i] * exp(+2 pi j w_p (sqrt(1 - r_i^2) - 1))          (Eq. 9, adjoint sign)
  *   radial[p][k] = du^2 * sum_i 2 pi r_i dr J0(2 pi rho_k r_i) f_p(r_i)  (Eq. 12, matrix form)
- * computed as one batched matrix product (K_out x R) x (R x 2P).  Also writes the cubic
+ * computed as one batched matrix product (K_out x R) x (R x 2P).  With kernelgen ==
+ * WP_KG_PROJSLICE the line is instead the v = 0 slice of the 2D transform of the same
+ * function sampled on the undersampled M x M workspace (Section 4.2), obtained by the
+ * projection-slice theorem (Section 4.3.1): column sums, zero padding to M os, 1D FFT,
+ * scaled by (FOV/M)^2 du^2; sample k is taken at index k mod (M os).  Also writes the cubic
  * spline second derivatives of each line (Section 4.3.2; clamped slope 0 at rho = 0,
  * natural at rho_{K_out-1}) and, if plan->trunc_frac > 0, the support of each plane
  * (Section 3.1: last rho_k with |radial| >= trunc_frac * max, ceil to whole cells,
@@ -345,6 +351,7 @@ int wp_grad_radial(const wp_plan* plan, const wp_wkernels* kernels, const float*
  * grad_taper[i] += sum_p Re(conj(dF_p,i) exp(+2 pi j w_p (n_i - 1))).
  *   workspace: the kernel-generation workspace prepared by wp_kernelgen_prepare;
  *   grad_taper [R] float, ACCUMULATED into.
+ * Matrix routes only: a plan with kernelgen == WP_KG_PROJSLICE returns WP_ERR_UNSUPPORTED.
  */
 int wp_hankel_adjoint(const wp_plan* plan, const double* w_planes, int32_t P, void* workspace,
                       size_t workspace_bytes, const float* grad_radial, const float* grad_spline_m,
