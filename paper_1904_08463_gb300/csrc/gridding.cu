@@ -6,13 +6,19 @@
 //   --  sort     counting sort by (plane, T x T centre tile; T = 64 or 32): histogram, scan,
 //                scatter (uv-sorted binning: consecutive records share a plane and a tile)
 //   --  items    work items (plane, output tile) that some visibility's footprint reaches
-//   K10 grid     persistent blocks pull work items in plane-major order; a block owns one
-//                T x T output tile in registers (warp w owns rows (T/8) w .. , lane l owns
-//                columns l, l + 32, ..); each warp walks the binned visibilities of the
-//                neighbouring centre tiles on its own (no block barrier inside an item),
-//                two at a time with all 32 tap loads issued before the FMAs, accumulates
-//                tap x visibility with no atomics, and flushes the tile to the grid once
-//                (one float2 atomic per touched cell)
+//   K10 grid     persistent blocks pull work items in plane-major order and own one T x T
+//                output tile each, flushed once per item (one float2 atomic per touched
+//                cell).  Five shapes, equal up to FP32 summation order, picked per problem
+//                class by the autotuner:
+//                  0 register tile: warp w owns rows (T/8) w .., lane l columns l, l+32, ..;
+//                    every warp walks the neighbouring bins' visibilities on its own
+//                  1 shared-memory tile, each warp takes whole visibilities and spreads the
+//                    footprint over its lanes (shared float atomics)
+//                  2 per-warp shared-memory 32 x 32 tiles over groups of 8 planes
+//                  3 shared-memory tile; the block decodes the candidates once into a
+//                    compact list of those that meet the tile, and warp w updates only rows
+//                    w, w + 8, .. (plain read-modify-write, no atomics) -- the fastest
+//                  4 as 3, each tap interpolated from the plane's radial line (no cache)
 //   K11 degrid   one warp per visibility gathers conj(tap) x grid over the footprint and
 //                reduces with shuffles
 #include <cuda_runtime.h>
