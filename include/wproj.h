@@ -53,7 +53,7 @@ extern "C" {
 #define WP_ERR_CUDA       -5   /* a CUDA / cuFFT call failed                          */
 #define WP_ERR_TIMEOUT    -6   /* a bounded device-side wait expired                  */
 #define WP_ERR_DEVICE     -7   /* current device is not sm_103 (GB300)                */
-#define WP_ERR_UNSUPPORTED -8  /* valid request outside what this build implements    */
+#define WP_ERR_UNSUPPORTED -8  /* valid request outside what the library implements     */
 
 /* plan.interp (Section 4.3.2: linear or cubic-spline interpolation of the radial line) */
 #define WP_INTERP_CUBIC    0

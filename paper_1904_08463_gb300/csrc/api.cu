@@ -144,7 +144,7 @@ const char* wp_strerror(int code) {
         case WP_ERR_CUDA: return "CUDA or cuFFT call failed";
         case WP_ERR_TIMEOUT: return "a bounded device-side wait expired";
         case WP_ERR_DEVICE: return "current device is not sm_103 (GB300)";
-        case WP_ERR_UNSUPPORTED: return "request not supported by this build";
+        case WP_ERR_UNSUPPORTED: return "request not supported by the library";
         default: return "unknown status";
     }
 }

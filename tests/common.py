@@ -36,7 +36,3 @@ def supports_match(gpu_sup, oracle_radial, oracle_sup, tau, os_, rel=1e-4) -> bo
             return False
     return True
 
-
-def cfg1_inputs():
-    d = synth.small_imaging()
-    return d

@@ -155,14 +155,14 @@ def test_spline_reproduces_admissible_cubic():
 
 
 # -------------------------------------------------------------------- 2D kernel cache
-def _cfg1_geometry(R=512):
+def _small_imaging_geometry(R=512):
     return o.Geometry(256, np.deg2rad(2.0) / 256, 8, 15, 3, 0.01, R)
 
 
 def test_resample_matches_direct_transform_at_tap_radius():
     """Every tap equals the Hankel transform evaluated directly at the tap's exact radius,
     up to the cubic-spline error; taps beyond the support radius are zero."""
-    g = _cfg1_geometry()
+    g = _small_imaging_geometry()
     tap = o.gaussian_taper(g)
     w, S = 450.0, 6
     C = o.radial_kernel(g, tap, w)
@@ -191,7 +191,7 @@ def test_resample_matches_direct_transform_at_tap_radius():
 def test_subkernel_symmetry():
     """Radial symmetry: with fu == fv a sub-kernel is symmetric under jx <-> jy; and the
     (fu, fv) sub-kernel is the transpose of the (fv, fu) one."""
-    g = _cfg1_geometry()
+    g = _small_imaging_geometry()
     C = o.radial_kernel(g, o.gaussian_taper(g), 300.0)
     k = o.resample(g, C, 5)
     for f in range(g.oversampling):
@@ -201,7 +201,7 @@ def test_subkernel_symmetry():
 
 def test_truncation_support():
     """Section 3.1: the support is the last radius where |C| >= 1 % of max, in whole cells."""
-    g = _cfg1_geometry()
+    g = _small_imaging_geometry()
     C = np.zeros(g.k_out, dtype=np.complex128)
     C[:50] = np.linspace(1.0, 0.0, 50)          # |C[k]| >= 0.01 for k <= 49*0.99 -> k <= 49
     C[49] = 0.0100000001
