@@ -195,3 +195,24 @@ def test_resample_largest_support():
         c = wk.cache[int(off[p]):int(off[p + 1])].cpu().numpy()
         e = rel_l2(c, ks.cache[ks.offsets[p]:ks.offsets[p + 1]])
         assert e < KERNEL_TOL, f"plane {p} (S = {sup[p]}): cache rel. L2 {e:.3e}"
+
+
+@pytest.mark.parametrize("kernelgen", ["tf32x3", "projslice"])
+def test_every_radial_line_of_the_512_plane_batch(kernelgen):
+    """All 512 radial lines of the headline batch (R 4096, K_out 1152, |w| to 20000) against
+    the FP64 oracle, each within the kernel tolerance (the caches are sampled elsewhere)."""
+    wp = _wp()
+    dev = torch.device("cuda")
+    N, dl, R = 4096, np.deg2rad(8.0) / 4096, 4096
+    _, aw, sup = synth.kernel_batch_planes()
+    plan = wp.Plan(N, dl, 8, 127, 7, 0.0, R, "cubic", kernelgen)
+    taper = synth.gaussian_taper_samples(N, dl, R)
+    ws = wp.kernelgen_prepare(plan, len(aw))
+    radial, _, _ = wp.hankel_radial(plan, torch.tensor(taper, dtype=torch.float32, device=dev),
+                                    torch.tensor(aw, dtype=torch.float64, device=dev), ws)
+    radial = radial.cpu().numpy()
+    g = o.Geometry(N, dl, 8, 127, 7, 0.0, R)
+    ks = o.wkernels(g, f32(taper), aw, supports=sup, with_cache=False,
+                    route="hankel" if kernelgen != "projslice" else "projslice")
+    errs = np.array([rel_l2(radial[p], ks.radial[p]) for p in range(len(aw))])
+    assert errs.max() < KERNEL_TOL, f"worst plane {errs.argmax()}: {errs.max():.3e}"
