@@ -186,6 +186,19 @@ def oracle_kernel_rate(n_planes: int = 512):
                            f"transform matrix excluded; resample single-threaded")
 
 
+def oracle_rate_one_thread(n_planes: int = 64):
+    """The same oracle timing with one OpenMP thread (a child process: the thread count of
+    the loaded oracle library is fixed), on n_planes planes spread over the batch."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    code = ("import json, bench; r, t, s = bench.oracle_kernel_rate(%d); print(json.dumps(r))" % n_planes)
+    try:
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT,
+                             timeout=300)
+        return float(out.stdout.strip().splitlines()[-1]) if out.returncode == 0 else None
+    except (subprocess.TimeoutExpired, ValueError, IndexError):
+        return None
+
+
 # ------------------------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import torch
@@ -299,6 +312,10 @@ def run_gpu(args):
         rate, thr, sample = oracle_kernel_rate()
         out["cpu_baseline"] = {"value": rate, "unit": "w-kernels/s", "cores": thr, "kind": "oracle",
                                "sample": sample}
+        one = oracle_rate_one_thread()
+        if one is not None:
+            # the paper's parallel efficiency (Section 6): T_1 / (n T_n) = rate_n / (n rate_1)
+            out["cpu_baseline"].update({"value_1_thread": one, "parallel_efficiency": rate / (thr * one)})
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
