@@ -60,36 +60,51 @@ __global__ void k_sub_scatter(const int* __restrict__ n_valid, const int4* __res
     }
 }
 
+// Q of one visibility at the grid cell G: conj(g) G for w >= 0, g conj(G) for w < 0, with
+// gg = (g, s g): Re Q = g.x G.x + g.y G.y, Im Q = s (g.x G.y - g.y G.x).
+__device__ __forceinline__ void q_add(float4 gg, float2 G, float& qr, float& qi) {
+    qr = fmaf(gg.x, G.x, fmaf(gg.y, G.y, qr));
+    qi = fmaf(gg.z, G.y, fmaf(-gg.w, G.x, qi));
+}
+
 // Sum of Q over the visibilities [vb, ve) of one sub-kernel at up to two columns (ca, and cb
-// when two_c) and two rows (ra, and rb when two_r) of the footprint.
+// when two_c) and two rows (ra, and rb when two_r) of the footprint.  Two visibilities per
+// pass, all their grid loads issued before the sums (the loads come from L2).
 __device__ __forceinline__ void tap_sum(int vb, int ve, bool on, int N, int S, const int* __restrict__ uv2,
                                         const float4* __restrict__ g4, const float2* __restrict__ grid,
                                         int ca, int cb, bool two_c, int ra, int rb, bool two_r,
                                         float& qr, float& qi) {
-    for (int v = vb; v < ve; ++v) {
-        const int uv = uv2[v];
-        const float4 gg = g4[v];
-        if (!on) continue;
-        const int iu = uv & 0xffff, iv = (uv >> 16) & 0xffff;
-        const float2* g0 = grid + (int64_t)(iv - S) * N + (iu - S);
-        float2 G = g0[(int64_t)ra * N + ca];
-        qr = fmaf(gg.x, G.x, fmaf(gg.y, G.y, qr));
-        qi = fmaf(gg.z, G.y, fmaf(-gg.w, G.x, qi));
-        if (two_c) {
-            G = g0[(int64_t)ra * N + cb];
-            qr = fmaf(gg.x, G.x, fmaf(gg.y, G.y, qr));
-            qi = fmaf(gg.z, G.y, fmaf(-gg.w, G.x, qi));
-        }
-        if (two_r) {
-            G = g0[(int64_t)rb * N + ca];
-            qr = fmaf(gg.x, G.x, fmaf(gg.y, G.y, qr));
-            qi = fmaf(gg.z, G.y, fmaf(-gg.w, G.x, qi));
-            if (two_c) {
-                G = g0[(int64_t)rb * N + cb];
-                qr = fmaf(gg.x, G.x, fmaf(gg.y, G.y, qr));
-                qi = fmaf(gg.z, G.y, fmaf(-gg.w, G.x, qi));
-            }
-        }
+    if (!on) return;
+    const int64_t o_aa = (int64_t)ra * N + ca, o_ab = (int64_t)ra * N + cb;
+    const int64_t o_ba = (int64_t)rb * N + ca, o_bb = (int64_t)rb * N + cb;
+    const float2 zero = make_float2(0.0f, 0.0f);
+    int v = vb;
+    for (; v + 1 < ve; v += 2) {
+        const int u0 = uv2[v], u1 = uv2[v + 1];
+        const float4 h0 = g4[v], h1 = g4[v + 1];
+        const float2* p0 = grid + (int64_t)(((u0 >> 16) & 0xffff) - S) * N + ((u0 & 0xffff) - S);
+        const float2* p1 = grid + (int64_t)(((u1 >> 16) & 0xffff) - S) * N + ((u1 & 0xffff) - S);
+        const float2 a0 = p0[o_aa], a1 = p1[o_aa];
+        const float2 b0 = two_c ? p0[o_ab] : zero, b1 = two_c ? p1[o_ab] : zero;
+        const float2 c0 = two_r ? p0[o_ba] : zero, c1 = two_r ? p1[o_ba] : zero;
+        const float2 d0 = (two_r && two_c) ? p0[o_bb] : zero, d1 = (two_r && two_c) ? p1[o_bb] : zero;
+        q_add(h0, a0, qr, qi);
+        q_add(h1, a1, qr, qi);
+        q_add(h0, b0, qr, qi);
+        q_add(h1, b1, qr, qi);
+        q_add(h0, c0, qr, qi);
+        q_add(h1, c1, qr, qi);
+        q_add(h0, d0, qr, qi);
+        q_add(h1, d1, qr, qi);
+    }
+    if (v < ve) {
+        const int u0 = uv2[v];
+        const float4 h0 = g4[v];
+        const float2* p0 = grid + (int64_t)(((u0 >> 16) & 0xffff) - S) * N + ((u0 & 0xffff) - S);
+        q_add(h0, p0[o_aa], qr, qi);
+        if (two_c) q_add(h0, p0[o_ab], qr, qi);
+        if (two_r) q_add(h0, p0[o_ba], qr, qi);
+        if (two_r && two_c) q_add(h0, p0[o_bb], qr, qi);
     }
 }
 
