@@ -956,14 +956,29 @@ __global__ void __launch_bounds__(256) k_degrid(int N, int os, int s_max, int nb
     const float2* sub = cache + offsets[p] + (int64_t)(fv * os + fu) * W * W;
     const float2* g0 = grid + (int64_t)(iv - S) * N + (iu - S);
     float sr = 0.0f, si = 0.0f;
-    for (int jy = 0; jy < W; ++jy) {
+    // two footprint rows per pass: their tap and grid loads (L2) are in flight together
+    int jy = 0;
+    for (; jy + 1 < W; jy += 2) {
         const float2* trow = sub + jy * W;
         const float2* grow = g0 + (int64_t)jy * N;
         for (int jx = lane; jx < W; jx += 32) {
-            float2 tp = __ldg(trow + jx);
-            float ti = sgn * tp.y;
-            float2 gv = grow[jx];
+            const float2 tp0 = __ldg(trow + jx), tp1 = __ldg(trow + W + jx);
+            const float2 gv0 = grow[jx], gv1 = grow[N + jx];
             // conj(K) * g
+            const float ti0 = sgn * tp0.y, ti1 = sgn * tp1.y;
+            sr = fmaf(tp0.x, gv0.x, fmaf(ti0, gv0.y, sr));
+            si = fmaf(tp0.x, gv0.y, fmaf(-ti0, gv0.x, si));
+            sr = fmaf(tp1.x, gv1.x, fmaf(ti1, gv1.y, sr));
+            si = fmaf(tp1.x, gv1.y, fmaf(-ti1, gv1.x, si));
+        }
+    }
+    if (jy < W) {
+        const float2* trow = sub + jy * W;
+        const float2* grow = g0 + (int64_t)jy * N;
+        for (int jx = lane; jx < W; jx += 32) {
+            const float2 tp = __ldg(trow + jx);
+            const float ti = sgn * tp.y;
+            const float2 gv = grow[jx];
             sr = fmaf(tp.x, gv.x, fmaf(ti, gv.y, sr));
             si = fmaf(tp.x, gv.y, fmaf(-ti, gv.x, si));
         }
