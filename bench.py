@@ -579,6 +579,27 @@ def run_imaging(args, dev):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / n
     grid_ms = float(np.mean([x.elapsed_time(y) for x, y in evs]))
+    # end to end with host buffers: each step copies the visibilities (uvw, vis) in from
+    # pinned host memory and reads the dirty image back
+    uvw_h = uvw.reshape(-1).cpu().pin_memory()
+    vis_h = vis.cpu().pin_memory()
+    img_h = torch.empty(img.shape, dtype=img.dtype).pin_memory()
+    uvw_flat = uvw.reshape(-1)
+
+    def e2e_step():
+        uvw_flat.copy_(uvw_h, non_blocking=True)
+        vis.copy_(vis_h, non_blocking=True)
+        step()
+        img_h.copy_(img, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(n):
+        e2e_step()
+    b.record()
+    torch.cuda.synchronize()
+    ms_e2e = a.elapsed_time(b) / n
     sup_h = sup.cpu().numpy()
     # algorithmic work of gridding: 8 flop per tap of the (2S+1)^2 footprint of every
     # gridded visibility
@@ -598,6 +619,9 @@ def run_imaging(args, dev):
         "value": V / (ms * 1e-3) / 1e6,
         "unit": "Mvis/s",
         "ms_per_step": ms,
+        "e2e": {"value": V / (ms_e2e * 1e-3) / 1e6, "unit": "Mvis/s", "ms_per_step": ms_e2e,
+                "h2d_bytes_per_step": uvw_h.numel() * 4 + vis_h.numel() * 8,
+                "d2h_bytes_per_step": img_h.numel() * 4},
         "grid_ms": grid_ms,
         "gridding_mvis_per_s": V / (grid_ms * 1e-3) / 1e6,
         "supports": {"min": int(sup_h.min()), "max": int(sup_h.max()), "mean": float(sup_h.mean())},
