@@ -280,7 +280,9 @@ int kg_gemm_fp32(const Geom& g, const KgWork& w, int P, float2* radial, cudaStre
 // Spline: m = A^-1 rhs with rhs_0 = 6 (y1 - y0), rhs_k = 6 (y_{k+1} - 2 y_k + y_{k-1}),
 // rhs_{K-1} = 0 (zero slope at rho = 0, natural end), using the precomputed band of A^-1.
 // =======================================================================================
-__global__ void __launch_bounds__(256) k_trunc_spline(int K, int os, int s_min, int s_max, float tau,
+constexpr int TS_THREADS = 256;   // threads per plane of the truncation / spline kernel
+
+__global__ void __launch_bounds__(TS_THREADS) k_trunc_spline(int K, int os, int s_min, int s_max, float tau,
                                                       int do_trunc, int do_spline,
                                                       const float2* __restrict__ radial,
                                                       const float* __restrict__ band,
@@ -289,8 +291,8 @@ __global__ void __launch_bounds__(256) k_trunc_spline(int K, int os, int s_min, 
     extern __shared__ float2 sm[];   // y[K], rhs[K + 64] (rhs padded by 32 zeros on each side)
     float2* y = sm;
     float2* rhs = sm + K + 32;
-    __shared__ float red_f[8];
-    __shared__ int red_i[8];
+    __shared__ float red_f[TS_THREADS / 32];
+    __shared__ int red_i[TS_THREADS / 32];
     __shared__ float toe[65];        // one interior row of the band (Toeplitz coefficients)
     const int p = blockIdx.x;
     if (do_spline && threadIdx.x < 65) toe[threadIdx.x] = band[(int64_t)threadIdx.x * K + K / 2];
@@ -378,7 +380,7 @@ int kg_trunc_spline(const Geom& g, const KgWork& w, int P, const float2* radial,
     size_t smem = (size_t)(2 * g.k_out + 64) * sizeof(float2);
     if (smem > 48 * 1024)
         WP_CUDA(cudaFuncSetAttribute(k_trunc_spline, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_trunc_spline<<<P, 256, smem, st>>>(g.k_out, g.os, g.s_min, g.s_max, (float)g.tau, do_trunc,
+    k_trunc_spline<<<P, TS_THREADS, smem, st>>>(g.k_out, g.os, g.s_min, g.s_max, (float)g.tau, do_trunc,
                                          do_spline, radial, w.band, spline_m, support);
     WP_LAUNCH_CHECK("k_trunc_spline");
     return WP_OK;
