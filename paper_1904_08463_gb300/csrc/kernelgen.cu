@@ -440,14 +440,15 @@ constexpr int RS_THREADS = 384;
 // chunk c + 1 overwrites.
 template <bool CUBIC>
 __global__ void __launch_bounds__(RS_THREADS) k_resample(int K, int os, int s_max, int nrep, int n_items,
-                                                         int n_line, int slot,
+                                                         int n_line, int slot, int nsets,
                                                          const float2* __restrict__ radial,
                                                          const float2* __restrict__ spline_m,
                                                          const int32_t* __restrict__ support,
                                                          const int64_t* __restrict__ offsets,
                                                          float2* __restrict__ cache) {
     extern __shared__ float4 line[];   // skew(n_used) entries {y.re, y.im, m.re, m.im}, then
-                                       // 2 buffer sets x 4 regions x slot float2
+                                       // nsets (2, or 1 when two would cost a block per SM)
+                                       // buffer sets x 4 regions x slot float2
     float2* const stage = reinterpret_cast<float2*>(line + n_line);
     const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(stage);
     const int item = n_items - 1 - (int)blockIdx.x;
@@ -503,6 +504,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample(int K, int os, int s_ma
         const int oX = xself ? oF : so + slot + parity8(gX);
         const int oY = so + 2 * slot + parity8(gY);
         const int oXY = xself ? oY : so + 3 * slot + parity8(gXY);
+        if (nsets == 1 && chunk >= 1) {   // one set: chunk - 1's copies must have read it
+            if (threadIdx.x < 4) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            __syncthreads();
+        }
         int jy = r0 + jy_t, jx = jx_t;
         const int n_eval = (r1 - r0) * nx;
         for (int t = threadIdx.x; t < n_eval; t += blockDim.x) {
@@ -539,7 +544,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample(int K, int os, int s_ma
             }
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
-        so = so ? 0 : 4 * slot;
+        if (nsets == 2) so = so ? 0 : 4 * slot;
     }
     // bulk copies must finish reading shared memory before the block exits
     if (threadIdx.x < 4) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
@@ -559,14 +564,25 @@ int kg_resample(const Geom& g, int P, const float2* radial, const float2* spline
     WP_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
     WP_CUDA(cudaDeviceGetAttribute(&smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     WP_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    // (two buffer sets; when those would leave room for one block per SM but a single set
+    // would not, one set and a second barrier per chunk -- large supports at high os)
     const int w_max = 2 * g.s_max + 1;
     const long two_per_sm = (long)smem_sm / 2 - reserved - (long)line_bytes;
+    int nsets = 2;
     int cap = (int)(two_per_sm / (8 * (long)sizeof(float2))) - 2;
-    cap = cap > 1536 ? 1536 : cap;
+    if (cap < w_max + 1) {
+        const int cap1 = (int)(two_per_sm / (4 * (long)sizeof(float2))) - 2;
+        if (cap1 >= w_max + 1) {
+            nsets = 1;
+            cap = cap1;
+        }
+    }
+    const int cap_max = (nsets == 2) ? 1536 : 3072;   // about four taps per thread per chunk
+    cap = cap > cap_max ? cap_max : cap;
     cap &= ~1;
     if (cap < w_max + 1) cap = w_max + 1;   // even, >= one row
     const int slot = cap + 2;
-    const size_t smem = line_bytes + (size_t)8 * slot * sizeof(float2);
+    const size_t smem = line_bytes + (size_t)4 * nsets * slot * sizeof(float2);
     if (smem > (size_t)smem_block) {
         set_last_error("wp_resample", "staging for this support and oversampling exceeds shared memory");
         return WP_ERR_UNSUPPORTED;
@@ -577,11 +593,11 @@ int kg_resample(const Geom& g, int P, const float2* radial, const float2* spline
     dim3 grid((unsigned)n_items);
     if (g.interp == WP_INTERP_CUBIC) {
         WP_CUDA(cudaFuncSetAttribute(k_resample<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_resample<true><<<grid, RS_THREADS, smem, st>>>(g.k_out, g.os, g.s_max, nrep, n_items, n_line, slot,
+        k_resample<true><<<grid, RS_THREADS, smem, st>>>(g.k_out, g.os, g.s_max, nrep, n_items, n_line, slot, nsets,
                                                          radial, spline_m, support, offsets, cache);
     } else {
         WP_CUDA(cudaFuncSetAttribute(k_resample<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_resample<false><<<grid, RS_THREADS, smem, st>>>(g.k_out, g.os, g.s_max, nrep, n_items, n_line, slot,
+        k_resample<false><<<grid, RS_THREADS, smem, st>>>(g.k_out, g.os, g.s_max, nrep, n_items, n_line, slot, nsets,
                                                           radial, spline_m, support, offsets, cache);
     }
     WP_LAUNCH_CHECK("k_resample");
