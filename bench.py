@@ -34,9 +34,9 @@ import synth  # noqa: E402
 
 # DRAM read + write bytes of one k_resample launch on the 512-plane batch, from the ncu capture
 # summarised in profiles/k_resample_kernel_batch.md (every-2nd-plane case, scaled by the ratio
-# of algorithmic bytes).  Reported only while the resample section of the source is the one it
-# was measured on.
-RESAMPLE_TRAFFIC = {"bytes_per_launch": 5.931e+09, "source_sha1": "c2d6ce809a0c"}
+# of algorithmic bytes).  Reported only while the resample's source (its section of kernelgen.cu
+# and the shared tap evaluation) is the one it was measured on.
+RESAMPLE_TRAFFIC = {"bytes_per_launch": 5.9305e+09, "source_sha1": "0342e6b6a4b6"}
 
 GRID_METHOD_NAMES = {0: "register tile", 1: "shared-memory tile, footprint over the lanes (atomics)",
                      2: "warp-private shared-memory tiles", 3: "shared-memory tile, rows owned by warps",
@@ -70,19 +70,27 @@ def max_over_ranks(ms: float, device, world: int) -> float:
     return float(t.item())
 
 
-def resample_traffic():
+def resample_source_hash():
+    """sha1 of the resample kernel's source: its section of kernelgen.cu and the shared tap
+    evaluation it inlines."""
     import hashlib
 
-    path = os.path.join(ROOT, "paper_1904_08463_gb300", "csrc", "kernelgen.cu")
+    base = os.path.join(ROOT, "paper_1904_08463_gb300", "csrc")
     try:
-        src = open(path, "rb").read()
+        kg = open(os.path.join(base, "kernelgen.cu"), "rb").read()
+        hd = open(os.path.join(base, "wp_internal.cuh"), "rb").read()
     except OSError:
         return None
-    # the resample kernel and its launcher only: edits elsewhere in the file keep the figure
-    a, b = src.find(b"// K7: resample"), src.find(b"}  // namespace wp")
-    if a < 0 or b < 0:
+    a, b = kg.find(b"// K7: resample"), kg.find(b"}  // namespace wp")
+    c = hd.find(b"__device__ __forceinline__ int skew(int k)")
+    d = hd.find(b"#endif", c)
+    if min(a, b, c, d) < 0:
         return None
-    h = hashlib.sha1(src[a:b]).hexdigest()[:12]
+    return hashlib.sha1(kg[a:b] + hd[c:d]).hexdigest()[:12]
+
+
+def resample_traffic():
+    h = resample_source_hash()
     return RESAMPLE_TRAFFIC["bytes_per_launch"] if h == RESAMPLE_TRAFFIC["source_sha1"] else None
 
 
@@ -355,6 +363,19 @@ def time_routes(args, kb, plan, taper_d, wpl_d, sup_host, ws, radial, spline_m, 
 
     ms = timeit(hankel_other, max(3, min(args.steps, 10)))
     res[other + "_hankel"] = {"ms_per_step": ms, "w_kernels_per_s": P / (ms * 1e-3)}
+    # the BF16 hi/lo split on the tensor cores (kind::f16, twice the TF32 rate, ~2e-6 error)
+    if args.kernelgen != "bf16x3":
+        p4 = plan.replace(kernelgen="bf16x3")
+        ws4 = wp.workspace(wp.kernelgen_workspace_bytes(p4, P))
+        wp.kernelgen_prepare(p4, P, ws4)
+
+        def bf16x3():
+            wp.hankel_radial(p4, taper_d, wpl_d, ws4, radial, spline_m)
+            wp.resample(p4, radial, spline_m, sup_d, off_d, cache)
+
+        ms = timeit(bf16x3, max(3, min(args.steps, 10)))
+        res["bf16x3_hankel"] = {"ms_per_step": ms, "w_kernels_per_s": P / (ms * 1e-3)}
+        del ws4
     # the projection-slice realisation of the Hankel transform (the variant the paper timed):
     # workspace image summed over one axis, zero-padded by os, batched 1D cuFFT
     p3 = plan.replace(kernelgen="projslice")
@@ -482,7 +503,7 @@ def build_line(args, world, P, kb, ms_step, resample_ms, bytes_cache, alg_bytes,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if args.kernelgen == "fp32" else "tf32x3",
+        "dtype": {"fp32": "f32", "tf32x3": "tf32x3", "bf16x3": "bf16x3", "projslice": "f32"}[args.kernelgen],
         "data": "synthetic",
         "config": {
             "workload": "kernel-generation batch: 1024 signed w-planes linspace[-20000,20000] "
@@ -879,7 +900,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--kernelgen", default="tf32x3", choices=["fp32", "tf32x3"])
+    ap.add_argument("--kernelgen", default="tf32x3", choices=["fp32", "tf32x3", "bf16x3", "projslice"])
     ap.add_argument("--no-imaging", dest="imaging", action="store_false")
     ap.add_argument("--imaging-vis", type=int, default=1 << 23)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

@@ -35,7 +35,8 @@ int make_geom(const wp_plan* plan, Geom* g) {
     if (!(plan->trunc_frac < 1.0)) return WP_ERR_PLAN;
     if (plan->radial_samples < 8 || plan->radial_samples > 65536) return WP_ERR_PLAN;
     if (plan->interp != WP_INTERP_CUBIC && plan->interp != WP_INTERP_LINEAR) return WP_ERR_PLAN;
-    if (plan->kernelgen != WP_KG_FP32 && plan->kernelgen != WP_KG_TF32X3 && plan->kernelgen != WP_KG_PROJSLICE)
+    if (plan->kernelgen != WP_KG_FP32 && plan->kernelgen != WP_KG_TF32X3 && plan->kernelgen != WP_KG_BF16X3 &&
+        plan->kernelgen != WP_KG_PROJSLICE)
         return WP_ERR_PLAN;
     if (plan->grid_tile != 0 && plan->grid_tile != 32 && plan->grid_tile != 64) return WP_ERR_PLAN;
     if (plan->grid_method < 0 || plan->grid_method > 4) return WP_ERR_PLAN;
@@ -48,7 +49,7 @@ int make_geom(const wp_plan* plan, Geom* g) {
     g->s_min = plan->min_support;
     g->tau = plan->trunc_frac;
     g->R = plan->radial_samples;
-    g->r_pad = (int)round_up(plan->radial_samples, 32);
+    g->r_pad = (int)round_up(plan->radial_samples, 64);   // whole K slices for TF32 (32) and BF16 (64)
     g->k_out = (int)round_up((int64_t)plan->oversampling * (plan->max_support + 2), 128);
     g->interp = plan->interp;
     g->kernelgen = plan->kernelgen;
@@ -68,6 +69,9 @@ size_t carve_kg(const Geom& g, int P, void* ws, size_t bytes, KgWork* out) {
     w.h32 = c.take<float>(hk);
     w.h_hi = c.take<float>(hk);
     w.h_lo = c.take<float>(hk);
+    const bool bf = (g.kernelgen == WP_KG_BF16X3);
+    w.hb_hi = c.take<uint16_t>(bf ? hk : 0);
+    w.hb_lo = c.take<uint16_t>(bf ? hk : 0);
     w.band = c.take<float>((size_t)g.k_out * 65);
     w.nm1 = c.take<double>((size_t)g.r_pad);
     w.nm1f = c.take<float2>((size_t)g.r_pad);
@@ -77,6 +81,8 @@ size_t carve_kg(const Geom& g, int P, void* ws, size_t bytes, KgWork* out) {
     w.f32 = c.take<float>(fk);
     w.f_hi = c.take<float>(fk);
     w.f_lo = c.take<float>(fk);
+    w.fb_hi = c.take<uint16_t>(bf ? fk : 0);
+    w.fb_lo = c.take<uint16_t>(bf ? fk : 0);
     w.gct = c.take<float>((size_t)2 * p_pad(P) * g.k_out);
     w.status = c.take<int>(64);
     if (out) *out = w;
@@ -239,6 +245,8 @@ int wp_hankel_radial(const wp_plan* plan, const float* taper, const double* w_pl
         if ((rc = kg_screen(g, w, taper, w_planes, P, st))) return rc;
         if (g.kernelgen == WP_KG_TF32X3)
             rc = kg_gemm_tf32x3(g, w, P, reinterpret_cast<float2*>(radial), w.status, st);
+        else if (g.kernelgen == WP_KG_BF16X3)
+            rc = kg_gemm_bf16x3(g, w, P, reinterpret_cast<float2*>(radial), w.status, st);
         else
             rc = kg_gemm_fp32(g, w, P, reinterpret_cast<float2*>(radial), st);
     }

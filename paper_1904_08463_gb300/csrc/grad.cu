@@ -156,11 +156,9 @@ __global__ void __launch_bounds__(256) k_grad_taps(int N, int os, int s_max, int
         if (!xself && !yself) tap_sum(v11, e11, on, N, S, uv2, g4, grid, mj, mj, false, mjy, mjy, false, qr, qi);
         if (on && (qr != 0.0f || qi != 0.0f)) {
             // the resample's interpolation interval and weights at this radius
-            const float qf = (float)q;
-            const float x = qf * rsqrtf(fmaxf(qf, 1.0f));
-            const float tt = (x - 0.5f) + 12582912.0f;
-            const int k = __float_as_int(tt) - 0x4B400000;
-            const float a = x - (tt - 12582912.0f);
+            int k;
+            float a;
+            tap_interval(q, k, a);
             const float b = 1.0f - a;
             atomicAdd(&acc[k].x, b * qr);
             atomicAdd(&acc[k].y, b * qi);

@@ -6,7 +6,12 @@
 //
 // Precision: TF32 inputs carry 11 significant bits, so each operand is split into
 // hi = rna_tf32(x) and lo = rna_tf32(x - hi); the product is hi*hi' + hi*lo' + lo*hi'
-// (the lo*lo' term is below 2^-22 relative), accumulated in FP32 in tensor memory.
+// (the lo*lo' term is below 2^-22 relative), accumulated in FP32 in tensor memory.  The
+// BF16 variant splits into two BF16 values (8 bits each: the three products then carry an
+// operand error near 2^-17, measured 2e-6 relative on the transform) and runs kind::f16,
+// twice the TF32 rate: a 128-byte swizzle row holds 64 BF16 elements instead of 32 TF32
+// ones, and each MMA consumes 16 of them instead of 8 -- the same 32 bytes -- so the tile
+// layout, descriptors and issue loop are shared and only the K depth per stage doubles.
 //
 // Structure (one CTA = one 128 x 128 output tile, optionally one half of K):
 //   warp 0 lane 0   TMA producer: per 32-deep K slice loads A_hi, A_lo, B_hi, B_lo tiles
@@ -36,8 +41,9 @@ namespace wp {
 namespace tc {
 
 constexpr int BM = 128, BN = 128, BK = 32;           // BK fp32 = 128 bytes = one swizzle row
+constexpr int BK16 = 64;                             // BF16 elements per 128-byte swizzle row
 constexpr int STAGES = 3;
-constexpr int TILE_BYTES = BM * BK * 4;              // 16 KB (BN == BM)
+constexpr int TILE_BYTES = BM * BK * 4;              // 16 KB (BN == BM), either element type
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;          // A_hi, A_lo, B_hi, B_lo
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr int TMEM_COLS = 2 * BN;                   // two accumulator buffers
@@ -105,12 +111,32 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16 (format 1 for both: the two
+// operands must share one type), both K-major, N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n.reg .pred p;\n"
         "setp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
         ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+template <bool BF16>
+__device__ __forceinline__ void mma_x(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (BF16) mma_bf16(tmem_d, a, b, idesc, acc);
+    else mma_tf32(tmem_d, a, b, idesc, acc);
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -156,6 +182,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // step, one-signed).  So the MMA issuer accumulates only GROUP K-slices into one of two
 // TMEM buffers; the accumulation warps move each finished partial into FP32 registers
 // (IEEE adds) while the next group runs into the other buffer.
+template <bool BF16>
 __global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant__ CUtensorMap map_a_hi,
                                                           const __grid_constant__ CUtensorMap map_a_lo,
                                                           const __grid_constant__ CUtensorMap map_b_hi,
@@ -179,9 +206,10 @@ __global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant_
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+    constexpr int KS = BF16 ? BK16 : BK;               // K elements per stage
     const int kchunk = K / k_split;
     const int kbeg = blockIdx.z * kchunk;
-    const int nkb = kchunk / BK;
+    const int nkb = kchunk / KS;
     const int ngroups = (nkb + GROUP - 1) / GROUP;
 
     if (threadIdx.x == 0) {
@@ -219,7 +247,7 @@ __global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant_
                 const uint32_t st = base + s * STAGE_BYTES;
                 const uint32_t fb = bar_full0 + 8 * s;
                 mbar_expect_tx(fb, STAGE_BYTES);
-                const int x = kbeg + kb * BK;
+                const int x = kbeg + kb * KS;
                 tma_load_2d(st + 0 * TILE_BYTES, &map_a_hi, x, m0, fb);
                 tma_load_2d(st + 1 * TILE_BYTES, &map_a_lo, x, m0, fb);
                 tma_load_2d(st + 2 * TILE_BYTES, &map_b_hi, x, n0, fb);
@@ -235,7 +263,7 @@ __global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant_
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            const uint32_t idesc = idesc_tf32(BM, BN);
+            const uint32_t idesc = BF16 ? idesc_bf16(BM, BN) : idesc_tf32(BM, BN);
             bool ok = true;
             for (int g = 0; g < ngroups && ok; ++g) {
                 const int b = g & 1;
@@ -255,11 +283,12 @@ __global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant_
                     const uint64_t b_lo = smem_desc_sw128(st + 3 * TILE_BYTES);
                     const uint32_t first = (kb == g * GROUP) ? 1u : 0u;
 #pragma unroll
-                    for (int j = 0; j < BK / 8; ++j) {
-                        const uint64_t adv = (uint64_t)((j * 32) >> 4);   // 8 tf32 = 32 bytes along K
-                        mma_tf32(dacc, a_hi + adv, b_lo + adv, idesc, (first && j == 0) ? 0u : 1u);
-                        mma_tf32(dacc, a_lo + adv, b_hi + adv, idesc, 1u);
-                        mma_tf32(dacc, a_hi + adv, b_hi + adv, idesc, 1u);
+                    for (int j = 0; j < 4; ++j) {
+                        // 8 tf32 or 16 bf16 = 32 bytes along K per MMA
+                        const uint64_t adv = (uint64_t)((j * 32) >> 4);
+                        mma_x<BF16>(dacc, a_hi + adv, b_lo + adv, idesc, (first && j == 0) ? 0u : 1u);
+                        mma_x<BF16>(dacc, a_lo + adv, b_hi + adv, idesc, 1u);
+                        mma_x<BF16>(dacc, a_hi + adv, b_hi + adv, idesc, 1u);
                     }
                     mma_commit(bar_empty0 + 8 * s);
                 }
@@ -331,19 +360,21 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-// 2D row-major FP32 matrix [rows][cols] (cols contiguous), box 32 cols x 128 rows,
-// 128-byte swizzle.  Base must be 16-byte aligned and cols*4 a multiple of 16.
-int make_map(CUtensorMap* map, const float* ptr, int rows, int cols) {
+// 2D row-major matrix [rows][cols] (cols contiguous) of FP32 (box 32 cols x 128 rows) or
+// BF16 (box 64 cols x 128 rows): 128 bytes per box row, 128-byte swizzle.  Base must be
+// 16-byte aligned and the row pitch a multiple of 16 bytes.
+int make_map(CUtensorMap* map, const void* ptr, int rows, int cols, bool bf16 = false) {
     auto enc = get_encode();
     if (!enc) {
         set_last_error("cuTensorMapEncodeTiled", "driver entry point unavailable");
         return WP_ERR_CUDA;
     }
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * (bf16 ? 2u : 4u)};
+    cuuint32_t box[2] = {(cuuint32_t)(bf16 ? BK16 : BK), (cuuint32_t)BM};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides, box, estr,
+    CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                     const_cast<void*>(ptr), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -355,35 +386,56 @@ int make_map(CUtensorMap* map, const float* ptr, int rows, int cols) {
 
 }  // namespace tc
 
-int kg_gemm_tf32x3_ex(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st,
-                      long long budget, int withhold_loads) {
+namespace {
+template <bool BF16>
+int gemm_split3(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st,
+                long long budget, int withhold_loads) {
     using namespace tc;
+    constexpr int KS = BF16 ? BK16 : BK;
     const int M = g.k_out, N = 2 * p_pad(P), K = g.r_pad;
-    if (M % BM || N % BN || K % BK) {
-        set_last_error("kg_gemm_tf32x3", "shape not tile aligned");
+    if (M % BM || N % BN || K % KS) {
+        set_last_error("kg_gemm_split3", "shape not tile aligned");
         return WP_ERR_SIZE;
     }
     CUtensorMap ma_hi, ma_lo, mb_hi, mb_lo;
     int rc;
-    if ((rc = make_map(&ma_hi, w.h_hi, M, K))) return rc;
-    if ((rc = make_map(&ma_lo, w.h_lo, M, K))) return rc;
-    if ((rc = make_map(&mb_hi, w.f_hi, N, K))) return rc;
-    if ((rc = make_map(&mb_lo, w.f_lo, N, K))) return rc;
+    if (BF16) {
+        if ((rc = make_map(&ma_hi, w.hb_hi, M, K, true))) return rc;
+        if ((rc = make_map(&ma_lo, w.hb_lo, M, K, true))) return rc;
+        if ((rc = make_map(&mb_hi, w.fb_hi, N, K, true))) return rc;
+        if ((rc = make_map(&mb_lo, w.fb_lo, N, K, true))) return rc;
+    } else {
+        if ((rc = make_map(&ma_hi, w.h_hi, M, K))) return rc;
+        if ((rc = make_map(&ma_lo, w.h_lo, M, K))) return rc;
+        if ((rc = make_map(&mb_hi, w.f_hi, N, K))) return rc;
+        if ((rc = make_map(&mb_lo, w.f_lo, N, K))) return rc;
+    }
     const int tiles = (M / BM) * (N / BN);
-    const int split = (tiles < 152 && (K / 2) % BK == 0) ? 2 : 1;
+    const int split = (tiles < 152 && (K / 2) % KS == 0) ? 2 : 1;
     WP_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
     if (split > 1) WP_CUDA(cudaMemsetAsync(radial, 0, (size_t)P * M * sizeof(float2), st));
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(k_hankel_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        attr_err = cudaFuncSetAttribute(k_hankel_tf32x3<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        SMEM_BYTES);
     });
     WP_CUDA(attr_err);
     dim3 grid(N / BN, M / BM, split);
-    k_hankel_tf32x3<<<grid, 192, SMEM_BYTES, st>>>(ma_hi, ma_lo, mb_hi, mb_lo, M, K, split, P, radial,
-                                                   split > 1, status, budget, withhold_loads);
+    k_hankel_tf32x3<BF16><<<grid, 192, SMEM_BYTES, st>>>(ma_hi, ma_lo, mb_hi, mb_lo, M, K, split, P, radial,
+                                                         split > 1, status, budget, withhold_loads);
     WP_LAUNCH_CHECK("k_hankel_tf32x3");
     return WP_OK;
+}
+}  // namespace
+
+int kg_gemm_tf32x3_ex(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st,
+                      long long budget, int withhold_loads) {
+    return gemm_split3<false>(g, w, P, radial, status, st, budget, withhold_loads);
+}
+
+int kg_gemm_bf16x3(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st) {
+    return gemm_split3<true>(g, w, P, radial, status, st, tc::WAIT_BUDGET, 0);
 }
 
 int kg_gemm_tf32x3(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st) {

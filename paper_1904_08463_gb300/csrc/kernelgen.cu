@@ -5,6 +5,7 @@
 //   K5/K6          1 % truncation support and cubic-spline second derivatives
 //   K7 resample    oversampled 2D kernel cache from the radial line
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -26,6 +27,27 @@ __device__ __forceinline__ float to_tf32(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
+}
+
+// x split as hi + lo with hi = bf16(x) and lo = bf16(x - hi), both round-to-nearest-even:
+// together about 16 significant bits (the BF16x3 route's operands).
+__device__ __forceinline__ void split_bf16(float x, uint16_t& hi, uint16_t& lo) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(l);
+}
+
+// BF16 hi/lo split of an FP32 array (the transform matrix of the BF16x3 route; splitting the
+// FP32 value loses nothing: its 24 bits exceed the pair's 16).
+__global__ void k_split_bf16(int64_t n, const float* __restrict__ x, uint16_t* __restrict__ hi,
+                             uint16_t* __restrict__ lo) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint16_t h, l;
+    split_bf16(x[i], h, l);
+    hi[i] = h;
+    lo[i] = l;
 }
 
 __global__ void k_j0_matrix(int k_out, int R, int r_pad, int os, float* __restrict__ h32,
@@ -111,6 +133,10 @@ int kg_prepare(const Geom& g, const KgWork& w, cudaStream_t st) {
         k_j0_matrix<<<(unsigned)blocks, threads, 0, st>>>(g.k_out, g.R, g.r_pad, g.os, w.h32, w.h_hi,
                                                            w.h_lo);
         WP_LAUNCH_CHECK("k_j0_matrix");
+        if (g.kernelgen == WP_KG_BF16X3) {
+            k_split_bf16<<<(unsigned)blocks, threads, 0, st>>>(total, w.h32, w.hb_hi, w.hb_lo);
+            WP_LAUNCH_CHECK("k_split_bf16");
+        }
     }
     std::vector<float> band;
     spline_band_host(g.k_out, band);
@@ -132,10 +158,12 @@ int kg_prepare(const Geom& g, const KgWork& w, cudaStream_t st) {
 // p is exact, and one final rounding gives the reduced phase -- as accurate as the FP64
 // product rounded to float, on the FP32 units (FP64 throughput is low on this part).
 // =======================================================================================
-template <bool SPLIT>
+// MODE 0: FP32 rows (SIMT product); 1: TF32 hi/lo rows; 2: BF16 hi/lo rows.
+template <int MODE>
 __global__ void k_screen(int R, int r_pad, int P, int P_pad, const float2* __restrict__ nm1f,
                          const float* __restrict__ taper, const double* __restrict__ w_planes,
-                         float* __restrict__ f32, float* __restrict__ f_hi, float* __restrict__ f_lo) {
+                         float* __restrict__ f32, float* __restrict__ f_hi, float* __restrict__ f_lo,
+                         uint16_t* __restrict__ fb_hi, uint16_t* __restrict__ fb_lo) {
     __shared__ float2 wsplit;
     const int p = blockIdx.y;
     if (threadIdx.x == 0) {
@@ -162,12 +190,15 @@ __global__ void k_screen(int R, int r_pad, int P, int P_pad, const float2* __res
     }
     int64_t row_re = (int64_t)(2 * p) * r_pad + i;
     int64_t row_im = row_re + r_pad;
-    if (SPLIT) {
+    if (MODE == 1) {
         float hr = to_tf32(re), hi = to_tf32(im);
         f_hi[row_re] = hr;
         f_hi[row_im] = hi;
         f_lo[row_re] = to_tf32(re - hr);
         f_lo[row_im] = to_tf32(im - hi);
+    } else if (MODE == 2) {
+        split_bf16(re, fb_hi[row_re], fb_lo[row_re]);
+        split_bf16(im, fb_hi[row_im], fb_lo[row_im]);
     } else {
         f32[row_re] = re;
         f32[row_im] = im;
@@ -179,9 +210,14 @@ int kg_screen(const Geom& g, const KgWork& w, const float* taper, const double* 
     int Pp = p_pad(P);
     dim3 grid((g.r_pad + 255) / 256, Pp);
     if (g.kernelgen == WP_KG_TF32X3)
-        k_screen<true><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo);
+        k_screen<1><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo,
+                                          w.fb_hi, w.fb_lo);
+    else if (g.kernelgen == WP_KG_BF16X3)
+        k_screen<2><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo,
+                                          w.fb_hi, w.fb_lo);
     else
-        k_screen<false><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo);
+        k_screen<0><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo,
+                                          w.fb_hi, w.fb_lo);
     WP_LAUNCH_CHECK("k_screen");
     return WP_OK;
 }

@@ -76,6 +76,8 @@ struct KgWork {
     float* h32;        // [k_out][r_pad] FP32 transform matrix
     float* h_hi;       // [k_out][r_pad] TF32 high part
     float* h_lo;       // [k_out][r_pad] TF32 low part
+    uint16_t* hb_hi;   // [k_out][r_pad] BF16 high part (BF16x3 route)
+    uint16_t* hb_lo;   // [k_out][r_pad] BF16 low part
     float* band;       // [65][k_out] spline inverse band (row d holds A^-1[k][k + d - 32])
     double* nm1;       // [R] n - 1 = sqrt(1 - r_i^2) - 1 at the radial nodes
     float2* nm1f;      // [R] the same as an unevaluated float pair (hi, lo)
@@ -84,6 +86,8 @@ struct KgWork {
     float* f32;        // [2 P_pad][r_pad] image-domain functions (FP32 path)
     float* f_hi;       // [2 P_pad][r_pad]
     float* f_lo;       // [2 P_pad][r_pad]
+    uint16_t* fb_hi;   // [2 P_pad][r_pad] BF16 split of the image-domain functions (BF16x3 route)
+    uint16_t* fb_lo;   // [2 P_pad][r_pad]
     float* gct;        // [2 P_pad][k_out] radial-line gradient rows (re, im) for the adjoint
     int*   status;     // [4]
 };
@@ -120,17 +124,27 @@ size_t carve_grid(const Geom& g, int P, int64_t V, void* ws, size_t bytes, GridW
 #ifdef __CUDACC__
 __device__ __forceinline__ int skew(int k) { return k ^ ((k >> 3) & 7); }
 
+// Spline interval of radius x = sqrt(q) on the unit-spaced line: k = round(x - 1/2) through
+// the float mantissa (1.5 * 2^23) from an approximate x = q rsqrt(q) -- an off-by-one next
+// to an integer radius is harmless, the interpolant being continuous there -- and the offset
+// a = x - k formed as (q - k^2) / (x + k), the numerator exact in integers, so that a keeps
+// ~1e-7 absolute accuracy at radii of a thousand samples (x - k in FP32 keeps ~3e-5 there).
+__device__ __forceinline__ void tap_interval(int q, int& k, float& a) {
+    const float qf = (float)q;
+    const float x = qf * rsqrtf(fmaxf(qf, 1.0f));   // q = 0 gives 0
+    const float tt = (x - 0.5f) + 12582912.0f;
+    k = __float_as_int(tt) - 0x4B400000;
+    a = __fdividef((float)(q - k * k), fmaxf(x + (float)k, 1.0f));
+}
+
 template <bool CUBIC>
 __device__ __forceinline__ float2 resample_tap(const float4* __restrict__ line, int dx, int dy, int lim2) {
     const int q = dx * dx + dy * dy;
     float2 out = make_float2(0.0f, 0.0f);
     if (q <= lim2) {
-        const float qf = (float)q;
-        const float x = qf * rsqrtf(fmaxf(qf, 1.0f));   // q = 0 gives 0, else sqrt(q)
-        // round(x - 1/2) through the float mantissa (1.5 * 2^23): the interval index
-        const float tt = (x - 0.5f) + 12582912.0f;
-        const int k = __float_as_int(tt) - 0x4B400000;
-        const float a = x - (tt - 12582912.0f);
+        int k;
+        float a;
+        tap_interval(q, k, a);
         const float b = 1.0f - a;
         const float4 L0 = line[skew(k)];
         const float4 L1 = line[skew(k + 1)];
@@ -154,6 +168,7 @@ int kg_screen(const Geom& g, const KgWork& w, const float* taper, const double* 
 int kg_gemm_fp32(const Geom& g, const KgWork& w, int P, float2* radial, cudaStream_t st);
 int kg_gemm_tf32x3(const Geom& g, const KgWork& w, int P, float2* radial, int* status,
                    cudaStream_t st);
+int kg_gemm_bf16x3(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st);
 int kg_gemm_tf32x3_ex(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st,
                       long long budget, int withhold_loads);
 int kg_ps_prepare(const Geom& g, const KgWork& w, cudaStream_t st);

@@ -46,7 +46,7 @@ def _compare(g, wk, ks, tol=KERNEL_TOL):
         assert e < tol, f"plane {p}: cache rel. L2 {e:.3e}"
 
 
-@pytest.mark.parametrize("kernelgen", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("kernelgen", ["fp32", "tf32x3", "bf16x3"])
 def test_small_imaging_kernels(kernelgen):
     """256^2, 2 deg FOV, 16 |w|-planes <= 500, os 8, R 512, S_max 15, 1 % truncation."""
     N, dl = 256, np.deg2rad(2.0) / 256
@@ -55,7 +55,7 @@ def test_small_imaging_kernels(kernelgen):
     _compare(g, wk, ks)
 
 
-@pytest.mark.parametrize("kernelgen", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("kernelgen", ["fp32", "tf32x3", "bf16x3"])
 @pytest.mark.parametrize("os_,R,P,interp", [(1, 300, 5, "cubic"), (4, 97, 3, "linear"),
                                             (16, 256, 70, "cubic"), (8, 2048, 130, "linear")])
 def test_kernels_ragged_shapes(os_, R, P, interp, kernelgen):
@@ -69,7 +69,7 @@ def test_kernels_ragged_shapes(os_, R, P, interp, kernelgen):
     _compare(g, wk, ks)
 
 
-@pytest.mark.parametrize("kernelgen", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("kernelgen", ["fp32", "tf32x3", "bf16x3"])
 def test_large_w_kernels_sampled(kernelgen):
     """1024 signed planes linspace[-20000, 20000] (512 distinct |w|), R 4096, os 8,
     supports 7..127 growing with |w|, 8 degree FOV on 4096^2: every plane is generated
@@ -157,7 +157,7 @@ def test_resample_staged_rows_odd_os_unaligned_cache(os_, interp):
                 assert not np.any(k[:, fu][..., 0])
 
 
-@pytest.mark.parametrize("kernelgen", ["tf32x3", "projslice"])
+@pytest.mark.parametrize("kernelgen", ["tf32x3", "bf16x3", "projslice"])
 def test_prolate_taper_kernels(kernelgen):
     """The radially symmetric prolate spheroidal taper (c = 3 pi) instead of the Gaussian:
     the small imaging geometry's kernels against the oracle, by both Hankel routes."""
@@ -197,7 +197,7 @@ def test_resample_largest_support():
         assert e < KERNEL_TOL, f"plane {p} (S = {sup[p]}): cache rel. L2 {e:.3e}"
 
 
-@pytest.mark.parametrize("kernelgen", ["tf32x3", "projslice"])
+@pytest.mark.parametrize("kernelgen", ["tf32x3", "bf16x3", "projslice"])
 def test_every_radial_line_of_the_512_plane_batch(kernelgen):
     """All 512 radial lines of the headline batch (R 4096, K_out 1152, |w| to 20000) against
     the FP64 oracle, each within the kernel tolerance (the caches are sampled elsewhere)."""
