@@ -157,12 +157,13 @@ size_t wp_kernelgen_workspace_bytes(const wp_plan* plan, int32_t P);
 /*
  * Once per plan geometry (Section 4.3: the transform matrix does not depend on the plane, so it is built once):
  * builds in `workspace` the K_out x R transform matrix H[k][i] = du^2 2 pi r_i dr
- * J0(2 pi rho_k r_i) (J0 evaluated in FP64 on the device, stored as FP32 and as a TF32
- * hi/lo pair) and the band of the inverse of the spline system.  With kernelgen ==
- * WP_KG_PROJSLICE it builds instead the table of n - 1 at the M x M workspace pixels (FP64,
- * stored as float pairs).  Must precede wp_hankel_radial / wp_make_wkernels on that
- * workspace; they then accept any P' whose workspace size still fits.  Synchronizes
- * `stream` (a small host table is uploaded).
+ * J0(2 pi rho_k r_i) (J0 evaluated in FP64 on the device, stored as FP32, as a TF32 hi/lo
+ * pair and as a BF16 hi/lo pair), the table of n - 1 at the M x M workspace pixels of the
+ * projection route (FP64, stored as float pairs) and the band of the inverse of the spline
+ * system -- the tables of every kernelgen route, so one prepared workspace serves them all
+ * (the workspace layout does not depend on plan->kernelgen).  Must precede
+ * wp_hankel_radial / wp_make_wkernels on that workspace; they then accept any P' whose
+ * workspace size still fits.  Synchronizes `stream` (a small host table is uploaded).
  */
 int wp_kernelgen_prepare(const wp_plan* plan, int32_t P, void* workspace,
                          size_t workspace_bytes, void* stream);

@@ -1,7 +1,8 @@
 """Autotuner for the tunable launch shapes of the imaging path.
 
 Three choices do not change results, only speed: the kernel-generation route of the Hankel
-transform (FP32 SIMT or tcgen05 TF32x3 matrix product -- both meet the kernel tolerance),
+transform (FP32 SIMT, tcgen05 TF32x3 or BF16x3 matrix product -- all meet the kernel
+tolerance, 1e-6 or better on the caches),
 and the gridder's method (register tile; shared-memory tiles with the footprint spread over
 the lanes, per-warp copies, or warp-owned rows; warp-owned rows with taps interpolated from
 the radial line) and tile side (32 or 64 cells).  For a problem class -- grid size, plane
@@ -18,7 +19,7 @@ from typing import Callable
 
 import torch
 
-KERNELGEN_CHOICES = ("fp32", "tf32x3")
+KERNELGEN_CHOICES = ("fp32", "tf32x3", "bf16x3")
 TILE_CHOICES = (32, 64)
 GRID_CHOICES = tuple((m, t) for m in (0, 1, 3, 4) for t in TILE_CHOICES) + ((2, 32),)   # (grid_method, grid_tile)
 

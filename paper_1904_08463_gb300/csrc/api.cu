@@ -69,20 +69,19 @@ size_t carve_kg(const Geom& g, int P, void* ws, size_t bytes, KgWork* out) {
     w.h32 = c.take<float>(hk);
     w.h_hi = c.take<float>(hk);
     w.h_lo = c.take<float>(hk);
-    const bool bf = (g.kernelgen == WP_KG_BF16X3);
-    w.hb_hi = c.take<uint16_t>(bf ? hk : 0);
-    w.hb_lo = c.take<uint16_t>(bf ? hk : 0);
+    // every route's buffers, so that one prepared workspace serves all kernelgen routes
+    w.hb_hi = c.take<uint16_t>(hk);
+    w.hb_lo = c.take<uint16_t>(hk);
     w.band = c.take<float>((size_t)g.k_out * 65);
     w.nm1 = c.take<double>((size_t)g.r_pad);
     w.nm1f = c.take<float2>((size_t)g.r_pad);
-    const bool ps = (g.kernelgen == WP_KG_PROJSLICE);
-    w.ps_nm1 = c.take<float2>(ps ? (size_t)g.fft_m * g.fft_m : 0);
-    w.ps_x = c.take<float2>(ps ? (size_t)P * g.fft_m * g.os : 0);
+    w.ps_nm1 = c.take<float2>((size_t)g.fft_m * g.fft_m);
+    w.ps_x = c.take<float2>((size_t)P * g.fft_m * g.os);
     w.f32 = c.take<float>(fk);
     w.f_hi = c.take<float>(fk);
     w.f_lo = c.take<float>(fk);
-    w.fb_hi = c.take<uint16_t>(bf ? fk : 0);
-    w.fb_lo = c.take<uint16_t>(bf ? fk : 0);
+    w.fb_hi = c.take<uint16_t>(fk);
+    w.fb_lo = c.take<uint16_t>(fk);
     w.gct = c.take<float>((size_t)2 * p_pad(P) * g.k_out);
     w.status = c.take<int>(64);
     if (out) *out = w;

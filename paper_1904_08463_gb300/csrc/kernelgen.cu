@@ -123,20 +123,19 @@ __global__ void k_nm1(int R, int r_pad, double r_max, double* __restrict__ nm1, 
 int kg_prepare(const Geom& g, const KgWork& w, cudaStream_t st) {
     k_nm1<<<(g.r_pad + 255) / 256, 256, 0, st>>>(g.R, g.r_pad, g.r_max, w.nm1, w.nm1f);
     WP_LAUNCH_CHECK("k_nm1");
-    if (g.kernelgen == WP_KG_PROJSLICE) {
+    // the tables of every route (transform matrix as FP32, TF32 and BF16 pairs; the workspace
+    // n - 1 table of the projection route), so that any kernelgen route runs on this workspace
+    {
         int rc = kg_ps_prepare(g, w, st);
         if (rc) return rc;
-    } else {
         int64_t total = (int64_t)g.k_out * g.r_pad;
         int threads = 256;
         int64_t blocks = (total + threads - 1) / threads;
         k_j0_matrix<<<(unsigned)blocks, threads, 0, st>>>(g.k_out, g.R, g.r_pad, g.os, w.h32, w.h_hi,
                                                            w.h_lo);
         WP_LAUNCH_CHECK("k_j0_matrix");
-        if (g.kernelgen == WP_KG_BF16X3) {
-            k_split_bf16<<<(unsigned)blocks, threads, 0, st>>>(total, w.h32, w.hb_hi, w.hb_lo);
-            WP_LAUNCH_CHECK("k_split_bf16");
-        }
+        k_split_bf16<<<(unsigned)blocks, threads, 0, st>>>(total, w.h32, w.hb_hi, w.hb_lo);
+        WP_LAUNCH_CHECK("k_split_bf16");
     }
     std::vector<float> band;
     spline_band_host(g.k_out, band);

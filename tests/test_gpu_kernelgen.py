@@ -216,3 +216,22 @@ def test_every_radial_line_of_the_512_plane_batch(kernelgen):
                     route="hankel" if kernelgen != "projslice" else "projslice")
     errs = np.array([rel_l2(radial[p], ks.radial[p]) for p in range(len(aw))])
     assert errs.max() < KERNEL_TOL, f"worst plane {errs.argmax()}: {errs.max():.3e}"
+
+
+def test_one_prepared_workspace_serves_every_route():
+    """The workspace layout and tables do not depend on plan.kernelgen: a workspace prepared
+    under one route gives every other route the same radial lines, bit for bit, as a
+    workspace prepared under that route."""
+    wp = _wp()
+    dev = torch.device("cuda")
+    N, dl, R = 256, np.deg2rad(2.0) / 256, 512
+    planes = torch.tensor(np.linspace(0.0, 500.0, 16), dtype=torch.float64, device=dev)
+    taper = torch.tensor(synth.gaussian_taper_samples(N, dl, R), dtype=torch.float32, device=dev)
+    base = wp.Plan(N, dl, 8, 15, 3, 0.0, R, "cubic", "tf32x3")
+    shared = wp.kernelgen_prepare(base, 16)
+    for kg in ("fp32", "tf32x3", "bf16x3", "projslice"):
+        plan = base.replace(kernelgen=kg)
+        own = wp.kernelgen_prepare(plan, 16)
+        a = wp.hankel_radial(plan, taper, planes, shared)[0].cpu().numpy()
+        b = wp.hankel_radial(plan, taper, planes, own)[0].cpu().numpy()
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64)), kg
