@@ -124,17 +124,24 @@ size_t carve_grid(const Geom& g, int P, int64_t V, void* ws, size_t bytes, GridW
 #ifdef __CUDACC__
 __device__ __forceinline__ int skew(int k) { return k ^ ((k >> 3) & 7); }
 
-// Spline interval of radius x = sqrt(q) on the unit-spaced line: k = round(x - 1/2) through
-// the float mantissa (1.5 * 2^23) from an approximate x = q rsqrt(q) -- an off-by-one next
-// to an integer radius is harmless, the interpolant being continuous there -- and the offset
-// a = x - k formed as (q - k^2) / (x + k), the numerator exact in integers, so that a keeps
-// ~1e-7 absolute accuracy at radii of a thousand samples (x - k in FP32 keeps ~3e-5 there).
+// Spline interval of radius sqrt(q) on the unit-spaced line: k = round(x - 1/2) through the
+// float mantissa (1.5 * 2^23) from an approximate x = q rsqrt(q) -- an off-by-one next to an
+// integer radius is harmless, the interpolant being continuous there.  The offset keeps the
+// part of the root that FP32 x drops, by one Newton step: sqrt(q) = x + e / (2x) + O(e^2/x^3)
+// with the residual e = q - x^2 = (q - k^2) - (x - k)(x + k), where q - k^2 is exact in
+// integers (q itself may exceed 2^24) and x - k is exact (Sterbenz), so e carries ~1e-3 at
+// most of absolute error and a = (x - k) + e r / 2 keeps ~1e-7 absolute accuracy at radii of
+// thousands of samples, where x - k alone keeps ~3e-5.  No division.
 __device__ __forceinline__ void tap_interval(int q, int& k, float& a) {
     const float qf = (float)q;
-    const float x = qf * rsqrtf(fmaxf(qf, 1.0f));   // q = 0 gives 0
+    const float r = rsqrtf(fmaxf(qf, 1.0f));
+    const float x = qf * r;                          // q = 0 gives 0
     const float tt = (x - 0.5f) + 12582912.0f;
     k = __float_as_int(tt) - 0x4B400000;
-    a = __fdividef((float)(q - k * k), fmaxf(x + (float)k, 1.0f));
+    const float kf = tt - 12582912.0f;               // k as a float, exactly
+    const float xk = x - kf;
+    const float e = fmaf(-xk, x + kf, (float)(q - k * k));
+    a = fmaf(e, 0.5f * r, xk);
 }
 
 template <bool CUBIC>
