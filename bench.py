@@ -354,28 +354,20 @@ def time_routes(args, kb, plan, taper_d, wpl_d, sup_host, ws, radial, spline_m, 
         torch.cuda.synchronize()
         return a.elapsed_time(b) / n
 
-    other = "fp32" if args.kernelgen == "tf32x3" else "tf32x3"
-    p2 = plan.replace(kernelgen=other)
+    # the other matrix routes on the same prepared workspace (its layout and tables serve every
+    # route): FP32 SIMT; TF32 hi/lo (3 products); BF16 hi/lo (3 products, kind::f16 at twice the
+    # TF32 rate, ~2e-6 error); BF16 hi/lo/lo2 (6 products, TF32x3's accuracy)
+    for kg in ("fp32", "tf32x3", "bf16x3", "bf16x6"):
+        if kg == args.kernelgen:
+            continue
+        pk = plan.replace(kernelgen=kg)
 
-    def hankel_other():
-        wp.hankel_radial(p2, taper_d, wpl_d, ws, radial, spline_m)
-        wp.resample(p2, radial, spline_m, sup_d, off_d, cache)
+        def route(pk=pk):
+            wp.hankel_radial(pk, taper_d, wpl_d, ws, radial, spline_m)
+            wp.resample(pk, radial, spline_m, sup_d, off_d, cache)
 
-    ms = timeit(hankel_other, max(3, min(args.steps, 10)))
-    res[other + "_hankel"] = {"ms_per_step": ms, "w_kernels_per_s": P / (ms * 1e-3)}
-    # the BF16 hi/lo split on the tensor cores (kind::f16, twice the TF32 rate, ~2e-6 error)
-    if args.kernelgen != "bf16x3":
-        p4 = plan.replace(kernelgen="bf16x3")
-        ws4 = wp.workspace(wp.kernelgen_workspace_bytes(p4, P))
-        wp.kernelgen_prepare(p4, P, ws4)
-
-        def bf16x3():
-            wp.hankel_radial(p4, taper_d, wpl_d, ws4, radial, spline_m)
-            wp.resample(p4, radial, spline_m, sup_d, off_d, cache)
-
-        ms = timeit(bf16x3, max(3, min(args.steps, 10)))
-        res["bf16x3_hankel"] = {"ms_per_step": ms, "w_kernels_per_s": P / (ms * 1e-3)}
-        del ws4
+        ms = timeit(route, max(3, min(args.steps, 10)))
+        res[kg + "_hankel"] = {"ms_per_step": ms, "w_kernels_per_s": P / (ms * 1e-3)}
     # the projection-slice realisation of the Hankel transform (the variant the paper timed):
     # workspace image summed over one axis, zero-padded by os, batched 1D cuFFT
     p3 = plan.replace(kernelgen="projslice")
@@ -503,7 +495,8 @@ def build_line(args, world, P, kb, ms_step, resample_ms, bytes_cache, alg_bytes,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"fp32": "f32", "tf32x3": "tf32x3", "bf16x3": "bf16x3", "projslice": "f32"}[args.kernelgen],
+        "dtype": {"fp32": "f32", "tf32x3": "tf32x3", "bf16x3": "bf16x3", "bf16x6": "bf16x6",
+                  "projslice": "f32"}[args.kernelgen],
         "data": "synthetic",
         "config": {
             "workload": "kernel-generation batch: 1024 signed w-planes linspace[-20000,20000] "
@@ -814,10 +807,12 @@ def run_reference(args):
 
 def run_sweep(args):
     """Kernel-generation cost along the paper's scaling axes (its Figs. 3-7: number of
-    w-planes, kernel support, oversampling) on the headline geometry (4096^2, 8 deg, R 4096,
-    Gaussian taper, |w| linspace[0, 20000], every plane at the sweep's support), for the
-    matrix Hankel route (TF32x3), the projection-slice Hankel route and the standard 2D-FFT
-    route.  Each route's time covers the radial line (or the 2D transform) and the
+    w-planes, kernel support, oversampling, truncation level) on the headline geometry (4096^2,
+    8 deg, R 4096, Gaussian taper, |w| linspace[0, 20000]), for the matrix Hankel route
+    (TF32x3), the projection-slice Hankel route and the standard 2D-FFT route.  On the first
+    three axes every plane takes the sweep's support; on the truncation axis each plane's
+    support is the one its radial line gives at that level (S_max 255), the same supports
+    for every route.  Each route's time covers the radial line (or the 2D transform) and the
     oversampled cache of every plane.  Prints one JSON line with the table."""
     import ctypes
 
@@ -842,11 +837,19 @@ def run_sweep(args):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / n
 
-    def point(P, S, os_):
-        plan = wp.Plan(N_IMG, dl, os_, S, 1, 0.0, R_KG, "cubic", "tf32x3")
+    def point(P, S, os_, tau=0.0):
+        plan = wp.Plan(N_IMG, dl, os_, S, 1, tau, R_KG, "cubic", "tf32x3")
         wpl = torch.tensor(np.linspace(0.0, 20000.0, P), dtype=torch.float64, device=dev)
-        sup_h = [S] * P
-        sup = torch.tensor(sup_h, dtype=torch.int32, device=dev)
+        if tau > 0.0:
+            # supports from the truncation rule on the radial lines (read back once, untimed)
+            ws = wp.workspace(wp.kernelgen_workspace_bytes(plan, P), dev)
+            wp.kernelgen_prepare(plan, P, ws)
+            _, _, sup = wp.hankel_radial(plan, taper_d, wpl, ws)
+            sup_h = [int(v) for v in sup.cpu()]
+            del ws
+        else:
+            sup_h = [S] * P
+            sup = torch.tensor(sup_h, dtype=torch.int32, device=dev)
         off_h = wp.kernel_layout(plan, sup_h)
         off = torch.tensor(off_h, dtype=torch.int64, device=dev)
         cache = torch.empty(off_h[-1], dtype=torch.complex64, device=dev)
@@ -854,13 +857,19 @@ def run_sweep(args):
         radial = torch.empty((P, g.k_out), dtype=torch.complex64, device=dev)
         spl = torch.empty_like(radial)
         out = {"planes": P, "support": S, "oversampling": os_, "cache_gb": off_h[-1] * 8 / 1e9}
+        if tau > 0.0:
+            out.update(trunc_frac=tau, support_min=min(sup_h), support_mean=float(np.mean(sup_h)),
+                       support_max=max(sup_h))
         for route in ("tf32x3", "projslice"):
             pr = plan.replace(kernelgen=route)
             ws = wp.workspace(wp.kernelgen_workspace_bytes(pr, P), dev)
             wp.kernelgen_prepare(pr, P, ws)
 
-            def run(pr=pr, ws=ws):
-                wp.hankel_radial(pr, taper_d, wpl, ws, radial, spl)
+            # truncating routes recompute supports into scratch; the resample keeps the laid-out ones
+            scratch = torch.empty_like(sup) if tau > 0.0 else None
+
+            def run(pr=pr, ws=ws, scratch=scratch):
+                wp.hankel_radial(pr, taper_d, wpl, ws, radial, spl, scratch)
                 wp.resample(pr, radial, spl, sup, off, cache)
 
             out[route + "_ms"] = timeit(run, 5)
@@ -889,9 +898,12 @@ def run_sweep(args):
         rows.append(dict(axis="support", **point(64, S, 8)))
     for os_ in (1, 2, 4, 16):
         rows.append(dict(axis="oversampling", **point(64, 127, os_)))
+    for tau in (1e-4, 1e-3, 1e-2, 1e-1):
+        rows.append(dict(axis="truncation", **point(64, 255, 8, tau)))
     print(json.dumps({"sweep": "kernel generation: matrix Hankel (TF32x3), projection-slice Hankel, 2D FFT",
                       "geometry": "4096^2, 8 deg, R 4096, Gaussian taper, |w| linspace[0, 20000], all planes "
-                                  "at the listed support", "rows": rows}))
+                                  "at the listed support (truncation axis: supports from the truncation "
+                                  "rule, S_max 255)", "rows": rows}))
 
 
 def main():
@@ -900,7 +912,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--kernelgen", default="tf32x3", choices=["fp32", "tf32x3", "bf16x3", "projslice"])
+    ap.add_argument("--kernelgen", default="bf16x6", choices=["fp32", "tf32x3", "bf16x3", "bf16x6", "projslice"])
     ap.add_argument("--no-imaging", dest="imaging", action="store_false")
     ap.add_argument("--imaging-vis", type=int, default=1 << 23)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

@@ -67,6 +67,10 @@ extern "C" {
                                   split (3 products, kind::f16 at twice the TF32 rate),
                                   FP32 accumulation in TMEM: operand split error ~2e-6
                                   relative (TF32x3: ~3e-8)                               */
+#define WP_KG_BF16X6       4   /* Hankel transform on tcgen05 tensor cores, each operand
+                                  split into three BF16 parts (all 24 bits of FP32), the
+                                  six products of order <= 2 (kind::f16): TF32x3's
+                                  accuracy at the same tensor time                      */
 #define WP_KG_PROJSLICE    2   /* Hankel transform by the projection-slice theorem
                                   (Section 4.3.1, Alg. 2 steps 4-12): the taper x screen
                                   on the undersampled M x M workspace (Section 4.2) summed
@@ -88,7 +92,8 @@ typedef struct wp_plan {
                                (Section 3.1, default 0.01); <= 0: supports are given   */
     int32_t radial_samples; /* R, 8 <= R <= 65536                                      */
     int32_t interp;         /* WP_INTERP_CUBIC | WP_INTERP_LINEAR                      */
-    int32_t kernelgen;      /* WP_KG_FP32 | WP_KG_TF32X3 | WP_KG_BF16X3 | WP_KG_PROJSLICE */
+    int32_t kernelgen;      /* WP_KG_FP32 | WP_KG_TF32X3 | WP_KG_BF16X3 | WP_KG_BF16X6 |
+                               WP_KG_PROJSLICE                                           */
     int32_t grid_tile;      /* gridding tile side in cells: 0 (default, 64), 32 or 64    */
     int32_t grid_method;    /* 0 (default): register tile, lanes own grid cells;
                                1: shared-memory tile, footprint spread over the lanes;

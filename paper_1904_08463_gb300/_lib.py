@@ -24,7 +24,7 @@ ERRORS = {
     -5: "WP_ERR_CUDA", -6: "WP_ERR_TIMEOUT", -7: "WP_ERR_DEVICE", -8: "WP_ERR_UNSUPPORTED",
 }
 INTERP = {"cubic": 0, "linear": 1}
-KERNELGEN = {"fp32": 0, "tf32x3": 1, "projslice": 2, "bf16x3": 3}
+KERNELGEN = {"fp32": 0, "tf32x3": 1, "projslice": 2, "bf16x3": 3, "bf16x6": 4}
 
 
 class WpPlan(ctypes.Structure):

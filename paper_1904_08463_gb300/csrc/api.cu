@@ -36,7 +36,7 @@ int make_geom(const wp_plan* plan, Geom* g) {
     if (plan->radial_samples < 8 || plan->radial_samples > 65536) return WP_ERR_PLAN;
     if (plan->interp != WP_INTERP_CUBIC && plan->interp != WP_INTERP_LINEAR) return WP_ERR_PLAN;
     if (plan->kernelgen != WP_KG_FP32 && plan->kernelgen != WP_KG_TF32X3 && plan->kernelgen != WP_KG_BF16X3 &&
-        plan->kernelgen != WP_KG_PROJSLICE)
+        plan->kernelgen != WP_KG_BF16X6 && plan->kernelgen != WP_KG_PROJSLICE)
         return WP_ERR_PLAN;
     if (plan->grid_tile != 0 && plan->grid_tile != 32 && plan->grid_tile != 64) return WP_ERR_PLAN;
     if (plan->grid_method < 0 || plan->grid_method > 4) return WP_ERR_PLAN;
@@ -72,6 +72,7 @@ size_t carve_kg(const Geom& g, int P, void* ws, size_t bytes, KgWork* out) {
     // every route's buffers, so that one prepared workspace serves all kernelgen routes
     w.hb_hi = c.take<uint16_t>(hk);
     w.hb_lo = c.take<uint16_t>(hk);
+    w.hb_lo2 = c.take<uint16_t>(hk);
     w.band = c.take<float>((size_t)g.k_out * 65);
     w.nm1 = c.take<double>((size_t)g.r_pad);
     w.nm1f = c.take<float2>((size_t)g.r_pad);
@@ -82,6 +83,7 @@ size_t carve_kg(const Geom& g, int P, void* ws, size_t bytes, KgWork* out) {
     w.f_lo = c.take<float>(fk);
     w.fb_hi = c.take<uint16_t>(fk);
     w.fb_lo = c.take<uint16_t>(fk);
+    w.fb_lo2 = c.take<uint16_t>(fk);
     w.gct = c.take<float>((size_t)2 * p_pad(P) * g.k_out);
     w.status = c.take<int>(64);
     if (out) *out = w;
@@ -246,6 +248,8 @@ int wp_hankel_radial(const wp_plan* plan, const float* taper, const double* w_pl
             rc = kg_gemm_tf32x3(g, w, P, reinterpret_cast<float2*>(radial), w.status, st);
         else if (g.kernelgen == WP_KG_BF16X3)
             rc = kg_gemm_bf16x3(g, w, P, reinterpret_cast<float2*>(radial), w.status, st);
+        else if (g.kernelgen == WP_KG_BF16X6)
+            rc = kg_gemm_bf16x6(g, w, P, reinterpret_cast<float2*>(radial), w.status, st);
         else
             rc = kg_gemm_fp32(g, w, P, reinterpret_cast<float2*>(radial), st);
     }

@@ -12,12 +12,18 @@
 // twice the TF32 rate: a 128-byte swizzle row holds 64 BF16 elements instead of 32 TF32
 // ones, and each MMA consumes 16 of them instead of 8 -- the same 32 bytes -- so the tile
 // layout, descriptors and issue loop are shared and only the K depth per stage doubles.
+// The BF16x6 variant splits each operand into three BF16 parts x = x0 + x1 + x2 (24
+// significant bits, all of an FP32 value) and keeps the six products of order <= 2,
+// x0 y0 + (x0 y1 + x1 y0) + (x0 y2 + x1 y1 + x2 y0), issued smallest first; the dropped
+// terms are below 2^-24 relative, so it matches TF32x3's accuracy at the same tensor time
+// (six products at twice the rate) with 6 instead of 8 operand bytes per element.
 //
 // Structure (one CTA = one 128 x 128 output tile, optionally one half of K):
-//   warp 0 lane 0   TMA producer: per 32-deep K slice loads A_hi, A_lo, B_hi, B_lo tiles
-//                   (128 rows x 128 B each, 128-byte swizzle) into a 3-stage ring
-//   warp 1 lane 0   MMA issuer: 4 K-steps x 3 products of tcgen05.mma.kind::tf32
-//                   (M = 128, N = 128, K = 8) per slice into one of two TMEM buffers,
+//   warp 0 lane 0   TMA producer: per 128-byte K slice loads the split parts of A and B
+//                   (A_hi, A_lo, B_hi, B_lo; three parts each for BF16x6; 128 rows x 128 B
+//                   per tile, 128-byte swizzle) into a 3-stage ring (2 stages for BF16x6)
+//   warp 1 lane 0   MMA issuer: 4 K-steps x 3 (or 6) products of tcgen05.mma (M = 128,
+//                   N = 128, K = 8 TF32 or 16 BF16) per slice into one of two TMEM buffers,
 //                   commits each stage back to the producer and each group of slices
 //                   to the accumulation warps
 //   warps 2-5       accumulation: tcgen05.ld of each finished partial (warp w reads TMEM
@@ -42,12 +48,23 @@ namespace tc {
 
 constexpr int BM = 128, BN = 128, BK = 32;           // BK fp32 = 128 bytes = one swizzle row
 constexpr int BK16 = 64;                             // BF16 elements per 128-byte swizzle row
-constexpr int STAGES = 3;
 constexpr int TILE_BYTES = BM * BK * 4;              // 16 KB (BN == BM), either element type
-constexpr int STAGE_BYTES = 4 * TILE_BYTES;          // A_hi, A_lo, B_hi, B_lo
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr int TMEM_COLS = 2 * BN;                   // two accumulator buffers
-constexpr int GROUP = 2;                             // K-slices per TMEM partial sum
+
+// Per-route configuration: MODE 0 = TF32x3, 1 = BF16x3, 2 = BF16x6.
+template <int MODE>
+struct Cfg {
+    static constexpr bool BF16 = MODE != 0;
+    static constexpr int NT = (MODE == 2) ? 3 : 2;                   // split parts per operand
+    static constexpr int KS = BF16 ? BK16 : BK;                      // K elements per stage
+    static constexpr int STAGES = (MODE == 2) ? 2 : 3;               // 2 x 96 KB or 3 x 64 KB
+    static constexpr int STAGE_BYTES = 2 * NT * TILE_BYTES;          // A parts, then B parts
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+    // K-slices per TMEM partial sum: 24 MMAs per partial in every mode (2 slices x 4 steps x 3
+    // products, or 1 x 4 x 6)
+    static constexpr int GROUP = (MODE == 2) ? 1 : 2;
+};
+static_assert(Cfg<2>::SMEM_BYTES <= 232448, "BF16x6 stages exceed shared memory");
 constexpr long long WAIT_BUDGET = 4000000000LL;      // ~2 s of SM clock per wait (default)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -139,6 +156,27 @@ __device__ __forceinline__ void mma_x(uint32_t tmem_d, uint64_t a, uint64_t b, u
     else mma_tf32(tmem_d, a, b, idesc, acc);
 }
 
+// The split products of one 32-byte K step: a[i], b[i] are the descriptors of part i.
+// Two parts: hi*lo' + lo*hi' + hi*hi'; three parts: the six products of order <= 2, smallest
+// first.  `acc0` = 0 starts a fresh accumulator with the first product.
+template <int MODE>
+__device__ __forceinline__ void mma_split(uint32_t d, const uint64_t (&a)[3], const uint64_t (&b)[3], uint64_t adv,
+                                          uint32_t idesc, uint32_t acc0) {
+    constexpr bool BF = Cfg<MODE>::BF16;
+    if (MODE == 2) {
+        mma_x<BF>(d, a[2] + adv, b[0] + adv, idesc, acc0);
+        mma_x<BF>(d, a[1] + adv, b[1] + adv, idesc, 1u);
+        mma_x<BF>(d, a[0] + adv, b[2] + adv, idesc, 1u);
+        mma_x<BF>(d, a[1] + adv, b[0] + adv, idesc, 1u);
+        mma_x<BF>(d, a[0] + adv, b[1] + adv, idesc, 1u);
+        mma_x<BF>(d, a[0] + adv, b[0] + adv, idesc, 1u);
+    } else {
+        mma_x<BF>(d, a[0] + adv, b[1] + adv, idesc, acc0);
+        mma_x<BF>(d, a[1] + adv, b[0] + adv, idesc, 1u);
+        mma_x<BF>(d, a[0] + adv, b[0] + adv, idesc, 1u);
+    }
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -179,18 +217,22 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // epilogue (warp w reads TMEM lanes 32 (w % 4) .. +31, i.e. output rows of that quarter).
 // The tensor core's FP32 accumulation does not round to nearest: its error grows with the
 // number of MMA steps folded into one accumulator (about 2^-25 of the running sum per
-// step, one-signed).  So the MMA issuer accumulates only GROUP K-slices into one of two
+// step, one-signed).  So the MMA issuer accumulates only GROUP K-slices (24 MMAs) into one of two
 // TMEM buffers; the accumulation warps move each finished partial into FP32 registers
 // (IEEE adds) while the next group runs into the other buffer.
-template <bool BF16>
-__global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant__ CUtensorMap map_a_hi,
-                                                          const __grid_constant__ CUtensorMap map_a_lo,
-                                                          const __grid_constant__ CUtensorMap map_b_hi,
-                                                          const __grid_constant__ CUtensorMap map_b_lo,
+template <int MODE>
+__global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant__ CUtensorMap map_a0,
+                                                          const __grid_constant__ CUtensorMap map_a1,
+                                                          const __grid_constant__ CUtensorMap map_a2,
+                                                          const __grid_constant__ CUtensorMap map_b0,
+                                                          const __grid_constant__ CUtensorMap map_b1,
+                                                          const __grid_constant__ CUtensorMap map_b2,
                                                           int M, int K, int k_split, int P,
                                                           float2* __restrict__ radial, int use_atomic,
                                                           int* __restrict__ status, long long budget,
                                                           int withhold_loads) {
+    using C = Cfg<MODE>;
+    constexpr int STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES, NT = C::NT, GROUP = C::GROUP;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -206,7 +248,7 @@ __global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant_
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
-    constexpr int KS = BF16 ? BK16 : BK;               // K elements per stage
+    constexpr int KS = C::KS;                          // K elements per stage
     const int kchunk = K / k_split;
     const int kbeg = blockIdx.z * kchunk;
     const int nkb = kchunk / KS;
@@ -247,11 +289,13 @@ __global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant_
                 const uint32_t st = base + s * STAGE_BYTES;
                 const uint32_t fb = bar_full0 + 8 * s;
                 mbar_expect_tx(fb, STAGE_BYTES);
-                const int x = kbeg + kb * KS;
-                tma_load_2d(st + 0 * TILE_BYTES, &map_a_hi, x, m0, fb);
-                tma_load_2d(st + 1 * TILE_BYTES, &map_a_lo, x, m0, fb);
-                tma_load_2d(st + 2 * TILE_BYTES, &map_b_hi, x, n0, fb);
-                tma_load_2d(st + 3 * TILE_BYTES, &map_b_lo, x, n0, fb);
+                const int x = kbeg + kb * KS;   // a multiple of KS: 128-byte aligned inner coordinate
+                tma_load_2d(st + 0 * TILE_BYTES, &map_a0, x, m0, fb);
+                tma_load_2d(st + 1 * TILE_BYTES, &map_a1, x, m0, fb);
+                if (NT == 3) tma_load_2d(st + 2 * TILE_BYTES, &map_a2, x, m0, fb);
+                tma_load_2d(st + (NT + 0) * TILE_BYTES, &map_b0, x, n0, fb);
+                tma_load_2d(st + (NT + 1) * TILE_BYTES, &map_b1, x, n0, fb);
+                if (NT == 3) tma_load_2d(st + (NT + 2) * TILE_BYTES, &map_b2, x, n0, fb);
                 ++issued;
             }
             if (!ok) {
@@ -263,7 +307,7 @@ __global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant_
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            const uint32_t idesc = BF16 ? idesc_bf16(BM, BN) : idesc_tf32(BM, BN);
+            const uint32_t idesc = C::BF16 ? idesc_bf16(BM, BN) : idesc_tf32(BM, BN);
             bool ok = true;
             for (int g = 0; g < ngroups && ok; ++g) {
                 const int b = g & 1;
@@ -277,18 +321,19 @@ __global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant_
                     if (!mbar_wait(bar_full0 + 8 * s, (kb / STAGES) & 1, status, budget)) { ok = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t st = base + s * STAGE_BYTES;
-                    const uint64_t a_hi = smem_desc_sw128(st + 0 * TILE_BYTES);
-                    const uint64_t a_lo = smem_desc_sw128(st + 1 * TILE_BYTES);
-                    const uint64_t b_hi = smem_desc_sw128(st + 2 * TILE_BYTES);
-                    const uint64_t b_lo = smem_desc_sw128(st + 3 * TILE_BYTES);
+                    uint64_t da[3], db[3];
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) {
+                        const int tt = t < NT ? t : NT - 1;   // unused third part for two-part splits
+                        da[t] = smem_desc_sw128(st + tt * TILE_BYTES);
+                        db[t] = smem_desc_sw128(st + (NT + tt) * TILE_BYTES);
+                    }
                     const uint32_t first = (kb == g * GROUP) ? 1u : 0u;
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         // 8 tf32 or 16 bf16 = 32 bytes along K per MMA
                         const uint64_t adv = (uint64_t)((j * 32) >> 4);
-                        mma_x<BF16>(dacc, a_hi + adv, b_lo + adv, idesc, (first && j == 0) ? 0u : 1u);
-                        mma_x<BF16>(dacc, a_lo + adv, b_hi + adv, idesc, 1u);
-                        mma_x<BF16>(dacc, a_hi + adv, b_hi + adv, idesc, 1u);
+                        mma_split<MODE>(dacc, da, db, adv, idesc, (first && j == 0) ? 0u : 1u);
                     }
                     mma_commit(bar_empty0 + 8 * s);
                 }
@@ -387,28 +432,33 @@ int make_map(CUtensorMap* map, const void* ptr, int rows, int cols, bool bf16 = 
 }  // namespace tc
 
 namespace {
-template <bool BF16>
-int gemm_split3(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st,
-                long long budget, int withhold_loads) {
+template <int MODE>
+int gemm_split(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st,
+               long long budget, int withhold_loads) {
     using namespace tc;
-    constexpr int KS = BF16 ? BK16 : BK;
+    using C = Cfg<MODE>;
+    constexpr int KS = C::KS;
     const int M = g.k_out, N = 2 * p_pad(P), K = g.r_pad;
     if (M % BM || N % BN || K % KS) {
-        set_last_error("kg_gemm_split3", "shape not tile aligned");
+        set_last_error("kg_gemm_split", "shape not tile aligned");
         return WP_ERR_SIZE;
     }
-    CUtensorMap ma_hi, ma_lo, mb_hi, mb_lo;
+    CUtensorMap ma[3], mb[3];
     int rc;
-    if (BF16) {
-        if ((rc = make_map(&ma_hi, w.hb_hi, M, K, true))) return rc;
-        if ((rc = make_map(&ma_lo, w.hb_lo, M, K, true))) return rc;
-        if ((rc = make_map(&mb_hi, w.fb_hi, N, K, true))) return rc;
-        if ((rc = make_map(&mb_lo, w.fb_lo, N, K, true))) return rc;
+    if (C::BF16) {
+        if ((rc = make_map(&ma[0], w.hb_hi, M, K, true))) return rc;
+        if ((rc = make_map(&ma[1], w.hb_lo, M, K, true))) return rc;
+        if ((rc = make_map(&ma[2], w.hb_lo2, M, K, true))) return rc;
+        if ((rc = make_map(&mb[0], w.fb_hi, N, K, true))) return rc;
+        if ((rc = make_map(&mb[1], w.fb_lo, N, K, true))) return rc;
+        if ((rc = make_map(&mb[2], w.fb_lo2, N, K, true))) return rc;
     } else {
-        if ((rc = make_map(&ma_hi, w.h_hi, M, K))) return rc;
-        if ((rc = make_map(&ma_lo, w.h_lo, M, K))) return rc;
-        if ((rc = make_map(&mb_hi, w.f_hi, N, K))) return rc;
-        if ((rc = make_map(&mb_lo, w.f_lo, N, K))) return rc;
+        if ((rc = make_map(&ma[0], w.h_hi, M, K))) return rc;
+        if ((rc = make_map(&ma[1], w.h_lo, M, K))) return rc;
+        ma[2] = ma[1];   // no third part
+        if ((rc = make_map(&mb[0], w.f_hi, N, K))) return rc;
+        if ((rc = make_map(&mb[1], w.f_lo, N, K))) return rc;
+        mb[2] = mb[1];
     }
     const int tiles = (M / BM) * (N / BN);
     const int split = (tiles < 152 && (K / 2) % KS == 0) ? 2 : 1;
@@ -417,13 +467,13 @@ int gemm_split3(const Geom& g, const KgWork& w, int P, float2* radial, int* stat
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(k_hankel_tf32x3<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        SMEM_BYTES);
+        attr_err = cudaFuncSetAttribute(k_hankel_tf32x3<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        C::SMEM_BYTES);
     });
     WP_CUDA(attr_err);
     dim3 grid(N / BN, M / BM, split);
-    k_hankel_tf32x3<BF16><<<grid, 192, SMEM_BYTES, st>>>(ma_hi, ma_lo, mb_hi, mb_lo, M, K, split, P, radial,
-                                                         split > 1, status, budget, withhold_loads);
+    k_hankel_tf32x3<MODE><<<grid, 192, C::SMEM_BYTES, st>>>(ma[0], ma[1], ma[2], mb[0], mb[1], mb[2], M, K, split,
+                                                            P, radial, split > 1, status, budget, withhold_loads);
     WP_LAUNCH_CHECK("k_hankel_tf32x3");
     return WP_OK;
 }
@@ -431,11 +481,15 @@ int gemm_split3(const Geom& g, const KgWork& w, int P, float2* radial, int* stat
 
 int kg_gemm_tf32x3_ex(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st,
                       long long budget, int withhold_loads) {
-    return gemm_split3<false>(g, w, P, radial, status, st, budget, withhold_loads);
+    return gemm_split<0>(g, w, P, radial, status, st, budget, withhold_loads);
 }
 
 int kg_gemm_bf16x3(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st) {
-    return gemm_split3<true>(g, w, P, radial, status, st, tc::WAIT_BUDGET, 0);
+    return gemm_split<1>(g, w, P, radial, status, st, tc::WAIT_BUDGET, 0);
+}
+
+int kg_gemm_bf16x6(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st) {
+    return gemm_split<2>(g, w, P, radial, status, st, tc::WAIT_BUDGET, 0);
 }
 
 int kg_gemm_tf32x3(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st) {

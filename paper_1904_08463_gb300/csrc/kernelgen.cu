@@ -30,7 +30,8 @@ __device__ __forceinline__ float to_tf32(float x) {
 }
 
 // x split as hi + lo with hi = bf16(x) and lo = bf16(x - hi), both round-to-nearest-even:
-// together about 16 significant bits (the BF16x3 route's operands).
+// together about 16 significant bits (the BF16x3 route's operands).  Each remainder is
+// exact in FP32 (it holds the low bits of x).
 __device__ __forceinline__ void split_bf16(float x, uint16_t& hi, uint16_t& lo) {
     const __nv_bfloat16 h = __float2bfloat16_rn(x);
     const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
@@ -38,16 +39,29 @@ __device__ __forceinline__ void split_bf16(float x, uint16_t& hi, uint16_t& lo) 
     lo = __bfloat16_as_ushort(l);
 }
 
-// BF16 hi/lo split of an FP32 array (the transform matrix of the BF16x3 route; splitting the
-// FP32 value loses nothing: its 24 bits exceed the pair's 16).
+// Three-part split x = hi + lo + lo2 (the BF16x6 route's operands): lo2 = bf16 of what the
+// pair leaves, so the three parts carry all 24 bits of the FP32 value.
+__device__ __forceinline__ void split_bf16_3(float x, uint16_t& hi, uint16_t& lo, uint16_t& lo2) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(h);
+    const __nv_bfloat16 l = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 l2 = __float2bfloat16_rn(r1 - __bfloat162float(l));
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(l);
+    lo2 = __bfloat16_as_ushort(l2);
+}
+
+// BF16 split of an FP32 array into three parts (the transform matrix of the BF16 routes:
+// BF16x3 reads the first two, BF16x6 all three; hi and lo are the pair split_bf16 gives).
 __global__ void k_split_bf16(int64_t n, const float* __restrict__ x, uint16_t* __restrict__ hi,
-                             uint16_t* __restrict__ lo) {
+                             uint16_t* __restrict__ lo, uint16_t* __restrict__ lo2) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    uint16_t h, l;
-    split_bf16(x[i], h, l);
+    uint16_t h, l, l2;
+    split_bf16_3(x[i], h, l, l2);
     hi[i] = h;
     lo[i] = l;
+    lo2[i] = l2;
 }
 
 __global__ void k_j0_matrix(int k_out, int R, int r_pad, int os, float* __restrict__ h32,
@@ -134,7 +148,7 @@ int kg_prepare(const Geom& g, const KgWork& w, cudaStream_t st) {
         k_j0_matrix<<<(unsigned)blocks, threads, 0, st>>>(g.k_out, g.R, g.r_pad, g.os, w.h32, w.h_hi,
                                                            w.h_lo);
         WP_LAUNCH_CHECK("k_j0_matrix");
-        k_split_bf16<<<(unsigned)blocks, threads, 0, st>>>(total, w.h32, w.hb_hi, w.hb_lo);
+        k_split_bf16<<<(unsigned)blocks, threads, 0, st>>>(total, w.h32, w.hb_hi, w.hb_lo, w.hb_lo2);
         WP_LAUNCH_CHECK("k_split_bf16");
     }
     std::vector<float> band;
@@ -157,12 +171,14 @@ int kg_prepare(const Geom& g, const KgWork& w, cudaStream_t st) {
 // p is exact, and one final rounding gives the reduced phase -- as accurate as the FP64
 // product rounded to float, on the FP32 units (FP64 throughput is low on this part).
 // =======================================================================================
-// MODE 0: FP32 rows (SIMT product); 1: TF32 hi/lo rows; 2: BF16 hi/lo rows.
+// MODE 0: FP32 rows (SIMT product); 1: TF32 hi/lo rows; 2: BF16 hi/lo rows; 3: BF16
+// hi/lo/lo2 rows.
 template <int MODE>
 __global__ void k_screen(int R, int r_pad, int P, int P_pad, const float2* __restrict__ nm1f,
                          const float* __restrict__ taper, const double* __restrict__ w_planes,
                          float* __restrict__ f32, float* __restrict__ f_hi, float* __restrict__ f_lo,
-                         uint16_t* __restrict__ fb_hi, uint16_t* __restrict__ fb_lo) {
+                         uint16_t* __restrict__ fb_hi, uint16_t* __restrict__ fb_lo,
+                         uint16_t* __restrict__ fb_lo2) {
     __shared__ float2 wsplit;
     const int p = blockIdx.y;
     if (threadIdx.x == 0) {
@@ -198,6 +214,9 @@ __global__ void k_screen(int R, int r_pad, int P, int P_pad, const float2* __res
     } else if (MODE == 2) {
         split_bf16(re, fb_hi[row_re], fb_lo[row_re]);
         split_bf16(im, fb_hi[row_im], fb_lo[row_im]);
+    } else if (MODE == 3) {
+        split_bf16_3(re, fb_hi[row_re], fb_lo[row_re], fb_lo2[row_re]);
+        split_bf16_3(im, fb_hi[row_im], fb_lo[row_im], fb_lo2[row_im]);
     } else {
         f32[row_re] = re;
         f32[row_im] = im;
@@ -210,13 +229,16 @@ int kg_screen(const Geom& g, const KgWork& w, const float* taper, const double* 
     dim3 grid((g.r_pad + 255) / 256, Pp);
     if (g.kernelgen == WP_KG_TF32X3)
         k_screen<1><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo,
-                                          w.fb_hi, w.fb_lo);
+                                          w.fb_hi, w.fb_lo, w.fb_lo2);
     else if (g.kernelgen == WP_KG_BF16X3)
         k_screen<2><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo,
-                                          w.fb_hi, w.fb_lo);
+                                          w.fb_hi, w.fb_lo, w.fb_lo2);
+    else if (g.kernelgen == WP_KG_BF16X6)
+        k_screen<3><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo,
+                                          w.fb_hi, w.fb_lo, w.fb_lo2);
     else
         k_screen<0><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo,
-                                          w.fb_hi, w.fb_lo);
+                                          w.fb_hi, w.fb_lo, w.fb_lo2);
     WP_LAUNCH_CHECK("k_screen");
     return WP_OK;
 }

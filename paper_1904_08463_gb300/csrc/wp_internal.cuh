@@ -78,6 +78,7 @@ struct KgWork {
     float* h_lo;       // [k_out][r_pad] TF32 low part
     uint16_t* hb_hi;   // [k_out][r_pad] BF16 high part (BF16x3 route)
     uint16_t* hb_lo;   // [k_out][r_pad] BF16 low part
+    uint16_t* hb_lo2;  // [k_out][r_pad] BF16 third part (BF16x6 route)
     float* band;       // [65][k_out] spline inverse band (row d holds A^-1[k][k + d - 32])
     double* nm1;       // [R] n - 1 = sqrt(1 - r_i^2) - 1 at the radial nodes
     float2* nm1f;      // [R] the same as an unevaluated float pair (hi, lo)
@@ -88,6 +89,7 @@ struct KgWork {
     float* f_lo;       // [2 P_pad][r_pad]
     uint16_t* fb_hi;   // [2 P_pad][r_pad] BF16 split of the image-domain functions (BF16x3 route)
     uint16_t* fb_lo;   // [2 P_pad][r_pad]
+    uint16_t* fb_lo2;  // [2 P_pad][r_pad] third part (BF16x6 route)
     float* gct;        // [2 P_pad][k_out] radial-line gradient rows (re, im) for the adjoint
     int*   status;     // [4]
 };
@@ -176,6 +178,7 @@ int kg_gemm_fp32(const Geom& g, const KgWork& w, int P, float2* radial, cudaStre
 int kg_gemm_tf32x3(const Geom& g, const KgWork& w, int P, float2* radial, int* status,
                    cudaStream_t st);
 int kg_gemm_bf16x3(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st);
+int kg_gemm_bf16x6(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st);
 int kg_gemm_tf32x3_ex(const Geom& g, const KgWork& w, int P, float2* radial, int* status, cudaStream_t st,
                       long long budget, int withhold_loads);
 int kg_ps_prepare(const Geom& g, const KgWork& w, cudaStream_t st);

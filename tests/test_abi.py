@@ -48,10 +48,24 @@ def test_plan_geometry():
     assert g.k_out == 1152 and g.fft_workspace == 256
 
 
+def test_every_named_route_is_a_valid_plan():
+    """Each kernel-generation route the binding names (FP32, TF32x3, projection slice, BF16x3,
+    BF16x6) is accepted, and the workspace does not depend on the route."""
+    L, lib = _lib()
+    sizes = set()
+    for name, code in L.KERNELGEN.items():
+        p = L.WpPlan(256, 1e-4, 8, 15, 3, 0.01, 512, 0, code, 0, 0)
+        g = L.WpGeometry()
+        assert lib.wp_plan_geometry(ctypes.byref(p), ctypes.byref(g)) == 0, name
+        sizes.add(lib.wp_kernelgen_workspace_bytes(ctypes.byref(p), 100))
+    assert sorted(L.KERNELGEN.values()) == [0, 1, 2, 3, 4]
+    assert len(sizes) == 1 and sizes.pop() > 0
+
+
 @pytest.mark.parametrize("field,value", [("image_size", 255), ("image_size", 8), ("cell_size", 0.0),
                                          ("cell_size", 0.01), ("oversampling", 0), ("oversampling", 17),
                                          ("max_support", 0), ("max_support", 200), ("min_support", 16),
-                                         ("radial_samples", 4), ("interp", 2), ("kernelgen", 7),
+                                         ("radial_samples", 4), ("interp", 2), ("kernelgen", 5), ("kernelgen", -1),
                                          ("trunc_frac", 1.0), ("grid_tile", 48),
                                          ("grid_method", 5)])
 def test_invalid_plans_rejected(field, value):

@@ -46,7 +46,7 @@ def _compare(g, wk, ks, tol=KERNEL_TOL):
         assert e < tol, f"plane {p}: cache rel. L2 {e:.3e}"
 
 
-@pytest.mark.parametrize("kernelgen", ["fp32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("kernelgen", ["fp32", "tf32x3", "bf16x3", "bf16x6"])
 def test_small_imaging_kernels(kernelgen):
     """256^2, 2 deg FOV, 16 |w|-planes <= 500, os 8, R 512, S_max 15, 1 % truncation."""
     N, dl = 256, np.deg2rad(2.0) / 256
@@ -55,7 +55,7 @@ def test_small_imaging_kernels(kernelgen):
     _compare(g, wk, ks)
 
 
-@pytest.mark.parametrize("kernelgen", ["fp32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("kernelgen", ["fp32", "tf32x3", "bf16x3", "bf16x6"])
 @pytest.mark.parametrize("os_,R,P,interp", [(1, 300, 5, "cubic"), (4, 97, 3, "linear"),
                                             (16, 256, 70, "cubic"), (8, 2048, 130, "linear")])
 def test_kernels_ragged_shapes(os_, R, P, interp, kernelgen):
@@ -69,7 +69,7 @@ def test_kernels_ragged_shapes(os_, R, P, interp, kernelgen):
     _compare(g, wk, ks)
 
 
-@pytest.mark.parametrize("kernelgen", ["fp32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("kernelgen", ["fp32", "tf32x3", "bf16x3", "bf16x6"])
 def test_large_w_kernels_sampled(kernelgen):
     """1024 signed planes linspace[-20000, 20000] (512 distinct |w|), R 4096, os 8,
     supports 7..127 growing with |w|, 8 degree FOV on 4096^2: every plane is generated
@@ -96,8 +96,9 @@ def test_large_w_kernels_sampled(kernelgen):
 
 
 def test_tensor_core_route_matches_fp32_route_on_every_plane():
-    """All 512 planes of the large-|w| batch: the tcgen05 TF32x3 radial lines agree with the
-    FP32 SIMT ones to well inside the kernel tolerance (both are ~1e-7 from FP64)."""
+    """All 512 planes of the large-|w| batch: the tcgen05 TF32x3 and BF16x6 radial lines agree
+    with the FP32 SIMT ones to well inside the kernel tolerance (all are ~1e-7 from FP64;
+    the six-product BF16 split keeps all 24 bits of the FP32 operands)."""
     wp = _wp()
     dev = torch.device("cuda")
     N, dl, R = 4096, np.deg2rad(8.0) / 4096, 4096
@@ -105,13 +106,14 @@ def test_tensor_core_route_matches_fp32_route_on_every_plane():
     taper = torch.tensor(synth.gaussian_taper_samples(N, dl, R), dtype=torch.float32, device=dev)
     w = torch.tensor(aw, dtype=torch.float64, device=dev)
     out = {}
-    for kg in ("fp32", "tf32x3"):
+    for kg in ("fp32", "tf32x3", "bf16x6"):
         plan = wp.Plan(N, dl, 8, 127, 7, 0.0, R, "cubic", kg)
         ws = wp.kernelgen_prepare(plan, len(aw))
         out[kg] = wp.hankel_radial(plan, taper, w, ws)[0].cpu().numpy()
-    num = np.linalg.norm(out["fp32"] - out["tf32x3"], axis=1)
     den = np.linalg.norm(out["fp32"], axis=1)
-    assert (num / den).max() < 2e-6
+    for kg in ("tf32x3", "bf16x6"):
+        num = np.linalg.norm(out["fp32"] - out[kg], axis=1)
+        assert (num / den).max() < 2e-6, kg
 
 
 @pytest.mark.parametrize("os_,interp", [(3, "cubic"), (5, "linear"), (8, "cubic")])
@@ -157,7 +159,7 @@ def test_resample_staged_rows_odd_os_unaligned_cache(os_, interp):
                 assert not np.any(k[:, fu][..., 0])
 
 
-@pytest.mark.parametrize("kernelgen", ["tf32x3", "bf16x3", "projslice"])
+@pytest.mark.parametrize("kernelgen", ["tf32x3", "bf16x3", "bf16x6", "projslice"])
 def test_prolate_taper_kernels(kernelgen):
     """The radially symmetric prolate spheroidal taper (c = 3 pi) instead of the Gaussian:
     the small imaging geometry's kernels against the oracle, by both Hankel routes."""
@@ -197,7 +199,7 @@ def test_resample_largest_support():
         assert e < KERNEL_TOL, f"plane {p} (S = {sup[p]}): cache rel. L2 {e:.3e}"
 
 
-@pytest.mark.parametrize("kernelgen", ["tf32x3", "bf16x3", "projslice"])
+@pytest.mark.parametrize("kernelgen", ["tf32x3", "bf16x3", "bf16x6", "projslice"])
 def test_every_radial_line_of_the_512_plane_batch(kernelgen):
     """All 512 radial lines of the headline batch (R 4096, K_out 1152, |w| to 20000) against
     the FP64 oracle, each within the kernel tolerance (the caches are sampled elsewhere)."""
@@ -229,7 +231,7 @@ def test_one_prepared_workspace_serves_every_route():
     taper = torch.tensor(synth.gaussian_taper_samples(N, dl, R), dtype=torch.float32, device=dev)
     base = wp.Plan(N, dl, 8, 15, 3, 0.0, R, "cubic", "tf32x3")
     shared = wp.kernelgen_prepare(base, 16)
-    for kg in ("fp32", "tf32x3", "bf16x3", "projslice"):
+    for kg in ("fp32", "tf32x3", "bf16x3", "bf16x6", "projslice"):
         plan = base.replace(kernelgen=kg)
         own = wp.kernelgen_prepare(plan, 16)
         a = wp.hankel_radial(plan, taper, planes, shared)[0].cpu().numpy()
