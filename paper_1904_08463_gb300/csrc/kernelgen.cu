@@ -171,74 +171,100 @@ int kg_prepare(const Geom& g, const KgWork& w, cudaStream_t st) {
 // p is exact, and one final rounding gives the reduced phase -- as accurate as the FP64
 // product rounded to float, on the FP32 units (FP64 throughput is low on this part).
 // =======================================================================================
+// One block per plane: the plane's w is split once, then every thread takes pairs of
+// consecutive radial samples (one 8-byte FP32 / TF32 store or one 4-byte BF16-pair store per
+// row and part), which keeps the per-plane latency chain short and the stores wide.
 // MODE 0: FP32 rows (SIMT product); 1: TF32 hi/lo rows; 2: BF16 hi/lo rows; 3: BF16
 // hi/lo/lo2 rows.
-template <int MODE>
-__global__ void k_screen(int R, int r_pad, int P, int P_pad, const float2* __restrict__ nm1f,
-                         const float* __restrict__ taper, const double* __restrict__ w_planes,
-                         float* __restrict__ f32, float* __restrict__ f_hi, float* __restrict__ f_lo,
-                         uint16_t* __restrict__ fb_hi, uint16_t* __restrict__ fb_lo,
-                         uint16_t* __restrict__ fb_lo2) {
-    __shared__ float2 wsplit;
-    const int p = blockIdx.y;
-    if (threadIdx.x == 0) {
-        const double wd = (p < P) ? w_planes[p] : 0.0;
-        const float hi = (float)wd;
-        wsplit = make_float2(hi, (float)(wd - (double)hi));
-    }
-    __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= r_pad) return;
+constexpr int SC_THREADS = 256;
+
+__device__ __forceinline__ float2 screen_value(int i, int R, bool live, float2 w, const float2* __restrict__ nm1f,
+                                               const float* __restrict__ taper) {
     float re = 0.0f, im = 0.0f;
-    if (i < R && p < P) {
+    if (live && i < R) {
         const float2 n = nm1f[i];
-        const float2 w = wsplit;
         const float ph = w.x * n.x;
         float pl = fmaf(w.x, n.x, -ph);               // exact error of the high product
         pl = fmaf(w.x, n.y, fmaf(w.y, n.x, pl));      // cross terms
         const float fr = (ph - rintf(ph)) + pl;       // phase / (2 pi), reduced
-        float s, c;
-        sincospif(2.0f * fr, &s, &c);
-        float t = taper[i];
-        re = t * c;
-        im = t * s;
+        float sn, cs;
+        sincospif(2.0f * fr, &sn, &cs);
+        const float t = taper[i];
+        re = t * cs;
+        im = t * sn;
     }
-    int64_t row_re = (int64_t)(2 * p) * r_pad + i;
-    int64_t row_im = row_re + r_pad;
-    if (MODE == 1) {
-        float hr = to_tf32(re), hi = to_tf32(im);
-        f_hi[row_re] = hr;
-        f_hi[row_im] = hi;
-        f_lo[row_re] = to_tf32(re - hr);
-        f_lo[row_im] = to_tf32(im - hi);
-    } else if (MODE == 2) {
-        split_bf16(re, fb_hi[row_re], fb_lo[row_re]);
-        split_bf16(im, fb_hi[row_im], fb_lo[row_im]);
-    } else if (MODE == 3) {
-        split_bf16_3(re, fb_hi[row_re], fb_lo[row_re], fb_lo2[row_re]);
-        split_bf16_3(im, fb_hi[row_im], fb_lo[row_im], fb_lo2[row_im]);
-    } else {
-        f32[row_re] = re;
-        f32[row_im] = im;
+    return make_float2(re, im);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(uint16_t a, uint16_t b) { return (uint32_t)a | ((uint32_t)b << 16); }
+
+template <int MODE>
+__global__ void __launch_bounds__(SC_THREADS) k_screen(int R, int r_pad, int P, const float2* __restrict__ nm1f,
+                                                       const float* __restrict__ taper,
+                                                       const double* __restrict__ w_planes,
+                                                       float* __restrict__ f32, float* __restrict__ f_hi,
+                                                       float* __restrict__ f_lo, uint16_t* __restrict__ fb_hi,
+                                                       uint16_t* __restrict__ fb_lo, uint16_t* __restrict__ fb_lo2) {
+    const int p = blockIdx.x;
+    const bool live = p < P;
+    const double wd = live ? w_planes[p] : 0.0;
+    const float whi = (float)wd;
+    const float2 w = make_float2(whi, (float)(wd - (double)whi));
+    const int64_t row_re = (int64_t)(2 * p) * r_pad;
+    const int64_t row_im = row_re + r_pad;
+    for (int i = 2 * (int)threadIdx.x; i < r_pad; i += 2 * SC_THREADS) {   // r_pad is even
+        const float2 v0 = screen_value(i, R, live, w, nm1f, taper);
+        const float2 v1 = screen_value(i + 1, R, live, w, nm1f, taper);
+        if (MODE == 1) {
+            const float hr0 = to_tf32(v0.x), hr1 = to_tf32(v1.x), hi0 = to_tf32(v0.y), hi1 = to_tf32(v1.y);
+            *reinterpret_cast<float2*>(f_hi + row_re + i) = make_float2(hr0, hr1);
+            *reinterpret_cast<float2*>(f_hi + row_im + i) = make_float2(hi0, hi1);
+            *reinterpret_cast<float2*>(f_lo + row_re + i) = make_float2(to_tf32(v0.x - hr0), to_tf32(v1.x - hr1));
+            *reinterpret_cast<float2*>(f_lo + row_im + i) = make_float2(to_tf32(v0.y - hi0), to_tf32(v1.y - hi1));
+        } else if (MODE == 2) {
+            uint16_t a0, b0, a1, b1, c0, d0, c1, d1;
+            split_bf16(v0.x, a0, b0);
+            split_bf16(v1.x, a1, b1);
+            split_bf16(v0.y, c0, d0);
+            split_bf16(v1.y, c1, d1);
+            *reinterpret_cast<uint32_t*>(fb_hi + row_re + i) = pack_bf16(a0, a1);
+            *reinterpret_cast<uint32_t*>(fb_lo + row_re + i) = pack_bf16(b0, b1);
+            *reinterpret_cast<uint32_t*>(fb_hi + row_im + i) = pack_bf16(c0, c1);
+            *reinterpret_cast<uint32_t*>(fb_lo + row_im + i) = pack_bf16(d0, d1);
+        } else if (MODE == 3) {
+            uint16_t a0, b0, e0, a1, b1, e1, c0, d0, g0, c1, d1, g1;
+            split_bf16_3(v0.x, a0, b0, e0);
+            split_bf16_3(v1.x, a1, b1, e1);
+            split_bf16_3(v0.y, c0, d0, g0);
+            split_bf16_3(v1.y, c1, d1, g1);
+            *reinterpret_cast<uint32_t*>(fb_hi + row_re + i) = pack_bf16(a0, a1);
+            *reinterpret_cast<uint32_t*>(fb_lo + row_re + i) = pack_bf16(b0, b1);
+            *reinterpret_cast<uint32_t*>(fb_lo2 + row_re + i) = pack_bf16(e0, e1);
+            *reinterpret_cast<uint32_t*>(fb_hi + row_im + i) = pack_bf16(c0, c1);
+            *reinterpret_cast<uint32_t*>(fb_lo + row_im + i) = pack_bf16(d0, d1);
+            *reinterpret_cast<uint32_t*>(fb_lo2 + row_im + i) = pack_bf16(g0, g1);
+        } else {
+            *reinterpret_cast<float2*>(f32 + row_re + i) = make_float2(v0.x, v1.x);
+            *reinterpret_cast<float2*>(f32 + row_im + i) = make_float2(v0.y, v1.y);
+        }
     }
 }
 
 int kg_screen(const Geom& g, const KgWork& w, const float* taper, const double* w_planes, int P,
               cudaStream_t st) {
-    int Pp = p_pad(P);
-    dim3 grid((g.r_pad + 255) / 256, Pp);
+    const int Pp = p_pad(P);
     if (g.kernelgen == WP_KG_TF32X3)
-        k_screen<1><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo,
-                                          w.fb_hi, w.fb_lo, w.fb_lo2);
+        k_screen<1><<<Pp, SC_THREADS, 0, st>>>(g.R, g.r_pad, P, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo,
+                                               w.fb_hi, w.fb_lo, w.fb_lo2);
     else if (g.kernelgen == WP_KG_BF16X3)
-        k_screen<2><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo,
-                                          w.fb_hi, w.fb_lo, w.fb_lo2);
+        k_screen<2><<<Pp, SC_THREADS, 0, st>>>(g.R, g.r_pad, P, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo,
+                                               w.fb_hi, w.fb_lo, w.fb_lo2);
     else if (g.kernelgen == WP_KG_BF16X6)
-        k_screen<3><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo,
-                                          w.fb_hi, w.fb_lo, w.fb_lo2);
+        k_screen<3><<<Pp, SC_THREADS, 0, st>>>(g.R, g.r_pad, P, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo,
+                                               w.fb_hi, w.fb_lo, w.fb_lo2);
     else
-        k_screen<0><<<grid, 256, 0, st>>>(g.R, g.r_pad, P, Pp, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo,
-                                          w.fb_hi, w.fb_lo, w.fb_lo2);
+        k_screen<0><<<Pp, SC_THREADS, 0, st>>>(g.R, g.r_pad, P, w.nm1f, taper, w_planes, w.f32, w.f_hi, w.f_lo,
+                                               w.fb_hi, w.fb_lo, w.fb_lo2);
     WP_LAUNCH_CHECK("k_screen");
     return WP_OK;
 }
@@ -337,7 +363,7 @@ int kg_gemm_fp32(const Geom& g, const KgWork& w, int P, float2* radial, cudaStre
 // Spline: m = A^-1 rhs with rhs_0 = 6 (y1 - y0), rhs_k = 6 (y_{k+1} - 2 y_k + y_{k-1}),
 // rhs_{K-1} = 0 (zero slope at rho = 0, natural end), using the precomputed band of A^-1.
 // =======================================================================================
-constexpr int TS_THREADS = 256;   // threads per plane of the truncation / spline kernel
+constexpr int TS_THREADS = 384;   // threads per plane of the truncation / spline kernel (3 rows each at K 1152)
 
 __global__ void __launch_bounds__(TS_THREADS) k_trunc_spline(int K, int os, int s_min, int s_max, float tau,
                                                       int do_trunc, int do_spline,
@@ -351,8 +377,17 @@ __global__ void __launch_bounds__(TS_THREADS) k_trunc_spline(int K, int os, int 
     __shared__ float red_f[TS_THREADS / 32];
     __shared__ int red_i[TS_THREADS / 32];
     __shared__ float toe[65];        // one interior row of the band (Toeplitz coefficients)
+    __shared__ float edge[65 * 64];  // the band's 32 first and 32 last rows: edge[d * 64 + kk]
     const int p = blockIdx.x;
-    if (do_spline && threadIdx.x < 65) toe[threadIdx.x] = band[(int64_t)threadIdx.x * K + K / 2];
+    if (do_spline) {
+        if (threadIdx.x < 65) toe[threadIdx.x] = band[(int64_t)threadIdx.x * K + K / 2];
+        // staged by the whole block (coalesced along k) instead of 65 dependent strided loads
+        // on the first and last warps' critical path; K >= 128
+        for (int i = threadIdx.x; i < 65 * 64; i += blockDim.x) {
+            const int d = i >> 6, kk = i & 63;
+            edge[i] = band[(int64_t)d * K + (kk < 32 ? kk : K - 64 + kk)];
+        }
+    }
     const float2* src = radial + (int64_t)p * K;
     float local_max = 0.0f;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
@@ -416,9 +451,10 @@ __global__ void __launch_bounds__(TS_THREADS) k_trunc_spline(int K, int os, int 
                     mi = fmaf(toe[d], r.y, mi);
                 }
             } else {
+                const int kk = k < 32 ? k : k - (K - 64);
 #pragma unroll 13
                 for (int d = 0; d < 65; ++d) {
-                    const float c = band[(int64_t)d * K + k];    // zero where k + d - 32 is outside
+                    const float c = edge[d * 64 + kk];    // zero where k + d - 32 is outside
                     const float2 r = rhs[k + d - 32];
                     mr = fmaf(c, r.x, mr);
                     mi = fmaf(c, r.y, mi);
@@ -435,8 +471,8 @@ int kg_trunc_spline(const Geom& g, const KgWork& w, int P, const float2* radial,
     int do_spline = (g.interp == WP_INTERP_CUBIC) ? 1 : 0;
     if (!do_trunc && !do_spline) return WP_OK;
     size_t smem = (size_t)(2 * g.k_out + 64) * sizeof(float2);
-    if (smem > 48 * 1024)
-        WP_CUDA(cudaFuncSetAttribute(k_trunc_spline, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // static staging (~17 KB) + dynamic can pass the 48 KB default from K ~ 1900 on
+    WP_CUDA(cudaFuncSetAttribute(k_trunc_spline, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_trunc_spline<<<P, TS_THREADS, smem, st>>>(g.k_out, g.os, g.s_min, g.s_max, (float)g.tau, do_trunc,
                                          do_spline, radial, w.band, spline_m, support);
     WP_LAUNCH_CHECK("k_trunc_spline");
