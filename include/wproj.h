@@ -124,7 +124,11 @@ typedef struct wp_geometry {
  * and holds os*os sub-kernels [fv][fu], each (2 S_p + 1)^2 taps [jy][jx], where the
  * tap (jx, jy) of sub-kernel (fu, fv) is the kernel at uv offset
  * (jx - S_p - fu/os, jy - S_p - fv/os) cells.  Kernels are for +|w|; a visibility with
- * w < 0 uses the complex conjugate (Section 4.1).
+ * w < 0 uses the complex conjugate (Section 4.1).  offsets must give every block room for
+ * its support (wp_kernel_layout of the same supports, or wp_kernel_layout_max); a plane whose
+ * block is smaller is read and written with the largest support the block holds, or skipped
+ * when not even S = 1 fits, so a mismatched layout yields wrong taps for that plane but no
+ * access outside its block.
  */
 typedef struct wp_wkernels {
     int32_t        P;         /* number of |w| planes                                  */
@@ -223,7 +227,9 @@ int wp_selftest_bounded_wait(const wp_plan* plan, int32_t P, void* workspace,
  * x > os S (the truncated line rotated about rho = 0 has circular support).
  *   radial, spline_m  as written by wp_hankel_radial (spline_m unused for linear)
  *   support [P] int32 (values outside [1, S_max] are clamped), offsets [P+1] int64 (device),
- *   cache out (device memory), 8-byte aligned (WP_ERR_SIZE otherwise).
+ *   cache out (device memory), 8-byte aligned (WP_ERR_SIZE otherwise).  A plane whose block
+ *   [offsets[p], offsets[p+1]) is too small for its support gets the largest support that
+ *   fits (or is left unwritten): nothing is written outside the blocks.
  */
 int wp_resample(const wp_plan* plan, const float* radial, const float* spline_m, int32_t P,
                 const int32_t* support, const int64_t* offsets, float* cache, void* stream);

@@ -123,7 +123,8 @@ __global__ void __launch_bounds__(256) k_fft_extract(int L, int os, int s_max, i
                                                      const float2* __restrict__ Y, float2* __restrict__ cache) {
     const int b = blockIdx.z;
     const int p = p0 + b;
-    const int S = min(max(support[p], 1), s_max);
+    const int S = fit_support(min(max(support[p], 1), s_max), os, offsets, p);
+    if (S < 1) return;
     const int W = 2 * S + 1;
     const int span = os * W;                        // fine samples per axis of the footprint
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;

@@ -322,7 +322,8 @@ __global__ void __launch_bounds__(GRID_WARPS * 32, 3) k_grid(int N, int os, int 
         const int p = item / ntiles;
         const int t = item - p * ntiles;
         const int oy = t / ntx, ox = t - oy * ntx;
-        const int S = min(max(support[p], 1), s_max);
+        const int S = fit_support(min(max(support[p], 1), s_max), os, offsets, p);
+        if (S < 1) continue;   // block-uniform: the tile is untouched, the loop top syncs
         const int W = 2 * S + 1;
         const int W2 = W * W;
         const int D = (S + TILE - 1) / TILE;
@@ -398,7 +399,8 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_fm(int N, int os, int 
         const int p = item / ntiles;
         const int t = item - p * ntiles;
         const int oy = t / ntx, ox = t - oy * ntx;
-        const int S = min(max(support[p], 1), s_max);
+        const int S = fit_support(min(max(support[p], 1), s_max), os, offsets, p);
+        if (S < 1) continue;   // block-uniform: the tile is untouched, the loop top syncs
         const int W = 2 * S + 1;
         const int W2 = W * W;
         const int D = (S + TILE - 1) / TILE;
@@ -495,7 +497,8 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_ro(int N, int os, int 
         const int p = item / ntiles;
         const int t = item - p * ntiles;
         const int oy = t / ntx, ox = t - oy * ntx;
-        const int S = min(max(support[p], 1), s_max);
+        const int S = fit_support(min(max(support[p], 1), s_max), os, offsets, p);
+        if (S < 1) continue;   // block-uniform: the tile is untouched, the loop top syncs
         const int W = 2 * S + 1;
         const int W2 = W * W;
         const int D = (S + TILE - 1) / TILE;
@@ -742,7 +745,8 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_wp(int N, int os, int 
         const int ty0 = oy * WPT, tx0 = ox * WPT;
         int seq = 0;   // position in the item's visibility list (identical on every warp)
         for (int p = grp * PLANE_GROUP; p < min(P, (grp + 1) * PLANE_GROUP); ++p) {
-            const int S = min(max(support[p], 1), s_max);
+            const int S = fit_support(min(max(support[p], 1), s_max), os, offsets, p);
+            if (S < 1) continue;   // uniform over the block
             const int W = 2 * S + 1, W2 = W * W;
             const int D = (S + WPT - 1) / WPT;
             const float2* pcache = cache + offsets[p];
@@ -951,7 +955,8 @@ __global__ void __launch_bounds__(256) k_degrid(int N, int os, int s_max, int nb
     const int fu = r4.y & 0xff, fv = (r4.y >> 8) & 0xff;
     const float sgn = (r4.y >> 16) ? -1.0f : 1.0f;
     const int p = r4.z;
-    const int S = min(max(support[p], 1), s_max);
+    const int S = fit_support(min(max(support[p], 1), s_max), os, offsets, p);
+    if (S < 1) return;   // the whole warp; vis_out was zeroed
     const int W = 2 * S + 1;
     const float2* sub = cache + offsets[p] + (int64_t)(fv * os + fu) * W * W;
     const float2* g0 = grid + (int64_t)(iv - S) * N + (iu - S);

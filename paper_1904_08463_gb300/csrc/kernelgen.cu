@@ -549,7 +549,9 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample(int K, int os, int s_ma
     const int rep = item - p * nrep;
     const int h = os / 2;
     const int fv = rep / (h + 1), fu = rep - fv * (h + 1);   // 0 <= fu, fv <= os / 2
-    const int S = min(max(support[p], 1), s_max);   // supports outside [1, S_max] are clamped
+    // supports outside [1, S_max] are clamped, and to what the plane's block can hold
+    const int S = fit_support(min(max(support[p], 1), s_max), os, offsets, p);
+    if (S < 1) return;   // block-uniform, before any barrier
     const int W = 2 * S + 1;
     const int W2 = W * W;
     const int lim = os * S;

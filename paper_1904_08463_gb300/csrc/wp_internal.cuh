@@ -124,6 +124,20 @@ size_t carve_grid(const Geom& g, int P, int64_t V, void* ws, size_t bytes, GridW
 // resample (cache) and the on-the-fly gridder, so both produce the same bits.
 // ---------------------------------------------------------------------------------------
 #ifdef __CUDACC__
+// The support a kernel may use for plane p of a cache laid out by `offsets`: S itself when
+// its os^2 (2S+1)^2 taps fit the plane's block [offsets[p], offsets[p+1]) -- always, for a
+// layout from wp_kernel_layout of the same supports -- else the largest support that fits, or
+// 0 (skip the plane) when not even S = 1 does.  Every kernel that turns (support, offsets)
+// into cache indices goes through it, so a caller's inconsistent layout gives wrong taps for
+// that plane but no access outside its block.
+__device__ __forceinline__ int fit_support(int S, int os, const int64_t* __restrict__ offsets, int p) {
+    const int64_t blk = offsets[p + 1] - offsets[p];
+    const int64_t os2 = (int64_t)os * os;
+    int s = S;
+    while (s >= 1 && os2 * (2 * (int64_t)s + 1) * (2 * (int64_t)s + 1) > blk) --s;
+    return s;
+}
+
 __device__ __forceinline__ int skew(int k) { return k ^ ((k >> 3) & 7); }
 
 // Spline interval of radius sqrt(q) on the unit-spaced line: k = round(x - 1/2) through the
