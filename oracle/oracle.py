@@ -476,10 +476,15 @@ def dft_image(geom: Geometry, uvw: np.ndarray, vis: np.ndarray, wt=None, pixels=
 
 def mean_w_planes(w: np.ndarray, P: int) -> np.ndarray:
     """Plane values as in Alg. 2 steps 1-3: sort |w|, cut into P equal-count chunks, take
-    each chunk's mean (the paper's default, `wplanes_median: false`, Section 5)."""
+    each chunk's mean (the paper's default, `wplanes_median: false`, Section 5).  Reading:
+    non-finite |w| take no part (they are dropped at binning); a chunk left empty (fewer
+    finite values than planes) takes the largest finite |w| (0 if none), so the values stay
+    ascending."""
     aw = np.sort(np.abs(np.asarray(w, dtype=np.float64)))
+    aw = aw[np.isfinite(aw)]
+    top = aw[-1] if aw.size else 0.0
     chunks = np.array_split(aw, P)
-    return np.array([c.mean() for c in chunks], dtype=np.float64)
+    return np.array([c.mean() if c.size else top for c in chunks], dtype=np.float64)
 
 
 # --------------------------------------------------------------------------------------

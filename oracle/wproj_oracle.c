@@ -278,7 +278,8 @@ void or_resample(int K, const double *y, const double *m, int os, int S, int int
  *   conj   = 1 if w < 0 (kernel of -w is the conjugate of the kernel of |w|);
  *   uc     = u / du + N/2 (continuous grid coordinate), t = rint(uc * os),
  *   iu     = floor(t / os), fu = t - iu*os in [0, os)   (same for v);
- *   drop   = 1 if any tap of the (2S+1)^2 footprint leaves [0, N)^2.
+ *   drop   = 1 if any tap of the (2S+1)^2 footprint leaves [0, N)^2, or if u, v or w is
+ *            not finite (no nearest plane or grid cell exists for it).
  * Reading: the paper assigns equal-count chunks of the |w|-sorted data to planes;
  * this routine takes any ascending list of plane values and the nearest one
  * (a chunk's members are nearest to its own mean except near chunk borders).
@@ -306,7 +307,8 @@ void or_bin(int64_t V, const float *uvw, int P, const double *w_planes, const in
         double giu = floor(tu / (double)os);
         double giv = floor(tv / (double)os);
         int S = support[best];
-        int ok = (giu - S >= 0.0) && (giu + S <= (double)(N - 1)) && (giv - S >= 0.0) && (giv + S <= (double)(N - 1));
+        int ok = isfinite(u) && isfinite(v) && isfinite(w) &&
+                 (giu - S >= 0.0) && (giu + S <= (double)(N - 1)) && (giv - S >= 0.0) && (giv + S <= (double)(N - 1));
         drop[k] = ok ? 0 : 1;
         if (ok) {
             iu[k] = (int)giu;

@@ -149,8 +149,9 @@ __global__ void __launch_bounds__(256) k_bin(int64_t V, const float* __restrict_
         double giu = floor(__ddiv_rn(tu, (double)os));
         double giv = floor(__ddiv_rn(tv, (double)os));
         int S = min(max(support[p], 1), s_max);
-        bool ok = (giu - S >= 0.0) && (giu + S <= (double)(N - 1)) && (giv - S >= 0.0) &&
-                  (giv + S <= (double)(N - 1));
+        // non-finite u, v or w: no nearest plane or cell exists -- dropped and counted
+        bool ok = isfinite(u) && isfinite(v) && isfinite(w) && (giu - S >= 0.0) &&
+                  (giu + S <= (double)(N - 1)) && (giv - S >= 0.0) && (giv + S <= (double)(N - 1));
         if (ok) {
             int iu = (int)giu, iv = (int)giv;
             int fu = (int)(tu - giu * (double)os);

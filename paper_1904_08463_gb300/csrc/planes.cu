@@ -2,7 +2,10 @@
 // cut the sorted list into P equal-count chunks (the first V mod P chunks one longer) and
 // take each chunk's mean -- the paper's default of average w per plane.  The sort is a
 // radix sort of the float bit patterns (non-negative floats order like their bits); the
-// chunk means are FP64 sums, one block per chunk.
+// chunk means are FP64 sums, one block per chunk.  Non-finite |w| (bit patterns from
+// 0x7F800000 up) sort last and take no part: the chunks cut the finite values only, and a
+// chunk left empty (fewer finite values than planes) takes the largest finite |w| (0 if none),
+// so the plane values stay ascending; binning drops such visibilities.
 #include <cuda_runtime.h>
 #include <cub/device/device_radix_sort.cuh>
 
@@ -15,10 +18,21 @@ __global__ void k_abs_w_keys(int64_t V, const float* __restrict__ uvw, unsigned*
     if (k < V) keys[k] = __float_as_uint(fabsf(uvw[3 * k + 2]));
 }
 
-__global__ void __launch_bounds__(256) k_chunk_means(int64_t V, int P, const unsigned* __restrict__ sorted,
-                                                     double* __restrict__ out) {
+// number of finite |w| in the ascending keys (one thread: a binary search)
+__global__ void k_finite_count(int64_t V, const unsigned* __restrict__ sorted, int64_t* __restrict__ nf) {
+    int64_t lo = 0, hi = V;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (sorted[mid] < 0x7F800000u) lo = mid + 1; else hi = mid;
+    }
+    *nf = lo;
+}
+
+__global__ void __launch_bounds__(256) k_chunk_means(int P, const unsigned* __restrict__ sorted,
+                                                     const int64_t* __restrict__ nf, double* __restrict__ out) {
     __shared__ double red[8];
     const int c = blockIdx.x;
+    const int64_t V = *nf;
     const int64_t q = V / P, r = V % P;
     const int64_t beg = (int64_t)c * q + (c < r ? c : r);
     const int64_t n = q + (c < r ? 1 : 0);
@@ -30,7 +44,7 @@ __global__ void __launch_bounds__(256) k_chunk_means(int64_t V, int P, const uns
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        out[c] = t / (double)n;
+        out[c] = n > 0 ? t / (double)n : (V > 0 ? (double)__uint_as_float(sorted[V - 1]) : 0.0);
     }
 }
 
@@ -44,6 +58,7 @@ size_t plane_values_workspace_bytes(int64_t V) {
     Carver c(nullptr, 0);
     c.take<unsigned>((size_t)V);
     c.take<unsigned>((size_t)V);
+    c.take<int64_t>(1);
     c.take<char>(sort_temp_bytes(V));
     return (size_t)round_up((int64_t)c.off, 256);
 }
@@ -52,12 +67,15 @@ int plane_values(const float* uvw, int64_t V, int P, void* ws, size_t bytes, dou
     Carver c(ws, bytes);
     unsigned* keys = c.take<unsigned>((size_t)V);
     unsigned* sorted = c.take<unsigned>((size_t)V);
+    int64_t* nf = c.take<int64_t>(1);
     size_t tb = sort_temp_bytes(V);
     void* tmp = c.take<char>(tb);
     k_abs_w_keys<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(V, uvw, keys);
     WP_LAUNCH_CHECK("k_abs_w_keys");
     WP_CUDA(cub::DeviceRadixSort::SortKeys(tmp, tb, keys, sorted, (int)V, 0, 31, st));
-    k_chunk_means<<<P, 256, 0, st>>>(V, P, sorted, out);
+    k_finite_count<<<1, 1, 0, st>>>(V, sorted, nf);
+    WP_LAUNCH_CHECK("k_finite_count");
+    k_chunk_means<<<P, 256, 0, st>>>(P, sorted, nf, out);
     WP_LAUNCH_CHECK("k_chunk_means");
     return WP_OK;
 }

@@ -140,6 +140,39 @@ def test_plane_values_are_means_of_equal_count_chunks(V, P, seed):
     assert np.all(np.diff(got) >= 0)
 
 
+@pytest.mark.parametrize("grid_method", [0, 3])
+def test_non_finite_coordinates_are_dropped(grid_method):
+    """NaN / infinite u, v or w: the GPU binning drops and counts them as the oracle does, the
+    grid of the rest is unchanged, degridding returns 0 for them, and the plane values are the
+    chunk means of the finite |w| only."""
+    N, dl = 96, np.deg2rad(3.0) / 96
+    planes = np.array([0.0, 40.0, 130.0, 300.0, 800.0])
+    sup = np.array([1, 3, 6, 9, 12])
+    wp, dev, plan, g, taper, tap_d, wk, ks = _setup(N, dl, 4, 12, 128, planes, sup, grid_method=grid_method)
+    rng = np.random.default_rng(9)
+    V = 2000
+    du = g.du
+    uvw = np.stack([rng.uniform(-30, 30, V) * du, rng.uniform(-30, 30, V) * du,
+                    rng.uniform(-900, 900, V)], 1).astype(np.float32)
+    bad = rng.choice(V, 60, replace=False)
+    vals = np.array([np.nan, np.inf, -np.inf], dtype=np.float32)
+    uvw[bad, rng.integers(0, 3, 60)] = vals[rng.integers(0, 3, 60)]
+    vis = (rng.normal(size=V) + 1j * rng.normal(size=V)).astype(np.complex64)
+    u_d = torch.tensor(uvw, device=dev).reshape(-1)
+    G, stats = wp.grid(plan, wk, u_d, torch.tensor(vis, device=dev))
+    b = o.bin_vis(g, uvw, planes, sup)
+    assert (b.drop[bad] == 1).all()
+    assert stats[1].item() == (b.drop != 0).sum()
+    Go = o.grid(g, ks, b, vis)
+    assert np.abs(G.cpu().numpy() - Go).max() <= 1e-5 * np.abs(Go).max()
+    X = (rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))).astype(np.complex64)
+    Vd = wp.degrid(plan, wk, u_d, torch.tensor(X, device=dev)).cpu().numpy()
+    assert np.all(Vd[bad] == 0)
+    pv = wp.plane_values(u_d, 7).cpu().numpy()
+    assert np.allclose(pv, o.mean_w_planes(uvw[:, 2].astype(np.float64), 7), rtol=1e-13, atol=0)
+    assert np.all(np.isfinite(pv)) and np.all(np.diff(pv) >= 0)
+
+
 @pytest.mark.parametrize("interp", ["cubic", "linear"])
 def test_on_the_fly_taps_need_no_cache_and_match_the_cache_gridder(interp):
     """grid_method 4 interpolates every tap from the plane's radial line in shared memory with

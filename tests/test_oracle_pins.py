@@ -322,6 +322,24 @@ def test_mean_w_planes_equal_count_chunks():
     assert np.allclose(o.mean_w_planes(w, 3), [1.5, 3.5, 5.5])
 
 
+def test_non_finite_coordinates_are_dropped_and_left_out_of_the_plane_values():
+    """No nearest plane or grid cell exists for a NaN or infinite coordinate: such a
+    visibility is dropped (and counted) whatever its other coordinates, and its |w| takes no
+    part in the plane values; chunks left empty take the largest finite |w|."""
+    N, dl, os_ = 64, 1e-3, 8
+    g = o.Geometry(N, dl, os_, 4, 1, 0.01, 64)
+    nan, inf = np.float32(np.nan), np.float32(np.inf)
+    uvw = np.array([[0, 0, 10.0], [nan, 0, 10.0], [0, inf, 10.0], [0, 0, nan], [0, 0, -inf],
+                    [0, 0, 150.0]], dtype=np.float32)
+    b = o.bin_vis(g, uvw, [0.0, 100.0, 300.0], [4, 4, 4])
+    assert list(b.drop) == [0, 1, 1, 1, 1, 0]
+    assert list(b.plane[[0, 5]]) == [0, 1]
+    w = np.array([-5.0, np.nan, 1.0, 2.0, np.inf, -3.0, 4.0, 6.0, -np.inf])
+    assert np.allclose(o.mean_w_planes(w, 3), [1.5, 3.5, 5.5])
+    assert np.allclose(o.mean_w_planes(np.array([2.0, np.nan, 7.0]), 4), [2.0, 7.0, 7.0, 7.0])
+    assert np.allclose(o.mean_w_planes(np.array([np.nan, np.inf]), 2), [0.0, 0.0])
+
+
 # ------------------------------------------------------------------- gridding / degridding
 def _random_problem(seed=0, V=300):
     g = o.Geometry(64, np.deg2rad(2.0) / 64, 4, 5, 2, 0.01, 128)
