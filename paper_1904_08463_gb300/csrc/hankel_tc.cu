@@ -460,17 +460,16 @@ int gemm_split(const Geom& g, const KgWork& w, int P, float2* radial, int* statu
         if ((rc = make_map(&mb[1], w.f_lo, N, K))) return rc;
         mb[2] = mb[1];
     }
+    int dev = 0, sms = 0;
+    WP_CUDA(cudaGetDevice(&dev));
+    WP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // one CTA per SM: split K in two when the output tiles alone leave SMs idle
     const int tiles = (M / BM) * (N / BN);
-    const int split = (tiles < 152 && (K / 2) % KS == 0) ? 2 : 1;
+    const int split = (tiles < sms && (K / 2) % KS == 0) ? 2 : 1;
     WP_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
     if (split > 1) WP_CUDA(cudaMemsetAsync(radial, 0, (size_t)P * M * sizeof(float2), st));
-    static std::once_flag attr_once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(k_hankel_tf32x3<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        C::SMEM_BYTES);
-    });
-    WP_CUDA(attr_err);
+    // per call (cheap; the attribute belongs to the current device's context)
+    WP_CUDA(cudaFuncSetAttribute(k_hankel_tf32x3<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
     dim3 grid(N / BN, M / BM, split);
     k_hankel_tf32x3<MODE><<<grid, 192, C::SMEM_BYTES, st>>>(ma[0], ma[1], ma[2], mb[0], mb[1], mb[2], M, K, split,
                                                             P, radial, split > 1, status, budget, withhold_loads);

@@ -348,8 +348,11 @@ __global__ void __launch_bounds__(256) k_gemm_fp32(int M, int N, int K, int k_sp
 
 int kg_gemm_fp32(const Geom& g, const KgWork& w, int P, float2* radial, cudaStream_t st) {
     int M = g.k_out, N = 2 * p_pad(P), K = g.r_pad;
+    int dev = 0, sms = 0;
+    WP_CUDA(cudaGetDevice(&dev));
+    WP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int tiles = (M / GB_M) * (N / GB_N);
-    int split = (tiles < 152 && (K / 2) % GB_K == 0) ? 2 : 1;
+    int split = (tiles < sms && (K / 2) % GB_K == 0) ? 2 : 1;
     if (split > 1) WP_CUDA(cudaMemsetAsync(radial, 0, (size_t)P * M * sizeof(float2), st));
     dim3 grid(N / GB_N, M / GB_M, split);
     k_gemm_fp32<<<grid, 256, 0, st>>>(M, N, K, split, w.h32, w.f32, P, radial, split > 1);
