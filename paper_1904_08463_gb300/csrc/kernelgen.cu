@@ -521,7 +521,7 @@ __device__ __forceinline__ void bulk_store(float2* gdst, uint32_t saddr, uint32_
 
 __device__ __forceinline__ int parity8(const float2* g) { return (int)(((uintptr_t)g >> 3) & 1); }
 
-constexpr int RS_THREADS = 384;
+constexpr int RS_THREADS = 512;   // 16 warps, two blocks per SM (384 and 576+ measured slower)
 
 // Staged output: every chunk of whole evaluated rows [r0, r1) lands in at most four contiguous
 // cache ranges -- rows [r0, r1) of the sub-kernel itself (F) and of its x-mirror (X), the
@@ -654,8 +654,8 @@ int kg_resample(const Geom& g, int P, const float2* radial, const float2* spline
     if (n_max > g.k_out) n_max = g.k_out;
     const int n_line = (int)round_up(n_max, 8);
     const size_t line_bytes = (size_t)n_line * sizeof(float4);
-    // staging capacity per region (elements, even): up to 1536 -- about four taps per thread
-    // per chunk -- while two blocks still fit on an SM; never below one row of the largest
+    // staging capacity per region (elements, even): up to 1536 -- three taps per thread per
+    // chunk -- while two blocks still fit on an SM; never below one row of the largest
     // support
     int dev = 0, smem_sm = 0, smem_block = 0, reserved = 0;
     WP_CUDA(cudaGetDevice(&dev));
@@ -675,7 +675,7 @@ int kg_resample(const Geom& g, int P, const float2* radial, const float2* spline
             cap = cap1;
         }
     }
-    const int cap_max = (nsets == 2) ? 1536 : 3072;   // about four taps per thread per chunk
+    const int cap_max = (nsets == 2) ? 1536 : 3072;   // three (six) taps per thread per chunk
     cap = cap > cap_max ? cap_max : cap;
     cap &= ~1;
     if (cap < w_max + 1) cap = w_max + 1;   // even, >= one row

@@ -110,6 +110,7 @@ struct GridWork {
     int*    scan_tmp;   // scan scratch
     int*    ctrl;       // [8]  [0] item cursor, [1] item count, [2] status
     double* red;        // [2]  weight sum, drops (per call)
+    int*    seff;       // [P]  effective supports of the call (clamped, fitted to the cache layout)
 };
 size_t carve_grid(const Geom& g, int P, int64_t V, void* ws, size_t bytes, GridWork* out);
 
@@ -127,9 +128,11 @@ size_t carve_grid(const Geom& g, int P, int64_t V, void* ws, size_t bytes, GridW
 // The support a kernel may use for plane p of a cache laid out by `offsets`: S itself when
 // its os^2 (2S+1)^2 taps fit the plane's block [offsets[p], offsets[p+1]) -- always, for a
 // layout from wp_kernel_layout of the same supports -- else the largest support that fits, or
-// 0 (skip the plane) when not even S = 1 does.  Every kernel that turns (support, offsets)
-// into cache indices goes through it, so a caller's inconsistent layout gives wrong taps for
-// that plane but no access outside its block.
+// 0 (skip the plane) when not even S = 1 does.  Every path that turns (support, offsets) into
+// cache indices goes through it -- the resample and the 2D-FFT extraction per block, gridding
+// and degridding through the per-call effective supports that binning computes -- so a
+// caller's inconsistent layout gives wrong taps for that plane but no access outside its
+// block.
 __device__ __forceinline__ int fit_support(int S, int os, const int64_t* __restrict__ offsets, int p) {
     const int64_t blk = offsets[p + 1] - offsets[p];
     const int64_t os2 = (int64_t)os * os;
