@@ -365,8 +365,14 @@ int kg_gemm_fp32(const Geom& g, const KgWork& w, int P, float2* radial, cudaStre
 // Support: last k with |C_k| >= tau * max |C|, S = ceil(k / os) clamped to [S_min, S_max].
 // Spline: m = A^-1 rhs with rhs_0 = 6 (y1 - y0), rhs_k = 6 (y_{k+1} - 2 y_k + y_{k-1}),
 // rhs_{K-1} = 0 (zero slope at rho = 0, natural end), using the precomputed band of A^-1.
+// The inverse of this diagonally dominant tridiagonal matrix decays like (2 - sqrt 3)^|k-j| =
+// 0.268^|k-j| away from the diagonal, so the product keeps |k - j| <= 16 (the dropped tail is
+// below 2e-10 of the largest coefficient, 300x under FP32 resolution of the sum); rows k with
+// 16 <= k < K - 16 equal the interior (Toeplitz) row up to boundary reflections ~0.268^(2k),
+// so only the 16 first and 16 last rows use their own coefficients.
 // =======================================================================================
 constexpr int TS_THREADS = 384;   // threads per plane of the truncation / spline kernel (3 rows each at K 1152)
+constexpr int SPL_HW = 16;        // band half-width used by the product (the stored band holds 32)
 
 __global__ void __launch_bounds__(TS_THREADS) k_trunc_spline(int K, int os, int s_min, int s_max, float tau,
                                                       int do_trunc, int do_spline,
@@ -379,16 +385,17 @@ __global__ void __launch_bounds__(TS_THREADS) k_trunc_spline(int K, int os, int 
     float2* rhs = sm + K + 32;
     __shared__ float red_f[TS_THREADS / 32];
     __shared__ int red_i[TS_THREADS / 32];
-    __shared__ float toe[65];        // one interior row of the band (Toeplitz coefficients)
-    __shared__ float edge[65 * 64];  // the band's 32 first and 32 last rows: edge[d * 64 + kk]
+    constexpr int NB = 2 * SPL_HW + 1;              // band width used
+    __shared__ float toe[NB];                       // the interior (Toeplitz) row, offsets -16..16
+    __shared__ float edge[NB * 2 * SPL_HW];         // the 16 first and 16 last rows: edge[e * 32 + kk]
     const int p = blockIdx.x;
     if (do_spline) {
-        if (threadIdx.x < 65) toe[threadIdx.x] = band[(int64_t)threadIdx.x * K + K / 2];
-        // staged by the whole block (coalesced along k) instead of 65 dependent strided loads
-        // on the first and last warps' critical path; K >= 128
-        for (int i = threadIdx.x; i < 65 * 64; i += blockDim.x) {
-            const int d = i >> 6, kk = i & 63;
-            edge[i] = band[(int64_t)d * K + (kk < 32 ? kk : K - 64 + kk)];
+        // stored band row d holds A^-1[k][k + d - 32]; offsets -16..16 are d = 16..48
+        if (threadIdx.x < NB) toe[threadIdx.x] = band[(int64_t)(threadIdx.x + 32 - SPL_HW) * K + K / 2];
+        // staged by the whole block (coalesced along k); K >= 128
+        for (int i = threadIdx.x; i < NB * 2 * SPL_HW; i += blockDim.x) {
+            const int e = i / (2 * SPL_HW), kk = i - e * (2 * SPL_HW);
+            edge[i] = band[(int64_t)(e + 32 - SPL_HW) * K + (kk < SPL_HW ? kk : K - 2 * SPL_HW + kk)];
         }
     }
     const float2* src = radial + (int64_t)p * K;
@@ -442,23 +449,24 @@ __global__ void __launch_bounds__(TS_THREADS) k_trunc_spline(int K, int os, int 
         }
         __syncthreads();
         float2* dst = spline_m + (int64_t)p * K;
+        float tr[NB];                               // the Toeplitz row in registers
+#pragma unroll
+        for (int e = 0; e < NB; ++e) tr[e] = toe[e];
         for (int k = threadIdx.x; k < K; k += blockDim.x) {
             float mr = 0.0f, mi = 0.0f;
-            if (k >= 32 && k < K - 32) {
-                // interior rows: A^-1 is Toeplitz there (the end conditions reach row k only
-                // through terms ~0.268^min(k, K-1-k), below FP32 resolution at distance 32)
-#pragma unroll 13
-                for (int d = 0; d < 65; ++d) {
-                    const float2 r = rhs[k + d - 32];
-                    mr = fmaf(toe[d], r.x, mr);
-                    mi = fmaf(toe[d], r.y, mi);
+            if (k >= SPL_HW && k < K - SPL_HW) {
+#pragma unroll
+                for (int e = 0; e < NB; ++e) {
+                    const float2 r = rhs[k + e - SPL_HW];
+                    mr = fmaf(tr[e], r.x, mr);
+                    mi = fmaf(tr[e], r.y, mi);
                 }
             } else {
-                const int kk = k < 32 ? k : k - (K - 64);
-#pragma unroll 13
-                for (int d = 0; d < 65; ++d) {
-                    const float c = edge[d * 64 + kk];    // zero where k + d - 32 is outside
-                    const float2 r = rhs[k + d - 32];
+                const int kk = k < SPL_HW ? k : k - (K - 2 * SPL_HW);
+#pragma unroll
+                for (int e = 0; e < NB; ++e) {
+                    const float c = edge[e * 2 * SPL_HW + kk];   // zero where k + e - 16 is outside
+                    const float2 r = rhs[k + e - SPL_HW];
                     mr = fmaf(c, r.x, mr);
                     mi = fmaf(c, r.y, mi);
                 }
