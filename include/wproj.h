@@ -12,9 +12,10 @@
  * ---------------------------------------
  *  - Every array argument is a DEVICE pointer unless its comment says "host".
  *    Device memory is owned by the caller; the library allocates no device memory
- *    except cuFFT plans/work areas (wp_dirty_image, wp_image_to_grid,
- *    wp_fft_wkernels), which it caches per device and size until wp_release(), and the
- *    fixed scratch array of wp_grid_static.
+ *    except cuFFT plans/work areas (wp_dirty_image, wp_image_to_grid, wp_fft_wkernels, the
+ *    projection route of wp_hankel_radial), which it caches per device, size and stream
+ *    until wp_release() -- one per stream, so that calls overlapping on different streams
+ *    never share a work area -- and the fixed scratch array of wp_grid_static.
  *  - Complex values are interleaved float pairs (re, im) -- the layout of CUDA's
  *    float2 / cuFloatComplex / torch.complex64.
  *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*; NULL is

@@ -37,12 +37,14 @@ namespace wp {
 
 namespace {
 std::mutex g_mu;
-std::map<std::tuple<int, int, int>, cufftHandle> g_plans;   // (device, L, batch) -> plan
+// (device, L, batch, stream) -> plan: one plan (and work area) per stream, so concurrent
+// calls on different streams never share a work area
+std::map<std::tuple<int, int, int, uintptr_t>, cufftHandle> g_plans;
 
-int plan_many(int L, int batch, cufftHandle* out) {
+int plan_many(int L, int batch, cudaStream_t st, cufftHandle* out) {
     int dev = 0;
     WP_CUDA(cudaGetDevice(&dev));
-    auto key = std::make_tuple(dev, L, batch);
+    auto key = std::make_tuple(dev, L, batch, (uintptr_t)st);
     auto it = g_plans.find(key);
     if (it != g_plans.end()) { *out = it->second; return WP_OK; }
     cufftHandle h;
@@ -158,7 +160,7 @@ int fft_wkernels(const Geom& g, const float* taper, const double* w_planes, int 
     for (int p0 = 0; p0 < P; p0 += B) {
         const int nb = (P - p0 < B) ? (P - p0) : B;
         cufftHandle h;
-        int rc = plan_many(L, nb, &h);
+        int rc = plan_many(L, nb, st, &h);
         if (rc) return rc;
         WP_CUDA(cudaMemsetAsync(X, 0, (size_t)nb * L * L * sizeof(float2), st));
         k_fft_fill<<<dim3((M + 127) / 128, M, nb), 128, 0, st>>>(M, L, g.R, p0, nb, nm1, taper, w_planes, X);
@@ -181,12 +183,12 @@ int fft_wkernels(const Geom& g, const float* taper, const double* w_planes, int 
 // projection-slice route
 // ---------------------------------------------------------------------------------------
 namespace {
-std::map<std::tuple<int, int, int>, cufftHandle> g_plans1d;   // (device, L, batch) -> plan
+std::map<std::tuple<int, int, int, uintptr_t>, cufftHandle> g_plans1d;   // (device, L, batch, stream)
 
-int plan_1d(int L, int batch, cufftHandle* out) {
+int plan_1d(int L, int batch, cudaStream_t st, cufftHandle* out) {
     int dev = 0;
     WP_CUDA(cudaGetDevice(&dev));
-    auto key = std::make_tuple(dev, L, batch);
+    auto key = std::make_tuple(dev, L, batch, (uintptr_t)st);
     auto it = g_plans1d.find(key);
     if (it != g_plans1d.end()) { *out = it->second; return WP_OK; }
     cufftHandle h;
@@ -321,7 +323,7 @@ int kg_projslice(const Geom& g, const KgWork& w, const float* taper, const doubl
     {
         std::lock_guard<std::mutex> lk(g_mu);
         cufftHandle h;
-        int rc = plan_1d(L, P, &h);
+        int rc = plan_1d(L, P, st, &h);
         if (rc) return rc;
         if (cufftSetStream(h, st) != CUFFT_SUCCESS ||
             cufftExecC2C(h, reinterpret_cast<cufftComplex*>(w.ps_x), reinterpret_cast<cufftComplex*>(w.ps_x),

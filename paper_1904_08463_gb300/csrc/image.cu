@@ -12,6 +12,7 @@
 
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 
 #include "wp_internal.cuh"
@@ -20,12 +21,15 @@ namespace wp {
 
 namespace {
 std::mutex g_fft_mu;
-std::map<std::pair<int, int>, cufftHandle> g_fft_plans;   // (device, N) -> plan
+// (device, N, stream) -> plan: a plan's work area may serve one stream at a time, and
+// independent problems run their transforms concurrently on separate streams (also inside a
+// captured graph), so each stream has its own plan.
+std::map<std::tuple<int, int, uintptr_t>, cufftHandle> g_fft_plans;
 
-int get_plan(int N, cufftHandle* out) {
+int get_plan(int N, cudaStream_t st, cufftHandle* out) {
     int dev = 0;
     WP_CUDA(cudaGetDevice(&dev));
-    auto key = std::make_pair(dev, N);
+    auto key = std::make_tuple(dev, N, (uintptr_t)st);
     auto it = g_fft_plans.find(key);
     if (it != g_fft_plans.end()) {
         *out = it->second;
@@ -45,7 +49,7 @@ int get_plan(int N, cufftHandle* out) {
 int exec_fft(int N, float2* data, int direction, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_fft_mu);
     cufftHandle h;
-    int rc = get_plan(N, &h);
+    int rc = get_plan(N, st, &h);
     if (rc) return rc;
     if (cufftSetStream(h, st) != CUFFT_SUCCESS) {
         set_last_error("cufftSetStream", "failed");
