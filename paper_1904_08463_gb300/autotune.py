@@ -1,8 +1,8 @@
 """Autotuner for the tunable launch shapes of the imaging path.
 
-Three choices do not change results, only speed: the kernel-generation route of the Hankel
-transform (FP32 SIMT, tcgen05 TF32x3 or BF16x3 matrix product -- all meet the kernel
-tolerance, 1e-6 or better on the caches),
+Three choices do not change results beyond the kernel tolerance, only speed: the
+kernel-generation route of the Hankel transform (FP32 SIMT, or the tcgen05 matrix product with
+TF32x3, BF16x3 or BF16x6 split operands -- all within 1e-6 of the FP64 oracle on the caches),
 and the gridder's method (register tile; shared-memory tiles with the footprint spread over
 the lanes, per-warp copies, or warp-owned rows; warp-owned rows with taps interpolated from
 the radial line) and tile side (32 or 64 cells).  For a problem class -- grid size, plane
