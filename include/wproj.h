@@ -15,7 +15,9 @@
  *    except cuFFT plans/work areas (wp_dirty_image, wp_image_to_grid, wp_fft_wkernels, the
  *    projection route of wp_hankel_radial), which it caches per device, size and stream
  *    until wp_release() -- one per stream, so that calls overlapping on different streams
- *    never share a work area -- and the fixed scratch array of wp_grid_static.
+ *    never share a work area; the first such call on a stream creates its plan and must
+ *    therefore come before any stream capture that uses that stream -- and the fixed
+ *    scratch array of wp_grid_static.
  *  - Complex values are interleaved float pairs (re, im) -- the layout of CUDA's
  *    float2 / cuFloatComplex / torch.complex64.
  *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*; NULL is

@@ -100,7 +100,7 @@ class BatchImager:
         self.states = [_State(pb, tuner) for pb in problems]
         self.n_streams = max(1, n_streams)
         self.graph: torch.cuda.CUDAGraph | None = None
-        self.run_sequential()          # creates every cuFFT plan before any capture
+        self.run_sequential()          # plans, tuning and code loading outside any capture
         torch.cuda.synchronize()
 
     @property
@@ -117,29 +117,37 @@ class BatchImager:
         for s in self.states:
             s.step()
 
+    def _fork_join(self, cap: torch.cuda.Stream, streams, lanes) -> None:
+        fork = torch.cuda.Event()
+        fork.record(cap)
+        joins = []
+        for st, lane in zip(streams, lanes):
+            st.wait_event(fork)
+            with torch.cuda.stream(st):
+                for i in lane:
+                    self.states[i].step()
+                ev = torch.cuda.Event()
+                ev.record(st)
+            joins.append(ev)
+        for ev in joins:
+            cap.wait_event(ev)
+
     def capture(self) -> None:
         order = sorted(range(len(self.states)), key=lambda i: -self.states[i].cost())
         lanes = [[] for _ in range(self.n_streams)]
         for j, i in enumerate(order):
             lanes[j % self.n_streams].append(i)
         streams = [torch.cuda.Stream() for _ in range(self.n_streams)]
-        g = torch.cuda.CUDAGraph()
         cap = torch.cuda.Stream()
+        # one uncaptured pass on the same streams first: the library keeps one cuFFT plan per
+        # stream (concurrent branches never share a work area), and a plan cannot be created
+        # inside a capture
         torch.cuda.synchronize()
+        self._fork_join(cap, streams, lanes)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=cap):
-            fork = torch.cuda.Event()
-            fork.record(cap)
-            joins = []
-            for st, lane in zip(streams, lanes):
-                st.wait_event(fork)
-                with torch.cuda.stream(st):
-                    for i in lane:
-                        self.states[i].step()
-                    ev = torch.cuda.Event()
-                    ev.record(st)
-                joins.append(ev)
-            for ev in joins:
-                cap.wait_event(ev)
+            self._fork_join(cap, streams, lanes)
         self.graph = g
 
     def replay(self) -> None:
