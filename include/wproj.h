@@ -133,9 +133,11 @@ typedef struct wp_geometry {
  * when not even S = 1 fits, so a mismatched layout yields wrong taps for that plane but no
  * access outside its block.
  */
+#define WP_KERNELS_OWNED (1 << 30)   /* wp_wkernels.flags: arrays allocated by
+                                        wp_make_wkernels_owned (free with wp_free_kernels) */
 typedef struct wp_wkernels {
     int32_t        P;         /* number of |w| planes                                  */
-    int32_t        reserved;
+    int32_t        flags;     /* 0 for caller-owned arrays; WP_KERNELS_OWNED           */
     const double*  w_planes;  /* [P] plane |w| values, ascending, >= 0                 */
     const int32_t* support;   /* [P] support S_p, min_support <= S_p <= max_support    */
     const int64_t* offsets;   /* [P+1] complex-element offsets into cache              */
@@ -246,6 +248,31 @@ int wp_make_wkernels(const wp_plan* plan, const float* taper, const double* w_pl
                      int32_t P, int32_t* support, const int64_t* offsets, void* workspace,
                      size_t workspace_bytes, float* radial, float* spline_m, float* cache,
                      void* stream);
+
+/*
+ * The same kernels in device memory the library allocates: a complete kernel set from the
+ * problem statement alone (image geometry, taper, w-planes, oversampling, support).  The
+ * call allocates with cudaMalloc -- it is neither allocation-free nor capturable -- and
+ * synchronizes `stream` before returning.
+ *   taper     device [R] float
+ *   w_planes  HOST [P] plane |w| values, ascending, >= 0 (copied to the device)
+ *   support   HOST [P] supports in [1, max_support] when plan->trunc_frac <= 0; NULL when
+ *             the truncation rule (Section 3.1) picks them on the device -- they are then
+ *             read back to lay the cache out compactly
+ *   out       filled with device pointers to w_planes, support, offsets, cache, radial and
+ *             spline_m (NULL for linear interpolation), all owned by the library, and flags
+ *             = WP_KERNELS_OWNED; usable by every gridding call; release with wp_free_kernels
+ * On an error nothing stays allocated and *out is zeroed.
+ */
+int wp_make_wkernels_owned(const wp_plan* plan, const float* taper, const double* w_planes,
+                           int32_t P, const int32_t* support, wp_wkernels* out, void* stream);
+
+/*
+ * Frees a kernel set made by wp_make_wkernels_owned and zeroes *kernels.  Synchronizes the
+ * device first, so that no queued kernel still reads it.  A set whose flags lack
+ * WP_KERNELS_OWNED (caller-owned arrays) is refused with WP_ERR_UNSUPPORTED and left as is.
+ */
+int wp_free_kernels(wp_wkernels* kernels);
 
 /* ---- standard kernel generation by 2D FFT (the comparator; Alg. 1, Section 4.2) ------ */
 

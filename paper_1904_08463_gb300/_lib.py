@@ -57,7 +57,7 @@ class WpGeometry(ctypes.Structure):
 class WpWkernels(ctypes.Structure):
     _fields_ = [
         ("P", c_int32),
-        ("reserved", c_int32),
+        ("flags", c_int32),
         ("w_planes", c_void_p),
         ("support", c_void_p),
         ("offsets", c_void_p),
@@ -80,6 +80,9 @@ P_ = ctypes.POINTER
 _SIGS = {
     "wp_version": (c_int32, []),
     "wp_strerror": (ctypes.c_char_p, [c_int32]),
+    "wp_make_wkernels_owned": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_int32, c_void_p, P_(WpWkernels),
+                                         c_void_p]),
+    "wp_free_kernels": (c_int32, [P_(WpWkernels)]),
     "wp_last_error_string": (ctypes.c_char_p, []),
     "wp_release": (None, []),
     "wp_plan_geometry": (c_int32, [P_(WpPlan), P_(WpGeometry)]),

@@ -204,6 +204,47 @@ def make_wkernels(plan: Plan, taper: torch.Tensor, w_planes, supports=None,
     return WKernels(w_planes, sup, off, cache, radial, spline_m)
 
 
+class OwnedWKernels:
+    """A kernel set in device memory the library allocated (``wp_make_wkernels_owned``):
+    usable wherever a ``WKernels`` is (gridding, degridding); released by ``free()`` or when
+    the object is collected."""
+
+    def __init__(self, kc: _lib.WpWkernels):
+        self._kc = kc
+
+    @property
+    def P(self) -> int:
+        return int(self._kc.P)
+
+    def c(self) -> _lib.WpWkernels:
+        if not self._kc.flags:
+            raise RuntimeError("kernel set already freed")
+        return self._kc
+
+    def free(self) -> None:
+        if self._kc.flags:
+            _lib.check("wp_free_kernels", _lib.load().wp_free_kernels(ctypes.byref(self._kc)))
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:   # interpreter or CUDA teardown: the process releases the memory
+            pass
+
+
+def make_wkernels_owned(plan: Plan, taper: torch.Tensor, w_planes, supports=None, stream=None) -> OwnedWKernels:
+    """The kernels of ``make_wkernels`` in library-allocated device memory, from host plane
+    values (ascending, >= 0) and, with ``plan.trunc_frac <= 0``, host supports."""
+    _need(taper, torch.float32, "taper", plan.radial_samples)
+    w = torch.as_tensor(w_planes, dtype=torch.float64).contiguous().cpu()
+    sup = None if supports is None else torch.as_tensor(supports, dtype=torch.int32).contiguous().cpu()
+    kc = _lib.WpWkernels()
+    _lib.check("wp_make_wkernels_owned", _lib.load().wp_make_wkernels_owned(
+        ctypes.byref(plan.c()), _ptr(taper), ctypes.c_void_p(w.data_ptr()), int(w.numel()),
+        None if sup is None else ctypes.c_void_p(sup.data_ptr()), ctypes.byref(kc), _stream(stream)))
+    return OwnedWKernels(kc)
+
+
 def fft_wkernels(plan: Plan, taper: torch.Tensor, w_planes, supports, circular: bool = True,
                  ws: torch.Tensor | None = None, stream=None) -> WKernels:
     """Kernel cache by the standard 2D-FFT route (Alg. 1 with workspace undersampling),

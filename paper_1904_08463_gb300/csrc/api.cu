@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 #include "wp_internal.cuh"
 
@@ -320,6 +321,99 @@ int wp_make_wkernels(const wp_plan* plan, const float* taper, const double* w_pl
                               support, stream);
     if (rc) return rc;
     return wp_resample(plan, radial, spline_m, P, support, offsets, cache, stream);
+}
+
+int wp_make_wkernels_owned(const wp_plan* plan, const float* taper, const double* w_planes, int32_t P,
+                           const int32_t* support, wp_wkernels* out, void* stream) {
+    WP_RANGE("wp_make_wkernels_owned");
+    if (!out) return WP_ERR_NULL;
+    memset(out, 0, sizeof(*out));
+    Geom g;
+    int rc = make_geom(plan, &g);
+    if (rc) return rc;
+    if (P < 1 || P > 65536) return WP_ERR_SIZE;
+    if (!taper || !w_planes) return WP_ERR_NULL;
+    const bool trunc = g.tau > 0.0;
+    if (!trunc && !support) return WP_ERR_NULL;
+    for (int p = 0; p < P; ++p) {
+        if (!(w_planes[p] >= 0.0) || (p > 0 && w_planes[p] < w_planes[p - 1])) return WP_ERR_SIZE;
+        if (!trunc && (support[p] < 1 || support[p] > g.s_max)) return WP_ERR_SIZE;
+    }
+    if ((rc = check_device())) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool cubic = (g.interp == WP_INTERP_CUBIC);
+    // every allocation is released on any error path
+    std::vector<void*> held;
+    auto alloc = [&](void** p, size_t bytes) -> int {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) return cuda_fail("cudaMalloc", e);
+        held.push_back(*p);
+        return WP_OK;
+    };
+    auto fail = [&](int code) {
+        cudaStreamSynchronize(st);
+        for (void* p : held) cudaFree(p);
+        memset(out, 0, sizeof(*out));
+        return code;
+    };
+    const size_t ws_bytes = carve_kg(g, P, nullptr, 0, nullptr);
+    void *ws = nullptr, *d_w = nullptr, *d_sup = nullptr, *d_off = nullptr, *d_rad = nullptr, *d_spl = nullptr,
+         *d_cache = nullptr;
+    const size_t line_bytes = (size_t)P * g.k_out * sizeof(float2);
+    if ((rc = alloc(&ws, ws_bytes)) || (rc = alloc(&d_w, (size_t)P * sizeof(double))) ||
+        (rc = alloc(&d_sup, (size_t)P * sizeof(int32_t))) || (rc = alloc(&d_off, (size_t)(P + 1) * sizeof(int64_t))) ||
+        (rc = alloc(&d_rad, line_bytes)) || (cubic && (rc = alloc(&d_spl, line_bytes))))
+        return fail(rc);
+    cudaError_t e = cudaMemcpyAsync(d_w, w_planes, (size_t)P * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !trunc)
+        e = cudaMemcpyAsync(d_sup, support, (size_t)P * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail(cuda_fail("cudaMemcpyAsync", e));
+    if ((rc = wp_kernelgen_prepare(plan, P, ws, ws_bytes, stream))) return fail(rc);
+    if ((rc = wp_hankel_radial(plan, taper, (const double*)d_w, P, ws, ws_bytes, (float*)d_rad, (float*)d_spl,
+                               trunc ? (int32_t*)d_sup : nullptr, stream)))
+        return fail(rc);
+    std::vector<int32_t> sup_h((size_t)P);
+    std::vector<int64_t> off_h((size_t)P + 1);
+    if (trunc) {
+        e = cudaMemcpyAsync(sup_h.data(), d_sup, (size_t)P * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(cuda_fail("support read-back", e));
+    } else {
+        memcpy(sup_h.data(), support, (size_t)P * sizeof(int32_t));
+    }
+    if ((rc = wp_kernel_layout(plan, P, sup_h.data(), off_h.data()))) return fail(rc);
+    if ((rc = alloc(&d_cache, (size_t)off_h[P] * sizeof(float2)))) return fail(rc);
+    e = cudaMemcpyAsync(d_off, off_h.data(), (size_t)(P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail(cuda_fail("cudaMemcpyAsync", e));
+    if ((rc = wp_resample(plan, (const float*)d_rad, (const float*)d_spl, P, (const int32_t*)d_sup,
+                          (const int64_t*)d_off, (float*)d_cache, stream)))
+        return fail(rc);
+    e = cudaStreamSynchronize(st);   // host vectors above must outlive their copies
+    if (e != cudaSuccess) return fail(cuda_fail("cudaStreamSynchronize", e));
+    cudaFree(ws);
+    out->P = P;
+    out->flags = WP_KERNELS_OWNED;
+    out->w_planes = (const double*)d_w;
+    out->support = (const int32_t*)d_sup;
+    out->offsets = (const int64_t*)d_off;
+    out->cache = (const float*)d_cache;
+    out->radial = (const float*)d_rad;
+    out->spline_m = (const float*)d_spl;
+    return WP_OK;
+}
+
+int wp_free_kernels(wp_wkernels* k) {
+    if (!k) return WP_ERR_NULL;
+    if (!(k->flags & WP_KERNELS_OWNED)) {
+        set_last_error("wp_free_kernels", "kernel set not allocated by wp_make_wkernels_owned");
+        return WP_ERR_UNSUPPORTED;
+    }
+    WP_CUDA(cudaDeviceSynchronize());
+    const void* ptrs[6] = {k->w_planes, k->support, k->offsets, k->cache, k->radial, k->spline_m};
+    for (const void* p : ptrs)
+        if (p) WP_CUDA(cudaFree(const_cast<void*>(p)));
+    memset(k, 0, sizeof(*k));
+    return WP_OK;
 }
 
 size_t wp_fft_workspace_bytes(const wp_plan* plan, int32_t P) {

@@ -123,3 +123,23 @@ def test_product_path_refuses_to_run_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(L, "_lib", None)
     with pytest.raises(ImportError):
         L.load()
+
+
+def test_free_kernels_refuses_sets_the_library_did_not_allocate():
+    """wp_free_kernels frees only what wp_make_wkernels_owned allocated (flags carries
+    WP_KERNELS_OWNED); a caller-owned set and NULL are refused before any CUDA call."""
+    L, lib = _lib()
+    k = L.WpWkernels(3, 0, None, None, None, None, None, None)
+    assert lib.wp_free_kernels(ctypes.byref(k)) == -8
+    assert k.P == 3
+    assert lib.wp_free_kernels(None) == -1
+    out = L.WpWkernels()
+    p = L.WpPlan(256, 1e-4, 8, 15, 3, 0.0, 512, 0, 1, 0, 0)
+    # no supports with trunc_frac <= 0, and a descending plane list: rejected on the host
+    w = (ctypes.c_double * 2)(0.0, 10.0)
+    assert lib.wp_make_wkernels_owned(ctypes.byref(p), None, w, 2, None, ctypes.byref(out), None) == -1
+    wd = (ctypes.c_double * 2)(10.0, 0.0)
+    s = (ctypes.c_int32 * 2)(3, 4)
+    assert lib.wp_make_wkernels_owned(ctypes.byref(p), ctypes.c_void_p(16), wd, 2, s, ctypes.byref(out),
+                                      None) == -2
+    assert out.P == 0 and out.flags == 0
