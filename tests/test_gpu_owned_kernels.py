@@ -54,7 +54,10 @@ def test_owned_kernels_equal_caller_owned_and_grid_alike(trunc, interp):
     fixed = plan.replace(trunc_frac=0.0, grid_method=0)
     G1, _ = wp.grid(fixed, ref, u_d, vis)
     G2, _ = wp.grid(fixed, own, u_d, vis)
-    assert np.array_equal(_bits(G1), _bits(G2))
+    # same kernels (bitwise above); the grid's cells are flushed with atomics from several
+    # planes' items, whose order may differ between two runs
+    a, b = G1.cpu().numpy(), G2.cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-6 * np.abs(a).max()
     own.free()
     assert own._kc.flags == 0 and own._kc.P == 0
     with pytest.raises(RuntimeError):
