@@ -55,7 +55,7 @@ def _gpu_grads(g, planes, sup, uvw, vobs, wt, img, taper):
     vis = pr(I, t)
     L = chi2(vis, torch.tensor(vobs, device=dev), torch.tensor(wt, device=dev))
     L.backward()
-    return float(L), vis.detach().cpu().numpy(), I.grad.cpu().numpy(), t.grad.cpu().numpy()
+    return float(L.detach()), vis.detach().cpu().numpy(), I.grad.cpu().numpy(), t.grad.cpu().numpy()
 
 
 def test_forward_prediction_matches_oracle():
