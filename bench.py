@@ -582,7 +582,7 @@ def run_imaging(args, dev):
     stats = torch.zeros(2, dtype=torch.float64, device=dev)
     radial = torch.empty((P, plan.geometry().k_out), dtype=torch.complex64, device=dev)
     spl = torch.empty_like(radial)
-    wk = wp.WKernels(wpl, sup, off, cache, radial, spl, circular=True)
+    wk = wp.WKernels(wpl, sup, off, cache, radial, spl)
     # the gridder's launch shape (method x tile) is picked by the autotuner on this problem
     from paper_1904_08463_gb300.autotune import GRID_CHOICES, Autotuner
 

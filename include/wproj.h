@@ -133,16 +133,11 @@ typedef struct wp_geometry {
  * when not even S = 1 fits, so a mismatched layout yields wrong taps for that plane but no
  * access outside its block.
  */
-/* wp_wkernels.flags */
-#define WP_KERNELS_CIRCULAR 1         /* every tap beyond the support radius -- (os (jx - S) -
-                                        fu)^2 + (os (jy - S) - fv)^2 > (os S)^2 -- is exactly
-                                        zero (wp_resample always; wp_fft_wkernels with
-                                        circular != 0): degridding then skips those taps    */
-#define WP_KERNELS_OWNED (1 << 30)    /* arrays allocated by wp_make_wkernels_owned (free
-                                        with wp_free_kernels)                               */
+#define WP_KERNELS_OWNED (1 << 30)   /* wp_wkernels.flags: arrays allocated by
+                                        wp_make_wkernels_owned (free with wp_free_kernels) */
 typedef struct wp_wkernels {
     int32_t        P;         /* number of |w| planes                                  */
-    int32_t        flags;     /* WP_KERNELS_CIRCULAR | WP_KERNELS_OWNED, or 0           */
+    int32_t        flags;     /* 0 for caller-owned arrays; WP_KERNELS_OWNED           */
     const double*  w_planes;  /* [P] plane |w| values, ascending, >= 0                 */
     const int32_t* support;   /* [P] support S_p, min_support <= S_p <= max_support    */
     const int64_t* offsets;   /* [P+1] complex-element offsets into cache              */
@@ -266,8 +261,7 @@ int wp_make_wkernels(const wp_plan* plan, const float* taper, const double* w_pl
  *             read back to lay the cache out compactly
  *   out       filled with device pointers to w_planes, support, offsets, cache, radial and
  *             spline_m (NULL for linear interpolation), all owned by the library, and flags
- *             = WP_KERNELS_OWNED | WP_KERNELS_CIRCULAR; usable by every gridding call;
- *             release with wp_free_kernels
+ *             = WP_KERNELS_OWNED; usable by every gridding call; release with wp_free_kernels
  * On an error nothing stays allocated and *out is zeroed.
  */
 int wp_make_wkernels_owned(const wp_plan* plan, const float* taper, const double* w_planes,

@@ -80,14 +80,13 @@ class WKernels:
     cache: torch.Tensor         # [n] complex64
     radial: torch.Tensor | None = None     # [P][K_out] complex64
     spline_m: torch.Tensor | None = None   # [P][K_out] complex64
-    circular: bool = False      # taps beyond the support radius are exactly zero (WP_KERNELS_CIRCULAR)
 
     @property
     def P(self) -> int:
         return int(self.w_planes.numel())
 
     def c(self) -> _lib.WpWkernels:
-        return _lib.WpWkernels(self.P, 1 if self.circular else 0, self.w_planes.data_ptr(), self.support.data_ptr(),
+        return _lib.WpWkernels(self.P, 0, self.w_planes.data_ptr(), self.support.data_ptr(),
                                self.offsets.data_ptr(),
                                self.cache.data_ptr() if self.cache is not None else None,
                                self.radial.data_ptr() if self.radial is not None else None,
@@ -195,14 +194,14 @@ def make_wkernels(plan: Plan, taper: torch.Tensor, w_planes, supports=None,
         p_fixed = plan.replace(trunc_frac=0.0)
         radial, spline_m, _ = hankel_radial(p_fixed, taper, w_planes, ws, stream=stream)
         cache = resample(p_fixed, radial, spline_m, sup, off, stream=stream)
-        return WKernels(w_planes, sup, off, cache, radial, spline_m, circular=True)
+        return WKernels(w_planes, sup, off, cache, radial, spline_m)
     if plan.trunc_frac <= 0:
         raise ValueError("supports are required when plan.trunc_frac <= 0")
     radial, spline_m, sup = hankel_radial(plan, taper, w_planes, ws, stream=stream)
     sup_host = sup.cpu().tolist()
     off = torch.tensor(kernel_layout(plan, sup_host), dtype=torch.int64, device=dev)
     cache = resample(plan, radial, spline_m, sup, off, stream=stream)
-    return WKernels(w_planes, sup, off, cache, radial, spline_m, circular=True)
+    return WKernels(w_planes, sup, off, cache, radial, spline_m)
 
 
 class OwnedWKernels:
@@ -263,7 +262,7 @@ def fft_wkernels(plan: Plan, taper: torch.Tensor, w_planes, supports, circular: 
     _lib.check("wp_fft_wkernels", _lib.load().wp_fft_wkernels(
         ctypes.byref(plan.c()), _ptr(taper), _ptr(w_planes), P, _ptr(sup), _ptr(off), int(bool(circular)),
         _ptr(ws), ws.numel(), _ptr(cache), _stream(stream)))
-    return WKernels(w_planes, sup, off, cache, circular=bool(circular))
+    return WKernels(w_planes, sup, off, cache)
 
 
 def plane_values(uvw: torch.Tensor, P: int, stream=None) -> torch.Tensor:

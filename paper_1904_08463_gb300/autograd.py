@@ -48,7 +48,7 @@ class Predictor:
     def kernels(self, taper: torch.Tensor) -> WKernels:
         radial, spline_m, _ = hankel_radial(self.plan, taper, self.w_planes, self.kg_ws)
         cache = resample(self.plan, radial, spline_m, self.support, self.offsets)
-        return WKernels(self.w_planes, self.support, self.offsets, cache, radial, spline_m, circular=True)
+        return WKernels(self.w_planes, self.support, self.offsets, cache, radial, spline_m)
 
     def __call__(self, image: torch.Tensor, taper: torch.Tensor) -> torch.Tensor:
         return Visibilities.apply(image, taper, self)

@@ -54,8 +54,7 @@ class _State:
         self.grid = torch.zeros((N, N), dtype=torch.complex64, device=dev)
         self.image = torch.empty((N, N), dtype=torch.float32, device=dev)
         self.stats = torch.zeros(2, dtype=torch.float64, device=dev)
-        self.wk = WKernels(self.w_planes, self.support, self.offsets, self.cache, self.radial, self.spline_m,
-                           circular=True)
+        self.wk = WKernels(self.w_planes, self.support, self.offsets, self.cache, self.radial, self.spline_m)
         if tuner is not None:
             self._tune(tuner)
 

@@ -392,7 +392,7 @@ int wp_make_wkernels_owned(const wp_plan* plan, const float* taper, const double
     if (e != cudaSuccess) return fail(cuda_fail("cudaStreamSynchronize", e));
     cudaFree(ws);
     out->P = P;
-    out->flags = WP_KERNELS_OWNED | WP_KERNELS_CIRCULAR;   // the resample zeroes taps beyond radius S
+    out->flags = WP_KERNELS_OWNED;
     out->w_planes = (const double*)d_w;
     out->support = (const int32_t*)d_sup;
     out->offsets = (const int64_t*)d_off;

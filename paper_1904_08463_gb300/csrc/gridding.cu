@@ -954,13 +954,6 @@ int grid_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, float2* 
 // =======================================================================================
 // K11: degridding (adjoint).  One warp per binned visibility.
 // =======================================================================================
-// CIRC (kernel sets with WP_KERNELS_CIRCULAR): taps beyond the support radius are exact zeros,
-// so each footprint row visits only the 32-column chunks that meet its nonzero span
-// [lo, hi] = { jx : |os (jx - S) - fu| <= floor(sqrt((os S)^2 - dy^2)) } and loads nothing
-// outside it -- about a fifth of the tap and grid reads.  The spans of 32 rows are computed
-// at once, one row per lane, and broadcast by shuffles; every column stays on its lane and a
-// skipped product would have added an exact zero, so the result is the same bits.
-template <bool CIRC>
 __global__ void __launch_bounds__(256) k_degrid(int N, int os, int s_max, int nbins,
                                                 const int32_t* __restrict__ support,
                                                 const int64_t* __restrict__ offsets,
@@ -981,57 +974,6 @@ __global__ void __launch_bounds__(256) k_degrid(int N, int os, int s_max, int nb
     const float2* sub = cache + offsets[p] + (int64_t)(fv * os + fu) * W * W;
     const float2* g0 = grid + (int64_t)(iv - S) * N + (iu - S);
     float sr = 0.0f, si = 0.0f;
-    if (CIRC) {
-        const int lim2 = (os * S) * (os * S);
-        int lo_r = W, hi_r = -1;    // span of row jb + lane
-        int jb = -32;
-        for (int jy = 0; jy < W; jy += 2) {   // pairs (jy, jy + 1); groups of 32 rows start even
-            if (jy >= jb + 32) {
-                jb = jy;
-                const int r = jb + lane;
-                lo_r = W;
-                hi_r = -1;
-                if (r < W) {
-                    const int dy = os * (r - S) - fv;
-                    const int R2 = lim2 - dy * dy;
-                    if (R2 >= 0) {
-                        int R = (int)sqrtf((float)R2);             // then exact floor(sqrt(R2))
-                        R -= (R * R > R2);
-                        R += ((R + 1) * (R + 1) <= R2);
-                        const int a = fu - R, b = fu + R;          // os (jx - S) in [a, b]
-                        lo_r = max(S + (a > 0 ? 1 : -((-a) / os)), 0);
-                        hi_r = min(S + b / os, W - 1);
-                    }
-                }
-            }
-            const int i0 = jy - jb;
-            const int lo0 = __shfl_sync(0xffffffffu, lo_r, i0), hi0 = __shfl_sync(0xffffffffu, hi_r, i0);
-            const int lo1r = __shfl_sync(0xffffffffu, lo_r, (i0 + 1) & 31);
-            const int hi1r = __shfl_sync(0xffffffffu, hi_r, (i0 + 1) & 31);
-            const bool two = jy + 1 < W;
-            const int lo1 = two ? lo1r : W, hi1 = two ? hi1r : -1;
-            const int lo = min(lo0, lo1), hi = max(hi0, hi1);
-            if (lo > hi) continue;
-            const float2* trow = sub + jy * W;
-            const float2* grow = g0 + (int64_t)jy * N;
-            for (int jx = (lo & ~31) + lane; jx <= hi; jx += 32) {
-                if (jx >= lo0 && jx <= hi0) {
-                    const float2 tp0 = __ldg(trow + jx);
-                    const float2 gv0 = grow[jx];
-                    const float ti0 = sgn * tp0.y;
-                    sr = fmaf(tp0.x, gv0.x, fmaf(ti0, gv0.y, sr));
-                    si = fmaf(tp0.x, gv0.y, fmaf(-ti0, gv0.x, si));
-                }
-                if (jx >= lo1 && jx <= hi1) {
-                    const float2 tp1 = __ldg(trow + W + jx);
-                    const float2 gv1 = grow[N + jx];
-                    const float ti1 = sgn * tp1.y;
-                    sr = fmaf(tp1.x, gv1.x, fmaf(ti1, gv1.y, sr));
-                    si = fmaf(tp1.x, gv1.y, fmaf(-ti1, gv1.x, si));
-                }
-            }
-        }
-    } else {
     // two footprint rows per pass: their tap and grid loads (L2) are in flight together
     int jy = 0;
     for (; jy + 1 < W; jy += 2) {
@@ -1059,7 +1001,6 @@ __global__ void __launch_bounds__(256) k_degrid(int N, int os, int s_max, int nb
             si = fmaf(tp.x, gv.y, fmaf(-ti, gv.x, si));
         }
     }
-    }
     for (int o = 16; o; o >>= 1) {
         sr += __shfl_xor_sync(0xffffffffu, sr, o);
         si += __shfl_xor_sync(0xffffffffu, si, o);
@@ -1073,14 +1014,9 @@ int degrid_run(const Geom& g, const wp_wkernels* kern, int64_t V, const GridWork
     if (V == 0) return WP_OK;
     int64_t threads = V * 32;
     unsigned blocks = (unsigned)((threads + 255) / 256);
-    if (kern->flags & WP_KERNELS_CIRCULAR)
-        k_degrid<true><<<blocks, 256, 0, st>>>(g.N, g.os, g.s_max, (int)w.nbins, w.seff, kern->offsets,
-                                               reinterpret_cast<const float2*>(kern->cache), w.count, w.srec,
-                                               grid, vis_out, V);
-    else
-        k_degrid<false><<<blocks, 256, 0, st>>>(g.N, g.os, g.s_max, (int)w.nbins, w.seff, kern->offsets,
-                                                reinterpret_cast<const float2*>(kern->cache), w.count, w.srec,
-                                                grid, vis_out, V);
+    k_degrid<<<blocks, 256, 0, st>>>(g.N, g.os, g.s_max, (int)w.nbins, w.seff, kern->offsets,
+                                     reinterpret_cast<const float2*>(kern->cache), w.count, w.srec, grid,
+                                     vis_out, V);
     WP_LAUNCH_CHECK("k_degrid");
     return WP_OK;
 }

@@ -203,37 +203,3 @@ def test_on_the_fly_taps_need_no_cache_and_match_the_cache_gridder(interp):
     b = o.bin_vis(g, uvw, planes, sup)
     Go = o.grid(g, ks, b, vis.astype(np.complex128))
     assert rel_l2(G4, Go) < 1e-5
-
-
-@pytest.mark.parametrize("os_,route", [(8, "hankel"), (5, "hankel"), (8, "fft")])
-def test_circular_degrid_skips_only_zero_taps(os_, route):
-    """Kernel sets flagged circular (their taps beyond the support radius are exact zeros):
-    the degridder visits only each footprint row's nonzero span, and gives the same bits as
-    the full-footprint degridder on the same kernels, for an even and an odd oversampling and
-    for circular 2D-FFT kernels."""
-    import dataclasses
-
-    wp = _wp()
-    dev = torch.device("cuda")
-    N, dl, R = 256, np.deg2rad(3.0) / 256, 256
-    planes = np.array([0.0, 150.0, 600.0, 1500.0])
-    sup = np.array([3, 11, 24, 40])
-    plan = wp.Plan(N, dl, os_, 40, 1, 0.0, R, "cubic", "tf32x3")
-    taper = torch.tensor(synth.gaussian_taper_samples(N, dl, R), dtype=torch.float32, device=dev)
-    if route == "hankel":
-        wk = wp.make_wkernels(plan, taper, planes, supports=sup)
-    else:
-        wk = wp.fft_wkernels(plan, taper, planes, sup, circular=True)
-    assert wk.circular
-    full = dataclasses.replace(wk, circular=False)
-    rng = np.random.default_rng(os_)
-    V = 4000
-    du = plan.geometry().du
-    uvw = np.stack([rng.uniform(-80, 80, V) * du, rng.uniform(-80, 80, V) * du,
-                    rng.uniform(-1600, 1600, V)], 1).astype(np.float32)
-    u_d = torch.tensor(uvw, device=dev).reshape(-1)
-    X = torch.tensor((rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))).astype(np.complex64), device=dev)
-    a = wp.degrid(plan, wk, u_d, X).cpu().numpy()
-    b = wp.degrid(plan, full, u_d, X).cpu().numpy()
-    assert np.abs(a).max() > 0
-    assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
