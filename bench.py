@@ -32,10 +32,10 @@ if ROOT not in sys.path:
 
 import synth  # noqa: E402
 
-# DRAM read + write bytes of one k_resample launch on the 512-plane batch, from the ncu capture
-# summarised in profiles/k_resample_kernel_batch.md (every-2nd-plane case, scaled by the ratio
-# of algorithmic bytes).  Reported only while the resample's source (its section of kernelgen.cu
-# and the shared tap evaluation) is the one it was measured on.
+# DRAM read + write bytes of one k_resample launch on the 512-plane batch, from an ncu capture
+# of the every-2nd-plane case scaled by the ratio of algorithmic bytes.  Reported only while the
+# resample's source (its section of kernelgen.cu and the shared tap evaluation) is the one it
+# was measured on.
 RESAMPLE_TRAFFIC = {"bytes_per_launch": 5.9310e+09, "source_sha1": "288a38e8889e"}
 
 GRID_METHOD_NAMES = {0: "register tile", 1: "shared-memory tile, footprint over the lanes (atomics)",
@@ -191,7 +191,7 @@ def oracle_kernel_rate(n_planes: int = 512):
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return rate, threads, (f"{n_planes} of 512 |w| planes (supports {int(kb['support'][pick].min())}.."
                            f"{int(kb['support'][pick].max())}) in {dt:.1f} s, extrapolated by tap count; "
-                           f"transform matrix excluded; resample single-threaded")
+                           f"transform matrix excluded; OpenMP over planes' transform rows and sub-kernels")
 
 
 def oracle_rate_one_thread(n_planes: int = 64):
@@ -307,9 +307,10 @@ def run_gpu(args):
     resample_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
     value = world * P / (ms_step * 1e-3)
     bytes_cache = cache_bytes(sup_host)
-    # algorithmic bytes of one resample launch: cache written + radial line and spline
-    # coefficients read once per (plane, fv) block
-    alg_bytes = bytes_cache + P * OS * 16 * min(g.k_out, OS * 127 + 2)
+    # algorithmic bytes of one resample launch: cache written + each plane's radial line and
+    # spline coefficients read once (re-reads of the line by the launch's other blocks are L2
+    # traffic of this implementation, not algorithmic bytes)
+    alg_bytes = bytes_cache + P * 16 * min(g.k_out, OS * 127 + 2)
     hbm, bf16, src = _peaks()
     achieved = alg_bytes / (resample_ms * 1e-3) / 1e9
 
@@ -552,10 +553,12 @@ def log(msg):
 
 def run_imaging(args, dev):
     """Full imaging: kernel generation (1 % truncation, max-support layout, no host sync)
-    + gridding of 8M visibilities + dirty image, per step."""
+    + gridding of 8M visibilities + dirty image, per step (the package's Imager step)."""
     import torch
 
     import paper_1904_08463_gb300 as wp
+    from paper_1904_08463_gb300.autotune import GRID_CHOICES, Autotuner
+    from paper_1904_08463_gb300.imager import Imager
 
     log("imaging: generating inputs")
     d = synth.full_imaging(V=args.imaging_vis)
@@ -567,50 +570,29 @@ def run_imaging(args, dev):
     vis = vis + torch.complex(noise[:, 0], noise[:, 1]).to(torch.complex64).to(dev)
     V = vis.numel()
     P = args.imaging_planes
-    planes = wp.plane_values(uvw.reshape(-1), P).cpu().numpy()   # Alg. 2 steps 1-3 on the GPU
     plan = wp.Plan(N, dl, OS, 127, 3, 0.01, 512, "cubic", args.kernelgen)
     taper = torch.tensor(synth.gaussian_taper_samples(N, dl, 512), dtype=torch.float32, device=dev)
-    wpl = torch.tensor(planes, dtype=torch.float64, device=dev)
-    ws = wp.workspace(wp.kernelgen_workspace_bytes(plan, P), dev)
-    wp.kernelgen_prepare(plan, P, ws)
-    off = torch.tensor(wp.kernel_layout_max(plan, P), dtype=torch.int64, device=dev)
-    cache = torch.empty(int(off[-1].item()), dtype=torch.complex64, device=dev)
-    sup = torch.empty(P, dtype=torch.int32, device=dev)
-    gws = wp.workspace(max(wp.grid_workspace_bytes(plan.replace(grid_tile=t), P, V) for t in (32, 64)), dev)
-    G = torch.zeros((N, N), dtype=torch.complex64, device=dev)
-    img = torch.empty((N, N), dtype=torch.float32, device=dev)
-    stats = torch.zeros(2, dtype=torch.float64, device=dev)
-    radial = torch.empty((P, plan.geometry().k_out), dtype=torch.complex64, device=dev)
-    spl = torch.empty_like(radial)
-    wk = wp.WKernels(wpl, sup, off, cache, radial, spl)
+    uvw_flat = uvw.reshape(-1)
+    im = Imager(plan, taper, uvw_flat, P)        # plane values (Alg. 2 steps 1-3) on the GPU
+    planes = im.w_planes.cpu().numpy()
     # the gridder's launch shape (method x tile) is picked by the autotuner on this problem
-    from paper_1904_08463_gb300.autotune import GRID_CHOICES, Autotuner
-
-    wp.hankel_radial(plan, taper, wpl, ws, radial, spl, sup)
-    wp.resample(plan, radial, spl, sup, off, cache)
     tuner = Autotuner()
     choices = [list(c) for c in GRID_CHOICES]
     if args.grid_shape:
         choices = [[int(x) for x in args.grid_shape.split(",")]]
-    mt = tuner.choose(Autotuner.key("grid", N, P, 127, V), choices,
-                      lambda c: wp.grid(plan.replace(grid_method=int(c[0]), grid_tile=int(c[1])), wk,
-                                        uvw.reshape(-1), vis, None, G, gws, stats))
-    plan = plan.replace(grid_method=int(mt[0]), grid_tile=int(mt[1]))
-    gws_need = wp.grid_workspace_bytes(plan, P, V)
-    assert gws.numel() >= gws_need
+    im.autotune(uvw_flat, vis, None, tuner, choices)
+    plan = im.plan
+    img, stats, sup = im.image, im.stats, im.support
 
     def step(ev=None):
-        wp.hankel_radial(plan, taper, wpl, ws, radial, spl, sup)
-        wp.resample(plan, radial, spl, sup, off, cache)
-        G.zero_()
-        stats.zero_()
+        im.kernels()
         if ev is not None:
             ev[0].record()
-        wp.grid(plan, wk, uvw.reshape(-1), vis, None, G, gws, stats)
+        im.grid_only(uvw_flat, vis)
         if ev is not None:
             ev[1].record()
-        # the weight sum is V minus drops; pass the host-known upper value to avoid a sync
-        wp.dirty_image(plan, taper, G, float(V), img)
+        # normalised by the weight sum the gridder accumulated, read on the device (no sync)
+        im.image_only()
 
     log("imaging: warm-up")
     for _ in range(max(1, args.warmup)):
@@ -632,7 +614,6 @@ def run_imaging(args, dev):
     uvw_h = uvw.reshape(-1).cpu().pin_memory()
     vis_h = vis.cpu().pin_memory()
     img_h = torch.empty(img.shape, dtype=img.dtype).pin_memory()
-    uvw_flat = uvw.reshape(-1)
 
     def e2e_step():
         uvw_flat.copy_(uvw_h, non_blocking=True)
@@ -651,8 +632,6 @@ def run_imaging(args, dev):
     sup_h = sup.cpu().numpy()
     # algorithmic work of gridding: 8 flop per tap of the (2S+1)^2 footprint of every
     # gridded visibility
-    from collections import Counter
-
     aw = np.abs(d["uvw"][:, 2].astype(np.float64))
     idx = np.clip(np.searchsorted(planes, aw), 1, P - 1)
     lower = np.where(np.abs(aw - planes[idx - 1]) <= np.abs(planes[idx] - aw), idx - 1, idx)
@@ -814,20 +793,27 @@ def run_grad(args, dev):
 
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle timed as it stands on the same workload, each step a
-    bounded sample of 128 of the 512 planes (every fourth |w|), about 3 s of CPU work."""
+    bounded sample of 128 of the 512 planes (every fourth |w|), a few seconds of CPU work.
+    value and ms_per_step are those of the sample actually run: kernels made / step time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    vals = []
+    n_sample = 128
+    step_s = []
     t0 = time.perf_counter()
     for s in range(args.warmup + args.steps):
-        rate, thr, sample = oracle_kernel_rate(n_planes=128)
+        ts = time.perf_counter()
+        rate, thr, sample = oracle_kernel_rate(n_planes=n_sample)
         if s >= args.warmup:
-            vals.append(rate)
+            step_s.append(time.perf_counter() - ts)
     total = time.perf_counter() - t0
-    v = float(np.mean(vals))
+    ms = float(np.mean(step_s)) * 1e3
+    v = n_sample / (ms * 1e-3)
+    sample = (f"{n_sample} of the 512 |w| planes per step (every fourth, supports 7..127), screen + "
+              f"transform + spline + resample each; transform matrix excluded; value = {n_sample} kernels / "
+              f"measured step time")
     out = {"metric": METRIC, "value": v, "unit": "w-kernels/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 512 / v * 1e3, "higher_is_better": True,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": "kernel-generation batch: 1024 signed w-planes linspace[-20000,20000] "
                                   "(512 distinct |w| kernels), R=4096, os=8, support 7..127 by |w|, "

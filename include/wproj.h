@@ -57,6 +57,10 @@ extern "C" {
 #define WP_ERR_TIMEOUT    -6   /* a bounded device-side wait expired                  */
 #define WP_ERR_DEVICE     -7   /* current device is not sm_103 (GB300)                */
 #define WP_ERR_UNSUPPORTED -8  /* valid request outside what the library implements     */
+#define WP_ERR_INFLIGHT   -9   /* a bounded wait expired and the kernel had to exit with a
+                                  copy or tensor-core operation still in flight (a drain
+                                  wait ran out as well): results are void and the CUDA
+                                  context should be treated as suspect (reset it)         */
 
 /* plan.interp (Section 4.3.2: linear or cubic-spline interpolation of the radial line) */
 #define WP_INTERP_CUBIC    0
@@ -210,7 +214,9 @@ int wp_hankel_radial(const wp_plan* plan, const float* taper, const double* w_pl
 /*
  * Device-side status of the last kernel-generation call on `workspace` (synchronizes
  * `stream`): 0, or WP_ERR_TIMEOUT when a bounded wait of the tensor-core transform expired
- * (its output is then left unwritten, and the CUDA context stays usable).
+ * (its output is then left unwritten, and the CUDA context stays usable), or WP_ERR_INFLIGHT
+ * when, after such an expiry, the kernel could not see its own copies land within a second
+ * budget either and exited with them in flight (context suspect).
  */
 int wp_kernelgen_status(const wp_plan* plan, int32_t P, void* workspace, size_t workspace_bytes,
                         int32_t* status_host, void* stream);
@@ -350,13 +356,16 @@ int wp_degrid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw,
  * host framework whose plug-ins may only use memory they are handed -- and therefore
  * cannot provide the scratch that wp_grid takes.
  *  - Same arguments and result as wp_grid, minus the workspace: the scratch is one array of
- *    WP_GRID_STATIC_SCRATCH_BYTES (64 MiB) compiled into the library, which every GPU that
- *    loads the library holds until the process exits.
+ *    WP_GRID_STATIC_SCRATCH_BYTES (64 MiB) compiled into the library.
  *  - A problem whose scratch need (wp_grid_workspace_bytes) exceeds that size is rejected
  *    with WP_ERR_SIZE before any launch (roughly 1.5 million visibilities fit with a
  *    256^2 grid and 16 planes; fewer with large grids and many planes).
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *    with that device current; make that first call before any stream capture.
+ *    with that device current.  CUDA loads the module holding the array lazily, so it is this
+ *    first call that commits the 64 MiB on that device (held until the process exits), not
+ *    the loading of the library: a caller that reserves its memory pools up front must make
+ *    the first call before reserving them -- a call with V = 0 (uvw and vis may be NULL)
+ *    does the set-up and grids nothing -- and before any stream capture.
  *  - No cudaMalloc, cudaFree or allocating library routine is called.
  *  - All calls share the one array and it keeps the previous call's contents; each call
  *    clears what must start at zero.  Calls that overlap on the GPU (other streams or host
@@ -426,6 +435,18 @@ int wp_image_adjoint(const wp_plan* plan, const float* taper, const float* image
  */
 int wp_dirty_image(const wp_plan* plan, const float* taper, float* grid, double weight_sum,
                    float* image, void* stream);
+
+/*
+ * wp_dirty_image normalised by a weight sum that stays on the device: weight_sum_dev points to
+ * one device double -- normally stats[0] as accumulated by wp_grid, the sum of the weights of
+ * the visibilities actually gridded (dropped ones and non-unit weights accounted for; Section 3:
+ * the dirty image is the weighted mean of the gridded data).  The sum is read by the kernel, so
+ * the call needs no host read-back and can follow wp_grid inside a captured stream.  A sum
+ * <= 0 (nothing gridded) gives an all-zero image.  weight_sum_dev must be 8-byte aligned
+ * (WP_ERR_SIZE otherwise); other arguments as wp_dirty_image.
+ */
+int wp_dirty_image_stats(const wp_plan* plan, const float* taper, float* grid,
+                         const double* weight_sum_dev, float* image, void* stream);
 
 /*
  * Adjoint of wp_dirty_image's linear map (without taking the real part), used to

@@ -252,6 +252,8 @@ void or_resample(int K, const double *y, const double *m, int os, int S, int int
     double h = 1.0; /* x and the node spacing are both in radial-sample units */
     int64_t lim = (int64_t)os * S;
     lim = lim * lim;
+    /* the os^2 sub-kernels are independent: one per OpenMP iteration, same arithmetic */
+    #pragma omp parallel for collapse(2) schedule(dynamic, 1)
     for (int fv = 0; fv < os; ++fv)
         for (int fu = 0; fu < os; ++fu)
             for (int jy = 0; jy < W; ++jy)

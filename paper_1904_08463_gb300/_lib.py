@@ -119,6 +119,7 @@ _SIGS = {
     "wp_image_adjoint": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p,
                                    c_void_p]),
     "wp_dirty_image": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
+    "wp_dirty_image_stats": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "wp_image_to_grid": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
 }
 

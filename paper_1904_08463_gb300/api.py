@@ -325,14 +325,22 @@ def degrid(plan: Plan, wk: WKernels, uvw: torch.Tensor, grid_: torch.Tensor, out
     return out
 
 
-def dirty_image(plan: Plan, taper: torch.Tensor, grid_: torch.Tensor, weight_sum: float,
+def dirty_image(plan: Plan, taper: torch.Tensor, grid_: torch.Tensor, weight_sum,
                 out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """Dirty image; ``grid_`` is transformed in place (consumed)."""
+    """Dirty image; ``grid_`` is transformed in place (consumed).  ``weight_sum`` is a host
+    number, or a float64 CUDA tensor whose first element is read on the device -- normally the
+    ``stats`` that ``grid`` returned (``stats[0]`` = sum of the weights actually gridded), which
+    keeps the normalisation free of host read-backs."""
     N = plan.image_size
     _need(taper, torch.float32, "taper", plan.radial_samples)
     _need(grid_, torch.complex64, "grid", N * N)
     if out is None:
         out = torch.empty((N, N), dtype=torch.float32, device=grid_.device)
+    if isinstance(weight_sum, torch.Tensor):
+        _need(weight_sum, torch.float64, "weight_sum")
+        _lib.check("wp_dirty_image_stats", _lib.load().wp_dirty_image_stats(
+            ctypes.byref(plan.c()), _ptr(taper), _ptr(grid_), _ptr(weight_sum), _ptr(out), _stream(stream)))
+        return out
     _lib.check("wp_dirty_image", _lib.load().wp_dirty_image(
         ctypes.byref(plan.c()), _ptr(taper), _ptr(grid_), float(weight_sum), _ptr(out), _stream(stream)))
     return out

@@ -27,6 +27,7 @@ class Problem:
     uvw: torch.Tensor          # [3V] float32
     vis: torch.Tensor          # [V] complex64
     P: int                     # number of |w| planes
+    weight: torch.Tensor | None = None   # [V] float32 visibility weights (None: all 1)
 
 
 class _State:
@@ -72,7 +73,7 @@ class _State:
 
         def run_grid(mt):
             api.grid(self.plan.replace(grid_method=int(mt[0]), grid_tile=int(mt[1])), self.wk, pb.uvw, pb.vis,
-                     None, self.grid, self.grid_ws, self.stats)
+                     pb.weight, self.grid, self.grid_ws, self.stats)
 
         m, t = tuner.choose(k2, [list(c) for c in GRID_CHOICES], run_grid)
         self.plan = self.plan.replace(grid_method=int(m), grid_tile=int(t))
@@ -86,9 +87,9 @@ class _State:
         self.kernels(self.plan)
         self.grid.zero_()
         self.stats.zero_()
-        api.grid(self.plan, self.wk, self.pb.uvw, self.pb.vis, None, self.grid, self.grid_ws, self.stats)
-        # every footprint fits by construction, so the weight sum is the visibility count
-        api.dirty_image(self.plan, self.pb.taper, self.grid, float(self.V), self.image)
+        api.grid(self.plan, self.wk, self.pb.uvw, self.pb.vis, self.pb.weight, self.grid, self.grid_ws, self.stats)
+        # normalised by the weights actually gridded (drops and weights included), read on the device
+        api.dirty_image(self.plan, self.pb.taper, self.grid, self.stats, self.image)
 
     def cost(self) -> float:
         taps = float(self.V) * float((2 * self.pb.plan.max_support + 1) ** 2) / 4.0

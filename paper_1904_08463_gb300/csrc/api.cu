@@ -154,6 +154,7 @@ const char* wp_strerror(int code) {
         case WP_ERR_TIMEOUT: return "a bounded device-side wait expired";
         case WP_ERR_DEVICE: return "current device is not sm_103 (GB300)";
         case WP_ERR_UNSUPPORTED: return "request not supported by the library";
+        case WP_ERR_INFLIGHT: return "a bounded wait expired with device work still in flight (context suspect)";
         default: return "unknown status";
     }
 }
@@ -460,11 +461,15 @@ size_t wp_grid_workspace_bytes(const wp_plan* plan, int32_t P, int64_t V) {
     return carve_grid(g, P, V, nullptr, 0, nullptr);
 }
 
-static int check_grid_args(const wp_plan* plan, const wp_wkernels* k, const float* uvw, int64_t V,
-                           void* workspace, size_t workspace_bytes, Geom* g, bool gridding = false) {
+}  // extern "C"
+
+// Argument checks of every call that bins visibilities.  with_workspace = false skips the
+// caller-workspace checks (the allocation-free gridder supplies its own scratch).
+int wp::check_grid_args(const wp_plan* plan, const wp_wkernels* k, const float* uvw, int64_t V,
+                        void* workspace, size_t workspace_bytes, Geom* g, bool gridding, bool with_workspace) {
     int rc = make_geom(plan, g);
     if (rc) return rc;
-    if (!k || !workspace) return WP_ERR_NULL;
+    if (!k || (with_workspace && !workspace)) return WP_ERR_NULL;
     if (k->P < 1 || k->P > 8192) return WP_ERR_SIZE;
     if (!k->w_planes || !k->support || !k->offsets) return WP_ERR_NULL;
     if (gridding && g->grid_method == 4) {      // taps from the radial lines, no cache
@@ -475,10 +480,13 @@ static int check_grid_args(const wp_plan* plan, const wp_wkernels* k, const floa
     if (V < 0 || V > 2147483647LL) return WP_ERR_SIZE;
     if (V > 0 && !uvw) return WP_ERR_NULL;
     if ((int64_t)k->P * ((g->N + 63) / 64) * ((g->N + 63) / 64) >= 2147483647LL) return WP_ERR_SIZE;
-    if (!aligned256(workspace) || workspace_bytes < carve_grid(*g, k->P, V, nullptr, 0, nullptr))
+    if (with_workspace &&
+        (!aligned256(workspace) || workspace_bytes < carve_grid(*g, k->P, V, nullptr, 0, nullptr)))
         return WP_ERR_WORKSPACE;
     return check_device();
 }
+
+extern "C" {
 
 int wp_grid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw, const float* vis,
             const float* weight, int64_t V, void* workspace, size_t workspace_bytes, float* grid,
@@ -578,7 +586,19 @@ int wp_dirty_image(const wp_plan* plan, const float* taper, float* grid, double 
     if (!taper || !grid || !image) return WP_ERR_NULL;
     if (!(weight_sum > 0.0)) return WP_ERR_SIZE;
     if ((rc = check_device())) return rc;
-    return image_dirty(g, taper, reinterpret_cast<float2*>(grid), weight_sum, image, (cudaStream_t)stream);
+    return image_dirty(g, taper, reinterpret_cast<float2*>(grid), weight_sum, nullptr, image, (cudaStream_t)stream);
+}
+
+int wp_dirty_image_stats(const wp_plan* plan, const float* taper, float* grid, const double* weight_sum_dev,
+                         float* image, void* stream) {
+    WP_RANGE("wp_dirty_image_stats");
+    Geom g;
+    int rc = make_geom(plan, &g);
+    if (rc) return rc;
+    if (!taper || !grid || !weight_sum_dev || !image) return WP_ERR_NULL;
+    if ((uintptr_t)weight_sum_dev & 7u) return WP_ERR_SIZE;
+    if ((rc = check_device())) return rc;
+    return image_dirty(g, taper, reinterpret_cast<float2*>(grid), 0.0, weight_sum_dev, image, (cudaStream_t)stream);
 }
 
 int wp_image_to_grid(const wp_plan* plan, const float* taper, const float* image, double weight_sum,

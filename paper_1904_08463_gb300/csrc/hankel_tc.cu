@@ -32,6 +32,8 @@
 //                   along the radial index)
 // Every mbarrier wait is bounded by a clock budget; on expiry the kernel records
 // WP_ERR_TIMEOUT in `status`, stops issuing, drains what it issued, frees TMEM and returns.
+// A drain that itself runs out of budget (a copy or MMA still in flight at exit) records
+// WP_ERR_INFLIGHT instead, which callers must treat as a suspect context.
 // `withhold_loads` (self-test only) keeps the producer idle so that the first wait expires.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -97,7 +99,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* st
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > budget) {
-            atomicExch(status, WP_ERR_TIMEOUT);
+            atomicMin(status, WP_ERR_TIMEOUT);   // the most severe code recorded wins
             return false;
         }
     }
@@ -299,9 +301,14 @@ __global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant_
                 ++issued;
             }
             if (!ok) {
-                // every issued slice must land before the CTA may exit
+                // every issued slice must land before the CTA may exit; if one still has not
+                // after another budget, the CTA exits with a copy in flight into its shared
+                // memory, which is recorded as its own status (the context is then suspect)
                 for (int kb = max(0, issued - STAGES); kb < issued; ++kb)
-                    mbar_wait(bar_full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, status, budget);
+                    if (!mbar_wait(bar_full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, status, budget)) {
+                        atomicMin(status, WP_ERR_INFLIGHT);
+                        break;
+                    }
             }
         }
     } else if (warp == 1) {
@@ -380,8 +387,9 @@ __global__ void __launch_bounds__(192, 1) k_hankel_tf32x3(const __grid_constant_
         }
     }
     __syncwarp();
-    // no MMA may still write TMEM when it is freed
-    if (warp == 1) mbar_wait(bar_done, 0, status, budget);
+    // no MMA may still write TMEM when it is freed (if the wait gives up, that is recorded as
+    // the in-flight status: the tensor memory is then freed under a running MMA)
+    if (warp == 1 && lane == 0 && !mbar_wait(bar_done, 0, status, budget)) atomicMin(status, WP_ERR_INFLIGHT);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 1) {

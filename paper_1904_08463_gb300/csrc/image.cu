@@ -81,8 +81,21 @@ __device__ __forceinline__ float taper_at_pixel(const float* __restrict__ taper,
     return (1.0f - a) * taper[i0] + a * taper[i0 + 1];
 }
 
+// inv_wsum is 1 / weight_sum from the host, or, when wsum_dev is set, 1 / wsum_dev[0] read on the
+// device (the weight sum wp_grid accumulated in its stats) -- one FP64 division per block, broadcast
+// through shared memory; a sum <= 0 (nothing gridded) gives a zero image.
 __global__ void k_dirty_correct(int N, int R, const float* __restrict__ taper, float inv_wsum,
-                                const float2* __restrict__ F, float* __restrict__ image) {
+                                const double* __restrict__ wsum_dev, const float2* __restrict__ F,
+                                float* __restrict__ image) {
+    __shared__ float s_inv;
+    if (wsum_dev) {
+        if (threadIdx.x == 0) {
+            const double s = wsum_dev[0];
+            s_inv = (s > 0.0) ? (float)(1.0 / s) : 0.0f;
+        }
+        __syncthreads();
+        inv_wsum = s_inv;
+    }
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     int m = blockIdx.y;
     if (l >= N) return;
@@ -124,12 +137,13 @@ __global__ void k_checker(int N, float2* __restrict__ G) {
     }
 }
 
-int image_dirty(const Geom& g, const float* taper, float2* grid, double wsum, float* image,
-                cudaStream_t st) {
+int image_dirty(const Geom& g, const float* taper, float2* grid, double wsum, const double* wsum_dev,
+                float* image, cudaStream_t st) {
     int rc = exec_fft(g.N, grid, CUFFT_INVERSE, st);
     if (rc) return rc;
     dim3 blk(256), grd((g.N + 255) / 256, g.N);
-    k_dirty_correct<<<grd, blk, 0, st>>>(g.N, g.R, taper, (float)(1.0 / wsum), grid, image);
+    const float inv = wsum_dev ? 0.0f : (float)(1.0 / wsum);
+    k_dirty_correct<<<grd, blk, 0, st>>>(g.N, g.R, taper, inv, wsum_dev, grid, image);
     WP_LAUNCH_CHECK("k_dirty_correct");
     return WP_OK;
 }

@@ -15,7 +15,9 @@
 namespace wp {
 namespace {
 
-// The scratch.  Every GPU that loads libwproj.so holds these bytes until the process exits.
+// The scratch.  A device holds these bytes from the first wp_grid_static call on it until the
+// process exits: the runtime loads this file's module (and with it the array) lazily, when the
+// set-up below asks for the array's address -- not when the library is loaded.
 constexpr size_t kStaticScratchBytes = (size_t)WP_GRID_STATIC_SCRATCH_BYTES;
 __device__ __align__(256) unsigned char g_grid_scratch[kStaticScratchBytes];
 
@@ -49,26 +51,16 @@ extern "C" int wp_grid_static(const wp_plan* plan, const wp_wkernels* kernels, c
                               double* stats, void* stream) {
     WP_RANGE("wp_grid_static");
     Geom g;
-    int rc = make_geom(plan, &g);
+    // wp_grid's own checks (plan, kernels, sizes, device), minus the caller workspace
+    int rc = check_grid_args(plan, kernels, uvw, V, nullptr, 0, &g, true, false);
     if (rc) return rc;
-    if (!kernels || !grid) return WP_ERR_NULL;
-    if (kernels->P < 1 || kernels->P > 8192) return WP_ERR_SIZE;
-    if (!kernels->w_planes || !kernels->support || !kernels->offsets) return WP_ERR_NULL;
-    if (g.grid_method == 4) {           // taps from the radial lines, no cache
-        if (!kernels->radial || (g.interp == WP_INTERP_CUBIC && !kernels->spline_m)) return WP_ERR_NULL;
-    } else if (!kernels->cache) {
-        return WP_ERR_NULL;
-    }
-    if (V < 0 || V > 2147483647LL) return WP_ERR_SIZE;
-    if (V > 0 && (!uvw || !vis)) return WP_ERR_NULL;
-    if ((int64_t)kernels->P * ((g.N + 63) / 64) * ((g.N + 63) / 64) >= 2147483647LL) return WP_ERR_SIZE;
+    if (!grid || (V > 0 && !vis)) return WP_ERR_NULL;
     const size_t need = carve_grid(g, kernels->P, V, nullptr, 0, nullptr);
     if (need > kStaticScratchBytes) {
         set_last_error("wp_grid_static", "problem needs more scratch than the static array holds "
                                          "(WP_GRID_STATIC_SCRATCH_BYTES); use wp_grid");
         return WP_ERR_SIZE;
     }
-    if ((rc = check_device_public())) return rc;
     void* scratch = nullptr;
     if ((rc = scratch_for_current_device(&scratch))) return rc;
     cudaStream_t st = (cudaStream_t)stream;

@@ -46,6 +46,8 @@ struct Geom {
 };
 
 int make_geom(const wp_plan* plan, Geom* g);
+int check_grid_args(const wp_plan* plan, const wp_wkernels* k, const float* uvw, int64_t V, void* workspace,
+                    size_t workspace_bytes, Geom* g, bool gridding = false, bool with_workspace = true);
 int check_device_public();   // WP_OK when the current device is sm_103
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -216,8 +218,8 @@ int grid_run(const Geom& g, const wp_wkernels* k, const GridWork& w, float2* gri
 int degrid_run(const Geom& g, const wp_wkernels* k, int64_t V, const GridWork& w, const float2* grid,
                float2* vis_out, cudaStream_t st);
 
-int image_dirty(const Geom& g, const float* taper, float2* grid, double wsum, float* image,
-                cudaStream_t st);
+int image_dirty(const Geom& g, const float* taper, float2* grid, double wsum, const double* wsum_dev,
+                float* image, cudaStream_t st);
 int image_to_grid(const Geom& g, const float* taper, const float* image, double wsum, float2* grid,
                   cudaStream_t st);
 void release_fft_plans();

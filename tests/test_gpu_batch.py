@@ -1,31 +1,54 @@
 """Batched uneven imaging problems: the graph-replayed batch gives the same dirty images as
-running the problems one at a time and as the plain API calls; the autotuner's choices do
-not change results."""
+running the problems one at a time, as the plain API calls and as the FP64 oracle; the
+autotuner's choices do not change results; weights and dropped visibilities normalise the
+images by the weights actually gridded."""
 import numpy as np
 import pytest
 
 import synth
+from oracle import oracle as o
+from tests.common import IMAGE_TOL, f32
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
 
-def _problems(dev):
+def _problems(dev, n=5, seed=7, uv_scale=1.0, weights=False):
     import paper_1904_08463_gb300 as wp
     from paper_1904_08463_gb300.batch import Problem
 
-    specs = synth.batch_problems(n=5, seed=7, sizes=(256, 512), planes=(8, 40), vis=(2000, 60000))
+    specs = synth.batch_problems(n=n, seed=seed, sizes=(256, 512), planes=(8, 40), vis=(2000, 60000))
     out = []
-    for d in specs:
+    for i, d in enumerate(specs):
         R = 256
+        d["uvw"] = (d["uvw"] * np.float32(uv_scale)).astype(np.float32)
+        d["vis"] = synth.predict(d["uvw"], d["sky"])
+        d["wt"] = (np.random.default_rng(seed + i).uniform(0.3, 2.0, d["uvw"].shape[0]).astype(np.float32)
+                   if weights else None)
         plan = wp.Plan(d["N"], d["cell_size"], 8, d["max_support"], 3, 0.01, R, "cubic", "fp32")
         taper = torch.tensor(synth.gaussian_taper_samples(d["N"], d["cell_size"], R), dtype=torch.float32,
                              device=dev)
         uvw = torch.tensor(d["uvw"], device=dev).reshape(-1)
-        vis = torch.tensor(synth.predict(d["uvw"], d["sky"]), device=dev)
-        out.append(Problem(plan, taper, uvw, vis, d["P"]))
-    return out
+        vis = torch.tensor(d["vis"], device=dev)
+        wt = torch.tensor(d["wt"], device=dev) if weights else None
+        out.append(Problem(plan, taper, uvw, vis, d["P"], wt))
+    return specs, out
+
+
+def _oracle_image(d, R=256):
+    """The oracle's dirty image of one batch problem: its own plane values (means of
+    equal-count |w| chunks), FP64 kernels with its own 1 % supports, gridding and image,
+    normalised by the weights of the visibilities it kept."""
+    N, dl = d["N"], d["cell_size"]
+    g = o.Geometry(N, dl, 8, d["max_support"], 3, 0.01, R)
+    tap = f32(synth.gaussian_taper_samples(N, dl, R))
+    planes = o.mean_w_planes(d["uvw"][:, 2].astype(np.float64), d["P"])
+    ks = o.wkernels(g, tap, planes)
+    b = o.bin_vis(g, d["uvw"], planes, ks.support)
+    keep = b.drop == 0
+    wsum = float(np.sum(d["wt"][keep].astype(np.float64))) if d["wt"] is not None else float(keep.sum())
+    return g, ks, b, wsum, o.dirty_image(g, o.grid(g, ks, b, d["vis"], d["wt"]), tap, wsum)
 
 
 def test_graph_batch_matches_sequential_and_direct_calls(tmp_path):
@@ -34,7 +57,7 @@ def test_graph_batch_matches_sequential_and_direct_calls(tmp_path):
     from paper_1904_08463_gb300.batch import BatchImager
 
     dev = torch.device("cuda")
-    pbs = _problems(dev)
+    specs, pbs = _problems(dev)
     tuner = Autotuner(str(tmp_path / "tune.json"))
     b = BatchImager(pbs, n_streams=3, tuner=tuner)
     b.run_sequential()
@@ -56,6 +79,12 @@ def test_graph_batch_matches_sequential_and_direct_calls(tmp_path):
     img = wp.dirty_image(pb.plan, pb.taper, G, float(stats[0].item())).cpu().numpy()
     assert np.abs(img - seq[0]).max() <= 1e-5 * np.abs(img).max()
     assert len(tuner.table) >= 2
+    # the replayed images against the FP64 oracle, problem by problem (routes and gridder
+    # shapes as the autotuner picked them)
+    for i in range(len(pbs)):
+        g, ks, bo, wsum, ref = _oracle_image(specs[i])
+        assert np.array_equal(b.states[i].support.cpu().numpy(), ks.support), i
+        assert np.abs(rep[i] - ref).max() <= IMAGE_TOL * np.abs(ref).max(), i
 
 
 def test_graph_batch_of_large_grids_matches_sequential():
@@ -85,3 +114,30 @@ def test_graph_batch_of_large_grids_matches_sequential():
     torch.cuda.synchronize()
     for a, c in zip(seq, [im.cpu().numpy() for im in b.images]):
         assert np.abs(a - c).max() <= 1e-5 * np.abs(a).max()
+
+
+def test_batch_normalises_by_the_weights_actually_gridded():
+    """Non-unit weights and visibilities whose footprints leave the grid (dropped): every
+    batched image equals wp_dirty_image of the same grid with the true sum of gridded weights
+    (read back here), and the oracle's image (Section 3: weighted mean of the gridded data)."""
+    import paper_1904_08463_gb300 as wp
+    from paper_1904_08463_gb300.batch import BatchImager
+
+    dev = torch.device("cuda")
+    specs, pbs = _problems(dev, n=3, seed=17, uv_scale=1.12, weights=True)
+    b = BatchImager(pbs, n_streams=2)
+    assert b.dropped() > 0
+    b.replay()
+    b.replay()
+    torch.cuda.synchronize()
+    for i, (d, st) in enumerate(zip(specs, b.states)):
+        img = st.image.cpu().numpy()
+        g, ks, bo, wsum, ref = _oracle_image(d)
+        assert np.array_equal(st.support.cpu().numpy(), ks.support), i
+        stats = st.stats.cpu().numpy()
+        assert stats[1] == (bo.drop != 0).sum() > 0, i
+        assert stats[0] == pytest.approx(wsum, rel=1e-6), i
+        G, _ = wp.grid(st.plan, st.wk, pbs[i].uvw, pbs[i].vis, pbs[i].weight)
+        host = wp.dirty_image(st.plan, pbs[i].taper, G, float(stats[0])).cpu().numpy()
+        assert np.abs(img - host).max() <= 1e-5 * np.abs(host).max(), i
+        assert np.abs(img - ref).max() <= IMAGE_TOL * np.abs(ref).max(), i

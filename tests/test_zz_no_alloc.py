@@ -51,11 +51,16 @@ def test_static_scratch_gridding_matches_workspace_gridding_twice():
     ref, ref_stats = wp.grid(plan, wk, uvw, vis, wt)
     torch.cuda.synchronize()
     R = ref.cpu().numpy()
-    for _ in range(2):   # two calls in a row: the shared scratch must not leak between calls
-        G = torch.zeros_like(ref)
-        stats = torch.zeros(2, dtype=torch.float64, device=vis.device)
+    outs = [(torch.zeros_like(ref), torch.zeros(2, dtype=torch.float64, device=vis.device)) for _ in range(2)]
+    # set-up call (V = 0: looks up the array, which commits it on this device, grids nothing)
+    assert _call_static(lib, plan, wk, uvw, vis, wt, 0, outs[0][0], outs[0][1]) == 0
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for G, stats in outs:   # two calls in a row: the shared scratch must not leak between calls
         assert _call_static(lib, plan, wk, uvw, vis, wt, V, G, stats) == 0
         torch.cuda.synchronize()
+        # nothing allocated on the device by the calls, through torch or the driver
+        assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_allocated() == alloc0
         assert np.abs(G.cpu().numpy() - R).max() <= 1e-5 * np.abs(R).max()
         assert np.allclose(stats.cpu().numpy(), ref_stats.cpu().numpy(), rtol=1e-12)
 
