@@ -110,7 +110,11 @@ typedef struct wp_plan {
                                across the footprint's columns (no atomics in the tile);
                                4: as 3, each tap interpolated on the fly from the plane's
                                radial line (wp_wkernels.radial / spline_m) instead of
-                               read from the cache.
+                               read from the cache;
+                               5: as 3 over groups of 8 consecutive planes per work item
+                               (one flush of the tile for the whole group);
+                               6: groups of 8 planes, each warp's rows of the tile held in
+                               registers, lanes across the columns.
                                grid_tile and grid_method are tuning choices only: the
                                results agree to FP32 rounding order                      */
 } wp_plan;

@@ -139,37 +139,9 @@ __global__ void __launch_bounds__(256) k_bin(int64_t V, const float* __restrict_
     double wsum = 0.0, drops = 0.0;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < V) {
-        double u = (double)uvw[3 * k], v = (double)uvw[3 * k + 1], w = (double)uvw[3 * k + 2];
-        double aw = fabs(w);
-        // lower_bound over the ascending plane values, then nearest of the two neighbours
-        int lo = 0, hi = P;
-        while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (wps[mid] < aw) lo = mid + 1; else hi = mid;
-        }
-        int p;
-        if (lo == 0) p = 0;
-        else if (lo == P) p = P - 1;
-        else {
-            double dl_ = fabs(aw - wps[lo - 1]);
-            double dh_ = fabs(aw - wps[lo]);
-            p = (dh_ < dl_) ? lo : lo - 1;          // ties -> lower index
-        }
-        int conj = (w < 0.0) ? 1 : 0;
-        double uc = __dadd_rn(__ddiv_rn(u, du), (double)(N / 2));
-        double vc = __dadd_rn(__ddiv_rn(v, du), (double)(N / 2));
-        double tu = rint(__dmul_rn(uc, (double)os));
-        double tv = rint(__dmul_rn(vc, (double)os));
-        double giu = floor(__ddiv_rn(tu, (double)os));
-        double giv = floor(__ddiv_rn(tv, (double)os));
-        int S = support[p];   // effective support: 0 when the plane's cache block holds none
-        // non-finite u, v or w: no nearest plane or cell exists -- dropped and counted
-        bool ok = S >= 1 && isfinite(u) && isfinite(v) && isfinite(w) && (giu - S >= 0.0) &&
-                  (giu + S <= (double)(N - 1)) && (giv - S >= 0.0) && (giv + S <= (double)(N - 1));
+        int p, iu, iv, fu, fv, conj;
+        const bool ok = bin_decide(uvw, k, P, wps, support, N, du, os, &p, &iu, &iv, &fu, &fv, &conj);
         if (ok) {
-            int iu = (int)giu, iv = (int)giv;
-            int fu = (int)(tu - giu * (double)os);
-            int fv = (int)(tv - giv * (double)os);
             int kk = p * ntiles + (iv / T) * ntx + (iu / T);
             key[k] = kk;
             rec[k] = make_int4(iu | (iv << 16), fu | (fv << 8) | (conj << 16), p, (int)k);
@@ -852,8 +824,19 @@ int add_stats(double* stats, const double* red, cudaStream_t st) {
     return WP_OK;
 }
 
+int write_items(int64_t n, const GridWork& w, cudaStream_t st) {
+    k_item_write<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, w.flags, w.cursor, w.items, w.ctrl);
+    WP_LAUNCH_CHECK("k_item_write");
+    return WP_OK;
+}
+
 int grid_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, float2* grid, double* stats,
              cudaStream_t st) {
+    if (g.grid_method == 5 || g.grid_method == 6) {      // plane groups (grid_group.cu)
+        int rc = grid_run_group(g, kern, w, grid, st);
+        if (rc) return rc;
+        return stats ? add_stats(stats, w.red, st) : WP_OK;
+    }
     const int P = kern->P;
     const int ngrp = (P + PLANE_GROUP - 1) / PLANE_GROUP;
     const int64_t n = (g.grid_method == 2) ? (int64_t)ngrp * w.ntiles : (int64_t)P * w.ntiles;

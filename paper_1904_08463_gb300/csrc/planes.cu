@@ -1,13 +1,12 @@
 // w-plane values (Alg. 1 / Alg. 2 steps 1-3 of the paper): sort the visibilities' |w|,
 // cut the sorted list into P equal-count chunks (the first V mod P chunks one longer) and
-// take each chunk's mean -- the paper's default of average w per plane.  The sort is a
-// radix sort of the float bit patterns (non-negative floats order like their bits); the
-// chunk means are FP64 sums, one block per chunk.  Non-finite |w| (bit patterns from
+// take each chunk's mean -- the paper's default of average w per plane.  The sort is the
+// library's own radix sort (sort.cu) of the float bit patterns (non-negative floats order like
+// their bits); the chunk means are FP64 sums, one block per chunk.  Non-finite |w| (bit patterns from
 // 0x7F800000 up) sort last and take no part: the chunks cut the finite values only, and a
 // chunk left empty (fewer finite values than planes) takes the largest finite |w| (0 if none),
 // so the plane values stay ascending; binning drops such visibilities.
 #include <cuda_runtime.h>
-#include <cub/device/device_radix_sort.cuh>
 
 #include "wp_internal.cuh"
 
@@ -48,31 +47,30 @@ __global__ void __launch_bounds__(256) k_chunk_means(int P, const unsigned* __re
     }
 }
 
-static size_t sort_temp_bytes(int64_t V) {
-    size_t bytes = 0;
-    cub::DeviceRadixSort::SortKeys(nullptr, bytes, (const unsigned*)nullptr, (unsigned*)nullptr, (int)V, 0, 31);
-    return bytes;
-}
-
 size_t plane_values_workspace_bytes(int64_t V) {
     Carver c(nullptr, 0);
     c.take<unsigned>((size_t)V);
     c.take<unsigned>((size_t)V);
     c.take<int64_t>(1);
-    c.take<char>(sort_temp_bytes(V));
+    c.take<int>(radix_sort_hist_ints(V));
+    c.take<int>(scan_tmp_ints((int64_t)radix_sort_hist_ints(V)));
     return (size_t)round_up((int64_t)c.off, 256);
 }
 
 int plane_values(const float* uvw, int64_t V, int P, void* ws, size_t bytes, double* out, cudaStream_t st) {
     Carver c(ws, bytes);
     unsigned* keys = c.take<unsigned>((size_t)V);
-    unsigned* sorted = c.take<unsigned>((size_t)V);
+    unsigned* alt = c.take<unsigned>((size_t)V);
     int64_t* nf = c.take<int64_t>(1);
-    size_t tb = sort_temp_bytes(V);
-    void* tmp = c.take<char>(tb);
+    int* hist = c.take<int>(radix_sort_hist_ints(V));
+    int* stmp = c.take<int>(scan_tmp_ints((int64_t)radix_sort_hist_ints(V)));
     k_abs_w_keys<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(V, uvw, keys);
     WP_LAUNCH_CHECK("k_abs_w_keys");
-    WP_CUDA(cub::DeviceRadixSort::SortKeys(tmp, tb, keys, sorted, (int)V, 0, 31, st));
+    bool in_alt = false;
+    // |w| has a clear sign bit: bits 0..30 order the keys (four 8-bit passes)
+    int rc = radix_sort<uint32_t>(keys, nullptr, alt, nullptr, V, 31, hist, stmp, st, &in_alt);
+    if (rc) return rc;
+    const unsigned* sorted = in_alt ? alt : keys;
     k_finite_count<<<1, 1, 0, st>>>(V, sorted, nf);
     WP_LAUNCH_CHECK("k_finite_count");
     k_chunk_means<<<P, 256, 0, st>>>(P, sorted, nf, out);

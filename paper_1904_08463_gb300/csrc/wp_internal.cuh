@@ -145,6 +145,55 @@ __device__ __forceinline__ int fit_support(int S, int os, const int64_t* __restr
 
 __device__ __forceinline__ int skew(int k) { return k ^ ((k >> 3) & 7); }
 
+// Binning decisions of one visibility (Alg. 1 / Alg. 2: nearest |w| plane, ties to the lower
+// index; conjugation for w < 0, Section 4.1; grid cell and oversampling offset), all in FP64
+// with explicitly rounded operations so that every binning kernel takes the same decisions:
+//   t = rint((u/du + N/2) os), iu = floor(t/os), fu = t - iu os   (same for v).
+// wps: the P ascending plane values (shared memory); support: the call's effective supports
+// (0 when a plane's cache block holds none).  Returns false (dropped) when u, v or w is not
+// finite, the plane is unusable, or any tap of the (2S+1)^2 footprint leaves [0, N)^2.
+__device__ __forceinline__ bool bin_decide(const float* __restrict__ uvw, int64_t k, int P, const double* wps,
+                                           const int32_t* __restrict__ support, int N, double du, int os,
+                                           int* p_out, int* iu_out, int* iv_out, int* fu_out, int* fv_out,
+                                           int* conj_out) {
+    const double u = (double)uvw[3 * k], v = (double)uvw[3 * k + 1], w = (double)uvw[3 * k + 2];
+    const double aw = fabs(w);
+    // lower_bound over the ascending plane values, then nearest of the two neighbours
+    int lo = 0, hi = P;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (wps[mid] < aw) lo = mid + 1; else hi = mid;
+    }
+    int p;
+    if (lo == 0) p = 0;
+    else if (lo == P) p = P - 1;
+    else {
+        const double dl_ = fabs(aw - wps[lo - 1]);
+        const double dh_ = fabs(aw - wps[lo]);
+        p = (dh_ < dl_) ? lo : lo - 1;          // ties -> lower index
+    }
+    const double uc = __dadd_rn(__ddiv_rn(u, du), (double)(N / 2));
+    const double vc = __dadd_rn(__ddiv_rn(v, du), (double)(N / 2));
+    const double tu = rint(__dmul_rn(uc, (double)os));
+    const double tv = rint(__dmul_rn(vc, (double)os));
+    const double giu = floor(__ddiv_rn(tu, (double)os));
+    const double giv = floor(__ddiv_rn(tv, (double)os));
+    const int S = support[p];
+    const bool ok = S >= 1 && isfinite(u) && isfinite(v) && isfinite(w) && (giu - S >= 0.0) &&
+                    (giu + S <= (double)(N - 1)) && (giv - S >= 0.0) && (giv + S <= (double)(N - 1));
+    *p_out = p;
+    *conj_out = (w < 0.0) ? 1 : 0;
+    if (ok) {
+        *iu_out = (int)giu;
+        *iv_out = (int)giv;
+        *fu_out = (int)(tu - giu * (double)os);
+        *fv_out = (int)(tv - giv * (double)os);
+    } else {
+        *iu_out = *iv_out = *fu_out = *fv_out = 0;
+    }
+    return ok;
+}
+
 // Spline interval of radius sqrt(q) on the unit-spaced line: k = round(x - 1/2) through the
 // float mantissa (1.5 * 2^23) from an approximate x = q rsqrt(q) -- an off-by-one next to an
 // integer radius is harmless, the interpolant being continuous there.  The offset keeps the
@@ -211,10 +260,19 @@ int kg_resample(const Geom& g, int P, const float2* radial, const float2* spline
 int exclusive_scan_i32(const int* in, int* out, int64_t n, int* tmp, cudaStream_t st);
 size_t scan_tmp_ints(int64_t n);
 
+// stable LSD radix sort (sort.cu); KT = uint32_t or uint64_t, vals may be NULL
+int64_t radix_sort_tiles(int64_t n);
+size_t radix_sort_hist_ints(int64_t n);
+template <class KT>
+int radix_sort(KT* keys, uint32_t* vals, KT* keys_alt, uint32_t* vals_alt, int64_t n, int bits, int* hist,
+               int* scan_tmp, cudaStream_t st, bool* in_alt);
+
 int grid_bin(const Geom& g, const wp_wkernels* k, const float* uvw, const float2* vis,
              const float* weight, int64_t V, const GridWork& w, cudaStream_t st);
 int grid_run(const Geom& g, const wp_wkernels* k, const GridWork& w, float2* grid, double* stats,
              cudaStream_t st);
+int write_items(int64_t n, const GridWork& w, cudaStream_t st);   // compact live items (flags scanned into cursor)
+int grid_run_group(const Geom& g, const wp_wkernels* k, const GridWork& w, float2* grid, cudaStream_t st);
 int degrid_run(const Geom& g, const wp_wkernels* k, int64_t V, const GridWork& w, const float2* grid,
                float2* vis_out, cudaStream_t st);
 

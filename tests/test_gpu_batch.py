@@ -124,7 +124,7 @@ def test_batch_normalises_by_the_weights_actually_gridded():
     from paper_1904_08463_gb300.batch import BatchImager
 
     dev = torch.device("cuda")
-    specs, pbs = _problems(dev, n=3, seed=17, uv_scale=1.12, weights=True)
+    specs, pbs = _problems(dev, n=3, seed=17, uv_scale=1.6, weights=True)
     b = BatchImager(pbs, n_streams=2)
     assert b.dropped() > 0
     b.replay()

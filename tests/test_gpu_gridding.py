@@ -53,7 +53,7 @@ def test_small_imaging_grid_and_dirty_image():
     assert np.all(img[~o.disc_mask(g)] == 0)
 
 
-@pytest.mark.parametrize("grid_method", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("grid_method", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("grid_tile", [32, 64])
 @pytest.mark.parametrize("V,seed", [(0, 1), (1, 2), (37, 3), (5000, 4)])
 def test_grid_edges_and_conjugation(V, seed, grid_tile, grid_method):
@@ -140,7 +140,7 @@ def test_plane_values_are_means_of_equal_count_chunks(V, P, seed):
     assert np.all(np.diff(got) >= 0)
 
 
-@pytest.mark.parametrize("grid_method", [0, 3])
+@pytest.mark.parametrize("grid_method", [0, 3, 5, 6])
 def test_non_finite_coordinates_are_dropped(grid_method):
     """NaN / infinite u, v or w: the GPU binning drops and counts them as the oracle does, the
     grid of the rest is unchanged, degridding returns 0 for them, and the plane values are the
@@ -203,3 +203,27 @@ def test_on_the_fly_taps_need_no_cache_and_match_the_cache_gridder(interp):
     b = o.bin_vis(g, uvw, planes, sup)
     Go = o.grid(g, ks, b, vis.astype(np.complex128))
     assert rel_l2(G4, Go) < 1e-5
+
+
+@pytest.mark.parametrize("grid_method,grid_tile", [(5, 32), (5, 64), (6, 32), (6, 64)])
+def test_plane_groups_with_a_ragged_last_group(grid_method, grid_tile):
+    """19 planes -- two full groups of 8 and a ragged group of 3 -- with supports 2..38, so that
+    footprints reach up to two tiles away: the plane-group gridders against the oracle, with
+    weights and both signs of w."""
+    N, dl = 256, np.deg2rad(4.0) / 256
+    planes = np.linspace(0.0, 1800.0, 19)
+    sup = np.linspace(2, 38, 19).round().astype(int)
+    wp, dev, plan, g, taper, tap_d, wk, ks = _setup(N, dl, 4, 38, 256, planes, sup, grid_tile=grid_tile,
+                                                    grid_method=grid_method)
+    rng = np.random.default_rng(23)
+    V = 6000
+    uvw = np.stack([rng.uniform(-N / 2, N / 2, V) * g.du, rng.uniform(-N / 2, N / 2, V) * g.du,
+                    rng.uniform(-1900, 1900, V)], 1).astype(np.float32)
+    vis = (rng.normal(size=V) + 1j * rng.normal(size=V)).astype(np.complex64)
+    wt = rng.uniform(0.5, 2.0, V).astype(np.float32)
+    G, stats = wp.grid(plan, wk, torch.tensor(uvw, device=dev).reshape(-1), torch.tensor(vis, device=dev),
+                       torch.tensor(wt, device=dev))
+    b = o.bin_vis(g, uvw, planes, sup)
+    Go = o.grid(g, ks, b, vis, wt)
+    assert np.abs(G.cpu().numpy() - Go).max() <= 1e-5 * np.abs(Go).max()
+    assert stats[1].item() == (b.drop != 0).sum() > 0
