@@ -114,7 +114,9 @@ typedef struct wp_plan {
                                5: as 3 over groups of 8 consecutive planes per work item
                                (one flush of the tile for the whole group);
                                6: groups of 8 planes, each warp's rows of the tile held in
-                               registers, lanes across the columns.
+                               registers, lanes across the columns;
+                               7, 8: as 3, with 2 (7) or 4 (8) consecutive visibilities of a
+                               bin applied per shared-memory read-modify-write.
                                grid_tile and grid_method are tuning choices only: the
                                results agree to FP32 rounding order                      */
 } wp_plan;

@@ -40,7 +40,7 @@ int make_geom(const wp_plan* plan, Geom* g) {
         plan->kernelgen != WP_KG_BF16X6 && plan->kernelgen != WP_KG_PROJSLICE)
         return WP_ERR_PLAN;
     if (plan->grid_tile != 0 && plan->grid_tile != 32 && plan->grid_tile != 64) return WP_ERR_PLAN;
-    if (plan->grid_method < 0 || plan->grid_method > 6) return WP_ERR_PLAN;
+    if (plan->grid_method < 0 || plan->grid_method > 8) return WP_ERR_PLAN;
     g->N = N;
     g->dl = plan->cell_size;
     g->du = 1.0 / ((double)N * plan->cell_size);

@@ -567,6 +567,156 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_ro(int N, int os, int 
     }
 }
 
+// Row-owned shared tile with B entries per read-modify-write (grid_method 7: B = 2, 8: B = 4).
+// Method 3 pays, per tap, an 8-byte tap load and a 16-byte shared read-modify-write, all through
+// the L1 data path, which bounds it.  Here the candidates are compacted into the list in bin
+// order (a ballot per warp, so consecutive entries are consecutive visibilities of the bin --
+// usually the same baseline a few dumps apart, with nearly the same rectangle), and each warp
+// takes B consecutive entries at a time: over the union of their rectangles restricted to its
+// rows, every lane loads the taps of the entries that cover its cell and applies all of them in
+// one read-modify-write, so the shared traffic per tap drops by up to B.
+template <int TILE, int B>
+__global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_rb(int N, int os, int s_max, int ntx, int ntiles,
+                                                             const int32_t* __restrict__ support,
+                                                             const int64_t* __restrict__ offsets,
+                                                             const float2* __restrict__ cache,
+                                                             const int* __restrict__ start,
+                                                             const int4* __restrict__ srec,
+                                                             const float2* __restrict__ svis,
+                                                             const int* __restrict__ items,
+                                                             int* __restrict__ ctrl, float2* __restrict__ grid) {
+    constexpr int CH = TILE / 32;                 // column chunks of a tile row
+    __shared__ float2 tile[TILE * TILE];
+    __shared__ int l_off[RO_LIST];                // first tap of the intersection in the plane's cache
+    __shared__ uint32_t l_geo[RO_LIST];           // r0 | r1 << 8 | c0 << 16 | c1 << 24 (tile coordinates)
+    __shared__ float4 l_cf[RO_LIST];              // (Re V, -s Im V, s Re V, Im V), s = -1 for w < 0
+    __shared__ int s_wcnt[GRID_WARPS];
+    __shared__ int s_item;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int n_items = ctrl[1];
+    for (int i = threadIdx.x; i < TILE * TILE; i += blockDim.x) tile[i] = make_float2(0.0f, 0.0f);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&ctrl[0], 1);
+        __syncthreads();
+        const int item_idx = s_item;
+        __syncthreads();
+        if (item_idx >= n_items) break;
+        const int item = items[item_idx];
+        const int p = item / ntiles;
+        const int t = item - p * ntiles;
+        const int oy = t / ntx, ox = t - oy * ntx;
+        const int S = min(max(support[p], 1), s_max);
+        const int W = 2 * S + 1;
+        const int W2 = W * W;
+        const int D = (S + TILE - 1) / TILE;
+        const float2* pcache = cache + offsets[p];
+        const int ty0 = oy * TILE, tx0 = ox * TILE;
+        const int cx_lo = max(0, ox - D), cx_hi = min(ntx - 1, ox + D);
+        for (int cy = max(0, oy - D); cy <= min(ntx - 1, oy + D); ++cy) {
+            const int kb = p * ntiles + cy * ntx;
+            const int beg = start[kb + cx_lo], end = start[kb + cx_hi + 1];
+            for (int base = beg; base < end; base += RO_LIST) {
+                // decode one candidate per thread; compact in bin order (ballot + warp offsets)
+                const int q = base + (int)threadIdx.x;
+                int iu = 0, iv = 0, c0 = 0, c1 = -1, r0 = 0, r1 = -1;
+                int4 r4 = make_int4(0, 0, 0, 0);
+                if (q < end) {
+                    r4 = __ldg(srec + q);
+                    iu = r4.x & 0xffff;
+                    iv = (r4.x >> 16) & 0xffff;
+                    c0 = max(iu - S, tx0);
+                    c1 = min(iu + S, tx0 + TILE - 1);
+                    r0 = max(iv - S, ty0);
+                    r1 = min(iv + S, ty0 + TILE - 1);
+                }
+                const bool meets = c0 <= c1 && r0 <= r1;
+                const unsigned bal = __ballot_sync(0xffffffffu, meets);
+                if (lane == 0) s_wcnt[wid] = __popc(bal);
+                __syncthreads();
+                int woff = 0, n = 0;
+#pragma unroll
+                for (int w = 0; w < GRID_WARPS; ++w) {
+                    const int cw = s_wcnt[w];
+                    woff += (w < wid) ? cw : 0;
+                    n += cw;
+                }
+                if (meets) {
+                    const int slot = woff + __popc(bal & lt);
+                    const int fu = r4.y & 0xff, fv = (r4.y >> 8) & 0xff;
+                    const float sg = ((r4.y >> 16) & 1) ? -1.0f : 1.0f;
+                    const float2 vv = __ldg(svis + q);
+                    l_off[slot] = (fv * os + fu) * W2 + (r0 - (iv - S)) * W + (c0 - (iu - S));
+                    l_geo[slot] = (uint32_t)(r0 - ty0) | ((uint32_t)(r1 - ty0) << 8) |
+                                  ((uint32_t)(c0 - tx0) << 16) | ((uint32_t)(c1 - tx0) << 24);
+                    l_cf[slot] = make_float4(vv.x, -sg * vv.y, sg * vv.x, vv.y);
+                }
+                __syncthreads();
+                for (int e0 = 0; e0 < n; e0 += B) {
+                    int br0[B], br1[B], bc0[B], bc1[B], boff[B];
+                    float4 bcf[B];
+                    int R0 = TILE, R1 = -1, C0 = TILE, C1 = -1;
+#pragma unroll
+                    for (int b = 0; b < B; ++b) {
+                        if (e0 + b < n) {
+                            const uint32_t geo = l_geo[e0 + b];
+                            br0[b] = (int)(geo & 0xff);
+                            br1[b] = (int)((geo >> 8) & 0xff);
+                            bc0[b] = (int)((geo >> 16) & 0xff);
+                            bc1[b] = (int)(geo >> 24);
+                            boff[b] = l_off[e0 + b] - br0[b] * W - bc0[b];   // tap of tile cell (0, 0)
+                            bcf[b] = l_cf[e0 + b];
+                        } else {
+                            br0[b] = TILE; br1[b] = -1; bc0[b] = TILE; bc1[b] = -1; boff[b] = 0;
+                            bcf[b] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        }
+                        R0 = min(R0, br0[b]);
+                        R1 = max(R1, br1[b]);
+                        C0 = min(C0, bc0[b]);
+                        C1 = max(C1, bc1[b]);
+                    }
+                    const int rw = R0 + ((wid - R0) & (GRID_WARPS - 1));   // first owned row
+                    for (int r = rw; r <= R1; r += GRID_WARPS) {
+                        float2* trow = tile + r * TILE;
+#pragma unroll
+                        for (int k = 0; k < CH; ++k) {
+                            const int c = C0 + lane + 32 * k;
+                            if (c <= C1) {
+                                float2 tp[B];
+#pragma unroll
+                                for (int b = 0; b < B; ++b) {
+                                    const bool v = r >= br0[b] && r <= br1[b] && c >= bc0[b] && c <= bc1[b];
+                                    tp[b] = v ? __ldg(pcache + (boff[b] + r * W + c)) : make_float2(0.0f, 0.0f);
+                                }
+                                float2 a = trow[c];
+#pragma unroll
+                                for (int b = 0; b < B; ++b) {
+                                    a.x = fmaf(bcf[b].x, tp[b].x, fmaf(bcf[b].y, tp[b].y, a.x));
+                                    a.y = fmaf(bcf[b].z, tp[b].y, fmaf(bcf[b].w, tp[b].x, a.y));
+                                }
+                                trow[c] = a;
+                            }
+                        }
+                    }
+                    __syncwarp();   // the next entries may touch these cells from other lanes
+                }
+                __syncthreads();   // the list is rebuilt for the next round
+            }
+        }
+        __syncthreads();
+        // flush the tile (one atomic per touched cell) and clear it for the next item
+        for (int i = threadIdx.x; i < TILE * TILE; i += blockDim.x) {
+            const float2 a = tile[i];
+            if (a.x != 0.0f || a.y != 0.0f) {
+                const int gy = ty0 + i / TILE, gx = tx0 + (i & (TILE - 1));
+                if (gy < N && gx < N) atomicAdd(grid + (int64_t)gy * N + gx, a);
+                tile[i] = make_float2(0.0f, 0.0f);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // On-the-fly taps (grid_method 4): the row-owned tile of method 3, but each tap is
 // interpolated from the plane's radial line in shared memory (the resample's own evaluation,
 // so the values are the cache's bits) instead of being read from the cache.  The line is
@@ -885,6 +1035,20 @@ int grid_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, float2* 
             if (cubic) WP_LAUNCH_OTF(64, true); else WP_LAUNCH_OTF(64, false);
         }
 #undef WP_LAUNCH_OTF
+    } else if (g.grid_method == 7 || g.grid_method == 8) {
+#define WP_LAUNCH_RB(T, BB)                                                                                     \
+        do {                                                                                                    \
+            WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_rb<T, BB>, GRID_WARPS * 32, 0)); \
+            if (per_sm < 1) per_sm = 1;                                                                         \
+            k_grid_rb<T, BB><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(g.N, g.os, g.s_max, w.ntx, w.ntiles,     \
+                w.seff, kern->offsets, c2, w.count, w.srec, w.svis, w.items, w.ctrl, grid);                     \
+        } while (0)
+        if (w.T == 32) {
+            if (g.grid_method == 7) WP_LAUNCH_RB(32, 2); else WP_LAUNCH_RB(32, 4);
+        } else {
+            if (g.grid_method == 7) WP_LAUNCH_RB(64, 2); else WP_LAUNCH_RB(64, 4);
+        }
+#undef WP_LAUNCH_RB
     } else if (g.grid_method == 3) {
         if (w.T == 32) {
             WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_ro<32>, GRID_WARPS * 32, 0));
