@@ -40,7 +40,10 @@ RESAMPLE_TRAFFIC = {"bytes_per_launch": 5.9310e+09, "source_sha1": "288a38e8889e
 
 GRID_METHOD_NAMES = {0: "register tile", 1: "shared-memory tile, footprint over the lanes (atomics)",
                      2: "warp-private shared-memory tiles", 3: "shared-memory tile, rows owned by warps",
-                     4: "rows owned by warps, taps interpolated from the radial line"}
+                     4: "rows owned by warps, taps interpolated from the radial line",
+                     5: "shared-memory tile over groups of 8 planes", 6: "row registers over groups of 8 planes",
+                     7: "rows owned by warps, 2 visibilities per update", 8: "rows owned by warps, 4 visibilities per update",
+                     9: "slots: register sums along a Morton curve (Romein's work distribution)"}
 
 METRIC = "w-kernels/s (Hankel vs 2D-FFT) and Mvis/s gridded, 1 GB300, at stated FP64 error"
 N_IMG, FOV_DEG, R_KG, OS = 4096, 8.0, 4096, 8

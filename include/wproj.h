@@ -116,7 +116,11 @@ typedef struct wp_plan {
                                6: groups of 8 planes, each warp's rows of the tile held in
                                registers, lanes across the columns;
                                7, 8: as 3, with 2 (7) or 4 (8) consecutive visibilities of a
-                               bin applied per shared-memory read-modify-write.
+                               bin applied per shared-memory read-modify-write;
+                               9: slots -- each lane owns footprint positions modulo 2S+1 and
+                               sums its taps in registers over visibilities sorted along a
+                               Morton curve of their cells, writing to the grid only when
+                               its cell changes (grid_tile ignored).
                                grid_tile and grid_method are tuning choices only: the
                                results agree to FP32 rounding order                      */
 } wp_plan;

@@ -21,7 +21,7 @@ import torch
 
 KERNELGEN_CHOICES = ("fp32", "tf32x3", "bf16x3", "bf16x6")
 TILE_CHOICES = (32, 64)
-GRID_CHOICES = tuple((m, t) for m in (0, 1, 3, 4, 5, 6, 7, 8) for t in TILE_CHOICES) + ((2, 32),)   # (grid_method, grid_tile)
+GRID_CHOICES = tuple((m, t) for m in (0, 1, 3, 4, 5, 6, 7, 8) for t in TILE_CHOICES) + ((2, 32), (9, 64))   # (grid_method, grid_tile)
 
 
 def _bucket(x: int) -> int:

@@ -40,7 +40,7 @@ int make_geom(const wp_plan* plan, Geom* g) {
         plan->kernelgen != WP_KG_BF16X6 && plan->kernelgen != WP_KG_PROJSLICE)
         return WP_ERR_PLAN;
     if (plan->grid_tile != 0 && plan->grid_tile != 32 && plan->grid_tile != 64) return WP_ERR_PLAN;
-    if (plan->grid_method < 0 || plan->grid_method > 8) return WP_ERR_PLAN;
+    if (plan->grid_method < 0 || plan->grid_method > 9) return WP_ERR_PLAN;
     g->N = N;
     g->dl = plan->cell_size;
     g->du = 1.0 / ((double)N * plan->cell_size);
@@ -110,6 +110,18 @@ size_t carve_grid(const Geom& g, int P, int64_t V, void* ws, size_t bytes, GridW
     w.ctrl = c.take<int>(64);
     w.red = c.take<double>(8);
     w.seff = c.take<int>((size_t)P);
+    const bool slot = (g.grid_method == 9);
+    const size_t vs = slot ? (size_t)V : 0, ps = slot ? (size_t)P + 1 : 0;
+    const size_t hist = slot ? radix_sort_hist_ints(V) : 0;
+    w.skey = c.take<uint64_t>(vs);
+    w.skey_alt = c.take<uint64_t>(vs);
+    w.sidx = c.take<uint32_t>(vs);
+    w.sidx_alt = c.take<uint32_t>(vs);
+    w.rs_hist = c.take<int>(hist);
+    w.rs_tmp = c.take<int>(slot ? scan_tmp_ints((int64_t)hist) : 0);
+    w.vstart = c.take<int>(ps);
+    w.icount = c.take<int>(ps);
+    w.istart = c.take<int>(ps);
     if (out) *out = w;
     return (size_t)round_up((int64_t)c.off, 256);
 }
@@ -499,6 +511,9 @@ int wp_grid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw, c
     cudaStream_t st = (cudaStream_t)stream;
     GridWork w;
     carve_grid(g, kernels->P, V, workspace, workspace_bytes, &w);
+    if (g.grid_method == 9)      // slot gridder: its own binning (Morton-sorted planes)
+        return grid_slot(g, kernels, uvw, reinterpret_cast<const float2*>(vis), weight, V, w,
+                         reinterpret_cast<float2*>(grid), stats, st);
     if ((rc = grid_bin(g, kernels, uvw, reinterpret_cast<const float2*>(vis), weight, V, w, st))) return rc;
     return grid_run(g, kernels, w, reinterpret_cast<float2*>(grid), stats, st);
 }

@@ -1,0 +1,287 @@
+// Slot gridder (grid_method 9; Alg. 1 / Alg. 2 gridding step): register accumulation with the
+// work distribution of Romein (ICS 2012, "An efficient work-distribution strategy for gridding
+// radio-telescope data on GPUs"), fed by a sort of each plane's visibilities along a Morton
+// curve of their grid cells instead of by baseline.
+//
+// Every tap of a (2S+1)^2 footprint whose corner is (x0, y0) lands on a distinct residue class
+// (x mod W, y mod W), W = 2S+1.  A lane that owns the residue (a, b) -- a "slot" -- therefore
+// has exactly one tap of every visibility of the plane: the cell x = x0 + ((a - x0) mod W)
+// (same for y), tap offset (x - x0, y - y0).  It keeps that cell's sum in a register and writes
+// it to the grid (one float2 reduction) only when a later visibility moves its cell, which for
+// visibilities sorted along a Morton curve of their cells happens for a few percent of the
+// taps.  The fast path -- a visibility whose footprint corner equals the previous one's, 58 %
+// of the steps on the full-imaging workload -- is one address, one 8-byte tap load and four
+// FMAs per slot, every lane busy whatever the support.
+//
+// Binning for this method: the usual FP64 decisions (bin_decide), a key (plane, Morton code of
+// (iu, iv)) sorted by the library's radix sort, per-plane bounds of the sorted list, and one
+// gathered record per visibility: footprint corner, corner mod W, sub-kernel offset with the
+// conjugation flag, original index; the weighted value beside it.  Work item = (plane, chunk of
+// up to SLOT_CHUNK consecutive visibilities, 32 x SLOT_ROWS tile of the W x W slots), one warp
+// per item, pulled from a queue.
+#include <cuda_runtime.h>
+
+#include "wp_internal.cuh"
+
+namespace wp {
+
+namespace {
+constexpr int SLOT_ROWS = 16;        // slot rows per lane (registers: sum, cell, tap offset each)
+constexpr int SLOT_CHUNK = 512;      // visibilities per work item
+constexpr int SLOT_WARPS = 8;        // warps per block
+}  // namespace
+
+__device__ __forceinline__ uint32_t spread16(uint32_t v) {
+    v &= 0xffffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+// Binning decisions and sort keys: key = plane << mb | Morton(iu, iv); a dropped visibility gets
+// plane P (sorted after every kept one).  rec as k_bin's record; weight sum and drops reduced.
+__global__ void __launch_bounds__(256) k_bin_slot(int64_t V, const float* __restrict__ uvw, int P,
+                                                  const double* __restrict__ w_planes,
+                                                  const int32_t* __restrict__ support, int N, double du, int os,
+                                                  int mb, const float* __restrict__ weight,
+                                                  uint64_t* __restrict__ keys, uint32_t* __restrict__ idx,
+                                                  int4* __restrict__ rec, double* __restrict__ red) {
+    extern __shared__ double wps[];
+    __shared__ double red_w[8];
+    __shared__ double red_d[8];
+    for (int i = threadIdx.x; i < P; i += blockDim.x) wps[i] = w_planes[i];
+    __syncthreads();
+    double wsum = 0.0, drops = 0.0;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < V) {
+        int p, iu, iv, fu, fv, conj;
+        const bool ok = bin_decide(uvw, k, P, wps, support, N, du, os, &p, &iu, &iv, &fu, &fv, &conj);
+        if (ok) {
+            keys[k] = ((uint64_t)p << mb) | (uint64_t)(spread16((uint32_t)iu) | (spread16((uint32_t)iv) << 1));
+            rec[k] = make_int4(iu | (iv << 16), fu | (fv << 8) | (conj << 16), p, (int)k);
+            wsum = weight ? (double)weight[k] : 1.0;
+        } else {
+            keys[k] = (uint64_t)P << mb;
+            drops = 1.0;
+        }
+        idx[k] = (uint32_t)k;
+    }
+    for (int o = 16; o; o >>= 1) {
+        wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+        drops += __shfl_xor_sync(0xffffffffu, drops, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { red_w[wid] = wsum; red_d[wid] = drops; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a += red_w[q]; b += red_d[q]; }
+        if (a != 0.0) atomicAdd(&red[0], a);
+        if (b != 0.0) atomicAdd(&red[1], b);
+    }
+}
+
+// vstart[q] = first sorted position of plane q (q = 0..P; vstart[P] = number kept).  Each
+// position where the plane changes writes the starts of the planes it steps over.
+__global__ void __launch_bounds__(256) k_plane_bounds(int64_t V, int P, int mb, const uint64_t* __restrict__ keys,
+                                                      int* __restrict__ vstart) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (V == 0) {
+        for (int q = (int)i; q <= P; q += blockDim.x * gridDim.x) vstart[q] = 0;
+        return;
+    }
+    if (i >= V) return;
+    const int pi = (int)(keys[i] >> mb);
+    const int pprev = (i == 0) ? -1 : (int)(keys[i - 1] >> mb);
+    for (int q = pprev + 1; q <= pi; ++q) vstart[q] = (int)i;
+    if (i == V - 1)
+        for (int q = pi + 1; q <= P; ++q) vstart[q] = (int)V;
+}
+
+// Sorted records: x = x0 | y0 << 16 (footprint corner), y = (x0 mod W) | (y0 mod W) << 16,
+// z = sub-kernel offset (fv os + fu) W^2 | conj << 31, w = original index; weighted values.
+__global__ void __launch_bounds__(256) k_gather_slot(int64_t V, int os, int s_max, const int* __restrict__ vstart, int P,
+                                                     const uint32_t* __restrict__ idx, const int4* __restrict__ rec,
+                                                     const int32_t* __restrict__ support,
+                                                     const float2* __restrict__ vis, const float* __restrict__ weight,
+                                                     int4* __restrict__ srec, float2* __restrict__ svis) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= V || i >= vstart[P]) return;
+    const int k = (int)idx[i];
+    const int4 r = rec[k];
+    const int p = r.z;
+    const int S = min(max(support[p], 1), s_max);
+    const int W = 2 * S + 1;
+    const int x0 = (r.x & 0xffff) - S, y0 = ((r.x >> 16) & 0xffff) - S;
+    const int fu = r.y & 0xff, fv = (r.y >> 8) & 0xff, conj = (r.y >> 16) & 1;
+    srec[i] = make_int4(x0 | (y0 << 16), (x0 % W) | ((y0 % W) << 16),
+                        (int)((uint32_t)((fv * os + fu) * W * W) | ((uint32_t)conj << 31)), k);
+    if (svis) {
+        const float2 v = vis[k];
+        const float a = weight ? weight[k] : 1.0f;
+        svis[i] = make_float2(v.x * a, v.y * a);
+    }
+}
+
+// Items of plane q: ceil(n_q / SLOT_CHUNK) chunks x ceil(W/32) x ceil(W/SLOT_ROWS) slot tiles.
+__global__ void __launch_bounds__(256) k_plane_items(int P, int s_max, const int* __restrict__ vstart,
+                                                     const int32_t* __restrict__ support, int* __restrict__ icount) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q > P) return;
+    if (q == P) { icount[P] = 0; return; }
+    const int n = vstart[q + 1] - vstart[q];
+    const int W = 2 * min(max(support[q], 1), s_max) + 1;
+    icount[q] = (n > 0) ? ((n + SLOT_CHUNK - 1) / SLOT_CHUNK) * ((W + 31) / 32) * ((W + SLOT_ROWS - 1) / SLOT_ROWS) : 0;
+}
+
+__global__ void __launch_bounds__(SLOT_WARPS * 32, 2) k_grid_slot(int N, int P, int s_max,
+                                                                  const int32_t* __restrict__ support,
+                                                                  const int64_t* __restrict__ offsets,
+                                                                  const float2* __restrict__ cache,
+                                                                  const int* __restrict__ vstart,
+                                                                  const int* __restrict__ istart,
+                                                                  const int4* __restrict__ srec,
+                                                                  const float2* __restrict__ svis,
+                                                                  int* __restrict__ ctrl, float2* __restrict__ grid) {
+    const int lane = threadIdx.x & 31;
+    const int n_items = istart[P];
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(&ctrl[0], 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+        int lo = 0, hi = P;                       // largest plane with istart <= it
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (istart[mid] <= it) lo = mid; else hi = mid;
+        }
+        const int p = lo;
+        const int S = min(max(support[p], 1), s_max);
+        const int W = 2 * S + 1;
+        const int nxs = (W + 31) >> 5, nys = (W + SLOT_ROWS - 1) / SLOT_ROWS;
+        const int local = it - istart[p];
+        const int chunk = local / (nxs * nys);
+        const int tt = local - chunk * (nxs * nys);
+        const int tys = tt / nxs, txs = tt - tys * nxs;
+        const int v0 = vstart[p] + chunk * SLOT_CHUNK;
+        const int v1 = min(v0 + SLOT_CHUNK, vstart[p + 1]);
+        const float2* pc = cache + offsets[p];
+        const int a = txs * 32 + lane;            // the lane's slot column
+        const bool a_ok = a < W;
+        const int b0 = tys * SLOT_ROWS;           // slot rows b0 .. b0 + SLOT_ROWS - 1
+        float2 acc[SLOT_ROWS];
+        uint32_t held[SLOT_ROWS];
+        int toff[SLOT_ROWS];
+#pragma unroll
+        for (int j = 0; j < SLOT_ROWS; ++j) {
+            acc[j] = make_float2(0.0f, 0.0f);
+            held[j] = 0xffffffffu;
+            toff[j] = 0;
+        }
+        uint32_t prev = 0xffffffffu;              // no footprint corner packs to this
+        int4 rn = __ldg(srec + v0);
+        float2 vn = __ldg(svis + v0);
+        for (int q = v0; q < v1; ++q) {
+            const int4 r = rn;
+            const float2 v = vn;
+            if (q + 1 < v1) {                     // the next record while this one's taps load
+                rn = __ldg(srec + q + 1);
+                vn = __ldg(svis + q + 1);
+            }
+            if ((uint32_t)r.x != prev) {          // the footprint moved: new cells for the slots
+                prev = (uint32_t)r.x;
+                const int x0 = r.x & 0xffff, y0 = (r.x >> 16) & 0xffff;
+                const int xm = r.y & 0xffff, ym = (r.y >> 16) & 0xffff;
+                int jx = a - xm;
+                jx += (jx < 0) ? W : 0;
+                const uint32_t xc = (uint32_t)(x0 + jx);
+#pragma unroll
+                for (int j = 0; j < SLOT_ROWS; ++j) {
+                    int jy = b0 + j - ym;
+                    jy += (jy < 0) ? W : 0;
+                    const uint32_t cell = xc | ((uint32_t)(y0 + jy) << 16);
+                    if (cell != held[j]) {
+                        if (acc[j].x != 0.0f || acc[j].y != 0.0f)
+                            atomicAdd(grid + (int64_t)(held[j] >> 16) * N + (held[j] & 0xffffu), acc[j]);
+                        acc[j] = make_float2(0.0f, 0.0f);
+                        held[j] = cell;
+                    }
+                    toff[j] = jy * W + jx;
+                }
+            }
+            const float2* sub = pc + (r.z & 0x7fffffff);
+            const float sg = (r.z < 0) ? -1.0f : 1.0f;
+            const float cA = v.x, cB = -sg * v.y, cC = sg * v.x, cD = v.y;
+            float2 tp[SLOT_ROWS];
+#pragma unroll
+            for (int j = 0; j < SLOT_ROWS; ++j)
+                tp[j] = (a_ok && b0 + j < W) ? __ldg(sub + toff[j]) : make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int j = 0; j < SLOT_ROWS; ++j) {
+                acc[j].x = fmaf(cA, tp[j].x, fmaf(cB, tp[j].y, acc[j].x));
+                acc[j].y = fmaf(cC, tp[j].y, fmaf(cD, tp[j].x, acc[j].y));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < SLOT_ROWS; ++j)
+            if (acc[j].x != 0.0f || acc[j].y != 0.0f)
+                atomicAdd(grid + (int64_t)(held[j] >> 16) * N + (held[j] & 0xffffu), acc[j]);
+    }
+}
+
+static int bits_for(int64_t n) {       // bits to hold values 0 .. n - 1 (at least 1)
+    int b = 1;
+    while (((int64_t)1 << b) < n) ++b;
+    return b;
+}
+
+size_t slot_hist_ints(int64_t V) { return radix_sort_hist_ints(V); }
+
+int grid_slot(const Geom& g, const wp_wkernels* kern, const float* uvw, const float2* vis, const float* weight,
+              int64_t V, const GridWork& w, float2* grid, double* stats, cudaStream_t st) {
+    const int P = kern->P;
+    WP_CUDA(cudaMemsetAsync(w.ctrl, 0, sizeof(int) * 8, st));
+    WP_CUDA(cudaMemsetAsync(w.red, 0, sizeof(double) * 2, st));
+    k_fit_supports_launch(g, kern, w, st);
+    WP_LAUNCH_CHECK("k_fit_supports");
+    const int mb = 2 * bits_for(g.N);
+    const int bits = mb + bits_for((int64_t)P + 1);
+    if (V > 0) {
+        size_t smem = (size_t)P * sizeof(double);
+        if (smem > 48 * 1024)
+            WP_CUDA(cudaFuncSetAttribute(k_bin_slot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_bin_slot<<<(unsigned)((V + 255) / 256), 256, smem, st>>>(V, uvw, P, kern->w_planes, w.seff, g.N, g.du, g.os,
+                                                                  mb, weight, w.skey, w.sidx, w.rec, w.red);
+        WP_LAUNCH_CHECK("k_bin_slot");
+    }
+    bool in_alt = false;
+    int rc = radix_sort<uint64_t>(w.skey, w.sidx, w.skey_alt, w.sidx_alt, V, bits, w.rs_hist, w.rs_tmp, st, &in_alt);
+    if (rc) return rc;
+    const uint64_t* keys = in_alt ? w.skey_alt : w.skey;
+    const uint32_t* idx = in_alt ? w.sidx_alt : w.sidx;
+    k_plane_bounds<<<(unsigned)(V > 0 ? (V + 255) / 256 : 1), 256, 0, st>>>(V, P, mb, keys, w.vstart);
+    WP_LAUNCH_CHECK("k_plane_bounds");
+    if (V > 0) {
+        k_gather_slot<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(V, g.os, g.s_max, w.vstart, P, idx, w.rec, w.seff,
+                                                                   vis, weight, w.srec, w.svis);
+        WP_LAUNCH_CHECK("k_gather_slot");
+    }
+    k_plane_items<<<(unsigned)((P + 1 + 255) / 256), 256, 0, st>>>(P, g.s_max, w.vstart, w.seff, w.icount);
+    WP_LAUNCH_CHECK("k_plane_items");
+    rc = exclusive_scan_i32(w.icount, w.istart, (int64_t)P + 1, w.scan_tmp, st);
+    if (rc) return rc;
+    int dev = 0, sms = 0, per_sm = 0;
+    WP_CUDA(cudaGetDevice(&dev));
+    WP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_slot, SLOT_WARPS * 32, 0));
+    if (per_sm < 1) per_sm = 1;
+    k_grid_slot<<<sms * per_sm, SLOT_WARPS * 32, 0, st>>>(g.N, P, g.s_max, w.seff, kern->offsets,
+                                                          reinterpret_cast<const float2*>(kern->cache), w.vstart,
+                                                          w.istart, w.srec, w.svis, w.ctrl, grid);
+    WP_LAUNCH_CHECK("k_grid_slot");
+    return stats ? add_stats(stats, w.red, st) : WP_OK;
+}
+
+}  // namespace wp

@@ -217,6 +217,11 @@ __global__ void __launch_bounds__(256) k_item_write(int64_t n, const int* __rest
     if (it == n - 1) ctrl[1] = pos[it] + flags[it];
 }
 
+void k_fit_supports_launch(const Geom& g, const wp_wkernels* kern, const GridWork& w, cudaStream_t st) {
+    k_fit_supports<<<(kern->P + 255) / 256, 256, 0, st>>>(kern->P, g.os, g.s_max, kern->support,
+                                                         kern->cache ? kern->offsets : nullptr, w.seff);
+}
+
 int grid_bin(const Geom& g, const wp_wkernels* kern, const float* uvw, const float2* vis,
              const float* weight, int64_t V, const GridWork& w, cudaStream_t st) {
     const int P = kern->P;

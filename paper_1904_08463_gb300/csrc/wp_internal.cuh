@@ -113,6 +113,16 @@ struct GridWork {
     int*    ctrl;       // [8]  [0] item cursor, [1] item count, [2] status
     double* red;        // [2]  weight sum, drops (per call)
     int*    seff;       // [P]  effective supports of the call (clamped, fitted to the cache layout)
+    // slot gridder (grid_method 9) only; zero-sized otherwise
+    uint64_t* skey;     // [V]  (plane, Morton cell) keys, and their ping-pong copy
+    uint64_t* skey_alt;
+    uint32_t* sidx;     // [V]  visibility index carried by the sort, and its copy
+    uint32_t* sidx_alt;
+    int*    rs_hist;    // radix-sort digit histograms
+    int*    rs_tmp;     // their scan scratch
+    int*    vstart;     // [P + 1] first sorted visibility of each plane
+    int*    icount;     // [P + 1] work items per plane, then
+    int*    istart;     // [P + 1] their exclusive scan
 };
 size_t carve_grid(const Geom& g, int P, int64_t V, void* ws, size_t bytes, GridWork* out);
 
@@ -272,6 +282,11 @@ int grid_bin(const Geom& g, const wp_wkernels* k, const float* uvw, const float2
 int grid_run(const Geom& g, const wp_wkernels* k, const GridWork& w, float2* grid, double* stats,
              cudaStream_t st);
 int write_items(int64_t n, const GridWork& w, cudaStream_t st);   // compact live items (flags scanned into cursor)
+void k_fit_supports_launch(const Geom& g, const wp_wkernels* kern, const GridWork& w, cudaStream_t st);
+int add_stats(double* stats, const double* red, cudaStream_t st);
+size_t slot_hist_ints(int64_t V);
+int grid_slot(const Geom& g, const wp_wkernels* kern, const float* uvw, const float2* vis, const float* weight,
+              int64_t V, const GridWork& w, float2* grid, double* stats, cudaStream_t st);
 int grid_run_group(const Geom& g, const wp_wkernels* k, const GridWork& w, float2* grid, cudaStream_t st);
 int degrid_run(const Geom& g, const wp_wkernels* k, int64_t V, const GridWork& w, const float2* grid,
                float2* vis_out, cudaStream_t st);

@@ -67,7 +67,7 @@ def test_every_named_route_is_a_valid_plan():
                                          ("max_support", 0), ("max_support", 200), ("min_support", 16),
                                          ("radial_samples", 4), ("interp", 2), ("kernelgen", 5), ("kernelgen", -1),
                                          ("trunc_frac", 1.0), ("grid_tile", 48),
-                                         ("grid_method", 9), ("grid_method", -1)])
+                                         ("grid_method", 10), ("grid_method", -1)])
 def test_invalid_plans_rejected(field, value):
     L, lib = _lib()
     p = L.WpPlan(256, 1e-4, 8, 15, 3, 0.01, 512, 0, 0, 0, 0)

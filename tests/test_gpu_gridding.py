@@ -53,7 +53,7 @@ def test_small_imaging_grid_and_dirty_image():
     assert np.all(img[~o.disc_mask(g)] == 0)
 
 
-@pytest.mark.parametrize("grid_method", [0, 1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("grid_method", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9])
 @pytest.mark.parametrize("grid_tile", [32, 64])
 @pytest.mark.parametrize("V,seed", [(0, 1), (1, 2), (37, 3), (5000, 4)])
 def test_grid_edges_and_conjugation(V, seed, grid_tile, grid_method):
@@ -140,7 +140,7 @@ def test_plane_values_are_means_of_equal_count_chunks(V, P, seed):
     assert np.all(np.diff(got) >= 0)
 
 
-@pytest.mark.parametrize("grid_method", [0, 3, 5, 6, 7, 8])
+@pytest.mark.parametrize("grid_method", [0, 3, 5, 6, 7, 8, 9])
 def test_non_finite_coordinates_are_dropped(grid_method):
     """NaN / infinite u, v or w: the GPU binning drops and counts them as the oracle does, the
     grid of the rest is unchanged, degridding returns 0 for them, and the plane values are the
@@ -205,7 +205,7 @@ def test_on_the_fly_taps_need_no_cache_and_match_the_cache_gridder(interp):
     assert rel_l2(G4, Go) < 1e-5
 
 
-@pytest.mark.parametrize("grid_method,grid_tile", [(5, 32), (5, 64), (6, 32), (6, 64)])
+@pytest.mark.parametrize("grid_method,grid_tile", [(5, 32), (5, 64), (6, 32), (6, 64), (9, 64)])
 def test_plane_groups_with_a_ragged_last_group(grid_method, grid_tile):
     """19 planes -- two full groups of 8 and a ragged group of 3 -- with supports 2..38, so that
     footprints reach up to two tiles away: the plane-group gridders against the oracle, with
