@@ -26,7 +26,7 @@
 namespace wp {
 
 namespace {
-constexpr int SLOT_ROWS = 16;        // slot rows per lane (registers: sum, cell, tap offset each)
+constexpr int SLOT_ROWS = 8;         // slot rows per lane (registers: sum, cell, tap offset each)
 constexpr int SLOT_CHUNK = 512;      // visibilities per work item
 constexpr int SLOT_WARPS = 8;        // warps per block
 }  // namespace
@@ -136,6 +136,10 @@ __global__ void __launch_bounds__(256) k_plane_items(int P, int s_max, const int
     icount[q] = (n > 0) ? ((n + SLOT_CHUNK - 1) / SLOT_CHUNK) * ((W + 31) / 32) * ((W + SLOT_ROWS - 1) / SLOT_ROWS) : 0;
 }
 
+// Slots outside the W x W residues (lane columns a >= W of the last column tile, rows b >= W of
+// the last row tile) read tap 0 of the sub-kernel -- always in bounds -- and are never flushed,
+// so the tap loads need no guard.
+template <int ROWS>
 __global__ void __launch_bounds__(SLOT_WARPS * 32, 2) k_grid_slot(int N, int P, int s_max,
                                                                   const int32_t* __restrict__ support,
                                                                   const int64_t* __restrict__ offsets,
@@ -160,7 +164,7 @@ __global__ void __launch_bounds__(SLOT_WARPS * 32, 2) k_grid_slot(int N, int P, 
         const int p = lo;
         const int S = min(max(support[p], 1), s_max);
         const int W = 2 * S + 1;
-        const int nxs = (W + 31) >> 5, nys = (W + SLOT_ROWS - 1) / SLOT_ROWS;
+        const int nxs = (W + 31) >> 5, nys = (W + ROWS - 1) / ROWS;
         const int local = it - istart[p];
         const int chunk = local / (nxs * nys);
         const int tt = local - chunk * (nxs * nys);
@@ -170,12 +174,13 @@ __global__ void __launch_bounds__(SLOT_WARPS * 32, 2) k_grid_slot(int N, int P, 
         const float2* pc = cache + offsets[p];
         const int a = txs * 32 + lane;            // the lane's slot column
         const bool a_ok = a < W;
-        const int b0 = tys * SLOT_ROWS;           // slot rows b0 .. b0 + SLOT_ROWS - 1
-        float2 acc[SLOT_ROWS];
-        uint32_t held[SLOT_ROWS];
-        int toff[SLOT_ROWS];
+        const int b0 = tys * ROWS;                // slot rows b0 .. b0 + ROWS - 1
+        const int nrows = min(ROWS, W - b0);      // rows of this tile inside the W x W residues
+        float2 acc[ROWS];
+        uint32_t held[ROWS];
+        int toff[ROWS];
 #pragma unroll
-        for (int j = 0; j < SLOT_ROWS; ++j) {
+        for (int j = 0; j < ROWS; ++j) {
             acc[j] = make_float2(0.0f, 0.0f);
             held[j] = 0xffffffffu;
             toff[j] = 0;
@@ -197,36 +202,37 @@ __global__ void __launch_bounds__(SLOT_WARPS * 32, 2) k_grid_slot(int N, int P, 
                 int jx = a - xm;
                 jx += (jx < 0) ? W : 0;
                 const uint32_t xc = (uint32_t)(x0 + jx);
+                jx = a_ok ? jx : 0;
 #pragma unroll
-                for (int j = 0; j < SLOT_ROWS; ++j) {
+                for (int j = 0; j < ROWS; ++j) {
                     int jy = b0 + j - ym;
                     jy += (jy < 0) ? W : 0;
                     const uint32_t cell = xc | ((uint32_t)(y0 + jy) << 16);
+                    const bool ok = a_ok && j < nrows;
                     if (cell != held[j]) {
-                        if (acc[j].x != 0.0f || acc[j].y != 0.0f)
+                        if (ok && (acc[j].x != 0.0f || acc[j].y != 0.0f))
                             atomicAdd(grid + (int64_t)(held[j] >> 16) * N + (held[j] & 0xffffu), acc[j]);
                         acc[j] = make_float2(0.0f, 0.0f);
                         held[j] = cell;
                     }
-                    toff[j] = jy * W + jx;
+                    toff[j] = j < nrows ? jy * W + jx : 0;
                 }
             }
             const float2* sub = pc + (r.z & 0x7fffffff);
             const float sg = (r.z < 0) ? -1.0f : 1.0f;
             const float cA = v.x, cB = -sg * v.y, cC = sg * v.x, cD = v.y;
-            float2 tp[SLOT_ROWS];
+            float2 tp[ROWS];
 #pragma unroll
-            for (int j = 0; j < SLOT_ROWS; ++j)
-                tp[j] = (a_ok && b0 + j < W) ? __ldg(sub + toff[j]) : make_float2(0.0f, 0.0f);
+            for (int j = 0; j < ROWS; ++j) tp[j] = __ldg(sub + toff[j]);
 #pragma unroll
-            for (int j = 0; j < SLOT_ROWS; ++j) {
+            for (int j = 0; j < ROWS; ++j) {
                 acc[j].x = fmaf(cA, tp[j].x, fmaf(cB, tp[j].y, acc[j].x));
                 acc[j].y = fmaf(cC, tp[j].y, fmaf(cD, tp[j].x, acc[j].y));
             }
         }
 #pragma unroll
-        for (int j = 0; j < SLOT_ROWS; ++j)
-            if (acc[j].x != 0.0f || acc[j].y != 0.0f)
+        for (int j = 0; j < ROWS; ++j)
+            if (a_ok && j < nrows && (acc[j].x != 0.0f || acc[j].y != 0.0f))
                 atomicAdd(grid + (int64_t)(held[j] >> 16) * N + (held[j] & 0xffffu), acc[j]);
     }
 }
@@ -275,9 +281,9 @@ int grid_slot(const Geom& g, const wp_wkernels* kern, const float* uvw, const fl
     int dev = 0, sms = 0, per_sm = 0;
     WP_CUDA(cudaGetDevice(&dev));
     WP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_slot, SLOT_WARPS * 32, 0));
+    WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_slot<SLOT_ROWS>, SLOT_WARPS * 32, 0));
     if (per_sm < 1) per_sm = 1;
-    k_grid_slot<<<sms * per_sm, SLOT_WARPS * 32, 0, st>>>(g.N, P, g.s_max, w.seff, kern->offsets,
+    k_grid_slot<SLOT_ROWS><<<sms * per_sm, SLOT_WARPS * 32, 0, st>>>(g.N, P, g.s_max, w.seff, kern->offsets,
                                                           reinterpret_cast<const float2*>(kern->cache), w.vstart,
                                                           w.istart, w.srec, w.svis, w.ctrl, grid);
     WP_LAUNCH_CHECK("k_grid_slot");
