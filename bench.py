@@ -59,6 +59,57 @@ def _peaks():
         return 6800.0, 1900.0, "fallback"
 
 
+def measure_compute_peaks(dev) -> dict:
+    """FP32 FMA and TF32 tensor rates measured on this GPU in this run (the HBM and BF16 peaks
+    come from MEASURED_PEAKS.json): FP32 = register-resident FMA chains (wp_probe_fp32_fma,
+    8 blocks of 256 threads per SM), TF32 = torch.matmul of 8192^2 float32 matrices with TF32
+    allowed (cuBLAS, 2 n^3 flops); each the best of 5 CUDA-event timings after a warm-up."""
+    import ctypes
+
+    import torch
+
+    from paper_1904_08463_gb300 import _lib
+
+    lib = _lib.load()
+    sink = torch.zeros(1, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+    flops = ctypes.c_double()
+
+    def fma():
+        _lib.check("wp_probe_fp32_fma", lib.wp_probe_fp32_fma(4096, 8, ctypes.c_void_p(sink.data_ptr()),
+                                                               ctypes.byref(flops), ctypes.c_void_p(st.cuda_stream)))
+
+    def best(fn, n=5):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(n):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts)
+
+    fp32 = flops.value / (best(fma) * 1e-3) / 1e12
+    n = 8192
+    x = torch.randn(n, n, device=dev, dtype=torch.float32)
+    y = torch.randn(n, n, device=dev, dtype=torch.float32)
+    old = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        tf32 = 2.0 * n ** 3 / (best(lambda: torch.matmul(x, y)) * 1e-3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+    del x, y
+    hbm, bf16, src = _peaks()
+    return {"fp32_fma_tflops": fp32, "tf32_tflops": tf32, "bf16_tflops": bf16, "hbm_gbs": hbm,
+            "how": "FP32: FMA chains in registers, all SMs (wp_probe_fp32_fma); TF32: cuBLAS 8192^3 "
+                   "torch.matmul with TF32 allowed; best of 5 CUDA-event timings; HBM and BF16: "
+                   f"{src} MEASURED_PEAKS.json"}
+
+
 def max_over_ranks(ms: float, device, world: int) -> float:
     """Replicas only (every rank runs the whole workload on its own GPU): the job's time is the
     slowest rank's, so value = ranks x work / max time."""
@@ -331,6 +382,10 @@ def run_gpu(args):
     if args.routes and not args.hankel_only:
         out["routes"] = time_routes(args, kb, plan, taper_d, wpl_d, sup_host, ws, radial, spline_m, cache,
                                     sup_d, off_d, ms_step)
+    if rank == 0:
+        out["measured_peaks"] = args.peaks = measure_compute_peaks(dev)
+        if args.routes and not args.hankel_only and "routes" in out:
+            add_tensor_fractions(out["routes"], plan, P, args.peaks)
     if args.imaging and rank == 0:
         out["imaging"] = run_imaging(args, dev)
     if args.batch and rank == 0:
@@ -389,6 +444,12 @@ def time_routes(args, kb, plan, taper_d, wpl_d, sup_host, ws, radial, spline_m, 
 
         ms = timeit(route, max(3, min(args.steps, 10)))
         res[kg + "_hankel"] = {"ms_per_step": ms, "w_kernels_per_s": P / (ms * 1e-3)}
+    # the radial stage alone (screen, transform, truncation + spline) of every matrix route
+    for kg in ("fp32", "tf32x3", "bf16x3", "bf16x6"):
+        pk = plan.replace(kernelgen=kg)
+        ms = timeit(lambda pk=pk: wp.hankel_radial(pk, taper_d, wpl_d, ws, radial, spline_m),
+                    max(5, min(args.steps, 20)))
+        res.setdefault(kg + "_hankel", {})["radial_stage_ms"] = ms
     # the projection-slice realisation of the Hankel transform (the variant the paper timed):
     # workspace image summed over one axis, zero-padded by os, batched 1D cuFFT
     p3 = plan.replace(kernelgen="projslice")
@@ -421,6 +482,24 @@ def time_routes(args, kb, plan, taper_d, wpl_d, sup_host, ws, radial, spline_m, 
     res["speedup_hankel_vs_fft2d"] = ms / headline_ms
     del fws
     return res
+
+
+def add_tensor_fractions(routes, plan, P, peaks):
+    """Fraction of the tensor peak of each tcgen05 route's transform: split products x
+    2 K_out R_pad 2 P_pad flop over the radial stage's time (screen and spline included, so the
+    fraction is a lower bound), against the measured TF32 (this run) or BF16 (MEASURED_PEAKS)
+    rate."""
+    g = plan.geometry()
+    p_pad = (P + 63) // 64 * 64
+    flop_one = 2.0 * g.k_out * g.r_pad * 2 * p_pad
+    for kg, prods, peak_key in (("tf32x3", 3, "tf32_tflops"), ("bf16x3", 3, "bf16_tflops"),
+                                ("bf16x6", 6, "bf16_tflops")):
+        r = routes.get(kg + "_hankel")
+        if not r or "radial_stage_ms" not in r or not peaks.get(peak_key):
+            continue
+        tf = prods * flop_one / (r["radial_stage_ms"] * 1e-3) / 1e12
+        r["transform"] = {"products": prods, "gflop": prods * flop_one / 1e9, "tflops_over_radial_stage": tf,
+                          "peak": peaks[peak_key], "peak_kind": peak_key, "frac_lower_bound": tf / peaks[peak_key]}
 
 
 def measure_e2e(args, world, P, kb, sup_host, off_host, cache, taper_d, wpl_d, sup_d, off_d, step, stream):
@@ -640,7 +719,10 @@ def run_imaging(args, dev):
     lower = np.where(np.abs(aw - planes[idx - 1]) <= np.abs(planes[idx] - aw), idx - 1, idx)
     taps = float(np.sum((2 * sup_h[lower].astype(np.float64) + 1) ** 2))
     flops = 8.0 * taps
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12     # TFLOP/s: SMs x FP32 lanes x 2 x max clock
+    pk = getattr(args, "peaks", None) or {}
+    fp32_peak = pk.get("fp32_fma_tflops") or 152 * 128 * 2 * 2.07e9 / 1e12
+    fp32_src = ("measured in this run (register FMA chains on every SM)" if pk.get("fp32_fma_tflops")
+                else "nominal: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz")
     st = stats.cpu().numpy()
     return {
         "workload": f"full imaging: {V} visibilities (64-antenna 8 h track, dec -30, 1.4 GHz, uvw x "
@@ -662,7 +744,7 @@ def run_imaging(args, dev):
         "roofline": {"kernel": "k_grid", "bound": "alu", "achieved": flops / (grid_ms * 1e-3) / 1e12,
                      "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": flops / (grid_ms * 1e-3) / 1e12 / fp32_peak,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                     "peak_source": fp32_src,
                      "hbm_frac": (V * 24 + 2 * N * N * 8) / (grid_ms * 1e-3) / 1e9 / _peaks()[0]},
     }
 
@@ -788,10 +870,23 @@ def run_grad(args, dev):
     b.record()
     torch.cuda.synchronize()
     degrid_ms = a.elapsed_time(b) / n
+    # degridding roofline: 8 flop per footprint tap of every visibility (FP32 ALU), as gridding
+    sup_h = sup.cpu().numpy()
+    pl = planes.cpu().numpy()
+    aw = np.abs(d["uvw"][:, 2].astype(np.float64))
+    idx = np.clip(np.searchsorted(pl, aw), 1, P - 1)
+    lower = np.where(np.abs(aw - pl[idx - 1]) <= np.abs(pl[idx] - aw), idx - 1, idx)
+    taps = float(np.sum((2 * sup_h[lower].astype(np.float64) + 1) ** 2))
+    pk = getattr(args, "peaks", None) or {}
+    fp32_peak = pk.get("fp32_fma_tflops") or 152 * 128 * 2 * 2.07e9 / 1e12
+    achieved = 8.0 * taps / (degrid_ms * 1e-3) / 1e12
     return {"workload": f"{V} visibilities, 4096^2 float32 model image, 512 planes, 512-sample taper, chi^2",
             "ms_per_forward_backward": ms, "mvis_per_s": V / (ms * 1e-3) / 1e6,
             "grad_image_norm": float(image.grad.norm()), "grad_taper_norm": float(taper.grad.norm()),
-            "degrid_ms": degrid_ms}
+            "degrid_ms": degrid_ms, "degrid_taps_per_vis": taps / V,
+            "degrid_roofline": {"kernel": "k_degrid", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                                "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                                "peak_source": "measured in this run" if pk.get("fp32_fma_tflops") else "nominal"}}
 
 
 def run_reference(args):
@@ -944,8 +1039,10 @@ def main():
     ap.add_argument("--imaging-planes", type=int, default=512)
     ap.add_argument("--grid-shape", default="",
                     help="gridder 'method,tile' for the imaging workload instead of the autotuner's pick")
-    ap.add_argument("--batch", action="store_true", help="also time the batched uneven-problem workload")
-    ap.add_argument("--grad", action="store_true", help="also time forward + backward of the prediction")
+    ap.add_argument("--no-batch", dest="batch", action="store_false",
+                    help="skip the batched uneven-problem workload")
+    ap.add_argument("--no-grad", dest="grad", action="store_false",
+                    help="skip forward + backward of the prediction (differentiation workload)")
     ap.add_argument("--batch-problems", type=int, default=48)
     ap.add_argument("--hankel-only", action="store_true",
                     help="profiling aid: time only screen + Hankel product + spline (no cache)")

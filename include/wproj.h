@@ -468,6 +468,19 @@ int wp_dirty_image_stats(const wp_plan* plan, const float* taper, float* grid,
 int wp_image_to_grid(const wp_plan* plan, const float* taper, const float* image,
                      double weight_sum, float* grid, void* stream);
 
+/* ---- measurement --------------------------------------------------------------------- */
+
+/*
+ * Measurement helper with no counterpart in the paper: queues one launch of blocks_per_sm
+ * blocks per SM of 256 threads, each thread running eight independent register-resident FP32
+ * FMA chains for 16 * iters steps, and writes to *flops_out (host) the FLOP count of that launch
+ * (2 per FMA).  Timing it with CUDA events on `stream` gives the device's FP32 FMA rate -- the
+ * denominator of the gridder's ALU roofline.  sink: one device float, written only in a case
+ * the chains never reach.  WP_ERR_SIZE for iters < 1 or blocks_per_sm outside 1..64.
+ */
+int wp_probe_fp32_fma(int32_t iters, int32_t blocks_per_sm, float* sink, double* flops_out,
+                      void* stream);
+
 /* ---- misc ---------------------------------------------------------------------------- */
 const char* wp_strerror(int code);
 const char* wp_last_error_string(void);   /* last CUDA/cuFFT error text (thread-local) */

@@ -120,6 +120,7 @@ _SIGS = {
                                    c_void_p]),
     "wp_dirty_image": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
     "wp_dirty_image_stats": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "wp_probe_fp32_fma": (c_int32, [c_int32, c_int32, c_void_p, P_(c_double), c_void_p]),
     "wp_image_to_grid": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
 }
 
