@@ -796,6 +796,19 @@ def run_batch(args, dev):
         by_streams[ns] = timeit(b.replay)
     best_ns = min(by_streams, key=by_streams.get)
     ms_graph = by_streams[best_ns]
+    # the same problems with their gridding in ONE persistent launch (device work queue over
+    # every problem's scatter and (plane, tile) items, bounded waits), kernel generation and
+    # images as before; captured in a graph
+    b.persistent = True
+    by_streams_p = {}
+    for ns in (1, 2, 4):
+        b.n_streams = ns
+        b.graph = None
+        b.capture()
+        by_streams_p[ns] = timeit(b.replay)
+    status = b.status()
+    best_np = min(by_streams_p, key=by_streams_p.get)
+    ms_pers = by_streams_p[best_np]
     choices = {}
     for k, v in tuner.table.items():
         choices[str(v["best"])] = choices.get(str(v["best"]), 0) + 1
@@ -806,7 +819,11 @@ def run_batch(args, dev):
             "visibilities": V, "ms_graph": ms_graph, "ms_sequential": ms_seq,
             "mvis_per_s_graph": V / (ms_graph * 1e-3) / 1e6, "mvis_per_s_sequential": V / (ms_seq * 1e-3) / 1e6,
             "speedup_graph_vs_sequential": ms_seq / ms_graph, "graph_streams": best_ns,
-            "ms_graph_by_streams": by_streams, "tuned_choices": choices, "dropped": b.dropped()}
+            "ms_graph_by_streams": by_streams,
+            "ms_persistent": ms_pers, "mvis_per_s_persistent": V / (ms_pers * 1e-3) / 1e6,
+            "speedup_persistent_vs_sequential": ms_seq / ms_pers, "persistent_kernelgen_streams": best_np,
+            "ms_persistent_by_streams": by_streams_p, "persistent_status": status,
+            "tuned_choices": choices, "dropped": b.dropped()}
 
 
 def run_grad(args, dev):

@@ -386,6 +386,60 @@ int wp_grid_static(const wp_plan* plan, const wp_wkernels* kernels, const float*
                    const float* vis, const float* weight, int64_t V, float* grid,
                    double* stats, void* stream);
 
+/* ---- many independent problems in one persistent launch ----------------------------- */
+
+/*
+ * One gridding job of a batch: the arguments of one wp_grid call, by value.  The batch grids
+ * every job with the row-owned shared-tile method (grid_method 3) whatever plan.grid_method
+ * says; plan.grid_tile (0 = 64, or 32) must be the same for every job of a batch.
+ *   workspace  wp_grid_workspace_bytes(plan with grid_method 3, P, V) bytes, 256-byte aligned
+ *              (the job's own; jobs never share one)
+ */
+#define WP_GRID_BATCH_MAX_JOBS 128
+typedef struct wp_grid_job {
+    wp_plan        plan;
+    wp_wkernels    kernels;
+    const float*   uvw;
+    const float*   vis;
+    const float*   weight;
+    int64_t        V;
+    void*          workspace;
+    size_t         workspace_bytes;
+    float*         grid;
+    double*        stats;
+} wp_grid_job;
+
+/* Bytes of the batch's own control workspace (queue, per-job counters, status). */
+size_t wp_grid_batch_workspace_bytes(void);
+
+/*
+ * Grids n_jobs independent problems (1 <= n_jobs <= WP_GRID_BATCH_MAX_JOBS; jobs: host array)
+ * with the same result per job as wp_grid.  Each job is binned as in wp_grid up to its list of
+ * live (plane, tile) work items; then one persistent launch pulls work from a single device
+ * queue -- every job's scatter of its records into bin order first, then every job's gridding
+ * items, in the order of `jobs` (put large jobs first) -- so small problems fill the GPU
+ * beside large ones with no per-job tail.  A gridding item waits for its job's scatter; the
+ * wait is bounded (about a second of SM clock) and on expiry the item is skipped and the
+ * batch status records WP_ERR_TIMEOUT (read it with wp_grid_batch_status).  Argument errors of
+ * any job are reported before anything is launched.  Calls overlapping on the GPU must use
+ * different batch workspaces and job workspaces.
+ */
+int wp_grid_batch(int32_t n_jobs, const wp_grid_job* jobs, void* batch_workspace,
+                  size_t batch_workspace_bytes, void* stream);
+
+/* Device status of the last wp_grid_batch on batch_workspace (synchronizes `stream`):
+   0, or WP_ERR_TIMEOUT when a gridding item's wait expired. */
+int wp_grid_batch_status(const void* batch_workspace, int32_t* status_host, void* stream);
+
+/*
+ * Self-test of the batch's failure path: the same launch with the scatter withheld and a
+ * ~10 ms wait budget, so that every gridding item's wait expires; writes the resulting status
+ * to *status_host (expected WP_ERR_TIMEOUT) and synchronizes.  No grid cell is written, nothing
+ * faults or hangs, and the context stays usable.
+ */
+int wp_grid_batch_selftest(int32_t n_jobs, const wp_grid_job* jobs, void* batch_workspace,
+                           size_t batch_workspace_bytes, int32_t* status_host, void* stream);
+
 /* ---- differentiation of the visibility prediction ----------------------------------
  * Model: V = wp_degrid(K(t), wp_image_to_grid(I; t)) for a model image I and the radial
  * taper t, where the kernels K(t) come from wp_hankel_radial + wp_resample (supports and

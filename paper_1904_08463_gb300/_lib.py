@@ -67,6 +67,24 @@ class WpWkernels(ctypes.Structure):
     ]
 
 
+class WpGridJob(ctypes.Structure):
+    _fields_ = [
+        ("plan", WpPlan),
+        ("kernels", WpWkernels),
+        ("uvw", c_void_p),
+        ("vis", c_void_p),
+        ("weight", c_void_p),
+        ("V", c_int64),
+        ("workspace", c_void_p),
+        ("workspace_bytes", c_size_t),
+        ("grid", c_void_p),
+        ("stats", c_void_p),
+    ]
+
+
+GRID_BATCH_MAX_JOBS = 128
+
+
 class WPError(RuntimeError):
     def __init__(self, fn: str, code: int, detail: str = ""):
         self.code = code
@@ -120,6 +138,10 @@ _SIGS = {
                                    c_void_p]),
     "wp_dirty_image": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
     "wp_dirty_image_stats": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "wp_grid_batch_workspace_bytes": (c_size_t, []),
+    "wp_grid_batch": (c_int32, [c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "wp_grid_batch_status": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "wp_grid_batch_selftest": (c_int32, [c_int32, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),
     "wp_probe_fp32_fma": (c_int32, [c_int32, c_int32, c_void_p, P_(c_double), c_void_p]),
     "wp_image_to_grid": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
 }

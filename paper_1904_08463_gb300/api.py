@@ -356,3 +356,64 @@ def image_to_grid(plan: Plan, taper: torch.Tensor, image: torch.Tensor, weight_s
     _lib.check("wp_image_to_grid", _lib.load().wp_image_to_grid(
         ctypes.byref(plan.c()), _ptr(taper), _ptr(image), float(weight_sum), _ptr(out), _stream(stream)))
     return out
+
+
+# ------------------------------------------------------------------ persistent batches
+@dataclasses.dataclass
+class GridJob:
+    """One job of ``grid_batch``: the arguments of one ``grid`` call (workspace and stats
+    tensors included; the workspace must be sized for grid_method 3)."""
+
+    plan: Plan
+    wk: "WKernels | OwnedWKernels"
+    uvw: torch.Tensor
+    vis: torch.Tensor
+    weight: torch.Tensor | None
+    grid: torch.Tensor
+    ws: torch.Tensor
+    stats: torch.Tensor | None = None
+
+
+def grid_batch_workspace(device=None) -> torch.Tensor:
+    return workspace(int(_lib.load().wp_grid_batch_workspace_bytes()), device)
+
+
+def _job_array(jobs: list[GridJob]):
+    arr = (_lib.WpGridJob * len(jobs))()
+    for i, j in enumerate(jobs):
+        V = int(j.vis.numel())
+        _need(j.uvw, torch.float32, "uvw", 3 * V)
+        _need(j.vis, torch.complex64, "vis")
+        if j.weight is not None:
+            _need(j.weight, torch.float32, "weight", V)
+        _need(j.grid, torch.complex64, "grid", j.plan.image_size ** 2)
+        _need(j.ws, torch.uint8, "workspace")
+        arr[i] = _lib.WpGridJob(j.plan.c(), j.wk.c(), j.uvw.data_ptr(), j.vis.data_ptr(),
+                                j.weight.data_ptr() if j.weight is not None else None, V, j.ws.data_ptr(),
+                                j.ws.numel(), j.grid.data_ptr(),
+                                j.stats.data_ptr() if j.stats is not None else None)
+    return arr
+
+
+def grid_batch(jobs: list[GridJob], bws: torch.Tensor, stream=None) -> None:
+    """Grid every job in one persistent launch (see ``wp_grid_batch``); each job's grid and
+    stats as ``grid`` would leave them.  Order the jobs largest first."""
+    arr = _job_array(jobs)
+    _lib.check("wp_grid_batch", _lib.load().wp_grid_batch(len(jobs), arr, _ptr(bws), bws.numel(), _stream(stream)))
+
+
+def grid_batch_status(bws: torch.Tensor, stream=None) -> int:
+    st = ctypes.c_int32()
+    _lib.check("wp_grid_batch_status", _lib.load().wp_grid_batch_status(_ptr(bws), ctypes.byref(st),
+                                                                        _stream(stream)))
+    return int(st.value)
+
+
+def grid_batch_selftest(jobs: list[GridJob], bws: torch.Tensor, stream=None) -> int:
+    """Runs the batch with its scatter withheld so that every gridding wait expires; returns
+    the device status (WP_ERR_TIMEOUT = -6 expected)."""
+    arr = _job_array(jobs)
+    st = ctypes.c_int32()
+    _lib.check("wp_grid_batch_selftest", _lib.load().wp_grid_batch_selftest(
+        len(jobs), arr, _ptr(bws), bws.numel(), ctypes.byref(st), _stream(stream)))
+    return int(st.value)

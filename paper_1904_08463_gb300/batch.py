@@ -8,6 +8,8 @@ step of every problem is captured into one CUDA graph: the problems are spread o
 side streams (largest first, round robin) forked from and joined back into the capture
 stream, so small problems overlap with large ones and the host issues one launch for the
 whole batch.  `run_sequential` runs the same steps one problem at a time for comparison.
+With persistent=True the gridding of all problems is instead one persistent launch that pulls
+(problem, plane, tile) work from a single device queue (``api.grid_batch``).
 """
 from __future__ import annotations
 
@@ -17,7 +19,7 @@ import torch
 
 from . import api
 from .api import Plan, WKernels
-from .autotune import GRID_CHOICES, KERNELGEN_CHOICES, TILE_CHOICES, Autotuner
+from .autotune import GRID_CHOICES, KERNELGEN_CHOICES, Autotuner
 
 
 @dataclasses.dataclass
@@ -49,8 +51,9 @@ class _State:
         self.radial = torch.empty((pb.P, plan.geometry().k_out), dtype=torch.complex64, device=dev)
         self.spline_m = torch.empty_like(self.radial)
         self.cache = torch.empty(off_host[-1], dtype=torch.complex64, device=dev)
-        self.grid_ws = api.workspace(max(api.grid_workspace_bytes(self.plan.replace(grid_tile=t), pb.P, self.V)
-                                         for t in TILE_CHOICES), dev)
+        self.grid_ws = api.workspace(max(api.grid_workspace_bytes(self.plan.replace(grid_method=m, grid_tile=t),
+                                                                  pb.P, self.V)
+                                         for m, t in list(GRID_CHOICES) + [(3, 64)]), dev)
         N = plan.image_size
         self.grid = torch.zeros((N, N), dtype=torch.complex64, device=dev)
         self.image = torch.empty((N, N), dtype=torch.float32, device=dev)
@@ -97,11 +100,28 @@ class _State:
 
 
 class BatchImager:
-    def __init__(self, problems: list[Problem], n_streams: int = 4, tuner: Autotuner | None = None):
+    """persistent=False: each problem's whole step (its own tuned gridder) on one of a few forked
+    streams.  persistent=True: kernel generation of every problem on the forked streams, then
+    the gridding of ALL problems in one persistent launch pulling work from one device queue
+    (``api.grid_batch``: row-owned tiles of 64 cells, largest problems first), then the images."""
+
+    def __init__(self, problems: list[Problem], n_streams: int = 4, tuner: Autotuner | None = None,
+                 persistent: bool = False):
         self.states = [_State(pb, tuner) for pb in problems]
         self.n_streams = max(1, n_streams)
+        self.persistent = persistent
         self.graph: torch.cuda.CUDAGraph | None = None
+        dev = problems[0].vis.device
+        self.bws = api.grid_batch_workspace(dev)
+        order = sorted(range(len(self.states)), key=lambda i: -self.states[i].cost())
+        self.jobs = [api.GridJob(self.states[i].plan.replace(grid_method=3, grid_tile=64), self.states[i].wk,
+                                 self.states[i].pb.uvw, self.states[i].pb.vis, self.states[i].pb.weight,
+                                 self.states[i].grid, self.states[i].grid_ws, self.states[i].stats)
+                     for i in order]
         self.run_sequential()          # plans, tuning and code loading outside any capture
+        if persistent:
+            self._persistent_step(torch.cuda.current_stream(), [torch.cuda.current_stream()],
+                                  [list(range(len(self.states)))])
         torch.cuda.synchronize()
 
     @property
@@ -133,6 +153,32 @@ class BatchImager:
         for ev in joins:
             cap.wait_event(ev)
 
+    def _persistent_step(self, cap: torch.cuda.Stream, streams, lanes) -> None:
+        fork = torch.cuda.Event()
+        fork.record(cap)
+        joins = []
+        for st, lane in zip(streams, lanes):
+            st.wait_event(fork)
+            with torch.cuda.stream(st):
+                for i in lane:
+                    self.states[i].kernels(self.states[i].plan)
+                ev = torch.cuda.Event()
+                ev.record(st)
+            joins.append(ev)
+        for ev in joins:
+            cap.wait_event(ev)
+        with torch.cuda.stream(cap):
+            for s in self.states:
+                s.grid.zero_()
+                s.stats.zero_()
+            api.grid_batch(self.jobs, self.bws)
+            for s in self.states:
+                api.dirty_image(s.plan, s.pb.taper, s.grid, s.stats, s.image)
+
+    def status(self) -> int:
+        """Device status of the last persistent gridding launch (0 or WP_ERR_TIMEOUT)."""
+        return api.grid_batch_status(self.bws)
+
     def capture(self) -> None:
         order = sorted(range(len(self.states)), key=lambda i: -self.states[i].cost())
         lanes = [[] for _ in range(self.n_streams)]
@@ -143,12 +189,13 @@ class BatchImager:
         # one uncaptured pass on the same streams first: the library keeps one cuFFT plan per
         # stream (concurrent branches never share a work area), and a plan cannot be created
         # inside a capture
+        step = self._persistent_step if self.persistent else self._fork_join
         torch.cuda.synchronize()
-        self._fork_join(cap, streams, lanes)
+        step(cap, streams, lanes)
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=cap):
-            self._fork_join(cap, streams, lanes)
+            step(cap, streams, lanes)
         self.graph = g
 
     def replay(self) -> None:

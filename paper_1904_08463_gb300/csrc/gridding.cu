@@ -25,11 +25,11 @@
 #include <math.h>
 
 #include "wp_internal.cuh"
+#include "grid_ro.cuh"
 
 namespace wp {
 
 namespace {
-constexpr int GRID_WARPS = 8;      // warps per gridding block
 constexpr int SCAN_PER_BLOCK = 2048;
 }  // namespace
 
@@ -224,6 +224,20 @@ void k_fit_supports_launch(const Geom& g, const wp_wkernels* kern, const GridWor
 
 int grid_bin(const Geom& g, const wp_wkernels* kern, const float* uvw, const float2* vis,
              const float* weight, int64_t V, const GridWork& w, cudaStream_t st) {
+    int rc = grid_bin_noscatter(g, kern, uvw, weight, V, w, st);
+    if (rc) return rc;
+    if (V > 0) {
+        unsigned blocks = (unsigned)((V + 255) / 256);
+        k_scatter<<<blocks, 256, 0, st>>>(V, w.key, w.rec, vis, weight, w.count, w.cursor, w.srec,
+                                          vis ? w.svis : nullptr);
+        WP_LAUNCH_CHECK("k_scatter");
+    }
+    return WP_OK;
+}
+
+// Binning up to the scanned bin counts: records, keys, counts (no scatter into bin order).
+int grid_bin_noscatter(const Geom& g, const wp_wkernels* kern, const float* uvw, const float* weight, int64_t V,
+                       const GridWork& w, cudaStream_t st) {
     const int P = kern->P;
     WP_CUDA(cudaMemsetAsync(w.count, 0, sizeof(int) * (size_t)(w.nbins + 1), st));
     WP_CUDA(cudaMemsetAsync(w.cursor, 0, sizeof(int) * (size_t)w.nbins, st));
@@ -241,14 +255,15 @@ int grid_bin(const Geom& g, const wp_wkernels* kern, const float* uvw, const flo
                                          g.os, w.T, w.ntx, w.ntiles, weight, w.key, w.rec, w.count, w.red);
         WP_LAUNCH_CHECK("k_bin");
     }
-    int rc = exclusive_scan_i32(w.count, w.count, w.nbins + 1, w.scan_tmp, st);
-    if (rc) return rc;
-    if (V > 0) {
-        unsigned blocks = (unsigned)((V + 255) / 256);
-        k_scatter<<<blocks, 256, 0, st>>>(V, w.key, w.rec, vis, weight, w.count, w.cursor, w.srec,
-                                          vis ? w.svis : nullptr);
-        WP_LAUNCH_CHECK("k_scatter");
-    }
+    return exclusive_scan_i32(w.count, w.count, w.nbins + 1, w.scan_tmp, st);
+}
+
+// Flags of the per-plane work items (plane, tile) into w.flags[0 .. P * ntiles] (last = 0).
+int item_flags(const Geom& g, const wp_wkernels* kern, const GridWork& w, cudaStream_t st) {
+    const int64_t n = (int64_t)kern->P * w.ntiles;
+    k_item_flags<<<(unsigned)((n + 1 + 255) / 256), 256, 0, st>>>(kern->P, w.T, w.ntx, w.ntiles, g.s_max, w.seff,
+                                                                 w.count, w.flags);
+    WP_LAUNCH_CHECK("k_item_flags");
     return WP_OK;
 }
 
@@ -459,7 +474,6 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_fm(int N, int os, int 
 // never touch the same cell and neither do two lanes, so the accumulation is a plain
 // shared-memory read-modify-write: no atomics, no private copies, and a visibility is decoded
 // once per block rather than once per warp.
-constexpr int RO_LIST = GRID_WARPS * 32;   // candidates decoded per round (one per thread)
 
 template <int TILE>
 __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_ro(int N, int os, int s_max, int ntx, int ntiles,
@@ -471,13 +485,11 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_ro(int N, int os, int 
                                                              const float2* __restrict__ svis,
                                                              const int* __restrict__ items,
                                                              int* __restrict__ ctrl, float2* __restrict__ grid) {
-    constexpr int CH = TILE / 32;                 // column chunks of a tile row
     __shared__ float2 tile[TILE * TILE];
     __shared__ int l_off[RO_LIST];                // first tap of the intersection in the plane's cache
     __shared__ uint32_t l_geo[RO_LIST];           // r0 | r1 << 8 | c0 << 16 | (w - 1) << 24 | conj << 31
     __shared__ float2 l_vv[RO_LIST];
     __shared__ int s_item, s_n;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int n_items = ctrl[1];
     for (int i = threadIdx.x; i < TILE * TILE; i += blockDim.x) tile[i] = make_float2(0.0f, 0.0f);
     for (;;) {
@@ -487,88 +499,8 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_ro(int N, int os, int 
         __syncthreads();
         if (item_idx >= n_items) break;
         const int item = items[item_idx];
-        const int p = item / ntiles;
-        const int t = item - p * ntiles;
-        const int oy = t / ntx, ox = t - oy * ntx;
-        const int S = min(max(support[p], 1), s_max);
-        const int W = 2 * S + 1;
-        const int W2 = W * W;
-        const int D = (S + TILE - 1) / TILE;
-        const float2* pcache = cache + offsets[p];
-        const int ty0 = oy * TILE, tx0 = ox * TILE;
-        const int cx_lo = max(0, ox - D), cx_hi = min(ntx - 1, ox + D);
-        for (int cy = max(0, oy - D); cy <= min(ntx - 1, oy + D); ++cy) {
-            const int kb = p * ntiles + cy * ntx;
-            const int beg = start[kb + cx_lo], end = start[kb + cx_hi + 1];
-            for (int base = beg; base < end; base += RO_LIST) {
-                // decode: one candidate per thread, compacted into the list
-                if (threadIdx.x == 0) s_n = 0;
-                __syncthreads();
-                const int q = base + (int)threadIdx.x;
-                if (q < end) {
-                    const int4 r4 = __ldg(srec + q);
-                    const int iu = r4.x & 0xffff, iv = (r4.x >> 16) & 0xffff;
-                    const int c0 = max(iu - S, tx0), c1 = min(iu + S, tx0 + TILE - 1);
-                    const int r0 = max(iv - S, ty0), r1 = min(iv + S, ty0 + TILE - 1);
-                    if (c0 <= c1 && r0 <= r1) {
-                        // per-thread slots: the list order scatters runs of neighbouring
-                        // visibilities (same baseline, consecutive dumps), whose identical
-                        // rectangles would otherwise chain each warp's shared-memory updates
-                        const int slot = atomicAdd(&s_n, 1);
-                        const int fu = r4.y & 0xff, fv = (r4.y >> 8) & 0xff;
-                        l_off[slot] = (fv * os + fu) * W2 + (r0 - (iv - S)) * W + (c0 - (iu - S));
-                        l_geo[slot] = (uint32_t)(r0 - ty0) | ((uint32_t)(r1 - ty0) << 8) |
-                                      ((uint32_t)(c0 - tx0) << 16) | ((uint32_t)(c1 - c0) << 24) |
-                                      ((uint32_t)((r4.y >> 16) & 1) << 31);
-                        l_vv[slot] = __ldg(svis + q);
-                    }
-                }
-                __syncthreads();
-                const int n = s_n;
-                for (int e = 0; e < n; ++e) {
-                    const uint32_t geo = l_geo[e];
-                    const int r0 = (int)(geo & 0xff), r1 = (int)((geo >> 8) & 0xff);
-                    const int rw = r0 + ((wid - r0) & (GRID_WARPS - 1));   // first owned row
-                    if (rw > r1) continue;
-                    const int c0 = (int)((geo >> 16) & 0xff), w = (int)((geo >> 24) & 0x7f) + 1;
-                    const float sgn = (geo >> 31) ? -1.0f : 1.0f;
-                    const float2 vv = l_vv[e];
-                    const float2* sub = pcache + l_off[e] + (rw - r0) * W;
-                    float2* trow = tile + rw * TILE + c0;
-                    for (int r = rw; r <= r1; r += GRID_WARPS) {
-                        float2 tp[CH];
-#pragma unroll
-                        for (int k = 0; k < CH; ++k)
-                            tp[k] = (lane + 32 * k < w) ? __ldg(sub + lane + 32 * k) : make_float2(0.0f, 0.0f);
-#pragma unroll
-                        for (int k = 0; k < CH; ++k) {
-                            if (lane + 32 * k < w) {
-                                const float ti = sgn * tp[k].y;
-                                float2 a = trow[lane + 32 * k];
-                                a.x = fmaf(vv.x, tp[k].x, fmaf(-vv.y, ti, a.x));
-                                a.y = fmaf(vv.x, ti, fmaf(vv.y, tp[k].x, a.y));
-                                trow[lane + 32 * k] = a;
-                            }
-                        }
-                        sub += GRID_WARPS * W;
-                        trow += GRID_WARPS * TILE;
-                    }
-                    __syncwarp();   // the next entry may touch this one's cells from other lanes
-                }
-                __syncthreads();   // the list is rebuilt for the next round
-            }
-        }
-        __syncthreads();
-        // flush the tile (one atomic per touched cell) and clear it for the next item
-        for (int i = threadIdx.x; i < TILE * TILE; i += blockDim.x) {
-            const float2 a = tile[i];
-            if (a.x != 0.0f || a.y != 0.0f) {
-                const int gy = ty0 + i / TILE, gx = tx0 + (i & (TILE - 1));
-                if (gy < N && gx < N) atomicAdd(grid + (int64_t)gy * N + gx, a);
-                tile[i] = make_float2(0.0f, 0.0f);
-            }
-        }
-        __syncthreads();
+        ro_item<TILE, false>(item, N, os, s_max, ntx, ntiles, support, offsets, cache, start, srec, svis, grid,
+                             tile, l_off, l_geo, l_vv, &s_n);
     }
 }
 

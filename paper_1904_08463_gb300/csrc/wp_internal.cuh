@@ -279,6 +279,17 @@ int radix_sort(KT* keys, uint32_t* vals, KT* keys_alt, uint32_t* vals_alt, int64
 
 int grid_bin(const Geom& g, const wp_wkernels* k, const float* uvw, const float2* vis,
              const float* weight, int64_t V, const GridWork& w, cudaStream_t st);
+int grid_bin_noscatter(const Geom& g, const wp_wkernels* kern, const float* uvw, const float* weight, int64_t V,
+                       const GridWork& w, cudaStream_t st);
+int item_flags(const Geom& g, const wp_wkernels* kern, const GridWork& w, cudaStream_t st);
+// persistent multi-job gridding (grid_batch.cu)
+size_t grid_batch_ctrl_bytes();
+long long grid_batch_budget();
+int grid_batch_prepare(const Geom& g, const wp_wkernels* kern, const float* uvw, const float* weight, int64_t V,
+                       const GridWork& w, cudaStream_t st);
+int grid_batch_run(int n_jobs, const Geom* geoms, const wp_wkernels* kerns, const float* const* vis,
+                   const float* const* weight, const int64_t* Vs, const GridWork* works, float* const* grids,
+                   int tile, void* bws, long long budget, int withhold, cudaStream_t st);
 int grid_run(const Geom& g, const wp_wkernels* k, const GridWork& w, float2* grid, double* stats,
              cudaStream_t st);
 int write_items(int64_t n, const GridWork& w, cudaStream_t st);   // compact live items (flags scanned into cursor)

@@ -143,3 +143,23 @@ def test_free_kernels_refuses_sets_the_library_did_not_allocate():
     assert lib.wp_make_wkernels_owned(ctypes.byref(p), ctypes.c_void_p(16), wd, 2, s, ctypes.byref(out),
                                       None) == -2
     assert out.P == 0 and out.flags == 0
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes views of wp_plan, wp_wkernels and wp_grid_job have the sizes and field offsets
+    the C compiler gives the header's structs (checked with gcc, host only)."""
+    import ctypes
+    import subprocess
+
+    L, _ = _lib()
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "wproj.h"\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(wp_plan), sizeof(wp_wkernels),'
+                   ' sizeof(wp_grid_job), offsetof(wp_grid_job, kernels), offsetof(wp_grid_job, V),'
+                   ' offsetof(wp_grid_job, stats)); return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(L.WpPlan), ctypes.sizeof(L.WpWkernels), ctypes.sizeof(L.WpGridJob),
+            L.WpGridJob.kernels.offset, L.WpGridJob.V.offset, L.WpGridJob.stats.offset]
+    assert got == want

@@ -14,11 +14,11 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _problems(dev, n=5, seed=7, uv_scale=1.0, weights=False):
+def _problems(dev, n=5, seed=7, uv_scale=1.0, weights=False, vis_range=(2000, 60000)):
     import paper_1904_08463_gb300 as wp
     from paper_1904_08463_gb300.batch import Problem
 
-    specs = synth.batch_problems(n=n, seed=seed, sizes=(256, 512), planes=(8, 40), vis=(2000, 60000))
+    specs = synth.batch_problems(n=n, seed=seed, sizes=(256, 512), planes=(8, 40), vis=vis_range)
     out = []
     for i, d in enumerate(specs):
         R = 256
@@ -141,3 +141,60 @@ def test_batch_normalises_by_the_weights_actually_gridded():
         host = wp.dirty_image(st.plan, pbs[i].taper, G, float(stats[0])).cpu().numpy()
         assert np.abs(img - host).max() <= 1e-5 * np.abs(host).max(), i
         assert np.abs(img - ref).max() <= IMAGE_TOL * np.abs(ref).max(), i
+
+
+def test_persistent_batch_matches_per_problem_gridding_and_the_oracle():
+    """The persistent multi-problem gridder (one launch, one device queue for every problem's
+    scatter and (plane, tile) items, bounded waits between them) against each problem's own
+    wp_grid and, for the images, the oracle; replayed from a CUDA graph."""
+    import paper_1904_08463_gb300 as wp
+    from paper_1904_08463_gb300.batch import BatchImager
+
+    dev = torch.device("cuda")
+    specs, pbs = _problems(dev, n=5, seed=31, uv_scale=1.3, weights=True)
+    b = BatchImager(pbs, n_streams=2, persistent=True)
+    assert b.status() == 0
+    b.replay()
+    b.replay()
+    torch.cuda.synchronize()
+    assert b.status() == 0
+    assert b.dropped() > 0
+    for i, (d, st) in enumerate(zip(specs, b.states)):
+        G, stats = wp.grid(st.plan.replace(grid_method=3, grid_tile=64), st.wk, pbs[i].uvw, pbs[i].vis,
+                           pbs[i].weight)
+        assert np.allclose(st.stats.cpu().numpy(), stats.cpu().numpy(), rtol=1e-9), i
+        host = wp.dirty_image(st.plan, pbs[i].taper, G, float(stats[0].item())).cpu().numpy()
+        img = st.image.cpu().numpy()
+        assert np.abs(img - host).max() <= 1e-5 * np.abs(host).max(), i
+        g, ks, bo, wsum, ref = _oracle_image(d)
+        assert np.array_equal(st.support.cpu().numpy(), ks.support), i
+        assert np.abs(img - ref).max() <= IMAGE_TOL * np.abs(ref).max(), i
+
+
+def test_persistent_batch_bounded_wait_expires_and_context_survives():
+    """With the scatter withheld every gridding item's wait runs out: the batch status is
+    WP_ERR_TIMEOUT, no grid cell is written, and the same context then grids correctly."""
+    import paper_1904_08463_gb300 as wp
+    from paper_1904_08463_gb300 import api
+
+    dev = torch.device("cuda")
+    specs, pbs = _problems(dev, n=2, seed=41, vis_range=(2000, 6000))
+    jobs, refs = [], []
+    for d, pb in zip(specs, pbs):
+        plan = pb.plan.replace(trunc_frac=0.0, grid_method=3, grid_tile=64)
+        planes = o.mean_w_planes(d["uvw"][:, 2].astype(np.float64), d["P"])
+        wk = wp.make_wkernels(plan, pb.taper, planes, supports=[min(5, d["max_support"])] * d["P"])
+        ws = wp.workspace(wp.grid_workspace_bytes(plan, wk.P, pb.vis.numel()), dev)
+        G = torch.zeros((plan.image_size, plan.image_size), dtype=torch.complex64, device=dev)
+        jobs.append(api.GridJob(plan, wk, pb.uvw, pb.vis, None, G, ws,
+                                torch.zeros(2, dtype=torch.float64, device=dev)))
+        refs.append(wp.grid(plan, wk, pb.uvw, pb.vis)[0].cpu().numpy())
+    bws = api.grid_batch_workspace(dev)
+    assert api.grid_batch_selftest(jobs, bws) == -6
+    for j in jobs:
+        assert float(torch.abs(j.grid).max()) == 0.0
+    api.grid_batch(jobs, bws)
+    torch.cuda.synchronize()
+    assert api.grid_batch_status(bws) == 0
+    for j, r in zip(jobs, refs):
+        assert np.abs(j.grid.cpu().numpy() - r).max() <= 1e-5 * np.abs(r).max()
