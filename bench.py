@@ -92,7 +92,8 @@ def measure_compute_peaks(dev) -> dict:
             ts.append(a.elapsed_time(b))
         return min(ts)
 
-    fp32 = flops.value / (best(fma) * 1e-3) / 1e12
+    ms_fma = best(fma)                       # the call fills `flops`
+    fp32 = flops.value / (ms_fma * 1e-3) / 1e12
     n = 8192
     x = torch.randn(n, n, device=dev, dtype=torch.float32)
     y = torch.randn(n, n, device=dev, dtype=torch.float32)

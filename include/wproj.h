@@ -389,11 +389,12 @@ int wp_grid_static(const wp_plan* plan, const wp_wkernels* kernels, const float*
 /* ---- many independent problems in one persistent launch ----------------------------- */
 
 /*
- * One gridding job of a batch: the arguments of one wp_grid call, by value.  The batch grids
- * every job with the row-owned shared-tile method (grid_method 3) whatever plan.grid_method
- * says; plan.grid_tile (0 = 64, or 32) must be the same for every job of a batch.
- *   workspace  wp_grid_workspace_bytes(plan with grid_method 3, P, V) bytes, 256-byte aligned
- *              (the job's own; jobs never share one)
+ * One gridding job of a batch: the arguments of one wp_grid call, by value.  The batch grids a
+ * job with the slot method when plan.grid_method is 9, otherwise with the row-owned shared-tile
+ * method (grid_method 3) whatever plan.grid_method says; plan.grid_tile (0 = 64, or 32) must be
+ * the same for every row-owned job of a batch.
+ *   workspace  wp_grid_workspace_bytes(plan with grid_method 9 or 3, P, V) bytes, 256-byte
+ *              aligned (the job's own; jobs never share one)
  */
 #define WP_GRID_BATCH_MAX_JOBS 128
 typedef struct wp_grid_job {
@@ -415,10 +416,12 @@ size_t wp_grid_batch_workspace_bytes(void);
 /*
  * Grids n_jobs independent problems (1 <= n_jobs <= WP_GRID_BATCH_MAX_JOBS; jobs: host array)
  * with the same result per job as wp_grid.  Each job is binned as in wp_grid up to its list of
- * live (plane, tile) work items; then one persistent launch pulls work from a single device
- * queue -- every job's scatter of its records into bin order first, then every job's gridding
- * items, in the order of `jobs` (put large jobs first) -- so small problems fill the GPU
- * beside large ones with no per-job tail.  A gridding item waits for its job's scatter; the
+ * live work items; then one persistent launch pulls work from a single device queue -- every
+ * job's ordering of its records first (the scatter into bin order, or for slot jobs the gather
+ * into the sorted order), then every job's gridding items (a block per row-owned (plane, tile)
+ * item, eight slot items per block), in the order of `jobs` (put large jobs first) -- so small
+ * problems fill the GPU beside large ones with no per-job tail.  An item waits for its job's
+ * ordering; the
  * wait is bounded (about a second of SM clock) and on expiry the item is skipped and the
  * batch status records WP_ERR_TIMEOUT (read it with wp_grid_batch_status).  Argument errors of
  * any job are reported before anything is launched.  Calls overlapping on the GPU must use

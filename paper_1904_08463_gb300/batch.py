@@ -103,7 +103,8 @@ class BatchImager:
     """persistent=False: each problem's whole step (its own tuned gridder) on one of a few forked
     streams.  persistent=True: kernel generation of every problem on the forked streams, then
     the gridding of ALL problems in one persistent launch pulling work from one device queue
-    (``api.grid_batch``: row-owned tiles of 64 cells, largest problems first), then the images."""
+    (``api.grid_batch``: slot items for problems tuned to the slot gridder, row-owned tiles of 64
+    cells for the rest, largest problems first), then the images."""
 
     def __init__(self, problems: list[Problem], n_streams: int = 4, tuner: Autotuner | None = None,
                  persistent: bool = False):
@@ -114,7 +115,10 @@ class BatchImager:
         dev = problems[0].vis.device
         self.bws = api.grid_batch_workspace(dev)
         order = sorted(range(len(self.states)), key=lambda i: -self.states[i].cost())
-        self.jobs = [api.GridJob(self.states[i].plan.replace(grid_method=3, grid_tile=64), self.states[i].wk,
+        # each problem's tuned gridder when it is the slot method (9), else the row-owned tiles (3)
+        self.jobs = [api.GridJob(self.states[i].plan.replace(
+                                     grid_method=9 if self.states[i].plan.grid_method == 9 else 3, grid_tile=64),
+                                 self.states[i].wk,
                                  self.states[i].pb.uvw, self.states[i].pb.vis, self.states[i].pb.weight,
                                  self.states[i].grid, self.states[i].grid_ws, self.states[i].stats)
                      for i in order]

@@ -19,6 +19,7 @@
 
 #include "wp_internal.cuh"
 #include "grid_ro.cuh"
+#include "grid_slot.cuh"
 
 namespace wp {
 
@@ -28,7 +29,9 @@ constexpr long long WAIT_BUDGET = 1LL << 31;         // SM clock cycles (~1 s)
 }  // namespace
 
 struct BatchJob {
-    int N, os, s_max, ntx, ntiles, n_sc;      // n_sc: scatter chunks of the job
+    int mode;                                 // 3: row-owned tiles, 9: slots
+    int P;
+    int N, os, s_max, ntx, ntiles, n_sc;      // n_sc: producer chunks of the job (scatter or gather)
     int64_t V;
     const int32_t* seff;
     const int64_t* offsets;
@@ -42,8 +45,11 @@ struct BatchJob {
     int4* srec;
     float2* svis;
     const int* items;
-    const int* ctrl;                          // ctrl[1]: number of live items
+    const int* ctrl;                          // ctrl[1]: number of live items (row-owned)
     float2* grid;
+    const int* vstart;                        // slots: plane bounds of the sorted list,
+    const int* istart;                        //        item starts per plane (istart[P] = items),
+    const uint32_t* sidx;                     //        the sort's permutation
 };
 
 struct BatchTable {
@@ -51,11 +57,14 @@ struct BatchTable {
 };
 
 // ctrl layout: [0] queue head, [1] status, [2 .. 2 + n_jobs) finished scatter chunks per job
-template <int TILE>
+// HAS_RO / HAS_SLOT: which kinds of job the batch holds (the row-owned tile's shared memory and
+// the slot code's registers are only paid for when used).
+template <int TILE, bool HAS_RO, bool HAS_SLOT>
 __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_batch(const __grid_constant__ BatchTable tab, int n_jobs,
                                                                 int* __restrict__ bctrl, long long budget,
                                                                 int withhold_scatter) {
-    __shared__ float2 tile[TILE * TILE];
+    static_assert(SLOT_WARPS == GRID_WARPS, "a slot unit is one item per warp of the block");
+    __shared__ float2 tile[HAS_RO ? TILE * TILE : 1];
     __shared__ int l_off[RO_LIST];
     __shared__ uint32_t l_geo[RO_LIST];
     __shared__ float2 l_vv[RO_LIST];
@@ -68,7 +77,9 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_batch(const __grid_con
             pre_sc[k] = a;
             pre_gi[k] = b;
             a += tab.j[k].n_sc;
-            b += tab.j[k].ctrl[1];
+            // consumer units: one row-owned item, or one slot item per warp of the block
+            b += (tab.j[k].mode == 9) ? (tab.j[k].istart[tab.j[k].P] + SLOT_WARPS - 1) / SLOT_WARPS
+                                      : tab.j[k].ctrl[1];
         }
         pre_sc[n_jobs] = a;
         pre_gi[n_jobs] = b;
@@ -91,14 +102,21 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_batch(const __grid_con
             const BatchJob& J = tab.j[jb];
             if (withhold_scatter) continue;       // self-test: the chunk is never done
             const int64_t k0 = (int64_t)(idx - pre_sc[jb]) * SCATTER_CHUNK;
-            for (int64_t k = k0 + threadIdx.x; k < min(J.V, k0 + SCATTER_CHUNK); k += blockDim.x) {
-                const int kk = J.key[k];
-                if (kk < 0) continue;
-                const int pos = J.start[kk] + atomicAdd(&J.cursor[kk], 1);
-                J.srec[pos] = J.rec[k];
-                const float2 v = J.vis[k];
-                const float a = J.weight ? J.weight[k] : 1.0f;
-                J.svis[pos] = make_float2(v.x * a, v.y * a);
+            if (HAS_SLOT && J.mode == 9) {
+                // gather: sorted position i takes its record and weighted value
+                const int64_t n_kept = J.vstart[J.P];
+                for (int64_t i = k0 + threadIdx.x; i < min(n_kept, k0 + SCATTER_CHUNK); i += blockDim.x)
+                    slot_gather_one(i, J.os, J.s_max, J.sidx, J.rec, J.seff, J.vis, J.weight, J.srec, J.svis);
+            } else if (HAS_RO) {
+                for (int64_t k = k0 + threadIdx.x; k < min(J.V, k0 + SCATTER_CHUNK); k += blockDim.x) {
+                    const int kk = J.key[k];
+                    if (kk < 0) continue;
+                    const int pos = J.start[kk] + atomicAdd(&J.cursor[kk], 1);
+                    J.srec[pos] = J.rec[k];
+                    const float2 v = J.vis[k];
+                    const float a = J.weight ? J.weight[k] : 1.0f;
+                    J.svis[pos] = make_float2(v.x * a, v.y * a);
+                }
             }
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -128,9 +146,16 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_batch(const __grid_con
             }
             __syncthreads();
             if (!s_ok) continue;
-            const int item = J.items[g - pre_gi[jb]];
-            ro_item<TILE, true>(item, J.N, J.os, J.s_max, J.ntx, J.ntiles, J.seff, J.offsets, J.cache, J.start,
-                                J.srec, J.svis, J.grid, tile, l_off, l_geo, l_vv, &s_n);
+            if (HAS_SLOT && J.mode == 9) {
+                const int it = (g - pre_gi[jb]) * SLOT_WARPS + (int)(threadIdx.x >> 5);
+                if (it < J.istart[J.P])
+                    slot_item<SLOT_ROWS, true>(it, J.N, J.P, J.s_max, J.seff, J.offsets, J.cache, J.vstart,
+                                               J.istart, J.srec, J.svis, J.grid);
+            } else if (HAS_RO) {
+                const int item = J.items[g - pre_gi[jb]];
+                ro_item<TILE, true>(item, J.N, J.os, J.s_max, J.ntx, J.ntiles, J.seff, J.offsets, J.cache, J.start,
+                                    J.srec, J.svis, J.grid, tile, l_off, l_geo, l_vv, &s_n);
+            }
         }
     }
 }
@@ -163,11 +188,18 @@ int grid_batch_prepare(const Geom& g, const wp_wkernels* kern, const float* uvw,
 
 int grid_batch_run(int n_jobs, const Geom* geoms, const wp_wkernels* kerns, const float* const* vis,
                    const float* const* weight, const int64_t* Vs, const GridWork* works, float* const* grids,
-                   int tile, void* bws, long long budget, int withhold, cudaStream_t st) {
+                   const uint32_t* const* sidx, int tile, void* bws, long long budget, int withhold, cudaStream_t st) {
     BatchTable tab;
+    bool has_ro = false, has_slot = false;
     for (int k = 0; k < n_jobs; ++k) {
         BatchJob& J = tab.j[k];
         const GridWork& w = works[k];
+        J.mode = (geoms[k].grid_method == 9) ? 9 : 3;
+        (J.mode == 9 ? has_slot : has_ro) = true;
+        J.P = kerns[k].P;
+        J.vstart = w.vstart;
+        J.istart = w.istart;
+        J.sidx = sidx[k];
         J.N = geoms[k].N;
         J.os = geoms[k].os;
         J.s_max = geoms[k].s_max;
@@ -195,15 +227,16 @@ int grid_batch_run(int n_jobs, const Geom* geoms, const wp_wkernels* kerns, cons
     int dev = 0, sms = 0, per_sm = 0;
     WP_CUDA(cudaGetDevice(&dev));
     WP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (tile == 32) {
-        WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_batch<32>, GRID_WARPS * 32, 0));
-        if (per_sm < 1) per_sm = 1;
-        k_grid_batch<32><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(tab, n_jobs, bctrl, budget, withhold);
-    } else {
-        WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_batch<64>, GRID_WARPS * 32, 0));
-        if (per_sm < 1) per_sm = 1;
-        k_grid_batch<64><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(tab, n_jobs, bctrl, budget, withhold);
-    }
+#define WP_LAUNCH_BATCH(T, R, S)                                                                               \
+    do {                                                                                                       \
+        WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_batch<T, R, S>, GRID_WARPS * 32, 0)); \
+        if (per_sm < 1) per_sm = 1;                                                                            \
+        k_grid_batch<T, R, S><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(tab, n_jobs, bctrl, budget, withhold); \
+    } while (0)
+    if (!has_ro) WP_LAUNCH_BATCH(64, false, true);
+    else if (tile == 32) { if (has_slot) WP_LAUNCH_BATCH(32, true, true); else WP_LAUNCH_BATCH(32, true, false); }
+    else { if (has_slot) WP_LAUNCH_BATCH(64, true, true); else WP_LAUNCH_BATCH(64, true, false); }
+#undef WP_LAUNCH_BATCH
     WP_LAUNCH_CHECK("k_grid_batch");
     return WP_OK;
 }
@@ -220,7 +253,12 @@ int batch_call(int32_t n_jobs, const wp_grid_job* jobs, void* bws, size_t bws_by
     if (n_jobs < 1 || n_jobs > WP_GRID_BATCH_MAX_JOBS) return WP_ERR_SIZE;
     if (!jobs || !bws) return WP_ERR_NULL;
     if (((uintptr_t)bws & 255u) || bws_bytes < grid_batch_ctrl_bytes()) return WP_ERR_WORKSPACE;
-    const int tile = jobs[0].plan.grid_tile ? jobs[0].plan.grid_tile : 64;
+    int tile = 0;                                    // the row-owned jobs' tile (all the same)
+    for (int k = 0; k < n_jobs; ++k)
+        if (jobs[k].plan.grid_method != 9) {
+            tile = jobs[k].plan.grid_tile ? jobs[k].plan.grid_tile : 64;
+            break;
+        }
     std::vector<Geom> geoms((size_t)n_jobs);
     std::vector<GridWork> works((size_t)n_jobs);
     std::vector<wp_wkernels> kerns((size_t)n_jobs);
@@ -230,8 +268,10 @@ int batch_call(int32_t n_jobs, const wp_grid_job* jobs, void* bws, size_t bws_by
     for (int k = 0; k < n_jobs; ++k) {               // every job checked before any launch
         const wp_grid_job& J = jobs[k];
         wp_plan plan = J.plan;
-        if ((plan.grid_tile ? plan.grid_tile : 64) != tile) return WP_ERR_PLAN;
-        plan.grid_method = 3;
+        if (plan.grid_method != 9) {
+            if ((plan.grid_tile ? plan.grid_tile : 64) != tile) return WP_ERR_PLAN;
+            plan.grid_method = 3;
+        }
         int rc = check_grid_args(&plan, &J.kernels, J.uvw, J.V, J.workspace, J.workspace_bytes, &geoms[(size_t)k],
                                  true);
         if (rc) return rc;
@@ -243,13 +283,18 @@ int batch_call(int32_t n_jobs, const wp_grid_job* jobs, void* bws, size_t bws_by
         Vs[(size_t)k] = J.V;
         grids[(size_t)k] = J.grid;
     }
+    std::vector<const uint32_t*> sidx((size_t)n_jobs, nullptr);
     for (int k = 0; k < n_jobs; ++k) {
-        int rc = grid_batch_prepare(geoms[(size_t)k], &kerns[(size_t)k], jobs[k].uvw, jobs[k].weight, jobs[k].V,
-                                    works[(size_t)k], st);
+        const Geom& g = geoms[(size_t)k];
+        int rc = (g.grid_method == 9)
+                     ? grid_slot_prepare(g, &kerns[(size_t)k], jobs[k].uvw, jobs[k].weight, jobs[k].V, works[(size_t)k],
+                                         st, &sidx[(size_t)k])
+                     : grid_batch_prepare(g, &kerns[(size_t)k], jobs[k].uvw, jobs[k].weight, jobs[k].V,
+                                          works[(size_t)k], st);
         if (rc) return rc;
     }
     int rc = grid_batch_run(n_jobs, geoms.data(), kerns.data(), vis.data(), weight.data(), Vs.data(), works.data(),
-                            grids.data(), tile, bws, budget, withhold, st);
+                            grids.data(), sidx.data(), tile ? tile : 64, bws, budget, withhold, st);
     if (rc) return rc;
     if (!withhold)
         for (int k = 0; k < n_jobs; ++k)

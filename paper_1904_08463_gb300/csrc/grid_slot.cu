@@ -22,14 +22,10 @@
 #include <cuda_runtime.h>
 
 #include "wp_internal.cuh"
+#include "grid_slot.cuh"
 
 namespace wp {
 
-namespace {
-constexpr int SLOT_ROWS = 8;         // slot rows per lane (registers: sum, cell, tap offset each)
-constexpr int SLOT_CHUNK = 512;      // visibilities per work item
-constexpr int SLOT_WARPS = 8;        // warps per block
-}  // namespace
 
 __device__ __forceinline__ uint32_t spread16(uint32_t v) {
     v &= 0xffffu;
@@ -100,8 +96,6 @@ __global__ void __launch_bounds__(256) k_plane_bounds(int64_t V, int P, int mb, 
         for (int q = pi + 1; q <= P; ++q) vstart[q] = (int)V;
 }
 
-// Sorted records: x = x0 | y0 << 16 (footprint corner), y = (x0 mod W) | (y0 mod W) << 16,
-// z = sub-kernel offset (fv os + fu) W^2 | conj << 31, w = original index; weighted values.
 __global__ void __launch_bounds__(256) k_gather_slot(int64_t V, int os, int s_max, const int* __restrict__ vstart, int P,
                                                      const uint32_t* __restrict__ idx, const int4* __restrict__ rec,
                                                      const int32_t* __restrict__ support,
@@ -109,20 +103,7 @@ __global__ void __launch_bounds__(256) k_gather_slot(int64_t V, int os, int s_ma
                                                      int4* __restrict__ srec, float2* __restrict__ svis) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= V || i >= vstart[P]) return;
-    const int k = (int)idx[i];
-    const int4 r = rec[k];
-    const int p = r.z;
-    const int S = min(max(support[p], 1), s_max);
-    const int W = 2 * S + 1;
-    const int x0 = (r.x & 0xffff) - S, y0 = ((r.x >> 16) & 0xffff) - S;
-    const int fu = r.y & 0xff, fv = (r.y >> 8) & 0xff, conj = (r.y >> 16) & 1;
-    srec[i] = make_int4(x0 | (y0 << 16), (x0 % W) | ((y0 % W) << 16),
-                        (int)((uint32_t)((fv * os + fu) * W * W) | ((uint32_t)conj << 31)), k);
-    if (svis) {
-        const float2 v = vis[k];
-        const float a = weight ? weight[k] : 1.0f;
-        svis[i] = make_float2(v.x * a, v.y * a);
-    }
+    slot_gather_one(i, os, s_max, idx, rec, support, vis, weight, srec, svis);
 }
 
 // Items of plane q: ceil(n_q / SLOT_CHUNK) chunks x ceil(W/32) x ceil(W/SLOT_ROWS) slot tiles.
@@ -136,9 +117,6 @@ __global__ void __launch_bounds__(256) k_plane_items(int P, int s_max, const int
     icount[q] = (n > 0) ? ((n + SLOT_CHUNK - 1) / SLOT_CHUNK) * ((W + 31) / 32) * ((W + SLOT_ROWS - 1) / SLOT_ROWS) : 0;
 }
 
-// Slots outside the W x W residues (lane columns a >= W of the last column tile, rows b >= W of
-// the last row tile) read tap 0 of the sub-kernel -- always in bounds -- and are never flushed,
-// so the tap loads need no guard.
 template <int ROWS>
 __global__ void __launch_bounds__(SLOT_WARPS * 32, 2) k_grid_slot(int N, int P, int s_max,
                                                                   const int32_t* __restrict__ support,
@@ -156,84 +134,7 @@ __global__ void __launch_bounds__(SLOT_WARPS * 32, 2) k_grid_slot(int N, int P, 
         if (lane == 0) it = atomicAdd(&ctrl[0], 1);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n_items) break;
-        int lo = 0, hi = P;                       // largest plane with istart <= it
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (istart[mid] <= it) lo = mid; else hi = mid;
-        }
-        const int p = lo;
-        const int S = min(max(support[p], 1), s_max);
-        const int W = 2 * S + 1;
-        const int nxs = (W + 31) >> 5, nys = (W + ROWS - 1) / ROWS;
-        const int local = it - istart[p];
-        const int chunk = local / (nxs * nys);
-        const int tt = local - chunk * (nxs * nys);
-        const int tys = tt / nxs, txs = tt - tys * nxs;
-        const int v0 = vstart[p] + chunk * SLOT_CHUNK;
-        const int v1 = min(v0 + SLOT_CHUNK, vstart[p + 1]);
-        const float2* pc = cache + offsets[p];
-        const int a = txs * 32 + lane;            // the lane's slot column
-        const bool a_ok = a < W;
-        const int b0 = tys * ROWS;                // slot rows b0 .. b0 + ROWS - 1
-        const int nrows = min(ROWS, W - b0);      // rows of this tile inside the W x W residues
-        float2 acc[ROWS];
-        uint32_t held[ROWS];
-        int toff[ROWS];
-#pragma unroll
-        for (int j = 0; j < ROWS; ++j) {
-            acc[j] = make_float2(0.0f, 0.0f);
-            held[j] = 0xffffffffu;
-            toff[j] = 0;
-        }
-        uint32_t prev = 0xffffffffu;              // no footprint corner packs to this
-        int4 rn = __ldg(srec + v0);
-        float2 vn = __ldg(svis + v0);
-        for (int q = v0; q < v1; ++q) {
-            const int4 r = rn;
-            const float2 v = vn;
-            if (q + 1 < v1) {                     // the next record while this one's taps load
-                rn = __ldg(srec + q + 1);
-                vn = __ldg(svis + q + 1);
-            }
-            if ((uint32_t)r.x != prev) {          // the footprint moved: new cells for the slots
-                prev = (uint32_t)r.x;
-                const int x0 = r.x & 0xffff, y0 = (r.x >> 16) & 0xffff;
-                const int xm = r.y & 0xffff, ym = (r.y >> 16) & 0xffff;
-                int jx = a - xm;
-                jx += (jx < 0) ? W : 0;
-                const uint32_t xc = (uint32_t)(x0 + jx);
-                jx = a_ok ? jx : 0;
-#pragma unroll
-                for (int j = 0; j < ROWS; ++j) {
-                    int jy = b0 + j - ym;
-                    jy += (jy < 0) ? W : 0;
-                    const uint32_t cell = xc | ((uint32_t)(y0 + jy) << 16);
-                    const bool ok = a_ok && j < nrows;
-                    if (cell != held[j]) {
-                        if (ok && (acc[j].x != 0.0f || acc[j].y != 0.0f))
-                            atomicAdd(grid + (int64_t)(held[j] >> 16) * N + (held[j] & 0xffffu), acc[j]);
-                        acc[j] = make_float2(0.0f, 0.0f);
-                        held[j] = cell;
-                    }
-                    toff[j] = j < nrows ? jy * W + jx : 0;
-                }
-            }
-            const float2* sub = pc + (r.z & 0x7fffffff);
-            const float sg = (r.z < 0) ? -1.0f : 1.0f;
-            const float cA = v.x, cB = -sg * v.y, cC = sg * v.x, cD = v.y;
-            float2 tp[ROWS];
-#pragma unroll
-            for (int j = 0; j < ROWS; ++j) tp[j] = __ldg(sub + toff[j]);
-#pragma unroll
-            for (int j = 0; j < ROWS; ++j) {
-                acc[j].x = fmaf(cA, tp[j].x, fmaf(cB, tp[j].y, acc[j].x));
-                acc[j].y = fmaf(cC, tp[j].y, fmaf(cD, tp[j].x, acc[j].y));
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < ROWS; ++j)
-            if (a_ok && j < nrows && (acc[j].x != 0.0f || acc[j].y != 0.0f))
-                atomicAdd(grid + (int64_t)(held[j] >> 16) * N + (held[j] & 0xffffu), acc[j]);
+        slot_item<ROWS, false>(it, N, P, s_max, support, offsets, cache, vstart, istart, srec, svis, grid);
     }
 }
 
@@ -248,6 +149,33 @@ size_t slot_hist_ints(int64_t V) { return radix_sort_hist_ints(V); }
 int grid_slot(const Geom& g, const wp_wkernels* kern, const float* uvw, const float2* vis, const float* weight,
               int64_t V, const GridWork& w, float2* grid, double* stats, cudaStream_t st) {
     const int P = kern->P;
+    const uint32_t* idx = nullptr;
+    int rc = grid_slot_prepare(g, kern, uvw, weight, V, w, st, &idx);
+    if (rc) return rc;
+    if (V > 0) {
+        k_gather_slot<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(V, g.os, g.s_max, w.vstart, P, idx, w.rec, w.seff,
+                                                                   vis, weight, w.srec, w.svis);
+        WP_LAUNCH_CHECK("k_gather_slot");
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    WP_CUDA(cudaGetDevice(&dev));
+    WP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_slot<SLOT_ROWS>, SLOT_WARPS * 32, 0));
+    if (per_sm < 1) per_sm = 1;
+    k_grid_slot<SLOT_ROWS><<<sms * per_sm, SLOT_WARPS * 32, 0, st>>>(g.N, P, g.s_max, w.seff, kern->offsets,
+                                                          reinterpret_cast<const float2*>(kern->cache), w.vstart,
+                                                          w.istart, w.srec, w.svis, w.ctrl, grid);
+    WP_LAUNCH_CHECK("k_grid_slot");
+    return stats ? add_stats(stats, w.red, st) : WP_OK;
+}
+
+// Binning of the slot gridder up to its item list: effective supports, decisions and keys, the
+// sort, plane bounds, item counts and their scan; *idx_sorted = the sort's permutation.  The gather
+// of the sorted records (k_gather_slot / slot_gather_one) is left to the caller.
+int grid_slot_prepare(const Geom& g, const wp_wkernels* kern, const float* uvw, const float* weight, int64_t V,
+                      const GridWork& w, cudaStream_t st, const uint32_t** idx_sorted) {
+    const int P = kern->P;
+    int rc = WP_OK;
     WP_CUDA(cudaMemsetAsync(w.ctrl, 0, sizeof(int) * 8, st));
     WP_CUDA(cudaMemsetAsync(w.red, 0, sizeof(double) * 2, st));
     k_fit_supports_launch(g, kern, w, st);
@@ -263,31 +191,18 @@ int grid_slot(const Geom& g, const wp_wkernels* kern, const float* uvw, const fl
         WP_LAUNCH_CHECK("k_bin_slot");
     }
     bool in_alt = false;
-    int rc = radix_sort<uint64_t>(w.skey, w.sidx, w.skey_alt, w.sidx_alt, V, bits, w.rs_hist, w.rs_tmp, st, &in_alt);
+    rc = radix_sort<uint64_t>(w.skey, w.sidx, w.skey_alt, w.sidx_alt, V, bits, w.rs_hist, w.rs_tmp, st, &in_alt);
     if (rc) return rc;
     const uint64_t* keys = in_alt ? w.skey_alt : w.skey;
     const uint32_t* idx = in_alt ? w.sidx_alt : w.sidx;
     k_plane_bounds<<<(unsigned)(V > 0 ? (V + 255) / 256 : 1), 256, 0, st>>>(V, P, mb, keys, w.vstart);
     WP_LAUNCH_CHECK("k_plane_bounds");
-    if (V > 0) {
-        k_gather_slot<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(V, g.os, g.s_max, w.vstart, P, idx, w.rec, w.seff,
-                                                                   vis, weight, w.srec, w.svis);
-        WP_LAUNCH_CHECK("k_gather_slot");
-    }
     k_plane_items<<<(unsigned)((P + 1 + 255) / 256), 256, 0, st>>>(P, g.s_max, w.vstart, w.seff, w.icount);
     WP_LAUNCH_CHECK("k_plane_items");
     rc = exclusive_scan_i32(w.icount, w.istart, (int64_t)P + 1, w.scan_tmp, st);
     if (rc) return rc;
-    int dev = 0, sms = 0, per_sm = 0;
-    WP_CUDA(cudaGetDevice(&dev));
-    WP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_slot<SLOT_ROWS>, SLOT_WARPS * 32, 0));
-    if (per_sm < 1) per_sm = 1;
-    k_grid_slot<SLOT_ROWS><<<sms * per_sm, SLOT_WARPS * 32, 0, st>>>(g.N, P, g.s_max, w.seff, kern->offsets,
-                                                          reinterpret_cast<const float2*>(kern->cache), w.vstart,
-                                                          w.istart, w.srec, w.svis, w.ctrl, grid);
-    WP_LAUNCH_CHECK("k_grid_slot");
-    return stats ? add_stats(stats, w.red, st) : WP_OK;
+    *idx_sorted = idx;
+    return WP_OK;
 }
 
 }  // namespace wp

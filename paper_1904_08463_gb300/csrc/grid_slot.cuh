@@ -1,0 +1,140 @@
+// One work item of the slot gridder (grid_method 9), shared by the per-call kernel
+// (k_grid_slot) and the persistent multi-job kernel (k_grid_batch): item `it` of the call's
+// item list = (plane, chunk of up to SLOT_CHUNK Morton-sorted visibilities, 32 x ROWS tile of the
+// W x W slots), processed by one warp.
+//
+// Every tap of a (2S+1)^2 footprint whose corner is (x0, y0) lands on a distinct residue class
+// (x mod W, y mod W), W = 2S+1.  The lane owning the residue (a, b) -- a "slot" -- therefore has
+// exactly one tap of every visibility of the plane: the cell x = x0 + ((a - x0) mod W) (same for
+// y), tap offset (x - x0, y - y0).  It keeps that cell's sum in a register and writes it to the
+// grid (one float2 reduction) only when a later visibility moves its cell.  Slots outside the
+// W x W residues (lane columns a >= W of the last column tile, rows b >= W of the last row tile)
+// read tap 0 of the sub-kernel -- always in bounds -- and are never flushed, so the tap loads
+// need no guard.  COHERENT: the sorted records were written by the same launch (read through
+// L2, not the non-coherent read-only path).
+#pragma once
+
+#include "wp_internal.cuh"
+
+namespace wp {
+
+constexpr int SLOT_ROWS = 8;         // slot rows per lane (registers: sum, cell, tap offset each)
+constexpr int SLOT_CHUNK = 512;      // visibilities per work item
+constexpr int SLOT_WARPS = 8;        // warps per block
+
+template <bool COHERENT>
+__device__ __forceinline__ int4 ld_slot_rec(const int4* p) { return COHERENT ? __ldcg(p) : __ldg(p); }
+template <bool COHERENT>
+__device__ __forceinline__ float2 ld_slot_vis(const float2* p) { return COHERENT ? __ldcg(p) : __ldg(p); }
+
+// Sorted record i of the slot gridder: x = x0 | y0 << 16 (footprint corner), y = (x0 mod W) |
+// (y0 mod W) << 16, z = sub-kernel offset (fv os + fu) W^2 | conj << 31, w = original index; the
+// weighted value beside it.  idx: the sort's permutation; rec: the unsorted binning records.
+__device__ __forceinline__ void slot_gather_one(int64_t i, int os, int s_max, const uint32_t* __restrict__ idx,
+                                                const int4* __restrict__ rec, const int32_t* __restrict__ support,
+                                                const float2* __restrict__ vis, const float* __restrict__ weight,
+                                                int4* __restrict__ srec, float2* __restrict__ svis) {
+    const int k = (int)idx[i];
+    const int4 r = rec[k];
+    const int p = r.z;
+    const int S = min(max(support[p], 1), s_max);
+    const int W = 2 * S + 1;
+    const int x0 = (r.x & 0xffff) - S, y0 = ((r.x >> 16) & 0xffff) - S;
+    const int fu = r.y & 0xff, fv = (r.y >> 8) & 0xff, conj = (r.y >> 16) & 1;
+    srec[i] = make_int4(x0 | (y0 << 16), (x0 % W) | ((y0 % W) << 16),
+                        (int)((uint32_t)((fv * os + fu) * W * W) | ((uint32_t)conj << 31)), k);
+    if (svis) {
+        const float2 v = vis[k];
+        const float a = weight ? weight[k] : 1.0f;
+        svis[i] = make_float2(v.x * a, v.y * a);
+    }
+}
+
+template <int ROWS, bool COHERENT>
+__device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const int32_t* __restrict__ support,
+                                          const int64_t* __restrict__ offsets, const float2* __restrict__ cache,
+                                          const int* __restrict__ vstart, const int* __restrict__ istart,
+                                          const int4* __restrict__ srec, const float2* __restrict__ svis,
+                                          float2* __restrict__ grid) {
+    const int lane = threadIdx.x & 31;
+    int lo = 0, hi = P;                       // largest plane with istart <= it
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (istart[mid] <= it) lo = mid; else hi = mid;
+    }
+    const int p = lo;
+    const int S = min(max(support[p], 1), s_max);
+    const int W = 2 * S + 1;
+    const int nxs = (W + 31) >> 5, nys = (W + ROWS - 1) / ROWS;
+    const int local = it - istart[p];
+    const int chunk = local / (nxs * nys);
+    const int tt = local - chunk * (nxs * nys);
+    const int tys = tt / nxs, txs = tt - tys * nxs;
+    const int v0 = vstart[p] + chunk * SLOT_CHUNK;
+    const int v1 = min(v0 + SLOT_CHUNK, vstart[p + 1]);
+    const float2* pc = cache + offsets[p];
+    const int a = txs * 32 + lane;            // the lane's slot column
+    const bool a_ok = a < W;
+    const int b0 = tys * ROWS;                // slot rows b0 .. b0 + ROWS - 1
+    const int nrows = min(ROWS, W - b0);      // rows of this tile inside the W x W residues
+    float2 acc[ROWS];
+    uint32_t held[ROWS];
+    int toff[ROWS];
+#pragma unroll
+    for (int j = 0; j < ROWS; ++j) {
+        acc[j] = make_float2(0.0f, 0.0f);
+        held[j] = 0xffffffffu;
+        toff[j] = 0;
+    }
+    uint32_t prev = 0xffffffffu;              // no footprint corner packs to this
+    int4 rn = ld_slot_rec<COHERENT>(srec + v0);
+    float2 vn = ld_slot_vis<COHERENT>(svis + v0);
+    for (int q = v0; q < v1; ++q) {
+        const int4 r = rn;
+        const float2 v = vn;
+        if (q + 1 < v1) {                     // the next record while this one's taps load
+            rn = ld_slot_rec<COHERENT>(srec + q + 1);
+            vn = ld_slot_vis<COHERENT>(svis + q + 1);
+        }
+        if ((uint32_t)r.x != prev) {          // the footprint moved: new cells for the slots
+            prev = (uint32_t)r.x;
+            const int x0 = r.x & 0xffff, y0 = (r.x >> 16) & 0xffff;
+            const int xm = r.y & 0xffff, ym = (r.y >> 16) & 0xffff;
+            int jx = a - xm;
+            jx += (jx < 0) ? W : 0;
+            const uint32_t xc = (uint32_t)(x0 + jx);
+            jx = a_ok ? jx : 0;
+#pragma unroll
+            for (int j = 0; j < ROWS; ++j) {
+                int jy = b0 + j - ym;
+                jy += (jy < 0) ? W : 0;
+                const uint32_t cell = xc | ((uint32_t)(y0 + jy) << 16);
+                const bool ok = a_ok && j < nrows;
+                if (cell != held[j]) {
+                    if (ok && (acc[j].x != 0.0f || acc[j].y != 0.0f))
+                        atomicAdd(grid + (int64_t)(held[j] >> 16) * N + (held[j] & 0xffffu), acc[j]);
+                    acc[j] = make_float2(0.0f, 0.0f);
+                    held[j] = cell;
+                }
+                toff[j] = j < nrows ? jy * W + jx : 0;
+            }
+        }
+        const float2* sub = pc + (r.z & 0x7fffffff);
+        const float sg = (r.z < 0) ? -1.0f : 1.0f;
+        const float cA = v.x, cB = -sg * v.y, cC = sg * v.x, cD = v.y;
+        float2 tp[ROWS];
+#pragma unroll
+        for (int j = 0; j < ROWS; ++j) tp[j] = __ldg(sub + toff[j]);
+#pragma unroll
+        for (int j = 0; j < ROWS; ++j) {
+            acc[j].x = fmaf(cA, tp[j].x, fmaf(cB, tp[j].y, acc[j].x));
+            acc[j].y = fmaf(cC, tp[j].y, fmaf(cD, tp[j].x, acc[j].y));
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < ROWS; ++j)
+        if (a_ok && j < nrows && (acc[j].x != 0.0f || acc[j].y != 0.0f))
+            atomicAdd(grid + (int64_t)(held[j] >> 16) * N + (held[j] & 0xffffu), acc[j]);
+}
+
+}  // namespace wp

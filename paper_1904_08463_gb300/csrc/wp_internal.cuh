@@ -289,7 +289,7 @@ int grid_batch_prepare(const Geom& g, const wp_wkernels* kern, const float* uvw,
                        const GridWork& w, cudaStream_t st);
 int grid_batch_run(int n_jobs, const Geom* geoms, const wp_wkernels* kerns, const float* const* vis,
                    const float* const* weight, const int64_t* Vs, const GridWork* works, float* const* grids,
-                   int tile, void* bws, long long budget, int withhold, cudaStream_t st);
+                   const uint32_t* const* sidx, int tile, void* bws, long long budget, int withhold, cudaStream_t st);
 int grid_run(const Geom& g, const wp_wkernels* k, const GridWork& w, float2* grid, double* stats,
              cudaStream_t st);
 int write_items(int64_t n, const GridWork& w, cudaStream_t st);   // compact live items (flags scanned into cursor)
@@ -298,6 +298,8 @@ int add_stats(double* stats, const double* red, cudaStream_t st);
 size_t slot_hist_ints(int64_t V);
 int grid_slot(const Geom& g, const wp_wkernels* kern, const float* uvw, const float2* vis, const float* weight,
               int64_t V, const GridWork& w, float2* grid, double* stats, cudaStream_t st);
+int grid_slot_prepare(const Geom& g, const wp_wkernels* kern, const float* uvw, const float* weight, int64_t V,
+                      const GridWork& w, cudaStream_t st, const uint32_t** idx_sorted);
 int grid_run_group(const Geom& g, const wp_wkernels* k, const GridWork& w, float2* grid, cudaStream_t st);
 int degrid_run(const Geom& g, const wp_wkernels* k, int64_t V, const GridWork& w, const float2* grid,
                float2* vis_out, cudaStream_t st);

@@ -171,17 +171,59 @@ def test_persistent_batch_matches_per_problem_gridding_and_the_oracle():
         assert np.abs(img - ref).max() <= IMAGE_TOL * np.abs(ref).max(), i
 
 
-def test_persistent_batch_bounded_wait_expires_and_context_survives():
-    """With the scatter withheld every gridding item's wait runs out: the batch status is
-    WP_ERR_TIMEOUT, no grid cell is written, and the same context then grids correctly."""
+def _jobs(dev, methods, seed, vis_range=(2000, 6000)):
+    import paper_1904_08463_gb300 as wp
+    from paper_1904_08463_gb300 import api
+
+    specs, pbs = _problems(dev, n=len(methods), seed=seed, vis_range=vis_range, weights=True, uv_scale=1.2)
+    jobs, refs = [], []
+    for d, pb, m in zip(specs, pbs, methods):
+        plan = pb.plan.replace(trunc_frac=0.0, grid_method=m, grid_tile=64)
+        planes = o.mean_w_planes(d["uvw"][:, 2].astype(np.float64), d["P"])
+        wk = wp.make_wkernels(plan, pb.taper, planes, supports=[min(9, d["max_support"])] * d["P"])
+        ws = wp.workspace(wp.grid_workspace_bytes(plan, wk.P, pb.vis.numel()), dev)
+        G = torch.zeros((plan.image_size, plan.image_size), dtype=torch.complex64, device=dev)
+        jobs.append(api.GridJob(plan, wk, pb.uvw, pb.vis, pb.weight, G, ws,
+                                torch.zeros(2, dtype=torch.float64, device=dev)))
+        refs.append([x.cpu().numpy() for x in wp.grid(plan.replace(grid_method=3), wk, pb.uvw, pb.vis, pb.weight)])
+    return jobs, refs
+
+
+@pytest.mark.parametrize("methods", [(9, 9, 9), (3, 9, 3, 9), (9,)])
+def test_persistent_batch_with_slot_jobs_matches_per_job_gridding(methods):
+    """Slot jobs (grid_method 9) -- alone or mixed with row-owned ones -- in one persistent launch:
+    the in-launch gather orders each slot job's records before its items run; every grid and
+    its stats equal the job's own wp_grid, twice in a row."""
+    from paper_1904_08463_gb300 import api
+
+    dev = torch.device("cuda")
+    jobs, refs = _jobs(dev, methods, seed=53)
+    bws = api.grid_batch_workspace(dev)
+    for _ in range(2):
+        for j in jobs:
+            j.grid.zero_()
+            j.stats.zero_()
+        api.grid_batch(jobs, bws)
+        torch.cuda.synchronize()
+        assert api.grid_batch_status(bws) == 0
+        for j, (G, st) in zip(jobs, refs):
+            assert np.abs(j.grid.cpu().numpy() - G).max() <= 1e-5 * np.abs(G).max()
+            assert np.allclose(j.stats.cpu().numpy(), st, rtol=1e-9)
+
+
+@pytest.mark.parametrize("methods", [(3, 3), (9, 3)])
+def test_persistent_batch_bounded_wait_expires_and_context_survives(methods):
+    """With the record ordering (scatter / gather) withheld every gridding item's wait runs out:
+    the batch status is WP_ERR_TIMEOUT, no grid cell is written, and the same context then grids
+    correctly."""
     import paper_1904_08463_gb300 as wp
     from paper_1904_08463_gb300 import api
 
     dev = torch.device("cuda")
-    specs, pbs = _problems(dev, n=2, seed=41, vis_range=(2000, 6000))
+    specs, pbs = _problems(dev, n=len(methods), seed=41, vis_range=(2000, 6000))
     jobs, refs = [], []
-    for d, pb in zip(specs, pbs):
-        plan = pb.plan.replace(trunc_frac=0.0, grid_method=3, grid_tile=64)
+    for d, pb, m in zip(specs, pbs, methods):
+        plan = pb.plan.replace(trunc_frac=0.0, grid_method=m, grid_tile=64)
         planes = o.mean_w_planes(d["uvw"][:, 2].astype(np.float64), d["P"])
         wk = wp.make_wkernels(plan, pb.taper, planes, supports=[min(5, d["max_support"])] * d["P"])
         ws = wp.workspace(wp.grid_workspace_bytes(plan, wk.P, pb.vis.numel()), dev)
