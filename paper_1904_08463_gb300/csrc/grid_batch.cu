@@ -26,6 +26,9 @@ namespace wp {
 namespace {
 constexpr int SCATTER_CHUNK = GRID_WARPS * 32 * 8;   // visibilities per scatter work item
 constexpr long long WAIT_BUDGET = 1LL << 31;         // SM clock cycles (~1 s)
+// batch control words: [0] row-owned queue head, [1] status, [2 .. 2 + MAX) finished producer
+// chunks per job, [2 + MAX] slot queue head, [BATCH_PRE ..) the four job prefixes
+constexpr int BATCH_PRE = 3 + WP_GRID_BATCH_MAX_JOBS + 1;
 }  // namespace
 
 struct BatchJob {
@@ -56,34 +59,84 @@ struct BatchTable {
     BatchJob j[WP_GRID_BATCH_MAX_JOBS];
 };
 
+// Bounded wait (one thread) until *done reaches `need` producer chunks; false -- with
+// WP_ERR_TIMEOUT recorded -- once the clock budget runs out or another wait already failed.
+// The acquire fence orders the job's records after its count.
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Polls with plain acquire loads (no read-modify-write: hundreds of blocks polling one counter
+// must not queue at its L2 slice ahead of the producers' increments) and backs off from 64 ns
+// to 4 us between polls.
+__device__ __forceinline__ int wait_done(int* done, int need, int* status, long long budget) {
+    if (ld_acquire(done) >= need) return 1;
+    int ok = 1;
+    unsigned ns = 64;
+    const long long t0 = clock64();
+    while (ld_acquire(done) < need) {
+        if (clock64() - t0 > budget || ld_acquire(status) != 0) {
+            atomicMin(status, WP_ERR_TIMEOUT);
+            ok = 0;
+            break;
+        }
+        __nanosleep(ns);
+        ns = ns < 4096 ? 2 * ns : 4096;
+    }
+    __threadfence();
+    return ok;
+}
+
 // ctrl layout: [0] queue head, [1] status, [2 .. 2 + n_jobs) finished scatter chunks per job
-// HAS_RO / HAS_SLOT: which kinds of job the batch holds (the row-owned tile's shared memory and
-// the slot code's registers are only paid for when used).
-template <int TILE, bool HAS_RO, bool HAS_SLOT>
-__global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_batch(const __grid_constant__ BatchTable tab, int n_jobs,
-                                                                int* __restrict__ bctrl, long long budget,
-                                                                int withhold_scatter) {
-    static_assert(SLOT_WARPS == GRID_WARPS, "a slot unit is one item per warp of the block");
-    __shared__ float2 tile[HAS_RO ? TILE * TILE : 1];
+// Job prefixes of both kernels' queues, once per batch (one warp): producer chunks and gridding
+// work of every job, counted where the binning left them on the device.  Layout after the
+// counters: pre[0 .. 4][n_jobs + 1] = row-owned chunks, row-owned items, slot chunks, slot items.
+constexpr int SLOT_GATHER = 32 * 32;     // sorted positions per gather work unit (one warp)
+
+__global__ void k_batch_prefix(const __grid_constant__ BatchTable tab, int n_jobs, int* __restrict__ pre) {
+    if (threadIdx.x != 0) return;
+    int a = 0, b = 0, c = 0, d = 0;
+    for (int k = 0; k <= n_jobs; ++k) {
+        pre[k] = a;
+        pre[(n_jobs + 1) + k] = b;
+        pre[2 * (n_jobs + 1) + k] = c;
+        pre[3 * (n_jobs + 1) + k] = d;
+        if (k == n_jobs) break;
+        const BatchJob& J = tab.j[k];
+        if (J.mode == 9) {
+            c += (int)((J.V + SLOT_GATHER - 1) / SLOT_GATHER);
+            d += J.istart[J.P];
+        } else {
+            a += J.n_sc;
+            b += J.ctrl[1];
+        }
+    }
+}
+
+// largest k in [0, n_jobs) with pre[k] <= idx (pre ascending, pre[0] = 0 <= idx)
+__device__ __forceinline__ int job_of(const int* __restrict__ pre, int n_jobs, int idx) {
+    int lo = 0, hi = n_jobs;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(pre + mid) <= idx) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Row-owned jobs: block-level work (a scatter chunk, or one (plane, tile) item per block).
+template <int TILE>
+__global__ void __launch_bounds__(GRID_WARPS * 32, 6) k_grid_batch_ro(const __grid_constant__ BatchTable tab, int n_jobs,
+                                                                   int* __restrict__ bctrl, long long budget,
+                                                                   int withhold_scatter) {
+    __shared__ float2 tile[TILE * TILE];
     __shared__ int l_off[RO_LIST];
     __shared__ uint32_t l_geo[RO_LIST];
     __shared__ float2 l_vv[RO_LIST];
     __shared__ int s_idx, s_n, s_ok;
-    __shared__ int pre_sc[WP_GRID_BATCH_MAX_JOBS + 1];   // prefix of scatter chunks
-    __shared__ int pre_gi[WP_GRID_BATCH_MAX_JOBS + 1];   // prefix of gridding items
-    if (threadIdx.x == 0) {
-        int a = 0, b = 0;
-        for (int k = 0; k < n_jobs; ++k) {
-            pre_sc[k] = a;
-            pre_gi[k] = b;
-            a += tab.j[k].n_sc;
-            // consumer units: one row-owned item, or one slot item per warp of the block
-            b += (tab.j[k].mode == 9) ? (tab.j[k].istart[tab.j[k].P] + SLOT_WARPS - 1) / SLOT_WARPS
-                                      : tab.j[k].ctrl[1];
-        }
-        pre_sc[n_jobs] = a;
-        pre_gi[n_jobs] = b;
-    }
+    const int* pre_sc = bctrl + BATCH_PRE;                    // prefix of scatter chunks
+    const int* pre_gi = pre_sc + (n_jobs + 1);                // prefix of gridding items
     for (int i = threadIdx.x; i < TILE * TILE; i += blockDim.x) tile[i] = make_float2(0.0f, 0.0f);
     __syncthreads();
     const int n_sc = pre_sc[n_jobs], n_gi = pre_gi[n_jobs];
@@ -97,26 +150,18 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_batch(const __grid_con
         if (idx >= n_sc + n_gi) break;
         if (idx < n_sc) {
             // ---- scatter chunk: records and weighted values into bin order
-            int jb = 0;
-            while (jb + 1 < n_jobs && pre_sc[jb + 1] <= idx) ++jb;
+            const int jb = job_of(pre_sc, n_jobs, idx);
             const BatchJob& J = tab.j[jb];
             if (withhold_scatter) continue;       // self-test: the chunk is never done
             const int64_t k0 = (int64_t)(idx - pre_sc[jb]) * SCATTER_CHUNK;
-            if (HAS_SLOT && J.mode == 9) {
-                // gather: sorted position i takes its record and weighted value
-                const int64_t n_kept = J.vstart[J.P];
-                for (int64_t i = k0 + threadIdx.x; i < min(n_kept, k0 + SCATTER_CHUNK); i += blockDim.x)
-                    slot_gather_one(i, J.os, J.s_max, J.sidx, J.rec, J.seff, J.vis, J.weight, J.srec, J.svis);
-            } else if (HAS_RO) {
-                for (int64_t k = k0 + threadIdx.x; k < min(J.V, k0 + SCATTER_CHUNK); k += blockDim.x) {
-                    const int kk = J.key[k];
-                    if (kk < 0) continue;
-                    const int pos = J.start[kk] + atomicAdd(&J.cursor[kk], 1);
-                    J.srec[pos] = J.rec[k];
-                    const float2 v = J.vis[k];
-                    const float a = J.weight ? J.weight[k] : 1.0f;
-                    J.svis[pos] = make_float2(v.x * a, v.y * a);
-                }
+            for (int64_t k = k0 + threadIdx.x; k < min(J.V, k0 + SCATTER_CHUNK); k += blockDim.x) {
+                const int kk = J.key[k];
+                if (kk < 0) continue;
+                const int pos = J.start[kk] + atomicAdd(&J.cursor[kk], 1);
+                J.srec[pos] = J.rec[k];
+                const float2 v = J.vis[k];
+                const float a = J.weight ? J.weight[k] : 1.0f;
+                J.svis[pos] = make_float2(v.x * a, v.y * a);
             }
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -126,36 +171,58 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid_batch(const __grid_con
         } else {
             // ---- gridding item: wait (bounded) for the job's scatter, then the row-owned tile
             const int g = idx - n_sc;
-            int jb = 0;
-            while (jb + 1 < n_jobs && pre_gi[jb + 1] <= g) ++jb;
+            const int jb = job_of(pre_gi, n_jobs, g);
             const BatchJob& J = tab.j[jb];
-            if (threadIdx.x == 0) {
-                int ok = 1;
-                const long long t0 = clock64();
-                while (atomicAdd(&done[jb], 0) < J.n_sc) {
-                    // after one expiry the batch has failed: later items give up at once
-                    if (clock64() - t0 > budget || atomicAdd(status, 0) != 0) {
-                        atomicMin(status, WP_ERR_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(256);
-                }
-                __threadfence();                  // the job's records after its count
-                s_ok = ok;
-            }
+            if (threadIdx.x == 0) s_ok = wait_done(&done[jb], J.n_sc, status, budget);
             __syncthreads();
             if (!s_ok) continue;
-            if (HAS_SLOT && J.mode == 9) {
-                const int it = (g - pre_gi[jb]) * SLOT_WARPS + (int)(threadIdx.x >> 5);
-                if (it < J.istart[J.P])
-                    slot_item<SLOT_ROWS, true>(it, J.N, J.P, J.s_max, J.seff, J.offsets, J.cache, J.vstart,
-                                               J.istart, J.srec, J.svis, J.grid);
-            } else if (HAS_RO) {
-                const int item = J.items[g - pre_gi[jb]];
-                ro_item<TILE, true>(item, J.N, J.os, J.s_max, J.ntx, J.ntiles, J.seff, J.offsets, J.cache, J.start,
-                                    J.srec, J.svis, J.grid, tile, l_off, l_geo, l_vv, &s_n);
+            const int item = J.items[g - pre_gi[jb]];
+            ro_item<TILE, true>(item, J.N, J.os, J.s_max, J.ntx, J.ntiles, J.seff, J.offsets, J.cache, J.start,
+                                J.srec, J.svis, J.grid, tile, l_off, l_geo, l_vv, &s_n);
+        }
+    }
+}
+
+// Slot jobs: warp-level work from the same kind of queue -- a gather chunk (SLOT_GATHER sorted
+// positions), or one slot item -- so that no warp waits for the others of its block.
+
+__global__ void __launch_bounds__(SLOT_WARPS * 32, 3) k_grid_batch_slot(const __grid_constant__ BatchTable tab,
+                                                                        int n_jobs, int* __restrict__ bctrl,
+                                                                        long long budget, int withhold_gather) {
+    const int* pre_sc = bctrl + BATCH_PRE + 2 * (n_jobs + 1);  // prefix of gather chunks
+    const int* pre_gi = pre_sc + (n_jobs + 1);                // prefix of slot items
+    const int lane = threadIdx.x & 31;
+    const int n_sc = pre_sc[n_jobs], n_gi = pre_gi[n_jobs];
+    int* head = bctrl + 2 + WP_GRID_BATCH_MAX_JOBS;
+    int* status = bctrl + 1;
+    int* done = bctrl + 2;
+    for (;;) {
+        int idx = 0;
+        if (lane == 0) idx = atomicAdd(head, 1);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= n_sc + n_gi) break;
+        if (idx < n_sc) {
+            const int jb = job_of(pre_sc, n_jobs, idx);
+            const BatchJob& J = tab.j[jb];
+            if (withhold_gather) continue;        // self-test: the chunk is never done
+            const int64_t i0 = (int64_t)(idx - pre_sc[jb]) * SLOT_GATHER;
+            const int64_t n_kept = J.vstart[J.P];
+            for (int64_t i = i0 + lane; i < min(n_kept, i0 + SLOT_GATHER); i += 32)
+                slot_gather_one(i, J.os, J.s_max, J.sidx, J.rec, J.seff, J.vis, J.weight, J.srec, J.svis);
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();                  // the chunk's writes before its count
+                atomicAdd(&done[jb], 1);
             }
+        } else {
+            const int g = idx - n_sc;
+            const int jb = job_of(pre_gi, n_jobs, g);
+            const BatchJob& J = tab.j[jb];
+            int ok = 0;
+            if (lane == 0) ok = wait_done(&done[jb], (int)((J.V + SLOT_GATHER - 1) / SLOT_GATHER), status, budget);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) continue;
+            slot_item<SLOT_ROWS, true>(g - pre_gi[jb], J.N, J.P, J.s_max, J.seff, J.offsets, J.cache, J.vstart,
+                                       J.istart, J.srec, J.svis, J.grid);
         }
     }
 }
@@ -169,7 +236,9 @@ __global__ void __launch_bounds__(256) k_item_write_pos(int64_t n, const int* __
     if (it == n - 1) ctrl[1] = pos[n];
 }
 
-size_t grid_batch_ctrl_bytes() { return (size_t)(2 + WP_GRID_BATCH_MAX_JOBS) * sizeof(int) + 256; }
+size_t grid_batch_ctrl_bytes() {
+    return (size_t)(BATCH_PRE + 4 * (WP_GRID_BATCH_MAX_JOBS + 1)) * sizeof(int) + 256;
+}
 
 // Binning of one job up to its item list (no scatter); the batch kernel scatters.
 int grid_batch_prepare(const Geom& g, const wp_wkernels* kern, const float* uvw, const float* weight, int64_t V,
@@ -223,21 +292,31 @@ int grid_batch_run(int n_jobs, const Geom* geoms, const wp_wkernels* kerns, cons
         J.grid = reinterpret_cast<float2*>(grids[k]);
     }
     int* bctrl = static_cast<int*>(bws);
-    WP_CUDA(cudaMemsetAsync(bctrl, 0, (size_t)(2 + n_jobs) * sizeof(int), st));
+    WP_CUDA(cudaMemsetAsync(bctrl, 0, (size_t)BATCH_PRE * sizeof(int), st));
+    k_batch_prefix<<<1, 32, 0, st>>>(tab, n_jobs, bctrl + BATCH_PRE);
+    WP_LAUNCH_CHECK("k_batch_prefix");
     int dev = 0, sms = 0, per_sm = 0;
     WP_CUDA(cudaGetDevice(&dev));
     WP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-#define WP_LAUNCH_BATCH(T, R, S)                                                                               \
-    do {                                                                                                       \
-        WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_batch<T, R, S>, GRID_WARPS * 32, 0)); \
-        if (per_sm < 1) per_sm = 1;                                                                            \
-        k_grid_batch<T, R, S><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(tab, n_jobs, bctrl, budget, withhold); \
-    } while (0)
-    if (!has_ro) WP_LAUNCH_BATCH(64, false, true);
-    else if (tile == 32) { if (has_slot) WP_LAUNCH_BATCH(32, true, true); else WP_LAUNCH_BATCH(32, true, false); }
-    else { if (has_slot) WP_LAUNCH_BATCH(64, true, true); else WP_LAUNCH_BATCH(64, true, false); }
-#undef WP_LAUNCH_BATCH
-    WP_LAUNCH_CHECK("k_grid_batch");
+    // the row-owned jobs first, then the slot jobs, each kernel with its own queue over its jobs
+    if (has_ro) {
+        if (tile == 32) {
+            WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_batch_ro<32>, GRID_WARPS * 32, 0));
+            if (per_sm < 1) per_sm = 1;
+            k_grid_batch_ro<32><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(tab, n_jobs, bctrl, budget, withhold);
+        } else {
+            WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_batch_ro<64>, GRID_WARPS * 32, 0));
+            if (per_sm < 1) per_sm = 1;
+            k_grid_batch_ro<64><<<sms * per_sm, GRID_WARPS * 32, 0, st>>>(tab, n_jobs, bctrl, budget, withhold);
+        }
+        WP_LAUNCH_CHECK("k_grid_batch_ro");
+    }
+    if (has_slot) {
+        WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_batch_slot, SLOT_WARPS * 32, 0));
+        if (per_sm < 1) per_sm = 1;
+        k_grid_batch_slot<<<sms * per_sm, SLOT_WARPS * 32, 0, st>>>(tab, n_jobs, bctrl, budget, withhold);
+    }
+    WP_LAUNCH_CHECK("k_grid_batch_slot");
     return WP_OK;
 }
 
