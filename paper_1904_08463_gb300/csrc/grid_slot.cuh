@@ -77,15 +77,22 @@ __device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const
     const bool a_ok = a < W;
     const int b0 = tys * ROWS;                // slot rows b0 .. b0 + ROWS - 1
     const int nrows = min(ROWS, W - b0);      // rows of this tile inside the W x W residues
+    // Slot (lane, j) has the tap (jx, jy[j]) of the current footprint and sums the cell
+    // (x0 + jx, y0 + jy[j]).  A move of the footprint corner by (dx, dy), |dx|, |dy| < W, changes
+    // the lane's column only if jx - dx leaves [0, W) (the cell moves by one period) and row j's
+    // only if jy[j] - dy does; every other slot keeps its cell and shifts its tap offset.  Larger
+    // moves recompute everything.
     float2 acc[ROWS];
-    uint32_t held[ROWS];
-    int toff[ROWS];
+    int jy[ROWS];
+    unsigned toff[ROWS];                      // byte offset of the slot's tap in its sub-kernel
 #pragma unroll
     for (int j = 0; j < ROWS; ++j) {
         acc[j] = make_float2(0.0f, 0.0f);
-        held[j] = 0xffffffffu;
+        jy[j] = 0;
         toff[j] = 0;
     }
+    int jx = 0;
+    int x0p = -1, y0p = -1;                   // corner of the previous footprint (none yet)
     uint32_t prev = 0xffffffffu;              // no footprint corner packs to this
     int4 rn = ld_slot_rec<COHERENT>(srec + v0);
     float2 vn = ld_slot_vis<COHERENT>(svis + v0);
@@ -96,35 +103,57 @@ __device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const
             rn = ld_slot_rec<COHERENT>(srec + q + 1);
             vn = ld_slot_vis<COHERENT>(svis + q + 1);
         }
-        if ((uint32_t)r.x != prev) {          // the footprint moved: new cells for the slots
+        if ((uint32_t)r.x != prev) {          // the footprint moved: new cells for some slots
             prev = (uint32_t)r.x;
             const int x0 = r.x & 0xffff, y0 = (r.x >> 16) & 0xffff;
-            const int xm = r.y & 0xffff, ym = (r.y >> 16) & 0xffff;
-            int jx = a - xm;
-            jx += (jx < 0) ? W : 0;
-            const uint32_t xc = (uint32_t)(x0 + jx);
-            jx = a_ok ? jx : 0;
+            const int dx = x0 - x0p, dy = y0 - y0p;
+            if (x0p < 0 || dx >= W || dx <= -W || dy >= W || dy <= -W) {
+                // first footprint or a long jump: every slot flushes and starts over
+                const int xm = r.y & 0xffff, ym = (r.y >> 16) & 0xffff;
 #pragma unroll
-            for (int j = 0; j < ROWS; ++j) {
-                int jy = b0 + j - ym;
-                jy += (jy < 0) ? W : 0;
-                const uint32_t cell = xc | ((uint32_t)(y0 + jy) << 16);
-                const bool ok = a_ok && j < nrows;
-                if (cell != held[j]) {
-                    if (ok && (acc[j].x != 0.0f || acc[j].y != 0.0f))
-                        atomicAdd(grid + (int64_t)(held[j] >> 16) * N + (held[j] & 0xffffu), acc[j]);
+                for (int j = 0; j < ROWS; ++j) {
+                    if (a_ok && j < nrows && (acc[j].x != 0.0f || acc[j].y != 0.0f))
+                        atomicAdd(grid + (int64_t)(y0p + jy[j]) * N + (x0p + jx), acc[j]);
                     acc[j] = make_float2(0.0f, 0.0f);
-                    held[j] = cell;
                 }
-                toff[j] = j < nrows ? jy * W + jx : 0;
+                int nx = a - xm;
+                nx += (nx < 0) ? W : 0;
+                jx = a_ok ? nx : 0;
+#pragma unroll
+                for (int j = 0; j < ROWS; ++j) {
+                    int ny = b0 + j - ym;
+                    ny += (ny < 0) ? W : 0;
+                    jy[j] = j < nrows ? ny : 0;
+                    toff[j] = (unsigned)(jy[j] * W + jx) * 8u;
+                }
+            } else {
+                int nx = jx - dx;
+                const bool xw = nx < 0 || nx >= W;            // the lane's column changes period
+                nx += (nx < 0) ? W : ((nx >= W) ? -W : 0);
+#pragma unroll
+                for (int j = 0; j < ROWS; ++j) {
+                    int ny = jy[j] - dy;
+                    const bool yw = ny < 0 || ny >= W;        // row j changes period
+                    ny += (ny < 0) ? W : ((ny >= W) ? -W : 0);
+                    if (xw || yw) {
+                        if (a_ok && j < nrows && (acc[j].x != 0.0f || acc[j].y != 0.0f))
+                            atomicAdd(grid + (int64_t)(y0p + jy[j]) * N + (x0p + jx), acc[j]);
+                        acc[j] = make_float2(0.0f, 0.0f);
+                    }
+                    jy[j] = ny;
+                    toff[j] = (unsigned)(ny * W + nx) * 8u;
+                }
+                jx = nx;
             }
+            x0p = x0;
+            y0p = y0;
         }
         const float2* sub = pc + (r.z & 0x7fffffff);
         const float sg = (r.z < 0) ? -1.0f : 1.0f;
         const float cA = v.x, cB = -sg * v.y, cC = sg * v.x, cD = v.y;
         float2 tp[ROWS];
 #pragma unroll
-        for (int j = 0; j < ROWS; ++j) tp[j] = __ldg(sub + toff[j]);
+        for (int j = 0; j < ROWS; ++j) tp[j] = __ldg(reinterpret_cast<const float2*>(reinterpret_cast<const char*>(sub) + toff[j]));
 #pragma unroll
         for (int j = 0; j < ROWS; ++j) {
             acc[j].x = fmaf(cA, tp[j].x, fmaf(cB, tp[j].y, acc[j].x));
@@ -134,7 +163,7 @@ __device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const
 #pragma unroll
     for (int j = 0; j < ROWS; ++j)
         if (a_ok && j < nrows && (acc[j].x != 0.0f || acc[j].y != 0.0f))
-            atomicAdd(grid + (int64_t)(held[j] >> 16) * N + (held[j] & 0xffffu), acc[j]);
+            atomicAdd(grid + (int64_t)(y0p + jy[j]) * N + (x0p + jx), acc[j]);
 }
 
 }  // namespace wp
