@@ -82,6 +82,14 @@ __device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const
     // the lane's column only if jx - dx leaves [0, W) (the cell moves by one period) and row j's
     // only if jy[j] - dy does; every other slot keeps its cell and shifts its tap offset.  Larger
     // moves recompute everything.
+    // Slot (lane, j) has the tap (jx, jy[j]) of the current footprint and sums the cell
+    // (x0 + jx, y0 + jy[j]).  A move of the footprint corner by (dx, dy), |dx|, |dy| < W, changes
+    // the lane's column only if jx - dx leaves [0, W) (the cell moves by one period) and row j's
+    // only if jy[j] - dy does; every other slot keeps its cell and shifts its tap offset.  Larger
+    // moves recompute everything.  Lanes and rows beyond the W x W residues track the residue
+    // a mod W (b mod W) of a slot that exists, so that every tap offset is always inside the
+    // sub-kernel; they are never flushed.
+    const int a_res = a % W;
     float2 acc[ROWS];
     int jy[ROWS];
     unsigned toff[ROWS];                      // byte offset of the slot's tap in its sub-kernel
@@ -116,16 +124,29 @@ __device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const
                         atomicAdd(grid + (int64_t)(y0p + jy[j]) * N + (x0p + jx), acc[j]);
                     acc[j] = make_float2(0.0f, 0.0f);
                 }
-                int nx = a - xm;
+                int nx = a_res - xm;
                 nx += (nx < 0) ? W : 0;
-                jx = a_ok ? nx : 0;
+                jx = nx;
 #pragma unroll
                 for (int j = 0; j < ROWS; ++j) {
-                    int ny = b0 + j - ym;
+                    int ny = (b0 + j) % W - ym;
                     ny += (ny < 0) ? W : 0;
-                    jy[j] = j < nrows ? ny : 0;
-                    toff[j] = (unsigned)(jy[j] * W + jx) * 8u;
+                    jy[j] = ny;
+                    toff[j] = (unsigned)(ny * W + nx) * 8u;
                 }
+            } else if (!__any_sync(0xffffffffu, jx - dx < 0 || jx - dx >= W ||
+                                                 (lane < ROWS && (jy[0] + lane >= W || jy[0] + lane - dy < 0 ||
+                                                                  jy[0] + lane - dy >= W)))) {
+                // no slot of this warp changes its cell: row j's tap row is jy[0] + j here (a
+                // tile whose rows pass W counts as a change above), and every tap offset shifts
+                // by the same amount
+                const unsigned d = (unsigned)(dy * W + dx) * 8u;
+#pragma unroll
+                for (int j = 0; j < ROWS; ++j) {
+                    jy[j] -= dy;
+                    toff[j] -= d;
+                }
+                jx -= dx;
             } else {
                 int nx = jx - dx;
                 const bool xw = nx < 0 || nx >= W;            // the lane's column changes period
