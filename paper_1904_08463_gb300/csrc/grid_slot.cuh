@@ -18,7 +18,7 @@
 
 namespace wp {
 
-constexpr int SLOT_ROWS = 8;         // slot rows per lane (registers: sum, cell, tap offset each)
+constexpr int SLOT_ROWS = 10;        // slot rows per lane (registers: sum, tap row, tap offset each)
 constexpr int SLOT_CHUNK = 512;      // visibilities per work item
 constexpr int SLOT_WARPS = 8;        // warps per block
 
