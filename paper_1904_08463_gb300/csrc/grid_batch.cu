@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(GRID_WARPS * 32, 6) k_grid_batch_ro(const __gr
 // Slot jobs: warp-level work from the same kind of queue -- a gather chunk (SLOT_GATHER sorted
 // positions), or one slot item -- so that no warp waits for the others of its block.
 
-__global__ void __launch_bounds__(SLOT_WARPS * 32, 4) k_grid_batch_slot(const __grid_constant__ BatchTable tab,
+__global__ void __launch_bounds__(SLOT_WARPS * 32, 3) k_grid_batch_slot(const __grid_constant__ BatchTable tab,
                                                                         int n_jobs, int* __restrict__ bctrl,
                                                                         long long budget, int withhold_gather) {
     const int* pre_sc = bctrl + BATCH_PRE + 2 * (n_jobs + 1);  // prefix of gather chunks
