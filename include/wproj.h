@@ -353,7 +353,9 @@ int wp_grid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw,
 /*
  * Degridding, the adjoint of wp_grid with unit weights:
  *   vis_out[k] = sum_taps conj(K) grid[iv - S + jy][iu - S + jx]   (0 if dropped)
- * Same binning rules and workspace as wp_grid.
+ * Same binning rules and workspace as wp_grid.  plan.grid_method 9 walks the slots (each holds
+ * the grid value of its cell and reloads it only when the cell changes); any other value uses a
+ * warp per visibility.  The results agree to FP32 summation order.
  */
 int wp_degrid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw,
               const float* grid, int64_t V, void* workspace, size_t workspace_bytes,

@@ -528,6 +528,9 @@ int wp_degrid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw,
     cudaStream_t st = (cudaStream_t)stream;
     GridWork w;
     carve_grid(g, kernels->P, V, workspace, workspace_bytes, &w);
+    if (g.grid_method == 9)      // slot degridder: the adjoint walk over Morton-sorted planes
+        return degrid_slot(g, kernels, uvw, V, w, reinterpret_cast<const float2*>(grid),
+                           reinterpret_cast<float2*>(vis_out), st);
     if ((rc = grid_bin(g, kernels, uvw, nullptr, nullptr, V, w, st))) return rc;
     return degrid_run(g, kernels, V, w, reinterpret_cast<const float2*>(grid),
                       reinterpret_cast<float2*>(vis_out), st);

@@ -138,6 +138,31 @@ __global__ void __launch_bounds__(SLOT_WARPS * 32, 4) k_grid_slot(int N, int P, 
     }
 }
 
+// Degridding with slots (grid_method 9): the adjoint walk -- each slot holds the grid value of
+// its cell, reloaded only when the cell changes; per visibility and slot tile the warp's sum of
+// conj(tap) x value is added into vis_out (zeroed first) by lane 0.
+template <int ROWS>
+__global__ void __launch_bounds__(SLOT_WARPS * 32, 4) k_degrid_slot(int N, int P, int s_max,
+                                                                    const int32_t* __restrict__ support,
+                                                                    const int64_t* __restrict__ offsets,
+                                                                    const float2* __restrict__ cache,
+                                                                    const int* __restrict__ vstart,
+                                                                    const int* __restrict__ istart,
+                                                                    const int4* __restrict__ srec,
+                                                                    const float2* __restrict__ grid,
+                                                                    int* __restrict__ ctrl, float2* __restrict__ vis_out) {
+    const int lane = threadIdx.x & 31;
+    const int n_items = istart[P];
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(&ctrl[0], 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+        slot_walk<ROWS, false, true>(it, N, P, s_max, support, offsets, cache, vstart, istart, srec, nullptr,
+                                     const_cast<float2*>(grid), vis_out);
+    }
+}
+
 static int bits_for(int64_t n) {       // bits to hold values 0 .. n - 1 (at least 1)
     int b = 1;
     while (((int64_t)1 << b) < n) ++b;
@@ -202,6 +227,29 @@ int grid_slot_prepare(const Geom& g, const wp_wkernels* kern, const float* uvw, 
     rc = exclusive_scan_i32(w.icount, w.istart, (int64_t)P + 1, w.scan_tmp, st);
     if (rc) return rc;
     *idx_sorted = idx;
+    return WP_OK;
+}
+
+int degrid_slot(const Geom& g, const wp_wkernels* kern, const float* uvw, int64_t V, const GridWork& w,
+                const float2* grid, float2* vis_out, cudaStream_t st) {
+    const int P = kern->P;
+    WP_CUDA(cudaMemsetAsync(vis_out, 0, sizeof(float2) * (size_t)V, st));
+    const uint32_t* idx = nullptr;
+    int rc = grid_slot_prepare(g, kern, uvw, nullptr, V, w, st, &idx);
+    if (rc) return rc;
+    if (V == 0) return WP_OK;
+    k_gather_slot<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(V, g.os, g.s_max, w.vstart, P, idx, w.rec, w.seff,
+                                                               nullptr, nullptr, w.srec, nullptr);
+    WP_LAUNCH_CHECK("k_gather_slot");
+    int dev = 0, sms = 0, per_sm = 0;
+    WP_CUDA(cudaGetDevice(&dev));
+    WP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid_slot<SLOT_ROWS>, SLOT_WARPS * 32, 0));
+    if (per_sm < 1) per_sm = 1;
+    k_degrid_slot<SLOT_ROWS><<<sms * per_sm, SLOT_WARPS * 32, 0, st>>>(g.N, P, g.s_max, w.seff, kern->offsets,
+                                                            reinterpret_cast<const float2*>(kern->cache), w.vstart,
+                                                            w.istart, w.srec, grid, w.ctrl, vis_out);
+    WP_LAUNCH_CHECK("k_degrid_slot");
     return WP_OK;
 }
 

@@ -50,12 +50,16 @@ __device__ __forceinline__ void slot_gather_one(int64_t i, int os, int s_max, co
     }
 }
 
-template <int ROWS, bool COHERENT>
-__device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const int32_t* __restrict__ support,
+// DEGRID = false: gridding (each slot sums V x tap into its cell and flushes the sum to `grid`
+// when the cell changes).  DEGRID = true: degridding, the adjoint (each slot holds the value of
+// `grid` at its cell, reloaded when the cell changes; per visibility the warp sums conj(tap) x
+// value over its slots and adds the sum into vis_out[original index]; svis is not read).
+template <int ROWS, bool COHERENT, bool DEGRID>
+__device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const int32_t* __restrict__ support,
                                           const int64_t* __restrict__ offsets, const float2* __restrict__ cache,
                                           const int* __restrict__ vstart, const int* __restrict__ istart,
                                           const int4* __restrict__ srec, const float2* __restrict__ svis,
-                                          float2* __restrict__ grid) {
+                                          float2* __restrict__ grid, float2* __restrict__ vis_out) {
     const int lane = threadIdx.x & 31;
     int lo = 0, hi = P;                       // largest plane with istart <= it
     while (hi - lo > 1) {
@@ -77,11 +81,13 @@ __device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const
     const bool a_ok = a < W;
     const int b0 = tys * ROWS;                // slot rows b0 .. b0 + ROWS - 1
     const int nrows = min(ROWS, W - b0);      // rows of this tile inside the W x W residues
+    // (for DEGRID, acc[j] holds the grid value at the slot's cell instead of a running sum)
     // Slot (lane, j) has the tap (jx, jy[j]) of the current footprint and sums the cell
     // (x0 + jx, y0 + jy[j]).  A move of the footprint corner by (dx, dy), |dx|, |dy| < W, changes
     // the lane's column only if jx - dx leaves [0, W) (the cell moves by one period) and row j's
     // only if jy[j] - dy does; every other slot keeps its cell and shifts its tap offset.  Larger
     // moves recompute everything.
+    // (for DEGRID, acc[j] holds the grid value at the slot's cell instead of a running sum)
     // Slot (lane, j) has the tap (jx, jy[j]) of the current footprint and sums the cell
     // (x0 + jx, y0 + jy[j]).  A move of the footprint corner by (dx, dy), |dx|, |dy| < W, changes
     // the lane's column only if jx - dx leaves [0, W) (the cell moves by one period) and row j's
@@ -103,26 +109,28 @@ __device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const
     int x0p = -1, y0p = -1;                   // corner of the previous footprint (none yet)
     uint32_t prev = 0xffffffffu;              // no footprint corner packs to this
     int4 rn = ld_slot_rec<COHERENT>(srec + v0);
-    float2 vn = ld_slot_vis<COHERENT>(svis + v0);
+    float2 vn = DEGRID ? make_float2(0.0f, 0.0f) : ld_slot_vis<COHERENT>(svis + v0);
     for (int q = v0; q < v1; ++q) {
         const int4 r = rn;
         const float2 v = vn;
         if (q + 1 < v1) {                     // the next record while this one's taps load
             rn = ld_slot_rec<COHERENT>(srec + q + 1);
-            vn = ld_slot_vis<COHERENT>(svis + q + 1);
+            if (!DEGRID) vn = ld_slot_vis<COHERENT>(svis + q + 1);
         }
         if ((uint32_t)r.x != prev) {          // the footprint moved: new cells for some slots
             prev = (uint32_t)r.x;
             const int x0 = r.x & 0xffff, y0 = (r.x >> 16) & 0xffff;
             const int dx = x0 - x0p, dy = y0 - y0p;
             if (x0p < 0 || dx >= W || dx <= -W || dy >= W || dy <= -W) {
-                // first footprint or a long jump: every slot flushes and starts over
+                // first footprint or a long jump: every slot flushes (gridding) and starts over
                 const int xm = r.y & 0xffff, ym = (r.y >> 16) & 0xffff;
+                if (!DEGRID) {
 #pragma unroll
-                for (int j = 0; j < ROWS; ++j) {
-                    if (a_ok && j < nrows && (acc[j].x != 0.0f || acc[j].y != 0.0f))
-                        atomicAdd(grid + (int64_t)(y0p + jy[j]) * N + (x0p + jx), acc[j]);
-                    acc[j] = make_float2(0.0f, 0.0f);
+                    for (int j = 0; j < ROWS; ++j) {
+                        if (a_ok && j < nrows && (acc[j].x != 0.0f || acc[j].y != 0.0f))
+                            atomicAdd(grid + (int64_t)(y0p + jy[j]) * N + (x0p + jx), acc[j]);
+                        acc[j] = make_float2(0.0f, 0.0f);
+                    }
                 }
                 int nx = a_res - xm;
                 nx += (nx < 0) ? W : 0;
@@ -133,6 +141,8 @@ __device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const
                     ny += (ny < 0) ? W : 0;
                     jy[j] = ny;
                     toff[j] = (unsigned)(ny * W + nx) * 8u;
+                    if (DEGRID)
+                        acc[j] = (a_ok && j < nrows) ? __ldg(grid + (int64_t)(y0 + ny) * N + (x0 + nx)) : make_float2(0.0f, 0.0f);
                 }
             } else if (!__any_sync(0xffffffffu, jx - dx < 0 || jx - dx >= W ||
                                                  (lane < ROWS && (jy[0] + lane >= W || jy[0] + lane - dy < 0 ||
@@ -157,9 +167,13 @@ __device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const
                     const bool yw = ny < 0 || ny >= W;        // row j changes period
                     ny += (ny < 0) ? W : ((ny >= W) ? -W : 0);
                     if (xw || yw) {
-                        if (a_ok && j < nrows && (acc[j].x != 0.0f || acc[j].y != 0.0f))
-                            atomicAdd(grid + (int64_t)(y0p + jy[j]) * N + (x0p + jx), acc[j]);
-                        acc[j] = make_float2(0.0f, 0.0f);
+                        if (DEGRID) {
+                            if (a_ok && j < nrows) acc[j] = __ldg(grid + (int64_t)(y0 + ny) * N + (x0 + nx));
+                        } else {
+                            if (a_ok && j < nrows && (acc[j].x != 0.0f || acc[j].y != 0.0f))
+                                atomicAdd(grid + (int64_t)(y0p + jy[j]) * N + (x0p + jx), acc[j]);
+                            acc[j] = make_float2(0.0f, 0.0f);
+                        }
                     }
                     jy[j] = ny;
                     toff[j] = (unsigned)(ny * W + nx) * 8u;
@@ -171,20 +185,48 @@ __device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const
         }
         const float2* sub = pc + (r.z & 0x7fffffff);
         const float sg = (r.z < 0) ? -1.0f : 1.0f;
-        const float cA = v.x, cB = -sg * v.y, cC = sg * v.x, cD = v.y;
         float2 tp[ROWS];
 #pragma unroll
         for (int j = 0; j < ROWS; ++j) tp[j] = __ldg(reinterpret_cast<const float2*>(reinterpret_cast<const char*>(sub) + toff[j]));
+        if (DEGRID) {
+            // conj(K) x value, K conjugated for w < 0: (tx, s ty)* (gx, gy)
+            float sr = 0.0f, si = 0.0f;
 #pragma unroll
-        for (int j = 0; j < ROWS; ++j) {
-            acc[j].x = fmaf(cA, tp[j].x, fmaf(cB, tp[j].y, acc[j].x));
-            acc[j].y = fmaf(cC, tp[j].y, fmaf(cD, tp[j].x, acc[j].y));
+            for (int j = 0; j < ROWS; ++j) {
+                const float ti = sg * tp[j].y;
+                sr = fmaf(tp[j].x, acc[j].x, fmaf(ti, acc[j].y, sr));
+                si = fmaf(tp[j].x, acc[j].y, fmaf(-ti, acc[j].x, si));
+            }
+            for (int o = 16; o; o >>= 1) {
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                si += __shfl_xor_sync(0xffffffffu, si, o);
+            }
+            if (lane == 0 && (sr != 0.0f || si != 0.0f)) atomicAdd(vis_out + r.w, make_float2(sr, si));
+        } else {
+            const float cA = v.x, cB = -sg * v.y, cC = sg * v.x, cD = v.y;
+#pragma unroll
+            for (int j = 0; j < ROWS; ++j) {
+                acc[j].x = fmaf(cA, tp[j].x, fmaf(cB, tp[j].y, acc[j].x));
+                acc[j].y = fmaf(cC, tp[j].y, fmaf(cD, tp[j].x, acc[j].y));
+            }
         }
     }
+    if (!DEGRID) {
 #pragma unroll
-    for (int j = 0; j < ROWS; ++j)
-        if (a_ok && j < nrows && (acc[j].x != 0.0f || acc[j].y != 0.0f))
-            atomicAdd(grid + (int64_t)(y0p + jy[j]) * N + (x0p + jx), acc[j]);
+        for (int j = 0; j < ROWS; ++j)
+            if (a_ok && j < nrows && (acc[j].x != 0.0f || acc[j].y != 0.0f))
+                atomicAdd(grid + (int64_t)(y0p + jy[j]) * N + (x0p + jx), acc[j]);
+    }
+}
+
+template <int ROWS, bool COHERENT>
+__device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const int32_t* __restrict__ support,
+                                          const int64_t* __restrict__ offsets, const float2* __restrict__ cache,
+                                          const int* __restrict__ vstart, const int* __restrict__ istart,
+                                          const int4* __restrict__ srec, const float2* __restrict__ svis,
+                                          float2* __restrict__ grid) {
+    slot_walk<ROWS, COHERENT, false>(it, N, P, s_max, support, offsets, cache, vstart, istart, srec, svis, grid,
+                                     nullptr);
 }
 
 }  // namespace wp

@@ -43,12 +43,13 @@ def _oracle_loss(g, planes, sup, uvw, vobs, wt, img, taper):
     return float(np.sum(wt.astype(np.float64) * (r.real ** 2 + r.imag ** 2))), v
 
 
-def _gpu_grads(g, planes, sup, uvw, vobs, wt, img, taper):
+def _gpu_grads(g, planes, sup, uvw, vobs, wt, img, taper, grid_method=3):
     import paper_1904_08463_gb300 as wp
     from paper_1904_08463_gb300.autograd import Predictor, chi2
 
     dev = torch.device("cuda")
-    plan = wp.Plan(g.image_size, g.cell_size, g.oversampling, g.max_support, 1, 0.0, g.radial_samples)
+    plan = wp.Plan(g.image_size, g.cell_size, g.oversampling, g.max_support, 1, 0.0, g.radial_samples,
+                   grid_method=grid_method)
     pr = Predictor(plan, planes, sup, torch.tensor(uvw, device=dev))
     I = torch.tensor(img, device=dev, requires_grad=True)
     t = torch.tensor(taper, device=dev, requires_grad=True)
@@ -58,17 +59,21 @@ def _gpu_grads(g, planes, sup, uvw, vobs, wt, img, taper):
     return float(L.detach()), vis.detach().cpu().numpy(), I.grad.cpu().numpy(), t.grad.cpu().numpy()
 
 
-def test_forward_prediction_matches_oracle():
+@pytest.mark.parametrize("grid_method", [3, 9])
+def test_forward_prediction_matches_oracle(grid_method):
+    """Prediction (degridding of the model image's grid) by the warp-per-visibility degridder
+    (method 3's plan) and by the slot walk (method 9)."""
     g, planes, sup, uvw, vobs, wt, img, taper = _problem()
-    L, vis, _, _ = _gpu_grads(g, planes, sup, uvw, vobs, wt, img, taper)
+    L, vis, _, _ = _gpu_grads(g, planes, sup, uvw, vobs, wt, img, taper, grid_method)
     L0, v0 = _oracle_loss(g, planes, sup, uvw, vobs, wt, img, taper)
     assert np.abs(vis - v0).max() < 1e-4 * np.abs(v0).max()
     assert L == pytest.approx(L0, rel=1e-4)
 
 
-def test_image_gradient_matches_oracle_adjoint_and_finite_differences():
+@pytest.mark.parametrize("grid_method", [3, 9])
+def test_image_gradient_matches_oracle_adjoint_and_finite_differences(grid_method):
     g, planes, sup, uvw, vobs, wt, img, taper = _problem(1)
-    _, _, gI, _ = _gpu_grads(g, planes, sup, uvw, vobs, wt, img, taper)
+    _, _, gI, _ = _gpu_grads(g, planes, sup, uvw, vobs, wt, img, taper, grid_method)
     # oracle analytic gradient: dL/dI = Re(A^H gv), gv = 2 wt (V - Vobs): grid(gv) then the
     # dirty-image map (both adjoints in the oracle)
     _, v0 = _oracle_loss(g, planes, sup, uvw, vobs, wt, img, taper)

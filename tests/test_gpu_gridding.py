@@ -85,12 +85,13 @@ def test_grid_edges_and_conjugation(V, seed, grid_tile, grid_method):
         assert np.abs(Vd.cpu().numpy() - Vo).max() <= 2e-5 * max(np.abs(Vo).max(), 1e-30)
 
 
-def test_grid_degrid_adjoint_on_gpu():
+@pytest.mark.parametrize("grid_method", [0, 9])
+def test_grid_degrid_adjoint_on_gpu(grid_method):
     """<grid(V), X> = <V, degrid(X)> for the GPU operators (unit weights)."""
     N, dl = 128, np.deg2rad(4.0) / 128
     planes = np.linspace(0, 1000, 9)
     sup = np.arange(2, 11)
-    wp, dev, plan, g, taper, tap_d, wk, ks = _setup(N, dl, 8, 12, 256, planes, sup)
+    wp, dev, plan, g, taper, tap_d, wk, ks = _setup(N, dl, 8, 12, 256, planes, sup, grid_method=grid_method)
     rng = np.random.default_rng(9)
     V = 20000
     uvw = synth.uniform_disc_uvw(V, (N / 2 - 14) * g.du, 1000.0, 10)
