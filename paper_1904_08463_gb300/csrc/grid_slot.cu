@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256) k_plane_items(int P, int s_max, const int
 }
 
 template <int ROWS>
-__global__ void __launch_bounds__(SLOT_WARPS * 32, 4) k_grid_slot(int N, int P, int s_max,
+__global__ void __launch_bounds__(SLOT_WARPS * 32, 3) k_grid_slot(int N, int P, int s_max,
                                                                   const int32_t* __restrict__ support,
                                                                   const int64_t* __restrict__ offsets,
                                                                   const float2* __restrict__ cache,

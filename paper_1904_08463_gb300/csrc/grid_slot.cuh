@@ -21,6 +21,7 @@ namespace wp {
 constexpr int SLOT_ROWS = 10;        // slot rows per lane (registers: sum, tap row, tap offset each)
 constexpr int SLOT_CHUNK = 512;      // visibilities per work item
 constexpr int SLOT_WARPS = 8;        // warps per block
+constexpr bool SLOT_PAIR = false;    // gridding sums as two packed-FMA pairs (fma.rn.f32x2)
 
 template <bool COHERENT>
 __device__ __forceinline__ int4 ld_slot_rec(const int4* p) { return COHERENT ? __ldcg(p) : __ldg(p); }
@@ -47,6 +48,53 @@ __device__ __forceinline__ void slot_gather_one(int64_t i, int os, int s_max, co
         const float2 v = vis[k];
         const float a = weight ? weight[k] : 1.0f;
         svis[i] = make_float2(v.x * a, v.y * a);
+    }
+}
+
+// a running sum worth writing (either part non-zero; -0 counts as zero)
+__device__ __forceinline__ bool slot_nonzero(float2 a) {
+    return ((__float_as_uint(a.x) | __float_as_uint(a.y)) & 0x7fffffffu) != 0u;
+}
+
+// a + b x c on both halves of a pair in one instruction (IEEE fma, round to nearest, per half)
+__device__ __forceinline__ float2 ffma2(float2 b, float2 c, float2 a) {
+    unsigned long long d;
+    asm("{\n\t.reg .b64 pb, pc, pa;\n\tmov.b64 pb, {%1, %2};\n\tmov.b64 pc, {%3, %4};\n\tmov.b64 pa, {%5, %6};\n\t"
+        "fma.rn.f32x2 %0, pb, pc, pa;\n\t}"
+        : "=l"(d) : "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y), "f"(a.x), "f"(a.y));
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(d));
+    return r;
+}
+
+// The grid value of a slot's running sum.  SLOT_PAIR keeps P = sum (cA tx, cC ty) and
+// Q = sum (cD tx, cB ty) (two packed FMAs per tap); the sum is (P.x + Q.y, P.y + Q.x).
+__device__ __forceinline__ float2 slot_value(float2 p, float2 q) {
+    return SLOT_PAIR ? make_float2(p.x + q.y, p.y + q.x) : p;
+}
+
+// Places the slots for the footprint of record r (corner x0 | y0 << 16 in r.x, the corner mod W
+// in r.y): the lane's column cell cx, row `lane`'s cell row cyt (lanes < ROWS), every tap offset,
+// and the sums zeroed (gridding) or the cells' grid values read (DEGRID).
+template <int ROWS, bool DEGRID>
+__device__ __forceinline__ void slot_place(int4 r, int W, int N, int a_res, int b_res, int nval,
+                                           const float2* __restrict__ grid, int& cx, int& cyt, unsigned& cb, unsigned (&coff)[ROWS],
+                                           float2 (&acc)[ROWS], float2 (&acq)[ROWS]) {
+    const int x0 = r.x & 0xffff, y0 = (r.x >> 16) & 0xffff;
+    const int xm = r.y & 0xffff, ym = (r.y >> 16) & 0xffff;
+    int nx = a_res - xm;
+    nx += (nx < 0) ? W : 0;
+    int ny = b_res - ym;
+    ny += (ny < 0) ? W : 0;
+    cx = x0 + nx;
+    cyt = y0 + ny;
+    cb = (unsigned)(y0 * W + x0) * 8u;
+#pragma unroll
+    for (int j = 0; j < ROWS; ++j) {
+        const int cyj = __shfl_sync(0xffffffffu, cyt, j);
+        coff[j] = (unsigned)(cyj * W + cx) * 8u;
+        acc[j] = (DEGRID && j < nval) ? __ldg(grid + (int64_t)cyj * N + cx) : make_float2(0.0f, 0.0f);
+        acq[j] = make_float2(0.0f, 0.0f);
     }
 }
 
@@ -81,35 +129,31 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
     const bool a_ok = a < W;
     const int b0 = tys * ROWS;                // slot rows b0 .. b0 + ROWS - 1
     const int nrows = min(ROWS, W - b0);      // rows of this tile inside the W x W residues
-    // (for DEGRID, acc[j] holds the grid value at the slot's cell instead of a running sum)
-    // Slot (lane, j) has the tap (jx, jy[j]) of the current footprint and sums the cell
-    // (x0 + jx, y0 + jy[j]).  A move of the footprint corner by (dx, dy), |dx|, |dy| < W, changes
-    // the lane's column only if jx - dx leaves [0, W) (the cell moves by one period) and row j's
-    // only if jy[j] - dy does; every other slot keeps its cell and shifts its tap offset.  Larger
-    // moves recompute everything.
-    // (for DEGRID, acc[j] holds the grid value at the slot's cell instead of a running sum)
-    // Slot (lane, j) has the tap (jx, jy[j]) of the current footprint and sums the cell
-    // (x0 + jx, y0 + jy[j]).  A move of the footprint corner by (dx, dy), |dx|, |dy| < W, changes
-    // the lane's column only if jx - dx leaves [0, W) (the cell moves by one period) and row j's
-    // only if jy[j] - dy does; every other slot keeps its cell and shifts its tap offset.  Larger
-    // moves recompute everything.  Lanes and rows beyond the W x W residues track the residue
-    // a mod W (b mod W) of a slot that exists, so that every tap offset is always inside the
-    // sub-kernel; they are never flushed.
+    // Slot (lane, j) sums the cell (cx, cy[j]): column cx of the lane, row cy[j] of row j.  Its
+    // tap in the footprint with corner (x0, y0) is (cx - x0, cy[j] - y0), at byte offset
+    // ((cy[j] - y0) W + cx - x0) x 8 = coff[j] - cb of the sub-kernel, coff[j] = (cy[j] W + cx) x 8
+    // depending on the cell alone and cb = (y0 W + x0) x 8 on the corner alone.  A footprint move
+    // keeps every cell and changes cb only; a slot whose cell leaves the new footprint (cx - x0
+    // or cy[j] - y0 outside [0, W)) writes its sum to the grid and moves its cell by a period W.  The row
+    // cells are the same in every lane and live one per lane (lane j < ROWS holds cy[j]), so the
+    // rows that move are one ballot and the columns that move one vote.  Lanes and rows beyond
+    // the W x W residues track the residue a mod W (b mod W) of a slot that exists, so every tap
+    // offset stays inside the sub-kernel; they are never flushed.  (For DEGRID, acc[j] holds the
+    // grid value at the slot's cell instead of a running sum, reloaded when the cell moves.)
+    static_assert(ROWS <= 32, "one lane per slot row");
+    const unsigned FULL = 0xffffffffu;
     const int a_res = a % W;
+    const int b_res = (b0 + (lane < ROWS ? lane : 0)) % W;
+    const int nval = a_ok ? nrows : 0;        // rows j < nval of this lane are real slots
     float2 acc[ROWS];
-    int jy[ROWS];
-    unsigned toff[ROWS];                      // byte offset of the slot's tap in its sub-kernel
-#pragma unroll
-    for (int j = 0; j < ROWS; ++j) {
-        acc[j] = make_float2(0.0f, 0.0f);
-        jy[j] = 0;
-        toff[j] = 0;
-    }
-    int jx = 0;
-    int x0p = -1, y0p = -1;                   // corner of the previous footprint (none yet)
-    uint32_t prev = 0xffffffffu;              // no footprint corner packs to this
+    float2 acq[ROWS];                         // second pair of the packed-FMA sums (SLOT_PAIR)
+    unsigned coff[ROWS];                      // (cy[j] W + cx) x 8: the cell's part of the tap offset
+    unsigned cb;                              // (y0 W + x0) x 8 of the current corner
     int4 rn = ld_slot_rec<COHERENT>(srec + v0);
     float2 vn = DEGRID ? make_float2(0.0f, 0.0f) : ld_slot_vis<COHERENT>(svis + v0);
+    uint32_t prev = (uint32_t)rn.x;           // corner of the current footprint: x0 | y0 << 16
+    int cx, cyt;
+    slot_place<ROWS, DEGRID>(rn, W, N, a_res, b_res, nval, grid, cx, cyt, cb, coff, acc, acq);
     for (int q = v0; q < v1; ++q) {
         const int4 r = rn;
         const float2 v = vn;
@@ -117,77 +161,76 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
             rn = ld_slot_rec<COHERENT>(srec + q + 1);
             if (!DEGRID) vn = ld_slot_vis<COHERENT>(svis + q + 1);
         }
-        if ((uint32_t)r.x != prev) {          // the footprint moved: new cells for some slots
-            prev = (uint32_t)r.x;
+        if ((uint32_t)r.x != prev) {          // the footprint moved
             const int x0 = r.x & 0xffff, y0 = (r.x >> 16) & 0xffff;
-            const int dx = x0 - x0p, dy = y0 - y0p;
-            if (x0p < 0 || dx >= W || dx <= -W || dy >= W || dy <= -W) {
-                // first footprint or a long jump: every slot flushes (gridding) and starts over
-                const int xm = r.y & 0xffff, ym = (r.y >> 16) & 0xffff;
+            const int dx = x0 - (int)(prev & 0xffffu), dy = y0 - (int)(prev >> 16);
+            prev = (uint32_t)r.x;
+            if (dx >= W || dx <= -W || dy >= W || dy <= -W) {
+                // a long jump: every slot writes its sum and is placed anew
                 if (!DEGRID) {
 #pragma unroll
                     for (int j = 0; j < ROWS; ++j) {
-                        if (a_ok && j < nrows && (acc[j].x != 0.0f || acc[j].y != 0.0f))
-                            atomicAdd(grid + (int64_t)(y0p + jy[j]) * N + (x0p + jx), acc[j]);
-                        acc[j] = make_float2(0.0f, 0.0f);
+                        const int cyj = __shfl_sync(FULL, cyt, j);
+                        const float2 sj = slot_value(acc[j], acq[j]);
+                        if (j < nval && slot_nonzero(sj)) atomicAdd(grid + (int64_t)cyj * N + cx, sj);
                     }
                 }
-                int nx = a_res - xm;
-                nx += (nx < 0) ? W : 0;
-                jx = nx;
-#pragma unroll
-                for (int j = 0; j < ROWS; ++j) {
-                    int ny = (b0 + j) % W - ym;
-                    ny += (ny < 0) ? W : 0;
-                    jy[j] = ny;
-                    toff[j] = (unsigned)(ny * W + nx) * 8u;
-                    if (DEGRID)
-                        acc[j] = (a_ok && j < nrows) ? __ldg(grid + (int64_t)(y0 + ny) * N + (x0 + nx)) : make_float2(0.0f, 0.0f);
-                }
-            } else if (!__any_sync(0xffffffffu, jx - dx < 0 || jx - dx >= W ||
-                                                 (lane < ROWS && (jy[0] + lane >= W || jy[0] + lane - dy < 0 ||
-                                                                  jy[0] + lane - dy >= W)))) {
-                // no slot of this warp changes its cell: row j's tap row is jy[0] + j here (a
-                // tile whose rows pass W counts as a change above), and every tap offset shifts
-                // by the same amount
-                const unsigned d = (unsigned)(dy * W + dx) * 8u;
-#pragma unroll
-                for (int j = 0; j < ROWS; ++j) {
-                    jy[j] -= dy;
-                    toff[j] -= d;
-                }
-                jx -= dx;
+                slot_place<ROWS, DEGRID>(r, W, N, a_res, b_res, nval, grid, cx, cyt, cb, coff, acc, acq);
             } else {
-                int nx = jx - dx;
-                const bool xw = nx < 0 || nx >= W;            // the lane's column changes period
-                nx += (nx < 0) ? W : ((nx >= W) ? -W : 0);
+                cb = (unsigned)(y0 * W + x0) * 8u;
+                int tx = cx - x0;                 // the lane's column moves when tx leaves [0, W)
+                const bool xw = (unsigned)tx >= (unsigned)W;
+                const unsigned rm = __ballot_sync(FULL, lane < ROWS && (unsigned)(cyt - y0) >= (unsigned)W);
+                if (__any_sync(FULL, xw)) {       // columns that move: every row of those lanes
+                    tx += (tx < 0) ? W : ((tx >= W) ? -W : 0);
+                    const int cxn = x0 + tx;
+                    const unsigned dxo = (unsigned)(cxn - cx) * 8u;
 #pragma unroll
-                for (int j = 0; j < ROWS; ++j) {
-                    int ny = jy[j] - dy;
-                    const bool yw = ny < 0 || ny >= W;        // row j changes period
-                    ny += (ny < 0) ? W : ((ny >= W) ? -W : 0);
-                    if (xw || yw) {
-                        if (DEGRID) {
-                            if (a_ok && j < nrows) acc[j] = __ldg(grid + (int64_t)(y0 + ny) * N + (x0 + nx));
-                        } else {
-                            if (a_ok && j < nrows && (acc[j].x != 0.0f || acc[j].y != 0.0f))
-                                atomicAdd(grid + (int64_t)(y0p + jy[j]) * N + (x0p + jx), acc[j]);
-                            acc[j] = make_float2(0.0f, 0.0f);
+                    for (int j = 0; j < ROWS; ++j) {
+                        const int cyj = __shfl_sync(FULL, cyt, j);
+                        if (!DEGRID) {
+                            const float2 sj = slot_value(acc[j], acq[j]);
+                            if (xw && j < nval && slot_nonzero(sj)) atomicAdd(grid + (int64_t)cyj * N + cx, sj);
+                            acc[j] = xw ? make_float2(0.0f, 0.0f) : acc[j];
+                            acq[j] = xw ? make_float2(0.0f, 0.0f) : acq[j];
+                        }
+                        coff[j] += xw ? dxo : 0u;
+                    }
+                    cx = cxn;
+                }
+                if (rm) {                            // rows that move: every lane of those rows
+#pragma unroll
+                    for (int j = 0; j < ROWS; ++j) {
+                        if (rm & (1u << j)) {
+                            const int cyj = __shfl_sync(FULL, cyt, j);
+                            const int cyn = cyj + ((cyj < y0) ? W : -W);
+                            if (!DEGRID) {
+                                const float2 sj = slot_value(acc[j], acq[j]);
+                                if (j < nval && slot_nonzero(sj)) atomicAdd(grid + (int64_t)cyj * N + cx, sj);
+                                acc[j] = make_float2(0.0f, 0.0f);
+                                acq[j] = make_float2(0.0f, 0.0f);
+                            }
+                            coff[j] += (unsigned)((cyn - cyj) * W) * 8u;
+                            if (DEGRID && j < nval) acc[j] = __ldg(grid + (int64_t)cyn * N + cx);
                         }
                     }
-                    jy[j] = ny;
-                    toff[j] = (unsigned)(ny * W + nx) * 8u;
+                    if (lane < ROWS && (rm & (1u << lane))) cyt += (cyt < y0) ? W : -W;
                 }
-                jx = nx;
+                if (DEGRID && __any_sync(FULL, xw)) {    // moved columns read their new cells
+#pragma unroll
+                    for (int j = 0; j < ROWS; ++j) {
+                        const int cyj = __shfl_sync(FULL, cyt, j);
+                        if (xw && j < nval) acc[j] = __ldg(grid + (int64_t)cyj * N + cx);
+                    }
+                }
             }
-            x0p = x0;
-            y0p = y0;
         }
-        const float2* sub = pc + (r.z & 0x7fffffff);
+        // tap (cx - x0, cy[j] - y0) of the sub-kernel: byte offset coff[j] - cb from its start
+        const char* sub = reinterpret_cast<const char*>(pc + (r.z & 0x7fffffff)) - (int64_t)cb;
         const float sg = (r.z < 0) ? -1.0f : 1.0f;
         float2 tp[ROWS];
 #pragma unroll
-        for (int j = 0; j < ROWS; ++j) tp[j] = __ldg(reinterpret_cast<const float2*>(reinterpret_cast<const char*>(sub) + toff[j]));
+        for (int j = 0; j < ROWS; ++j) tp[j] = __ldg(reinterpret_cast<const float2*>(sub + coff[j]));
         if (DEGRID) {
             // conj(K) x value, K conjugated for w < 0: (tx, s ty)* (gx, gy)
             float sr = 0.0f, si = 0.0f;
@@ -206,16 +249,23 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
             const float cA = v.x, cB = -sg * v.y, cC = sg * v.x, cD = v.y;
 #pragma unroll
             for (int j = 0; j < ROWS; ++j) {
-                acc[j].x = fmaf(cA, tp[j].x, fmaf(cB, tp[j].y, acc[j].x));
-                acc[j].y = fmaf(cC, tp[j].y, fmaf(cD, tp[j].x, acc[j].y));
+                if (SLOT_PAIR) {
+                    acc[j] = ffma2(make_float2(cA, cC), tp[j], acc[j]);
+                    acq[j] = ffma2(make_float2(cD, cB), tp[j], acq[j]);
+                } else {
+                    acc[j].x = fmaf(cA, tp[j].x, fmaf(cB, tp[j].y, acc[j].x));
+                    acc[j].y = fmaf(cC, tp[j].y, fmaf(cD, tp[j].x, acc[j].y));
+                }
             }
         }
     }
     if (!DEGRID) {
 #pragma unroll
-        for (int j = 0; j < ROWS; ++j)
-            if (a_ok && j < nrows && (acc[j].x != 0.0f || acc[j].y != 0.0f))
-                atomicAdd(grid + (int64_t)(y0p + jy[j]) * N + (x0p + jx), acc[j]);
+        for (int j = 0; j < ROWS; ++j) {
+            const int cyj = __shfl_sync(FULL, cyt, j);
+            const float2 sj = slot_value(acc[j], acq[j]);
+            if (j < nval && slot_nonzero(sj)) atomicAdd(grid + (int64_t)cyj * N + cx, sj);
+        }
     }
 }
 
