@@ -94,6 +94,19 @@ def measure_compute_peaks(dev) -> dict:
 
     ms_fma = best(fma)                       # the call fills `flops`
     fp32 = flops.value / (ms_fma * 1e-3) / 1e12
+    # L2 rate of the gridder's tap-load shape: ten rows of 32 complex64 at random 8-byte offsets of
+    # a 64 MB buffer (L2-resident), rows 67 values apart; best over 3, 4 and 8 blocks per SM
+    tbuf = torch.zeros(8 << 20, dtype=torch.complex64, device=dev)
+    nbytes = ctypes.c_double()
+    l2 = 0.0
+    for bps in (3, 4, 8):
+        def taps():
+            _lib.check("wp_probe_l2_taps", lib.wp_probe_l2_taps(
+                ctypes.c_void_p(tbuf.data_ptr()), tbuf.numel(), 67, 2000, bps, ctypes.c_void_p(sink.data_ptr()),
+                ctypes.byref(nbytes), ctypes.c_void_p(st.cuda_stream)))
+        ms = best(taps)
+        l2 = max(l2, nbytes.value / (ms * 1e-3) / 1e9)
+    del tbuf
     n = 8192
     x = torch.randn(n, n, device=dev, dtype=torch.float32)
     y = torch.randn(n, n, device=dev, dtype=torch.float32)
@@ -106,9 +119,11 @@ def measure_compute_peaks(dev) -> dict:
     del x, y
     hbm, bf16, src = _peaks()
     return {"fp32_fma_tflops": fp32, "tf32_tflops": tf32, "bf16_tflops": bf16, "hbm_gbs": hbm,
+            "l2_tap_gbs": l2,
             "how": "FP32: FMA chains in registers, all SMs (wp_probe_fp32_fma); TF32: cuBLAS 8192^3 "
-                   "torch.matmul with TF32 allowed; best of 5 CUDA-event timings; HBM and BF16: "
-                   f"{src} MEASURED_PEAKS.json"}
+                   "torch.matmul with TF32 allowed; L2 taps: the gridder's tap-load shape on an "
+                   "L2-resident 64 MB buffer (wp_probe_l2_taps); best of 5 CUDA-event timings; HBM and "
+                   f"BF16: {src} MEASURED_PEAKS.json"}
 
 
 def max_over_ranks(ms: float, device, world: int) -> float:
@@ -746,7 +761,13 @@ def run_imaging(args, dev):
                      "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": flops / (grid_ms * 1e-3) / 1e12 / fp32_peak,
                      "peak_source": fp32_src,
-                     "hbm_frac": (V * 24 + 2 * N * N * 8) / (grid_ms * 1e-3) / 1e9 / _peaks()[0]},
+                     "hbm_frac": (V * 24 + 2 * N * N * 8) / (grid_ms * 1e-3) / 1e9 / _peaks()[0],
+                     # what bounds the cache gridders: every tap is one 8-byte L2 read
+                     "l2": ({"achieved_gbs": 8.0 * taps / (grid_ms * 1e-3) / 1e9, "peak_gbs": pk["l2_tap_gbs"],
+                             "frac": 8.0 * taps / (grid_ms * 1e-3) / 1e9 / pk["l2_tap_gbs"],
+                             "peak_source": "measured in this run: the tap-load shape (ten rows of 32 "
+                                            "complex64 at random offsets) on an L2-resident buffer"}
+                            if pk.get("l2_tap_gbs") else None)},
     }
 
 

@@ -540,6 +540,21 @@ int wp_image_to_grid(const wp_plan* plan, const float* taper, const float* image
 int wp_probe_fp32_fma(int32_t iters, int32_t blocks_per_sm, float* sink, double* flops_out,
                       void* stream);
 
+/*
+ * Measurement helper with no counterpart in the paper: queues one launch of blocks_per_sm blocks
+ * per SM of 256 threads in which every warp, steps times, reads ten rows of 32 consecutive
+ * complex64 values at a pseudo-random position of buf, the rows W values apart -- the shape of
+ * the slot gridder's tap loads (one 8-byte load per lane per row of a sub-kernel) -- and writes
+ * to *bytes_out (host) the bytes that launch reads.  Timed with CUDA events on `stream`, it gives
+ * the rate at which L2 serves that pattern when buf (n_elems complex64, device memory, 8-byte
+ * aligned) fits in L2: the denominator of the gridder's L2 roofline.  sink: one device float,
+ * written only in a case the loads never reach.  WP_ERR_SIZE for W outside 1..4096, steps < 1,
+ * blocks_per_sm outside 1..64, an unaligned buf, or n_elems not above 9 W + 32 or more than
+ * 2^32 above it.
+ */
+int wp_probe_l2_taps(const void* buf, int64_t n_elems, int32_t W, int32_t steps, int32_t blocks_per_sm,
+                     float* sink, double* bytes_out, void* stream);
+
 /* ---- misc ---------------------------------------------------------------------------- */
 const char* wp_strerror(int code);
 const char* wp_last_error_string(void);   /* last CUDA/cuFFT error text (thread-local) */

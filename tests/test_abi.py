@@ -99,6 +99,14 @@ def test_layout_and_argument_errors():
     assert lib.wp_dirty_image(ctypes.byref(p), ws, ws, 0.0, ws, None) == -2
     assert lib.wp_strerror(-4) == b"workspace too small or not 256-byte aligned"
     assert lib.wp_version() >= 100
+    # measurement probes: argument errors before any device work
+    out = ctypes.c_double()
+    assert lib.wp_probe_fp32_fma(0, 8, ws, ctypes.byref(out), None) == -2
+    assert lib.wp_probe_fp32_fma(16, 8, None, ctypes.byref(out), None) == -1
+    assert lib.wp_probe_l2_taps(None, 1 << 20, 67, 10, 3, ws, ctypes.byref(out), None) == -1
+    assert lib.wp_probe_l2_taps(ws, 1 << 20, 0, 10, 3, ws, ctypes.byref(out), None) == -2
+    assert lib.wp_probe_l2_taps(ws, 9 * 67 + 32, 67, 10, 3, ws, ctypes.byref(out), None) == -2
+    assert lib.wp_probe_l2_taps(ctypes.c_void_p(260), 1 << 20, 67, 10, 3, ws, ctypes.byref(out), None) == -2
 
 
 def test_projection_route_plan_and_workspace():
