@@ -555,6 +555,22 @@ int wp_probe_fp32_fma(int32_t iters, int32_t blocks_per_sm, float* sink, double*
 int wp_probe_l2_taps(const void* buf, int64_t n_elems, int32_t W, int32_t steps, int32_t blocks_per_sm,
                      float* sink, double* bytes_out, void* stream);
 
+/* ---- checked build ------------------------------------------------------------------- */
+
+/*
+ * A stand-in for a memory checker, with no counterpart in the paper.  The library compiled with
+ * -DWP_CHECK_BOUNDS (paper_1904_08463_gb300.build.build_checked) tests the index of every tap
+ * read and grid cell access of the gridders (grid_method 3 and 9, per call and batched), the
+ * degridders (0 and 9) and every kernel-cache row the resample writes, against the extent of
+ * its buffer: the plane's block [offsets[p], offsets[p+1]) of the cache, the N x N grid, the V
+ * visibilities.  An access outside is skipped, and the first one of each translation unit is
+ * recorded as site << 48 | (index & 0xffffffffffff), sites 1 cache row written, 2 tap read,
+ * 3 grid cell, 4 visibility written.  wp_bounds_status synchronizes the device, writes to
+ * *first (host) the first record found (0: none) and clears the records when clear != 0.
+ * The default build keeps no checks and returns WP_ERR_UNSUPPORTED.
+ */
+int wp_bounds_status(uint64_t* first, int32_t clear);
+
 /* ---- misc ---------------------------------------------------------------------------- */
 const char* wp_strerror(int code);
 const char* wp_last_error_string(void);   /* last CUDA/cuFFT error text (thread-local) */

@@ -143,6 +143,7 @@ _SIGS = {
     "wp_grid_batch_status": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "wp_grid_batch_selftest": (c_int32, [c_int32, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),
     "wp_probe_fp32_fma": (c_int32, [c_int32, c_int32, c_void_p, P_(c_double), c_void_p]),
+    "wp_bounds_status": (c_int32, [P_(ctypes.c_uint64), c_int32]),
     "wp_probe_l2_taps": (c_int32, [c_void_p, c_int64, c_int32, c_int32, c_int32, c_void_p, P_(c_double), c_void_p]),
     "wp_image_to_grid": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
 }

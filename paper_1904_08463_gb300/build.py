@@ -2,7 +2,9 @@
 
 Every translation unit is compiled for sm_103a only, in parallel, then linked with the
 CUDA runtime (shared) and cuFFT.  Rebuilds only when a source or header is newer than
-the library.
+the library.  build_checked() makes libwproj_checked.so, the same sources compiled with
+-DWP_CHECK_BOUNDS (index checks on the kernels' main buffer accesses, read back with
+wp_bounds_status); it is a test build, never the one the package loads by default.
 """
 from __future__ import annotations
 
@@ -17,6 +19,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libwproj.so")
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(PKG, "libwproj_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -35,10 +39,10 @@ def _deps() -> list[str]:
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "wproj.h")]
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+def needs_build(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
@@ -48,19 +52,27 @@ def flags() -> list[str]:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not needs_build():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    return _build(LIB, BUILD, [], force, verbose)
+
+
+def build_checked(force: bool = False, verbose: bool = False) -> str:
+    return _build(LIB_CHECKED, BUILD_CHECKED, ["-DWP_CHECK_BOUNDS"], force, verbose)
+
+
+def _build(lib: str, build_dir: str, defines: list[str], force: bool, verbose: bool) -> str:
+    if not force and not needs_build(lib):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     cuda_home = os.path.dirname(os.path.dirname(nvcc))
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, *flags(), "-c", src, "-o", obj]
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
+        cmd = [nvcc, *flags(), *defines, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
-        log = os.path.join(BUILD, os.path.basename(src) + ".ptxas.txt")
+        log = os.path.join(build_dir, os.path.basename(src) + ".ptxas.txt")
         with open(log, "w") as fh:
             fh.write(r.stderr)
         if verbose:
@@ -69,7 +81,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     libdir = os.path.join(cuda_home, "lib64")
     if not os.path.isdir(libdir):
         libdir = os.path.join(cuda_home, "lib")
@@ -78,8 +90,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -145,6 +145,17 @@ static bool aligned256(const void* p) { return ((uintptr_t)p & 255u) == 0; }
 
 int check_device_public() { return check_device(); }
 
+// the bounds records of the checked build, one reader per translation unit
+static std::vector<int (*)(unsigned long long*, bool)>& bounds_units() {
+    static std::vector<int (*)(unsigned long long*, bool)> units;
+    return units;
+}
+
+int bounds_register(int (*read)(unsigned long long* first, bool clear)) {
+    bounds_units().push_back(read);
+    return 0;
+}
+
 }  // namespace wp
 
 using namespace wp;
@@ -169,6 +180,25 @@ const char* wp_strerror(int code) {
         case WP_ERR_INFLIGHT: return "a bounded wait expired with device work still in flight (context suspect)";
         default: return "unknown status";
     }
+}
+
+int wp_bounds_status(uint64_t* first, int32_t clear) {
+#ifdef WP_CHECK_BOUNDS
+    if (!first) return WP_ERR_NULL;
+    *first = 0;
+    WP_CUDA(cudaDeviceSynchronize());
+    for (auto read : bounds_units()) {
+        unsigned long long v = 0;
+        int rc = read(&v, clear != 0);
+        if (rc) return rc;
+        if (*first == 0 && v != 0) *first = v;
+    }
+    return WP_OK;
+#else
+    (void)first;
+    (void)clear;
+    return WP_ERR_UNSUPPORTED;
+#endif
 }
 
 void wp_release(void) {

@@ -40,6 +40,7 @@ __device__ __forceinline__ void ro_item(int item, int N, int os, int s_max, int 
     const int W2 = W * W;
     const int D = (S + TILE - 1) / TILE;
     const float2* pcache = cache + offsets[p];
+    const int64_t blk = offsets[p + 1] - offsets[p];   // the plane's block (checked build)
     const int ty0 = oy * TILE, tx0 = ox * TILE;
     const int cx_lo = max(0, ox - D), cx_hi = min(ntx - 1, ox + D);
     for (int cy = max(0, oy - D); cy <= min(ntx - 1, oy + D); ++cy) {
@@ -79,12 +80,14 @@ __device__ __forceinline__ void ro_item(int item, int N, int os, int s_max, int 
                 const float sgn = (geo >> 31) ? -1.0f : 1.0f;
                 const float2 vv = l_vv[e];
                 const float2* sub = pcache + l_off[e] + (rw - r0) * W;
+                int64_t tix = (int64_t)l_off[e] + (int64_t)(rw - r0) * W;   // element of sub (checked build)
                 float2* trow = tile + rw * TILE + c0;
                 for (int r = rw; r <= r1; r += GRID_WARPS) {
                     float2 tp[CH];
 #pragma unroll
                     for (int k = 0; k < CH; ++k)
-                        tp[k] = (lane + 32 * k < w) ? __ldg(sub + lane + 32 * k) : make_float2(0.0f, 0.0f);
+                        tp[k] = (lane + 32 * k < w && in_bounds(tix + lane + 32 * k, blk, BS_TAP))
+                                    ? __ldg(sub + lane + 32 * k) : make_float2(0.0f, 0.0f);
 #pragma unroll
                     for (int k = 0; k < CH; ++k) {
                         if (lane + 32 * k < w) {
@@ -96,6 +99,7 @@ __device__ __forceinline__ void ro_item(int item, int N, int os, int s_max, int 
                         }
                     }
                     sub += GRID_WARPS * W;
+                    tix += GRID_WARPS * W;
                     trow += GRID_WARPS * TILE;
                 }
                 __syncwarp();   // the next entry may touch this one's cells from other lanes
@@ -109,7 +113,8 @@ __device__ __forceinline__ void ro_item(int item, int N, int os, int s_max, int 
         const float2 a = tile[i];
         if (a.x != 0.0f || a.y != 0.0f) {
             const int gy = ty0 + i / TILE, gx = tx0 + (i & (TILE - 1));
-            if (gy < N && gx < N) atomicAdd(grid + (int64_t)gy * N + gx, a);
+            if (gy < N && gx < N && in_bounds((int64_t)gy * N + gx, (int64_t)N * N, BS_GRID))
+                atomicAdd(grid + (int64_t)gy * N + gx, a);
             tile[i] = make_float2(0.0f, 0.0f);
         }
     }

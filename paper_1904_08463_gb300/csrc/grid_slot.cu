@@ -150,7 +150,8 @@ __global__ void __launch_bounds__(SLOT_WARPS * 32, 4) k_degrid_slot(int N, int P
                                                                     const int* __restrict__ istart,
                                                                     const int4* __restrict__ srec,
                                                                     const float2* __restrict__ grid,
-                                                                    int* __restrict__ ctrl, float2* __restrict__ vis_out) {
+                                                                    int* __restrict__ ctrl, float2* __restrict__ vis_out,
+                                                                    int64_t V) {
     const int lane = threadIdx.x & 31;
     const int n_items = istart[P];
     for (;;) {
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(SLOT_WARPS * 32, 4) k_degrid_slot(int N, int P
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n_items) break;
         slot_walk<ROWS, false, true>(it, N, P, s_max, support, offsets, cache, vstart, istart, srec, nullptr,
-                                     const_cast<float2*>(grid), vis_out);
+                                     const_cast<float2*>(grid), vis_out, V);
     }
 }
 
@@ -248,7 +249,7 @@ int degrid_slot(const Geom& g, const wp_wkernels* kern, const float* uvw, int64_
     if (per_sm < 1) per_sm = 1;
     k_degrid_slot<SLOT_ROWS><<<sms * per_sm, SLOT_WARPS * 32, 0, st>>>(g.N, P, g.s_max, w.seff, kern->offsets,
                                                             reinterpret_cast<const float2*>(kern->cache), w.vstart,
-                                                            w.istart, w.srec, grid, w.ctrl, vis_out);
+                                                            w.istart, w.srec, grid, w.ctrl, vis_out, V);
     WP_LAUNCH_CHECK("k_degrid_slot");
     return WP_OK;
 }

@@ -51,6 +51,15 @@ __device__ __forceinline__ void slot_gather_one(int64_t i, int os, int s_max, co
     }
 }
 
+// a grid cell written or read by a slot (bounds-checked in the checked build)
+__device__ __forceinline__ void slot_add(float2* grid, int N, int cy, int cx, float2 v) {
+    if (in_bounds(cx, N, BS_GRID) && in_bounds(cy, N, BS_GRID)) atomicAdd(grid + (int64_t)cy * N + cx, v);
+}
+__device__ __forceinline__ float2 slot_get(const float2* grid, int N, int cy, int cx) {
+    return (in_bounds(cx, N, BS_GRID) && in_bounds(cy, N, BS_GRID)) ? __ldg(grid + (int64_t)cy * N + cx)
+                                                                    : make_float2(0.0f, 0.0f);
+}
+
 // a running sum worth writing (either part non-zero; -0 counts as zero)
 __device__ __forceinline__ bool slot_nonzero(float2 a) {
     return ((__float_as_uint(a.x) | __float_as_uint(a.y)) & 0x7fffffffu) != 0u;
@@ -93,7 +102,7 @@ __device__ __forceinline__ void slot_place(int4 r, int W, int N, int a_res, int 
     for (int j = 0; j < ROWS; ++j) {
         const int cyj = __shfl_sync(0xffffffffu, cyt, j);
         coff[j] = (unsigned)(cyj * W + cx) * 8u;
-        acc[j] = (DEGRID && j < nval) ? __ldg(grid + (int64_t)cyj * N + cx) : make_float2(0.0f, 0.0f);
+        acc[j] = (DEGRID && j < nval) ? slot_get(grid, N, cyj, cx) : make_float2(0.0f, 0.0f);
         acq[j] = make_float2(0.0f, 0.0f);
     }
 }
@@ -107,7 +116,7 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
                                           const int64_t* __restrict__ offsets, const float2* __restrict__ cache,
                                           const int* __restrict__ vstart, const int* __restrict__ istart,
                                           const int4* __restrict__ srec, const float2* __restrict__ svis,
-                                          float2* __restrict__ grid, float2* __restrict__ vis_out) {
+                                          float2* __restrict__ grid, float2* __restrict__ vis_out, int64_t n_vis) {
     const int lane = threadIdx.x & 31;
     int lo = 0, hi = P;                       // largest plane with istart <= it
     while (hi - lo > 1) {
@@ -125,6 +134,7 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
     const int v0 = vstart[p] + chunk * SLOT_CHUNK;
     const int v1 = min(v0 + SLOT_CHUNK, vstart[p + 1]);
     const float2* pc = cache + offsets[p];
+    const int64_t blk = offsets[p + 1] - offsets[p];   // the plane's block (checked build)
     const int a = txs * 32 + lane;            // the lane's slot column
     const bool a_ok = a < W;
     const int b0 = tys * ROWS;                // slot rows b0 .. b0 + ROWS - 1
@@ -172,7 +182,7 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
                     for (int j = 0; j < ROWS; ++j) {
                         const int cyj = __shfl_sync(FULL, cyt, j);
                         const float2 sj = slot_value(acc[j], acq[j]);
-                        if (j < nval && slot_nonzero(sj)) atomicAdd(grid + (int64_t)cyj * N + cx, sj);
+                        if (j < nval && slot_nonzero(sj)) slot_add(grid, N, cyj, cx, sj);
                     }
                 }
                 slot_place<ROWS, DEGRID>(r, W, N, a_res, b_res, nval, grid, cx, cyt, cb, coff, acc, acq);
@@ -190,7 +200,7 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
                         const int cyj = __shfl_sync(FULL, cyt, j);
                         if (!DEGRID) {
                             const float2 sj = slot_value(acc[j], acq[j]);
-                            if (xw && j < nval && slot_nonzero(sj)) atomicAdd(grid + (int64_t)cyj * N + cx, sj);
+                            if (xw && j < nval && slot_nonzero(sj)) slot_add(grid, N, cyj, cx, sj);
                             acc[j] = xw ? make_float2(0.0f, 0.0f) : acc[j];
                             acq[j] = xw ? make_float2(0.0f, 0.0f) : acq[j];
                         }
@@ -206,12 +216,12 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
                             const int cyn = cyj + ((cyj < y0) ? W : -W);
                             if (!DEGRID) {
                                 const float2 sj = slot_value(acc[j], acq[j]);
-                                if (j < nval && slot_nonzero(sj)) atomicAdd(grid + (int64_t)cyj * N + cx, sj);
+                                if (j < nval && slot_nonzero(sj)) slot_add(grid, N, cyj, cx, sj);
                                 acc[j] = make_float2(0.0f, 0.0f);
                                 acq[j] = make_float2(0.0f, 0.0f);
                             }
                             coff[j] += (unsigned)((cyn - cyj) * W) * 8u;
-                            if (DEGRID && j < nval) acc[j] = __ldg(grid + (int64_t)cyn * N + cx);
+                            if (DEGRID && j < nval) acc[j] = slot_get(grid, N, cyn, cx);
                         }
                     }
                     if (lane < ROWS && (rm & (1u << lane))) cyt += (cyt < y0) ? W : -W;
@@ -220,7 +230,7 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
 #pragma unroll
                     for (int j = 0; j < ROWS; ++j) {
                         const int cyj = __shfl_sync(FULL, cyt, j);
-                        if (xw && j < nval) acc[j] = __ldg(grid + (int64_t)cyj * N + cx);
+                        if (xw && j < nval) acc[j] = slot_get(grid, N, cyj, cx);
                     }
                 }
             }
@@ -230,7 +240,9 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
         const float sg = (r.z < 0) ? -1.0f : 1.0f;
         float2 tp[ROWS];
 #pragma unroll
-        for (int j = 0; j < ROWS; ++j) tp[j] = __ldg(reinterpret_cast<const float2*>(sub + coff[j]));
+        for (int j = 0; j < ROWS; ++j)
+            tp[j] = in_bounds((int64_t)(r.z & 0x7fffffff) + ((int64_t)coff[j] - (int64_t)cb) / 8, blk, BS_TAP)
+                        ? __ldg(reinterpret_cast<const float2*>(sub + coff[j])) : make_float2(0.0f, 0.0f);
         if (DEGRID) {
             // conj(K) x value, K conjugated for w < 0: (tx, s ty)* (gx, gy)
             float sr = 0.0f, si = 0.0f;
@@ -244,7 +256,8 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
                 sr += __shfl_xor_sync(0xffffffffu, sr, o);
                 si += __shfl_xor_sync(0xffffffffu, si, o);
             }
-            if (lane == 0 && (sr != 0.0f || si != 0.0f)) atomicAdd(vis_out + r.w, make_float2(sr, si));
+            if (lane == 0 && (sr != 0.0f || si != 0.0f) && in_bounds(r.w, n_vis, BS_VIS))
+                atomicAdd(vis_out + r.w, make_float2(sr, si));
         } else {
             const float cA = v.x, cB = -sg * v.y, cC = sg * v.x, cD = v.y;
 #pragma unroll
@@ -264,7 +277,7 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
         for (int j = 0; j < ROWS; ++j) {
             const int cyj = __shfl_sync(FULL, cyt, j);
             const float2 sj = slot_value(acc[j], acq[j]);
-            if (j < nval && slot_nonzero(sj)) atomicAdd(grid + (int64_t)cyj * N + cx, sj);
+            if (j < nval && slot_nonzero(sj)) slot_add(grid, N, cyj, cx, sj);
         }
     }
 }
@@ -276,7 +289,7 @@ __device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const
                                           const int4* __restrict__ srec, const float2* __restrict__ svis,
                                           float2* __restrict__ grid) {
     slot_walk<ROWS, COHERENT, false>(it, N, P, s_max, support, offsets, cache, vstart, istart, srec, svis, grid,
-                                     nullptr);
+                                     nullptr, 0);
 }
 
 }  // namespace wp

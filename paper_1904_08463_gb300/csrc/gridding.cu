@@ -1055,8 +1055,11 @@ __global__ void __launch_bounds__(256) k_degrid(int N, int os, int s_max, int nb
     const int p = r4.z;
     const int S = min(max(support[p], 1), s_max);
     const int W = 2 * S + 1;
-    const float2* sub = cache + offsets[p] + (int64_t)(fv * os + fu) * W * W;
+    const int64_t sb = (int64_t)(fv * os + fu) * W * W;
+    const int64_t blk = offsets[p + 1] - offsets[p];   // the plane's block (checked build)
+    const float2* sub = cache + offsets[p] + sb;
     const float2* g0 = grid + (int64_t)(iv - S) * N + (iu - S);
+    const float2 zero = make_float2(0.0f, 0.0f);
     float sr = 0.0f, si = 0.0f;
     // two footprint rows per pass: their tap and grid loads (L2) are in flight together
     int jy = 0;
@@ -1064,8 +1067,11 @@ __global__ void __launch_bounds__(256) k_degrid(int N, int os, int s_max, int nb
         const float2* trow = sub + jy * W;
         const float2* grow = g0 + (int64_t)jy * N;
         for (int jx = lane; jx < W; jx += 32) {
-            const float2 tp0 = __ldg(trow + jx), tp1 = __ldg(trow + W + jx);
-            const float2 gv0 = grow[jx], gv1 = grow[N + jx];
+            const bool cx_ok = in_bounds(iu - S + jx, N, BS_GRID);
+            const float2 tp0 = in_bounds(sb + jy * W + jx, blk, BS_TAP) ? __ldg(trow + jx) : zero;
+            const float2 tp1 = in_bounds(sb + (jy + 1) * W + jx, blk, BS_TAP) ? __ldg(trow + W + jx) : zero;
+            const float2 gv0 = (cx_ok && in_bounds(iv - S + jy, N, BS_GRID)) ? grow[jx] : zero;
+            const float2 gv1 = (cx_ok && in_bounds(iv - S + jy + 1, N, BS_GRID)) ? grow[N + jx] : zero;
             // conj(K) * g
             const float ti0 = sgn * tp0.y, ti1 = sgn * tp1.y;
             sr = fmaf(tp0.x, gv0.x, fmaf(ti0, gv0.y, sr));
@@ -1078,9 +1084,9 @@ __global__ void __launch_bounds__(256) k_degrid(int N, int os, int s_max, int nb
         const float2* trow = sub + jy * W;
         const float2* grow = g0 + (int64_t)jy * N;
         for (int jx = lane; jx < W; jx += 32) {
-            const float2 tp = __ldg(trow + jx);
+            const float2 tp = in_bounds(sb + jy * W + jx, blk, BS_TAP) ? __ldg(trow + jx) : zero;
             const float ti = sgn * tp.y;
-            const float2 gv = grow[jx];
+            const float2 gv = (in_bounds(iu - S + jx, N, BS_GRID) && in_bounds(iv - S + jy, N, BS_GRID)) ? grow[jx] : zero;
             sr = fmaf(tp.x, gv.x, fmaf(ti, gv.y, sr));
             si = fmaf(tp.x, gv.y, fmaf(-ti, gv.x, si));
         }
@@ -1089,7 +1095,7 @@ __global__ void __launch_bounds__(256) k_degrid(int N, int os, int s_max, int nb
         sr += __shfl_xor_sync(0xffffffffu, sr, o);
         si += __shfl_xor_sync(0xffffffffu, si, o);
     }
-    if (lane == 0) vis_out[r4.w] = make_float2(sr, si);
+    if (lane == 0 && in_bounds(r4.w, V, BS_VIS)) vis_out[r4.w] = make_float2(sr, si);
 }
 
 int degrid_run(const Geom& g, const wp_wkernels* kern, int64_t V, const GridWork& w, const float2* grid,

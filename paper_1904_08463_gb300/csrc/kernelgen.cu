@@ -580,6 +580,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample(int K, int os, int s_ma
     const int nx = xself ? S + 1 : W, ny = (fv2 == fv) ? S + 1 : W;
     const int cx = fu ? W : W - 1, cy = fv ? W : W - 1;   // j -> c - j (j = 0 with f > 0: -> 0)
     float2* const base = cache + offsets[p];
+    const int64_t blk = offsets[p + 1] - offsets[p];   // the plane's block (checked build)
     float2* const d00 = base + (int64_t)(fv * os + fu) * W2;
     float2* const d10 = base + (int64_t)(fv * os + fu2) * W2;    // x-mirrored
     float2* const d01 = base + (int64_t)(fv2 * os + fu) * W2;    // y-mirrored
@@ -587,8 +588,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample(int K, int os, int s_ma
     const float2 zero = make_float2(0.0f, 0.0f);
     if (fv2 != fv)   // row 0 of the y-mirrored sub-kernels has no pre-image: zero
         for (int i = threadIdx.x; i < W; i += blockDim.x) {
-            __stcs(d01 + i, zero);
-            if (!xself) __stcs(d11 + i, zero);
+            if (in_bounds((d01 - base) + i, blk, BS_CACHE_WRITE)) __stcs(d01 + i, zero);
+            if (!xself && in_bounds((d11 - base) + i, blk, BS_CACHE_WRITE)) __stcs(d11 + i, zero);
         }
     const int lim2 = lim * lim;
     const int dy0 = -os * S - fv;   // os (jy - S) - fv at jy = 0
@@ -641,7 +642,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample(int K, int os, int s_ma
             float2* const g = k == 0 ? gF : k == 1 ? gX : k == 2 ? gY : gXY;
             const int o = k == 0 ? oF : k == 1 ? oX : k == 2 ? oY : oXY;
             const int n = k == 0 ? nF : k == 1 ? (xself ? 0 : nF) : k == 2 ? nY : (xself ? 0 : nY);
-            if (n > 0) {
+            if (n > 0 && in_bounds(g - base, blk, BS_CACHE_WRITE) && in_bounds((g - base) + n - 1, blk, BS_CACHE_WRITE)) {
                 const int sh = parity8(g);          // odd head element
                 const int nb = (n - sh) & ~1;       // aligned body
                 if (nb > 0) bulk_store(g + sh, stage_s + 8u * (uint32_t)(o + sh), (uint32_t)nb * 8u);

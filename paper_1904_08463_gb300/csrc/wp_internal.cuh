@@ -38,6 +38,43 @@ int cuda_fail(const char* where, cudaError_t e);
     } while (0)
 
 // ---------------------------------------------------------------------------------------
+// checked build (-DWP_CHECK_BOUNDS)
+// ---------------------------------------------------------------------------------------
+// The kernels test the index of each main buffer access against the buffer's extent with
+// in_bounds(); in the checked build an access outside is skipped and the first one of each
+// translation unit recorded in a device word of that unit (site << 48 | low 48 bits of the
+// index); wp_bounds_status gathers the words of every unit.  In the default build in_bounds is
+// a constant true and every check compiles away.
+enum BoundSite : int {
+    BS_CACHE_WRITE = 1,   // resample: a staged row copied into the kernel cache
+    BS_TAP = 2,           // a gridder or degridder reading a tap of its plane's cache block
+    BS_GRID = 3,          // a grid cell read or written
+    BS_VIS = 4,           // a visibility written by a degridder
+};
+int bounds_register(int (*read)(unsigned long long* first, bool clear));
+#ifdef WP_CHECK_BOUNDS
+namespace {
+__device__ unsigned long long g_bounds_first;       // one per translation unit
+int bounds_read_unit(unsigned long long* first, bool clear) {
+    WP_CUDA(cudaMemcpyFromSymbol(first, g_bounds_first, sizeof(unsigned long long)));
+    if (clear) {
+        const unsigned long long zero = 0;
+        WP_CUDA(cudaMemcpyToSymbol(g_bounds_first, &zero, sizeof(zero)));
+    }
+    return WP_OK;
+}
+const int g_bounds_registered = bounds_register(&bounds_read_unit);
+}  // namespace
+__device__ __forceinline__ bool in_bounds(int64_t i, int64_t n, int site) {
+    if ((uint64_t)i < (uint64_t)n) return true;
+    atomicCAS(&g_bounds_first, 0ull, ((unsigned long long)site << 48) | ((unsigned long long)i & 0xffffffffffffull));
+    return false;
+}
+#else
+__device__ __forceinline__ constexpr bool in_bounds(int64_t, int64_t, int) { return true; }
+#endif
+
+// ---------------------------------------------------------------------------------------
 // derived geometry of a plan
 // ---------------------------------------------------------------------------------------
 struct Geom {

@@ -99,6 +99,9 @@ def test_layout_and_argument_errors():
     assert lib.wp_dirty_image(ctypes.byref(p), ws, ws, 0.0, ws, None) == -2
     assert lib.wp_strerror(-4) == b"workspace too small or not 256-byte aligned"
     assert lib.wp_version() >= 100
+    # the default build keeps no bounds checks
+    first = ctypes.c_uint64(7)
+    assert lib.wp_bounds_status(ctypes.byref(first), 0) == -8
     # measurement probes: argument errors before any device work
     out = ctypes.c_double()
     assert lib.wp_probe_fp32_fma(0, 8, ws, ctypes.byref(out), None) == -2
@@ -171,3 +174,16 @@ def test_struct_layouts_match_the_header(tmp_path):
     want = [ctypes.sizeof(L.WpPlan), ctypes.sizeof(L.WpWkernels), ctypes.sizeof(L.WpGridJob),
             L.WpGridJob.kernels.offset, L.WpGridJob.V.offset, L.WpGridJob.stats.offset]
     assert got == want
+
+
+def test_checked_build_compiles_and_exports_the_same_symbols():
+    """The -DWP_CHECK_BOUNDS build (index checks on the kernels' main buffer accesses) compiles
+    from the same sources and exports every declared function; it is exercised on the GPU by
+    tests/test_gpu_bounds.py."""
+    from paper_1904_08463_gb300 import build
+
+    if not (shutil.which("nvcc") or os.path.exists("/usr/local/cuda/bin/nvcc")):
+        pytest.skip("nvcc not available")
+    lib = ctypes.CDLL(build.build_checked())
+    for n in _declared():
+        assert hasattr(lib, n), n
