@@ -863,12 +863,36 @@ def run_grad(args, dev):
     uvw = torch.tensor(d["uvw"], device=dev).reshape(-1)
     vobs = synth.predict_torch(d["uvw"], d["sky"], dev)
     planes = wp.plane_values(uvw, P)
-    # the slot walk grids the backward pass and degrids the forward one (grid_method 9)
+    # the backward pass grids with the slot walk (grid_method 9); the forward prediction degrids
+    # with whichever degridder is faster on these inputs (timed below: the warp per visibility,
+    # grid_method 0, or the slot walk in reverse, 9)
     plan0 = wp.Plan(N, dl, OS, 127, 3, 0.01, R, "cubic", "tf32x3", 64, 9)
     taper0 = torch.tensor(synth.gaussian_taper_samples(N, dl, R), dtype=torch.float32, device=dev)
     ws = wp.kernelgen_prepare(plan0, P)
     _, _, sup = wp.hankel_radial(plan0, taper0, planes, ws)
-    pr = Predictor(plan0.replace(trunc_frac=0.0), planes.cpu().numpy(), sup.cpu().tolist(), uvw)
+    p_fix = plan0.replace(trunc_frac=0.0)
+    V = vobs.numel()
+    wk = wp.make_wkernels(p_fix, taper0, planes, supports=sup.cpu().tolist())
+    X = torch.randn((N, N), dtype=torch.complex64, device=dev)
+    dws = wp.workspace(max(wp.grid_workspace_bytes(p_fix.replace(grid_method=m), P, V) for m in (0, 9)), dev)
+    dout = torch.empty(V, dtype=torch.complex64, device=dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 3
+    degrid_ms_by = {}
+    for m in (0, 9):
+        pm = p_fix.replace(grid_method=m)
+        for _ in range(2):
+            wp.degrid(pm, wk, uvw, X, out=dout, ws=dws)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(n):
+            wp.degrid(pm, wk, uvw, X, out=dout, ws=dws)
+        b.record()
+        torch.cuda.synchronize()
+        degrid_ms_by[m] = a.elapsed_time(b) / n
+    dm = min(degrid_ms_by, key=degrid_ms_by.get)
+    del X, dws, dout
+    pr = Predictor(p_fix, planes.cpu().numpy(), sup.cpu().tolist(), uvw, degrid_method=dm)
     # model image: the sky's point sources on their pixels (non-zero, so that the taper enters)
     img0 = torch.zeros((N, N), dtype=torch.float32)
     for l_, m_, f_ in zip(d["sky"].l, d["sky"].m, d["sky"].flux):
@@ -886,41 +910,12 @@ def run_grad(args, dev):
     for _ in range(2):
         step()
     torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n = 3
     a.record()
     for _ in range(n):
         step()
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / n
-    V = vobs.numel()
-    # the degridder alone on the same visibilities and kernels (the forward's main kernel)
-    p_fix = plan0.replace(trunc_frac=0.0)
-    wk = wp.make_wkernels(p_fix, taper0, planes, supports=sup.cpu().tolist())
-    X = torch.randn((N, N), dtype=torch.complex64, device=dev)
-    dws = wp.workspace(wp.grid_workspace_bytes(p_fix, P, V), dev)
-    dout = torch.empty(V, dtype=torch.complex64, device=dev)
-    for _ in range(2):
-        wp.degrid(p_fix, wk, uvw, X, out=dout, ws=dws)
-    torch.cuda.synchronize()
-    a.record()
-    for _ in range(n):
-        wp.degrid(p_fix, wk, uvw, X, out=dout, ws=dws)
-    b.record()
-    torch.cuda.synchronize()
-    degrid_ms = a.elapsed_time(b) / n
-    # the warp-per-visibility degridder on the same inputs, for comparison
-    p_warp = p_fix.replace(grid_method=3)
-    for _ in range(2):
-        wp.degrid(p_warp, wk, uvw, X, out=dout, ws=dws)
-    torch.cuda.synchronize()
-    a.record()
-    for _ in range(n):
-        wp.degrid(p_warp, wk, uvw, X, out=dout, ws=dws)
-    b.record()
-    torch.cuda.synchronize()
-    degrid_warp_ms = a.elapsed_time(b) / n
     # degridding roofline: 8 flop per footprint tap of every visibility (FP32 ALU), as gridding
     sup_h = sup.cpu().numpy()
     pl = planes.cpu().numpy()
@@ -930,13 +925,18 @@ def run_grad(args, dev):
     taps = float(np.sum((2 * sup_h[lower].astype(np.float64) + 1) ** 2))
     pk = getattr(args, "peaks", None) or {}
     fp32_peak = pk.get("fp32_fma_tflops") or 152 * 128 * 2 * 2.07e9 / 1e12
+    degrid_ms = degrid_ms_by[dm]
     achieved = 8.0 * taps / (degrid_ms * 1e-3) / 1e12
+    names = {0: "warp per visibility (grid_method 0)", 9: "slots in reverse (grid_method 9)"}
     return {"workload": f"{V} visibilities, 4096^2 float32 model image, 512 planes, 512-sample taper, chi^2",
             "ms_per_forward_backward": ms, "mvis_per_s": V / (ms * 1e-3) / 1e6,
             "grad_image_norm": float(image.grad.norm()), "grad_taper_norm": float(taper.grad.norm()),
-            "degrid_ms": degrid_ms, "degrid_method": "slots (grid_method 9)", "degrid_ms_warp_per_vis": degrid_warp_ms,
+            "gridder_backward": "slots (grid_method 9)",
+            "degrid_ms": degrid_ms, "degrid_method": names[dm],
+            "degrid_ms_by_method": {names[m]: t for m, t in degrid_ms_by.items()},
             "degrid_taps_per_vis": taps / V,
-            "degrid_roofline": {"kernel": "k_degrid_slot", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+            "degrid_roofline": {"kernel": "k_degrid" if dm == 0 else "k_degrid_slot", "bound": "alu",
+                                "achieved": achieved, "peak": fp32_peak,
                                 "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                                 "peak_source": "measured in this run" if pk.get("fp32_fma_tflops") else "nominal"}}
 

@@ -26,10 +26,14 @@ class Predictor:
     """Fixed geometry of a differentiable prediction: plan, |w|-plane values, supports and
     visibility coordinates, with the device workspaces reused across calls."""
 
-    def __init__(self, plan: Plan, w_planes, supports, uvw: torch.Tensor, weight_sum: float = 1.0):
+    def __init__(self, plan: Plan, w_planes, supports, uvw: torch.Tensor, weight_sum: float = 1.0,
+                 degrid_method: int | None = None):
+        """degrid_method: the degridder of the forward prediction (a ``grid_method``; default the
+        plan's own); the backward pass grids with the plan's method."""
         if plan.trunc_frac > 0:
             plan = plan.replace(trunc_frac=0.0)
         self.plan = plan
+        self.degrid_plan = plan if degrid_method is None else plan.replace(grid_method=int(degrid_method))
         dev = uvw.device
         self.uvw = _need(uvw.reshape(-1), torch.float32, "uvw")
         self.V = self.uvw.numel() // 3
@@ -41,6 +45,7 @@ class Predictor:
         self.kg_ws = workspace(kernelgen_workspace_bytes(plan, self.P), dev)
         kernelgen_prepare(plan, self.P, self.kg_ws)
         self.grid_ws = workspace(max(grid_workspace_bytes(plan, self.P, self.V),
+                                     grid_workspace_bytes(self.degrid_plan, self.P, self.V),
                                      int(_lib.load().wp_grad_workspace_bytes(ctypes.byref(plan.c()), self.P,
                                                                              self.V))), dev)
         self.weight_sum = float(weight_sum)
@@ -61,7 +66,7 @@ class Visibilities(torch.autograd.Function):
         taper = _need(taper.detach().contiguous(), torch.float32, "taper")
         wk = pr.kernels(taper)
         G = image_to_grid(pr.plan, taper, image, pr.weight_sum)
-        vis = degrid(pr.plan, wk, pr.uvw, G, ws=pr.grid_ws)
+        vis = degrid(pr.degrid_plan, wk, pr.uvw, G, ws=pr.grid_ws)
         ctx.pr = pr
         ctx.wk = wk
         ctx.save_for_backward(image, taper, G)

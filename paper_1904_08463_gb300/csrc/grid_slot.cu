@@ -106,15 +106,18 @@ __global__ void __launch_bounds__(256) k_gather_slot(int64_t V, int os, int s_ma
     slot_gather_one(i, os, s_max, idx, rec, support, vis, weight, srec, svis);
 }
 
-// Items of plane q: ceil(n_q / SLOT_CHUNK) chunks x ceil(W/32) x ceil(W/SLOT_ROWS) slot tiles.
+// Items of plane q: ceil(n_q / SLOT_CHUNK) chunks x ceil(W / cols) x ceil(W / tile_rows) slot tiles
+// (tile_rows = (32 / cols) x rows: the walk's tile shape).
 __global__ void __launch_bounds__(256) k_plane_items(int P, int s_max, const int* __restrict__ vstart,
-                                                     const int32_t* __restrict__ support, int* __restrict__ icount) {
+                                                     const int32_t* __restrict__ support, int cols, int tile_rows,
+                                                     int* __restrict__ icount) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q > P) return;
     if (q == P) { icount[P] = 0; return; }
     const int n = vstart[q + 1] - vstart[q];
     const int W = 2 * min(max(support[q], 1), s_max) + 1;
-    icount[q] = (n > 0) ? ((n + SLOT_CHUNK - 1) / SLOT_CHUNK) * ((W + 31) / 32) * ((W + SLOT_ROWS - 1) / SLOT_ROWS) : 0;
+    icount[q] = (n > 0) ? ((n + SLOT_CHUNK - 1) / SLOT_CHUNK) * ((W + cols - 1) / cols) * ((W + tile_rows - 1) / tile_rows)
+                        : 0;
 }
 
 template <int ROWS>
@@ -142,7 +145,7 @@ __global__ void __launch_bounds__(SLOT_WARPS * 32, 3) k_grid_slot(int N, int P, 
 // its cell, reloaded only when the cell changes; per visibility and slot tile the warp's sum of
 // conj(tap) x value is added into vis_out (zeroed first) by lane 0.
 template <int ROWS>
-__global__ void __launch_bounds__(SLOT_WARPS * 32, 4) k_degrid_slot(int N, int P, int s_max,
+__global__ void __launch_bounds__(SLOT_WARPS * 32, 3) k_degrid_slot(int N, int P, int s_max,
                                                                     const int32_t* __restrict__ support,
                                                                     const int64_t* __restrict__ offsets,
                                                                     const float2* __restrict__ cache,
@@ -176,7 +179,7 @@ int grid_slot(const Geom& g, const wp_wkernels* kern, const float* uvw, const fl
               int64_t V, const GridWork& w, float2* grid, double* stats, cudaStream_t st) {
     const int P = kern->P;
     const uint32_t* idx = nullptr;
-    int rc = grid_slot_prepare(g, kern, uvw, weight, V, w, st, &idx);
+    int rc = grid_slot_prepare(g, kern, uvw, weight, V, w, st, &idx, false);
     if (rc) return rc;
     if (V > 0) {
         k_gather_slot<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(V, g.os, g.s_max, w.vstart, P, idx, w.rec, w.seff,
@@ -199,7 +202,9 @@ int grid_slot(const Geom& g, const wp_wkernels* kern, const float* uvw, const fl
 // sort, plane bounds, item counts and their scan; *idx_sorted = the sort's permutation.  The gather
 // of the sorted records (k_gather_slot / slot_gather_one) is left to the caller.
 int grid_slot_prepare(const Geom& g, const wp_wkernels* kern, const float* uvw, const float* weight, int64_t V,
-                      const GridWork& w, cudaStream_t st, const uint32_t** idx_sorted) {
+                      const GridWork& w, cudaStream_t st, const uint32_t** idx_sorted, bool degrid) {
+    // the tile shape of the walk that will consume the items
+    const int cols = SLOT_COLS, tile_rows = (32 / SLOT_COLS) * (degrid ? SLOT_DEGRID_ROWS : SLOT_ROWS);
     const int P = kern->P;
     int rc = WP_OK;
     WP_CUDA(cudaMemsetAsync(w.ctrl, 0, sizeof(int) * 8, st));
@@ -223,7 +228,8 @@ int grid_slot_prepare(const Geom& g, const wp_wkernels* kern, const float* uvw, 
     const uint32_t* idx = in_alt ? w.sidx_alt : w.sidx;
     k_plane_bounds<<<(unsigned)(V > 0 ? (V + 255) / 256 : 1), 256, 0, st>>>(V, P, mb, keys, w.vstart);
     WP_LAUNCH_CHECK("k_plane_bounds");
-    k_plane_items<<<(unsigned)((P + 1 + 255) / 256), 256, 0, st>>>(P, g.s_max, w.vstart, w.seff, w.icount);
+    k_plane_items<<<(unsigned)((P + 1 + 255) / 256), 256, 0, st>>>(P, g.s_max, w.vstart, w.seff, cols, tile_rows,
+                                                                    w.icount);
     WP_LAUNCH_CHECK("k_plane_items");
     rc = exclusive_scan_i32(w.icount, w.istart, (int64_t)P + 1, w.scan_tmp, st);
     if (rc) return rc;
@@ -236,7 +242,7 @@ int degrid_slot(const Geom& g, const wp_wkernels* kern, const float* uvw, int64_
     const int P = kern->P;
     WP_CUDA(cudaMemsetAsync(vis_out, 0, sizeof(float2) * (size_t)V, st));
     const uint32_t* idx = nullptr;
-    int rc = grid_slot_prepare(g, kern, uvw, nullptr, V, w, st, &idx);
+    int rc = grid_slot_prepare(g, kern, uvw, nullptr, V, w, st, &idx, true);
     if (rc) return rc;
     if (V == 0) return WP_OK;
     k_gather_slot<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(V, g.os, g.s_max, w.vstart, P, idx, w.rec, w.seff,
@@ -245,9 +251,9 @@ int degrid_slot(const Geom& g, const wp_wkernels* kern, const float* uvw, int64_
     int dev = 0, sms = 0, per_sm = 0;
     WP_CUDA(cudaGetDevice(&dev));
     WP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid_slot<SLOT_ROWS>, SLOT_WARPS * 32, 0));
+    WP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid_slot<SLOT_DEGRID_ROWS>, SLOT_WARPS * 32, 0));
     if (per_sm < 1) per_sm = 1;
-    k_degrid_slot<SLOT_ROWS><<<sms * per_sm, SLOT_WARPS * 32, 0, st>>>(g.N, P, g.s_max, w.seff, kern->offsets,
+    k_degrid_slot<SLOT_DEGRID_ROWS><<<sms * per_sm, SLOT_WARPS * 32, 0, st>>>(g.N, P, g.s_max, w.seff, kern->offsets,
                                                             reinterpret_cast<const float2*>(kern->cache), w.vstart,
                                                             w.istart, w.srec, grid, w.ctrl, vis_out, V);
     WP_LAUNCH_CHECK("k_degrid_slot");

@@ -18,7 +18,9 @@
 
 namespace wp {
 
-constexpr int SLOT_ROWS = 10;        // slot rows per lane (registers: sum, tap row, tap offset each)
+constexpr int SLOT_ROWS = 10;        // slot rows per lane of the gridder (registers: sum, cell offset each)
+constexpr int SLOT_DEGRID_ROWS = 8;  // slot rows per lane of the degridder
+constexpr int SLOT_COLS = 32;        // slot columns of a warp tile (32; 16 with two row groups measured slower)
 constexpr int SLOT_CHUNK = 512;      // visibilities per work item
 constexpr int SLOT_WARPS = 8;        // warps per block
 constexpr bool SLOT_PAIR = false;    // gridding sums as two packed-FMA pairs (fma.rn.f32x2)
@@ -83,10 +85,11 @@ __device__ __forceinline__ float2 slot_value(float2 p, float2 q) {
 }
 
 // Places the slots for the footprint of record r (corner x0 | y0 << 16 in r.x, the corner mod W
-// in r.y): the lane's column cell cx, row `lane`'s cell row cyt (lanes < ROWS), every tap offset,
-// and the sums zeroed (gridding) or the cells' grid values read (DEGRID).
+// in r.y): the lane's column cell cx, the cell row cyt of tile row `lane` (lanes below the
+// tile's row count), every tap offset, and the sums zeroed (gridding) or the cells' grid values
+// read (DEGRID).  The lane's own rows are tile rows rbase .. rbase + ROWS - 1.
 template <int ROWS, bool DEGRID>
-__device__ __forceinline__ void slot_place(int4 r, int W, int N, int a_res, int b_res, int nval,
+__device__ __forceinline__ void slot_place(int4 r, int W, int N, int a_res, int b_res, int nval, int rbase,
                                            const float2* __restrict__ grid, int& cx, int& cyt, unsigned& cb, unsigned (&coff)[ROWS],
                                            float2 (&acc)[ROWS], float2 (&acq)[ROWS]) {
     const int x0 = r.x & 0xffff, y0 = (r.x >> 16) & 0xffff;
@@ -100,7 +103,7 @@ __device__ __forceinline__ void slot_place(int4 r, int W, int N, int a_res, int 
     cb = (unsigned)(y0 * W + x0) * 8u;
 #pragma unroll
     for (int j = 0; j < ROWS; ++j) {
-        const int cyj = __shfl_sync(0xffffffffu, cyt, j);
+        const int cyj = __shfl_sync(0xffffffffu, cyt, rbase + j);
         coff[j] = (unsigned)(cyj * W + cx) * 8u;
         acc[j] = (DEGRID && j < nval) ? slot_get(grid, N, cyj, cx) : make_float2(0.0f, 0.0f);
         acq[j] = make_float2(0.0f, 0.0f);
@@ -111,7 +114,7 @@ __device__ __forceinline__ void slot_place(int4 r, int W, int N, int a_res, int 
 // when the cell changes).  DEGRID = true: degridding, the adjoint (each slot holds the value of
 // `grid` at its cell, reloaded when the cell changes; per visibility the warp sums conj(tap) x
 // value over its slots and adds the sum into vis_out[original index]; svis is not read).
-template <int ROWS, bool COHERENT, bool DEGRID>
+template <int ROWS, bool COHERENT, bool DEGRID, int COLS = SLOT_COLS>
 __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const int32_t* __restrict__ support,
                                           const int64_t* __restrict__ offsets, const float2* __restrict__ cache,
                                           const int* __restrict__ vstart, const int* __restrict__ istart,
@@ -126,34 +129,39 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
     const int p = lo;
     const int S = min(max(support[p], 1), s_max);
     const int W = 2 * S + 1;
-    const int nxs = (W + 31) >> 5, nys = (W + ROWS - 1) / ROWS;
+    constexpr int TR = (32 / COLS) * ROWS;   // slot rows of a warp tile (one or two row groups)
+    static_assert(COLS == 32 || COLS == 16, "a warp tile is 32 or 16 columns wide");
+    static_assert(TR <= 32, "one lane per tile row");
+    const int nxs = (W + COLS - 1) / COLS, nys = (W + TR - 1) / TR;
     const int local = it - istart[p];
     const int chunk = local / (nxs * nys);
     const int tt = local - chunk * (nxs * nys);
     const int tys = tt / nxs, txs = tt - tys * nxs;
     const int v0 = vstart[p] + chunk * SLOT_CHUNK;
     const int v1 = min(v0 + SLOT_CHUNK, vstart[p + 1]);
+    if (v0 >= v1) return;   // no visibility (only an item list built for another tile shape gets here)
     const float2* pc = cache + offsets[p];
     const int64_t blk = offsets[p + 1] - offsets[p];   // the plane's block (checked build)
-    const int a = txs * 32 + lane;            // the lane's slot column
+    const int a = txs * COLS + lane % COLS;   // the lane's slot column
     const bool a_ok = a < W;
-    const int b0 = tys * ROWS;                // slot rows b0 .. b0 + ROWS - 1
-    const int nrows = min(ROWS, W - b0);      // rows of this tile inside the W x W residues
+    const int b0 = tys * TR;                  // slot rows b0 .. b0 + TR - 1 of the tile
+    const int rbase = (lane / COLS) * ROWS;   // the lane's rows: b0 + rbase .. b0 + rbase + ROWS - 1
+    const int nrows = max(0, min(ROWS, W - b0 - rbase));   // of them inside the W x W residues
     // Slot (lane, j) sums the cell (cx, cy[j]): column cx of the lane, row cy[j] of row j.  Its
     // tap in the footprint with corner (x0, y0) is (cx - x0, cy[j] - y0), at byte offset
     // ((cy[j] - y0) W + cx - x0) x 8 = coff[j] - cb of the sub-kernel, coff[j] = (cy[j] W + cx) x 8
     // depending on the cell alone and cb = (y0 W + x0) x 8 on the corner alone.  A footprint move
     // keeps every cell and changes cb only; a slot whose cell leaves the new footprint (cx - x0
     // or cy[j] - y0 outside [0, W)) writes its sum to the grid and moves its cell by a period W.  The row
-    // cells are the same in every lane and live one per lane (lane j < ROWS holds cy[j]), so the
-    // rows that move are one ballot and the columns that move one vote.  Lanes and rows beyond
+    // cells are the same in every lane of a row group and live one per lane (lane k < TR holds
+    // the cell row of tile row k), so the rows that move are one ballot and the columns that move
+    // one vote.  Lanes and rows beyond
     // the W x W residues track the residue a mod W (b mod W) of a slot that exists, so every tap
     // offset stays inside the sub-kernel; they are never flushed.  (For DEGRID, acc[j] holds the
     // grid value at the slot's cell instead of a running sum, reloaded when the cell moves.)
-    static_assert(ROWS <= 32, "one lane per slot row");
     const unsigned FULL = 0xffffffffu;
     const int a_res = a % W;
-    const int b_res = (b0 + (lane < ROWS ? lane : 0)) % W;
+    const int b_res = (b0 + (lane < TR ? lane : 0)) % W;
     const int nval = a_ok ? nrows : 0;        // rows j < nval of this lane are real slots
     float2 acc[ROWS];
     float2 acq[ROWS];                         // second pair of the packed-FMA sums (SLOT_PAIR)
@@ -163,7 +171,7 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
     float2 vn = DEGRID ? make_float2(0.0f, 0.0f) : ld_slot_vis<COHERENT>(svis + v0);
     uint32_t prev = (uint32_t)rn.x;           // corner of the current footprint: x0 | y0 << 16
     int cx, cyt;
-    slot_place<ROWS, DEGRID>(rn, W, N, a_res, b_res, nval, grid, cx, cyt, cb, coff, acc, acq);
+    slot_place<ROWS, DEGRID>(rn, W, N, a_res, b_res, nval, rbase, grid, cx, cyt, cb, coff, acc, acq);
     for (int q = v0; q < v1; ++q) {
         const int4 r = rn;
         const float2 v = vn;
@@ -180,24 +188,25 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
                 if (!DEGRID) {
 #pragma unroll
                     for (int j = 0; j < ROWS; ++j) {
-                        const int cyj = __shfl_sync(FULL, cyt, j);
+                        const int cyj = __shfl_sync(FULL, cyt, rbase + j);
                         const float2 sj = slot_value(acc[j], acq[j]);
                         if (j < nval && slot_nonzero(sj)) slot_add(grid, N, cyj, cx, sj);
                     }
                 }
-                slot_place<ROWS, DEGRID>(r, W, N, a_res, b_res, nval, grid, cx, cyt, cb, coff, acc, acq);
+                slot_place<ROWS, DEGRID>(r, W, N, a_res, b_res, nval, rbase, grid, cx, cyt, cb, coff, acc, acq);
             } else {
                 cb = (unsigned)(y0 * W + x0) * 8u;
                 int tx = cx - x0;                 // the lane's column moves when tx leaves [0, W)
                 const bool xw = (unsigned)tx >= (unsigned)W;
-                const unsigned rm = __ballot_sync(FULL, lane < ROWS && (unsigned)(cyt - y0) >= (unsigned)W);
+                const unsigned rm = __ballot_sync(FULL, lane < TR && (unsigned)(cyt - y0) >= (unsigned)W);
+                const unsigned my_rm = rm >> rbase;   // bit j: the lane's row j moves
                 if (__any_sync(FULL, xw)) {       // columns that move: every row of those lanes
                     tx += (tx < 0) ? W : ((tx >= W) ? -W : 0);
                     const int cxn = x0 + tx;
                     const unsigned dxo = (unsigned)(cxn - cx) * 8u;
 #pragma unroll
                     for (int j = 0; j < ROWS; ++j) {
-                        const int cyj = __shfl_sync(FULL, cyt, j);
+                        const int cyj = __shfl_sync(FULL, cyt, rbase + j);
                         if (!DEGRID) {
                             const float2 sj = slot_value(acc[j], acq[j]);
                             if (xw && j < nval && slot_nonzero(sj)) slot_add(grid, N, cyj, cx, sj);
@@ -211,25 +220,29 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
                 if (rm) {                            // rows that move: every lane of those rows
 #pragma unroll
                     for (int j = 0; j < ROWS; ++j) {
-                        if (rm & (1u << j)) {
-                            const int cyj = __shfl_sync(FULL, cyt, j);
-                            const int cyn = cyj + ((cyj < y0) ? W : -W);
-                            if (!DEGRID) {
-                                const float2 sj = slot_value(acc[j], acq[j]);
-                                if (j < nval && slot_nonzero(sj)) slot_add(grid, N, cyj, cx, sj);
-                                acc[j] = make_float2(0.0f, 0.0f);
-                                acq[j] = make_float2(0.0f, 0.0f);
+                        // row j of some row group moves (the same test in every lane)
+                        const bool any_j = (COLS == 32) ? ((rm >> j) & 1u) : (((rm >> j) | (rm >> (ROWS + j))) & 1u);
+                        if (any_j) {
+                            const int cyj = __shfl_sync(FULL, cyt, rbase + j);
+                            if ((my_rm >> j) & 1u) {
+                                const int cyn = cyj + ((cyj < y0) ? W : -W);
+                                if (!DEGRID) {
+                                    const float2 sj = slot_value(acc[j], acq[j]);
+                                    if (j < nval && slot_nonzero(sj)) slot_add(grid, N, cyj, cx, sj);
+                                    acc[j] = make_float2(0.0f, 0.0f);
+                                    acq[j] = make_float2(0.0f, 0.0f);
+                                }
+                                coff[j] += (unsigned)((cyn - cyj) * W) * 8u;
+                                if (DEGRID && j < nval) acc[j] = slot_get(grid, N, cyn, cx);
                             }
-                            coff[j] += (unsigned)((cyn - cyj) * W) * 8u;
-                            if (DEGRID && j < nval) acc[j] = slot_get(grid, N, cyn, cx);
                         }
                     }
-                    if (lane < ROWS && (rm & (1u << lane))) cyt += (cyt < y0) ? W : -W;
+                    if (lane < TR && ((rm >> lane) & 1u)) cyt += (cyt < y0) ? W : -W;
                 }
                 if (DEGRID && __any_sync(FULL, xw)) {    // moved columns read their new cells
 #pragma unroll
                     for (int j = 0; j < ROWS; ++j) {
-                        const int cyj = __shfl_sync(FULL, cyt, j);
+                        const int cyj = __shfl_sync(FULL, cyt, rbase + j);
                         if (xw && j < nval) acc[j] = slot_get(grid, N, cyj, cx);
                     }
                 }
@@ -275,7 +288,7 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
     if (!DEGRID) {
 #pragma unroll
         for (int j = 0; j < ROWS; ++j) {
-            const int cyj = __shfl_sync(FULL, cyt, j);
+            const int cyj = __shfl_sync(FULL, cyt, rbase + j);
             const float2 sj = slot_value(acc[j], acq[j]);
             if (j < nval && slot_nonzero(sj)) slot_add(grid, N, cyj, cx, sj);
         }

@@ -336,7 +336,7 @@ size_t slot_hist_ints(int64_t V);
 int grid_slot(const Geom& g, const wp_wkernels* kern, const float* uvw, const float2* vis, const float* weight,
               int64_t V, const GridWork& w, float2* grid, double* stats, cudaStream_t st);
 int grid_slot_prepare(const Geom& g, const wp_wkernels* kern, const float* uvw, const float* weight, int64_t V,
-                      const GridWork& w, cudaStream_t st, const uint32_t** idx_sorted);
+                      const GridWork& w, cudaStream_t st, const uint32_t** idx_sorted, bool degrid = false);
 int degrid_slot(const Geom& g, const wp_wkernels* kern, const float* uvw, int64_t V, const GridWork& w,
                 const float2* grid, float2* vis_out, cudaStream_t st);
 int grid_run_group(const Geom& g, const wp_wkernels* k, const GridWork& w, float2* grid, cudaStream_t st);
