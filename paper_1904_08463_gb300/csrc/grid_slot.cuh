@@ -23,7 +23,6 @@ constexpr int SLOT_DEGRID_ROWS = 8;  // slot rows per lane of the degridder
 constexpr int SLOT_COLS = 32;        // slot columns of a warp tile (32; 16 with two row groups measured slower)
 constexpr int SLOT_CHUNK = 512;      // visibilities per work item
 constexpr int SLOT_WARPS = 8;        // warps per block
-constexpr bool SLOT_PAIR = false;    // gridding sums as two packed-FMA pairs (fma.rn.f32x2)
 
 template <bool COHERENT>
 __device__ __forceinline__ int4 ld_slot_rec(const int4* p) { return COHERENT ? __ldcg(p) : __ldg(p); }
@@ -67,23 +66,6 @@ __device__ __forceinline__ bool slot_nonzero(float2 a) {
     return ((__float_as_uint(a.x) | __float_as_uint(a.y)) & 0x7fffffffu) != 0u;
 }
 
-// a + b x c on both halves of a pair in one instruction (IEEE fma, round to nearest, per half)
-__device__ __forceinline__ float2 ffma2(float2 b, float2 c, float2 a) {
-    unsigned long long d;
-    asm("{\n\t.reg .b64 pb, pc, pa;\n\tmov.b64 pb, {%1, %2};\n\tmov.b64 pc, {%3, %4};\n\tmov.b64 pa, {%5, %6};\n\t"
-        "fma.rn.f32x2 %0, pb, pc, pa;\n\t}"
-        : "=l"(d) : "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y), "f"(a.x), "f"(a.y));
-    float2 r;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(d));
-    return r;
-}
-
-// The grid value of a slot's running sum.  SLOT_PAIR keeps P = sum (cA tx, cC ty) and
-// Q = sum (cD tx, cB ty) (two packed FMAs per tap); the sum is (P.x + Q.y, P.y + Q.x).
-__device__ __forceinline__ float2 slot_value(float2 p, float2 q) {
-    return SLOT_PAIR ? make_float2(p.x + q.y, p.y + q.x) : p;
-}
-
 // Places the slots for the footprint of record r (corner x0 | y0 << 16 in r.x, the corner mod W
 // in r.y): the lane's column cell cx, the cell row cyt of tile row `lane` (lanes below the
 // tile's row count), every tap offset, and the sums zeroed (gridding) or the cells' grid values
@@ -91,7 +73,7 @@ __device__ __forceinline__ float2 slot_value(float2 p, float2 q) {
 template <int ROWS, bool DEGRID>
 __device__ __forceinline__ void slot_place(int4 r, int W, int N, int a_res, int b_res, int nval, int rbase,
                                            const float2* __restrict__ grid, int& cx, int& cyt, unsigned& cb, unsigned (&coff)[ROWS],
-                                           float2 (&acc)[ROWS], float2 (&acq)[ROWS]) {
+                                           float2 (&acc)[ROWS]) {
     const int x0 = r.x & 0xffff, y0 = (r.x >> 16) & 0xffff;
     const int xm = r.y & 0xffff, ym = (r.y >> 16) & 0xffff;
     int nx = a_res - xm;
@@ -106,7 +88,6 @@ __device__ __forceinline__ void slot_place(int4 r, int W, int N, int a_res, int 
         const int cyj = __shfl_sync(0xffffffffu, cyt, rbase + j);
         coff[j] = (unsigned)(cyj * W + cx) * 8u;
         acc[j] = (DEGRID && j < nval) ? slot_get(grid, N, cyj, cx) : make_float2(0.0f, 0.0f);
-        acq[j] = make_float2(0.0f, 0.0f);
     }
 }
 
@@ -164,14 +145,13 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
     const int b_res = (b0 + (lane < TR ? lane : 0)) % W;
     const int nval = a_ok ? nrows : 0;        // rows j < nval of this lane are real slots
     float2 acc[ROWS];
-    float2 acq[ROWS];                         // second pair of the packed-FMA sums (SLOT_PAIR)
     unsigned coff[ROWS];                      // (cy[j] W + cx) x 8: the cell's part of the tap offset
     unsigned cb;                              // (y0 W + x0) x 8 of the current corner
     int4 rn = ld_slot_rec<COHERENT>(srec + v0);
     float2 vn = DEGRID ? make_float2(0.0f, 0.0f) : ld_slot_vis<COHERENT>(svis + v0);
     uint32_t prev = (uint32_t)rn.x;           // corner of the current footprint: x0 | y0 << 16
     int cx, cyt;
-    slot_place<ROWS, DEGRID>(rn, W, N, a_res, b_res, nval, rbase, grid, cx, cyt, cb, coff, acc, acq);
+    slot_place<ROWS, DEGRID>(rn, W, N, a_res, b_res, nval, rbase, grid, cx, cyt, cb, coff, acc);
     for (int q = v0; q < v1; ++q) {
         const int4 r = rn;
         const float2 v = vn;
@@ -189,11 +169,11 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
 #pragma unroll
                     for (int j = 0; j < ROWS; ++j) {
                         const int cyj = __shfl_sync(FULL, cyt, rbase + j);
-                        const float2 sj = slot_value(acc[j], acq[j]);
+                        const float2 sj = acc[j];
                         if (j < nval && slot_nonzero(sj)) slot_add(grid, N, cyj, cx, sj);
                     }
                 }
-                slot_place<ROWS, DEGRID>(r, W, N, a_res, b_res, nval, rbase, grid, cx, cyt, cb, coff, acc, acq);
+                slot_place<ROWS, DEGRID>(r, W, N, a_res, b_res, nval, rbase, grid, cx, cyt, cb, coff, acc);
             } else {
                 cb = (unsigned)(y0 * W + x0) * 8u;
                 int tx = cx - x0;                 // the lane's column moves when tx leaves [0, W)
@@ -208,10 +188,9 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
                     for (int j = 0; j < ROWS; ++j) {
                         const int cyj = __shfl_sync(FULL, cyt, rbase + j);
                         if (!DEGRID) {
-                            const float2 sj = slot_value(acc[j], acq[j]);
+                            const float2 sj = acc[j];
                             if (xw && j < nval && slot_nonzero(sj)) slot_add(grid, N, cyj, cx, sj);
                             acc[j] = xw ? make_float2(0.0f, 0.0f) : acc[j];
-                            acq[j] = xw ? make_float2(0.0f, 0.0f) : acq[j];
                         }
                         coff[j] += xw ? dxo : 0u;
                     }
@@ -227,10 +206,9 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
                             if ((my_rm >> j) & 1u) {
                                 const int cyn = cyj + ((cyj < y0) ? W : -W);
                                 if (!DEGRID) {
-                                    const float2 sj = slot_value(acc[j], acq[j]);
+                                    const float2 sj = acc[j];
                                     if (j < nval && slot_nonzero(sj)) slot_add(grid, N, cyj, cx, sj);
                                     acc[j] = make_float2(0.0f, 0.0f);
-                                    acq[j] = make_float2(0.0f, 0.0f);
                                 }
                                 coff[j] += (unsigned)((cyn - cyj) * W) * 8u;
                                 if (DEGRID && j < nval) acc[j] = slot_get(grid, N, cyn, cx);
@@ -275,13 +253,8 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
             const float cA = v.x, cB = -sg * v.y, cC = sg * v.x, cD = v.y;
 #pragma unroll
             for (int j = 0; j < ROWS; ++j) {
-                if (SLOT_PAIR) {
-                    acc[j] = ffma2(make_float2(cA, cC), tp[j], acc[j]);
-                    acq[j] = ffma2(make_float2(cD, cB), tp[j], acq[j]);
-                } else {
-                    acc[j].x = fmaf(cA, tp[j].x, fmaf(cB, tp[j].y, acc[j].x));
-                    acc[j].y = fmaf(cC, tp[j].y, fmaf(cD, tp[j].x, acc[j].y));
-                }
+                acc[j].x = fmaf(cA, tp[j].x, fmaf(cB, tp[j].y, acc[j].x));
+                acc[j].y = fmaf(cC, tp[j].y, fmaf(cD, tp[j].x, acc[j].y));
             }
         }
     }
@@ -289,7 +262,7 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
 #pragma unroll
         for (int j = 0; j < ROWS; ++j) {
             const int cyj = __shfl_sync(FULL, cyt, rbase + j);
-            const float2 sj = slot_value(acc[j], acq[j]);
+            const float2 sj = acc[j];
             if (j < nval && slot_nonzero(sj)) slot_add(grid, N, cyj, cx, sj);
         }
     }
