@@ -2,7 +2,8 @@
 
 Every translation unit is compiled for sm_103a only, in parallel, then linked with the
 CUDA runtime (shared) and cuFFT.  Rebuilds only when a source or header is newer than
-the library.  build_checked() makes libwproj_checked.so, the same sources compiled with
+the library, and then only the objects older than their source or a header (objects built on
+another kind of machine or with other flags are never reused).  build_checked() makes libwproj_checked.so, the same sources compiled with
 -DWP_CHECK_BOUNDS (index checks on the kernels' main buffer accesses, read back with
 wp_bounds_status); it is a test build, never the one the package loads by default.
 """
@@ -11,6 +12,7 @@ from __future__ import annotations
 import concurrent.futures as cf
 import glob
 import os
+import platform
 import shutil
 import subprocess
 
@@ -66,8 +68,19 @@ def _build(lib: str, build_dir: str, defines: list[str], force: bool, verbose: b
     nvcc = _nvcc()
     cuda_home = os.path.dirname(os.path.dirname(nvcc))
 
+    headers = [d for d in _deps() if not d.endswith(".cu")]
+    t_headers = max(os.path.getmtime(h) for h in headers)
+    # objects are reused only when they were built on this kind of machine with these flags
+    stamp = os.path.join(build_dir, "stamp.txt")
+    key = f"{platform.machine()} {nvcc} {' '.join(flags() + defines)}"
+    if not os.path.exists(stamp) or open(stamp).read() != key:
+        force = True
+
     def compile_one(src: str) -> str:
         obj = os.path.join(build_dir, os.path.basename(src) + ".o")
+        # an object newer than its source and every header is reused
+        if not force and os.path.exists(obj) and os.path.getmtime(obj) > max(os.path.getmtime(src), t_headers):
+            return obj
         cmd = [nvcc, *flags(), *defines, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -81,6 +94,8 @@ def _build(lib: str, build_dir: str, defines: list[str], force: bool, verbose: b
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, sources()))
+    with open(stamp, "w") as fh:
+        fh.write(key)
     tmp = lib + f".{os.getpid()}.tmp"
     libdir = os.path.join(cuda_home, "lib64")
     if not os.path.isdir(libdir):

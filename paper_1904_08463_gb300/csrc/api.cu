@@ -505,6 +505,17 @@ size_t wp_grid_workspace_bytes(const wp_plan* plan, int32_t P, int64_t V) {
 
 }  // extern "C"
 
+// One gridding call on a carved workspace: the slot gridder (9) bins along a Morton curve of
+// each plane; every other method bins by (plane, tile) and runs from its item list.
+int wp::grid_dispatch(const Geom& g, const wp_wkernels* kern, const float* uvw, const float2* vis,
+                      const float* weight, int64_t V, const GridWork& w, float2* grid, double* stats,
+                      cudaStream_t st) {
+    if (g.grid_method == 9) return grid_slot(g, kern, uvw, vis, weight, V, w, grid, stats, st);
+    int rc = grid_bin(g, kern, uvw, vis, weight, V, w, st);
+    if (rc) return rc;
+    return grid_run(g, kern, w, grid, stats, st);
+}
+
 // Argument checks of every call that bins visibilities.  with_workspace = false skips the
 // caller-workspace checks (the allocation-free gridder supplies its own scratch).
 int wp::check_grid_args(const wp_plan* plan, const wp_wkernels* k, const float* uvw, int64_t V,
@@ -541,11 +552,8 @@ int wp_grid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw, c
     cudaStream_t st = (cudaStream_t)stream;
     GridWork w;
     carve_grid(g, kernels->P, V, workspace, workspace_bytes, &w);
-    if (g.grid_method == 9)      // slot gridder: its own binning (Morton-sorted planes)
-        return grid_slot(g, kernels, uvw, reinterpret_cast<const float2*>(vis), weight, V, w,
+    return grid_dispatch(g, kernels, uvw, reinterpret_cast<const float2*>(vis), weight, V, w,
                          reinterpret_cast<float2*>(grid), stats, st);
-    if ((rc = grid_bin(g, kernels, uvw, reinterpret_cast<const float2*>(vis), weight, V, w, st))) return rc;
-    return grid_run(g, kernels, w, reinterpret_cast<float2*>(grid), stats, st);
 }
 
 int wp_degrid(const wp_plan* plan, const wp_wkernels* kernels, const float* uvw, const float* grid,

@@ -66,9 +66,6 @@ extern "C" int wp_grid_static(const wp_plan* plan, const wp_wkernels* kernels, c
     cudaStream_t st = (cudaStream_t)stream;
     GridWork w;
     carve_grid(g, kernels->P, V, scratch, kStaticScratchBytes, &w);
-    if (g.grid_method == 9)
-        return grid_slot(g, kernels, uvw, reinterpret_cast<const float2*>(vis), weight, V, w,
+    return grid_dispatch(g, kernels, uvw, reinterpret_cast<const float2*>(vis), weight, V, w,
                          reinterpret_cast<float2*>(grid), stats, st);
-    if ((rc = grid_bin(g, kernels, uvw, reinterpret_cast<const float2*>(vis), weight, V, w, st))) return rc;
-    return grid_run(g, kernels, w, reinterpret_cast<float2*>(grid), stats, st);
 }

@@ -337,6 +337,9 @@ int grid_slot(const Geom& g, const wp_wkernels* kern, const float* uvw, const fl
               int64_t V, const GridWork& w, float2* grid, double* stats, cudaStream_t st);
 int grid_slot_prepare(const Geom& g, const wp_wkernels* kern, const float* uvw, const float* weight, int64_t V,
                       const GridWork& w, cudaStream_t st, const uint32_t** idx_sorted, bool degrid = false);
+// one gridding call on a carved workspace, by plan.grid_method (wp_grid and wp_grid_static)
+int grid_dispatch(const Geom& g, const wp_wkernels* kern, const float* uvw, const float2* vis, const float* weight,
+                  int64_t V, const GridWork& w, float2* grid, double* stats, cudaStream_t st);
 int degrid_slot(const Geom& g, const wp_wkernels* kern, const float* uvw, int64_t V, const GridWork& w,
                 const float2* grid, float2* vis_out, cudaStream_t st);
 int grid_run_group(const Geom& g, const wp_wkernels* k, const GridWork& w, float2* grid, cudaStream_t st);

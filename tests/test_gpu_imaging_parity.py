@@ -43,12 +43,27 @@ def _oracle_image(N, dl, R, P, uvw, vis, wt=None, s_max=127, taper=None):
     return g, ks, b, img
 
 
-def test_full_imaging_subset_through_the_benchmark_step():
+_ORACLE = {}
+
+
+def _subset_and_oracle():
+    """The subset and the oracle's image of it, computed once for every gridder below."""
+    if not _ORACLE:
+        N, dl, uvw, vis = _full_imaging_subset()
+        _ORACLE["inputs"] = (N, dl, uvw, vis)
+        _ORACLE["oracle"] = _oracle_image(N, dl, 512, 512, uvw, vis)
+    return _ORACLE["inputs"], _ORACLE["oracle"]
+
+
+@pytest.mark.parametrize("shape", [None, (9, 64)])
+def test_full_imaging_subset_through_the_benchmark_step(shape):
+    """shape None: the gridder the autotuner picks for the subset; otherwise that gridder (the
+    slot gridder, which the full-size benchmark picks) in the same step."""
     import paper_1904_08463_gb300 as wp
     from paper_1904_08463_gb300.imager import Imager
 
     dev = torch.device("cuda")
-    N, dl, uvw, vis = _full_imaging_subset()
+    (N, dl, uvw, vis), (g, ks, b, ref) = _subset_and_oracle()
     R, P = 512, 512
     plan = wp.Plan(N, dl, 8, 127, 3, 0.01, R, "cubic", "bf16x3")
     taper = synth.gaussian_taper_samples(N, dl, R)
@@ -56,10 +71,9 @@ def test_full_imaging_subset_through_the_benchmark_step():
     u_d = torch.tensor(uvw, device=dev).reshape(-1)
     v_d = torch.tensor(vis, device=dev)
     im = Imager(plan, tap_d, u_d, P)
-    im.autotune(u_d, v_d)
+    im.autotune(u_d, v_d, choices=None if shape is None else [list(shape)])
     img = im.step(u_d, v_d).cpu().numpy()
     stats = im.stats.cpu().numpy()
-    g, ks, b, ref = _oracle_image(N, dl, R, P, uvw, vis)
     # the device's plane values and 1 % supports are the oracle's
     assert np.allclose(im.w_planes.cpu().numpy(), ks.w_planes, rtol=1e-13, atol=0)
     assert np.array_equal(im.support.cpu().numpy(), ks.support)
