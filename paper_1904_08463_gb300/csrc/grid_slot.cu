@@ -17,8 +17,8 @@
 // (iu, iv)) sorted by the library's radix sort, per-plane bounds of the sorted list, and one
 // gathered record per visibility: footprint corner, corner mod W, sub-kernel offset with the
 // conjugation flag, original index; the weighted value beside it.  Work item = (plane, chunk of
-// up to SLOT_CHUNK consecutive visibilities, 32 x SLOT_ROWS tile of the W x W slots), one warp
-// per item, pulled from a queue.
+// up to SLOT_CHUNK consecutive visibilities, tile of the W x W slots: 32 x SLOT_ROWS, or
+// 16 x 2 SLOT_ROWS for the last W mod 32 <= 16 columns), one warp per item, pulled from a queue.
 #include <cuda_runtime.h>
 
 #include "wp_internal.cuh"
@@ -106,18 +106,19 @@ __global__ void __launch_bounds__(256) k_gather_slot(int64_t V, int os, int s_ma
     slot_gather_one(i, os, s_max, idx, rec, support, vis, weight, srec, svis);
 }
 
-// Items of plane q: ceil(n_q / SLOT_CHUNK) chunks x ceil(W / cols) x ceil(W / tile_rows) slot tiles
+// Items of plane q: ceil(n_q / SLOT_CHUNK) chunks x the slot tiles of one chunk -- for the
+// gridder (mixed) slot_tiles_mixed(W, rows), else ceil(W / cols) x ceil(W / tile_rows) tiles
 // (tile_rows = (32 / cols) x rows: the walk's tile shape).
 __global__ void __launch_bounds__(256) k_plane_items(int P, int s_max, const int* __restrict__ vstart,
                                                      const int32_t* __restrict__ support, int cols, int tile_rows,
-                                                     int* __restrict__ icount) {
+                                                     int mixed, int rows, int* __restrict__ icount) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q > P) return;
     if (q == P) { icount[P] = 0; return; }
     const int n = vstart[q + 1] - vstart[q];
     const int W = 2 * min(max(support[q], 1), s_max) + 1;
-    icount[q] = (n > 0) ? ((n + SLOT_CHUNK - 1) / SLOT_CHUNK) * ((W + cols - 1) / cols) * ((W + tile_rows - 1) / tile_rows)
-                        : 0;
+    const int tiles = mixed ? slot_tiles_mixed(W, rows) : ((W + cols - 1) / cols) * ((W + tile_rows - 1) / tile_rows);
+    icount[q] = (n > 0) ? ((n + SLOT_CHUNK - 1) / SLOT_CHUNK) * tiles : 0;
 }
 
 template <int ROWS>
@@ -229,7 +230,7 @@ int grid_slot_prepare(const Geom& g, const wp_wkernels* kern, const float* uvw, 
     k_plane_bounds<<<(unsigned)(V > 0 ? (V + 255) / 256 : 1), 256, 0, st>>>(V, P, mb, keys, w.vstart);
     WP_LAUNCH_CHECK("k_plane_bounds");
     k_plane_items<<<(unsigned)((P + 1 + 255) / 256), 256, 0, st>>>(P, g.s_max, w.vstart, w.seff, cols, tile_rows,
-                                                                    w.icount);
+                                                                    degrid ? 0 : 1, SLOT_ROWS, w.icount);
     WP_LAUNCH_CHECK("k_plane_items");
     rc = exclusive_scan_i32(w.icount, w.istart, (int64_t)P + 1, w.scan_tmp, st);
     if (rc) return rc;

@@ -1,7 +1,7 @@
 // One work item of the slot gridder (grid_method 9), shared by the per-call kernel
 // (k_grid_slot) and the persistent multi-job kernel (k_grid_batch): item `it` of the call's
-// item list = (plane, chunk of up to SLOT_CHUNK Morton-sorted visibilities, 32 x ROWS tile of the
-// W x W slots), processed by one warp.
+// item list = (plane, chunk of up to SLOT_CHUNK Morton-sorted visibilities, tile of the W x W
+// slots: 32 x ROWS, or 16 x 2 ROWS for the last W mod 32 <= 16 columns), processed by one warp.
 //
 // Every tap of a (2S+1)^2 footprint whose corner is (x0, y0) lands on a distinct residue class
 // (x mod W, y mod W), W = 2S+1.  The lane owning the residue (a, b) -- a "slot" -- therefore has
@@ -91,33 +91,43 @@ __device__ __forceinline__ void slot_place(int4 r, int W, int N, int a_res, int 
     }
 }
 
-// DEGRID = false: gridding (each slot sums V x tap into its cell and flushes the sum to `grid`
-// when the cell changes).  DEGRID = true: degridding, the adjoint (each slot holds the value of
-// `grid` at its cell, reloaded when the cell changes; per visibility the warp sums conj(tap) x
-// value over its slots and adds the sum into vis_out[original index]; svis is not read).
-template <int ROWS, bool COHERENT, bool DEGRID, int COLS = SLOT_COLS>
-__device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const int32_t* __restrict__ support,
-                                          const int64_t* __restrict__ offsets, const float2* __restrict__ cache,
-                                          const int* __restrict__ vstart, const int* __restrict__ istart,
-                                          const int4* __restrict__ srec, const float2* __restrict__ svis,
-                                          float2* __restrict__ grid, float2* __restrict__ vis_out, int64_t n_vis) {
-    const int lane = threadIdx.x & 31;
-    int lo = 0, hi = P;                       // largest plane with istart <= it
+// The plane of item `it`: the largest p with istart[p] <= it.
+__device__ __forceinline__ int slot_plane(int it, int P, const int* __restrict__ istart) {
+    int lo = 0, hi = P;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
         if (istart[mid] <= it) lo = mid; else hi = mid;
     }
-    const int p = lo;
-    const int S = min(max(support[p], 1), s_max);
-    const int W = 2 * S + 1;
+    return lo;
+}
+
+// Slot tiles per chunk of a plane with footprint width W.  Plain: ceil(W / COLS) x
+// ceil(W / TR) tiles of COLS x TR slots.  Mixed (the gridder): the floor(W / 32) full columns of
+// 32 x ROWS tiles, and the remaining c = W mod 32 columns (if any) in 16 x 2 ROWS tiles when
+// c <= 16 -- two row groups of 16 lanes, half the idle lanes of a 32-wide tile -- else in
+// 32 x ROWS tiles.
+__host__ __device__ __forceinline__ int slot_tiles_mixed(int W, int rows) {
+    const int nys = (W + rows - 1) / rows, nf = W / 32, c = W - 32 * nf;
+    const int nrem = (c == 0) ? 0 : ((c <= 16) ? (W + 2 * rows - 1) / (2 * rows) : nys);
+    return nf * nys + nrem;
+}
+
+// DEGRID = false: gridding (each slot sums V x tap into its cell and flushes the sum to `grid`
+// when the cell changes).  DEGRID = true: degridding, the adjoint (each slot holds the value of
+// `grid` at its cell, reloaded when the cell changes; per visibility the warp sums conj(tap) x
+// value over its slots and adds the sum into vis_out[original index]; svis is not read).
+// One tile: plane p (width W), chunk `chunk` of its sorted visibilities, slot columns
+// txs COLS .. + COLS - 1 and rows tys TR .. + TR - 1.
+template <int ROWS, bool COHERENT, bool DEGRID, int COLS>
+__device__ __forceinline__ void slot_walk_tile(int p, int W, int chunk, int txs, int tys, int N,
+                                               const int64_t* __restrict__ offsets, const float2* __restrict__ cache,
+                                               const int* __restrict__ vstart, const int4* __restrict__ srec,
+                                               const float2* __restrict__ svis, float2* __restrict__ grid,
+                                               float2* __restrict__ vis_out, int64_t n_vis) {
+    const int lane = threadIdx.x & 31;
     constexpr int TR = (32 / COLS) * ROWS;   // slot rows of a warp tile (one or two row groups)
     static_assert(COLS == 32 || COLS == 16, "a warp tile is 32 or 16 columns wide");
     static_assert(TR <= 32, "one lane per tile row");
-    const int nxs = (W + COLS - 1) / COLS, nys = (W + TR - 1) / TR;
-    const int local = it - istart[p];
-    const int chunk = local / (nxs * nys);
-    const int tt = local - chunk * (nxs * nys);
-    const int tys = tt / nxs, txs = tt - tys * nxs;
     const int v0 = vstart[p] + chunk * SLOT_CHUNK;
     const int v1 = min(v0 + SLOT_CHUNK, vstart[p + 1]);
     if (v0 >= v1) return;   // no visibility (only an item list built for another tile shape gets here)
@@ -268,14 +278,51 @@ __device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const
     }
 }
 
+// Item `it` of a plain item list (ceil(W / COLS) x ceil(W / TR) tiles per chunk): the degridder.
+template <int ROWS, bool COHERENT, bool DEGRID, int COLS = SLOT_COLS>
+__device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const int32_t* __restrict__ support,
+                                          const int64_t* __restrict__ offsets, const float2* __restrict__ cache,
+                                          const int* __restrict__ vstart, const int* __restrict__ istart,
+                                          const int4* __restrict__ srec, const float2* __restrict__ svis,
+                                          float2* __restrict__ grid, float2* __restrict__ vis_out, int64_t n_vis) {
+    const int p = slot_plane(it, P, istart);
+    const int W = 2 * min(max(support[p], 1), s_max) + 1;
+    constexpr int TR = (32 / COLS) * ROWS;
+    const int nxs = (W + COLS - 1) / COLS, nys = (W + TR - 1) / TR;
+    const int local = it - istart[p];
+    const int chunk = local / (nxs * nys);
+    const int tt = local - chunk * (nxs * nys);
+    const int tys = tt / nxs, txs = tt - tys * nxs;
+    slot_walk_tile<ROWS, COHERENT, DEGRID, COLS>(p, W, chunk, txs, tys, N, offsets, cache, vstart, srec, svis, grid,
+                                                 vis_out, n_vis);
+}
+
+// Item `it` of the gridder's mixed item list (slot_tiles_mixed tiles per chunk), shared by the
+// per-call kernel and the persistent batch.
 template <int ROWS, bool COHERENT>
 __device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const int32_t* __restrict__ support,
                                           const int64_t* __restrict__ offsets, const float2* __restrict__ cache,
                                           const int* __restrict__ vstart, const int* __restrict__ istart,
                                           const int4* __restrict__ srec, const float2* __restrict__ svis,
                                           float2* __restrict__ grid) {
-    slot_walk<ROWS, COHERENT, false>(it, N, P, s_max, support, offsets, cache, vstart, istart, srec, svis, grid,
-                                     nullptr, 0);
+    const int p = slot_plane(it, P, istart);
+    const int W = 2 * min(max(support[p], 1), s_max) + 1;
+    const int nys = (W + ROWS - 1) / ROWS, nf = W / 32, c = W - 32 * nf;
+    const int T = slot_tiles_mixed(W, ROWS);
+    const int local = it - istart[p];
+    const int chunk = local / T;
+    const int tt = local - chunk * T;
+    if (tt < nf * nys) {                      // a full 32-column tile
+        const int tys = tt / nf;
+        slot_walk_tile<ROWS, COHERENT, false, 32>(p, W, chunk, tt - tys * nf, tys, N, offsets, cache, vstart, srec,
+                                                  svis, grid, nullptr, 0);
+    } else if (c <= 16) {                     // the remaining columns, 16 x 2 ROWS tiles
+        slot_walk_tile<ROWS, COHERENT, false, 16>(p, W, chunk, 2 * nf, tt - nf * nys, N, offsets, cache, vstart,
+                                                  srec, svis, grid, nullptr, 0);
+    } else {                                  // the remaining columns, 32 x ROWS tiles
+        slot_walk_tile<ROWS, COHERENT, false, 32>(p, W, chunk, nf, tt - nf * nys, N, offsets, cache, vstart, srec,
+                                                  svis, grid, nullptr, 0);
+    }
 }
 
 }  // namespace wp
