@@ -67,6 +67,31 @@ __device__ __forceinline__ void q_add(float4 gg, float2 G, float& qr, float& qi)
     qi = fmaf(gg.z, G.y, fmaf(-gg.w, G.x, qi));
 }
 
+// Sum of Q over the visibilities [vb, ve) of one sub-kernel at one footprint position (column
+// ca, row ra): TAP_UNROLL visibilities per pass, all their grid loads issued before the sums
+// (the loads come from L2 and their latency bounds the kernel).
+constexpr int TAP_UNROLL = 8;
+__device__ __forceinline__ void tap_sum1(int vb, int ve, int N, int S, const int* __restrict__ uv2,
+                                         const float4* __restrict__ g4, const float2* __restrict__ grid, int ca,
+                                         int ra, float& qr, float& qi) {
+    const int64_t o = (int64_t)(ra - S) * N + (ca - S);
+    int v = vb;
+    for (; v + TAP_UNROLL <= ve; v += TAP_UNROLL) {
+        float2 G[TAP_UNROLL];
+#pragma unroll
+        for (int i = 0; i < TAP_UNROLL; ++i) {
+            const int u = uv2[v + i];
+            G[i] = grid[(int64_t)((u >> 16) & 0xffff) * N + (u & 0xffff) + o];
+        }
+#pragma unroll
+        for (int i = 0; i < TAP_UNROLL; ++i) q_add(g4[v + i], G[i], qr, qi);
+    }
+    for (; v < ve; ++v) {
+        const int u = uv2[v];
+        q_add(g4[v], grid[(int64_t)((u >> 16) & 0xffff) * N + (u & 0xffff) + o], qr, qi);
+    }
+}
+
 // Sum of Q over the visibilities [vb, ve) of one sub-kernel at up to two columns (ca, and cb
 // when two_c) and two rows (ra, and rb when two_r) of the footprint.  Two visibilities per
 // pass, all their grid loads issued before the sums (the loads come from L2).
@@ -75,6 +100,10 @@ __device__ __forceinline__ void tap_sum(int vb, int ve, bool on, int N, int S, c
                                         int ca, int cb, bool two_c, int ra, int rb, bool two_r,
                                         float& qr, float& qi) {
     if (!on) return;
+    if (!two_c && !two_r) {
+        tap_sum1(vb, ve, N, S, uv2, g4, grid, ca, ra, qr, qi);
+        return;
+    }
     const int64_t o_aa = (int64_t)ra * N + ca, o_ab = (int64_t)ra * N + cb;
     const int64_t o_ba = (int64_t)rb * N + ca, o_bb = (int64_t)rb * N + cb;
     const float2 zero = make_float2(0.0f, 0.0f);

@@ -106,19 +106,17 @@ __global__ void __launch_bounds__(256) k_gather_slot(int64_t V, int os, int s_ma
     slot_gather_one(i, os, s_max, idx, rec, support, vis, weight, srec, svis);
 }
 
-// Items of plane q: ceil(n_q / SLOT_CHUNK) chunks x the slot tiles of one chunk -- for the
-// gridder (mixed) slot_tiles_mixed(W, rows), else ceil(W / cols) x ceil(W / tile_rows) tiles
-// (tile_rows = (32 / cols) x rows: the walk's tile shape).
+// Items of plane q: ceil(n_q / SLOT_CHUNK) chunks x slot_tiles_mixed(W, rows) tiles (rows: the
+// slot rows per lane of the walk that consumes the items).
 __global__ void __launch_bounds__(256) k_plane_items(int P, int s_max, const int* __restrict__ vstart,
-                                                     const int32_t* __restrict__ support, int cols, int tile_rows,
-                                                     int mixed, int rows, int* __restrict__ icount) {
+                                                     const int32_t* __restrict__ support, int rows,
+                                                     int* __restrict__ icount) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q > P) return;
     if (q == P) { icount[P] = 0; return; }
     const int n = vstart[q + 1] - vstart[q];
     const int W = 2 * min(max(support[q], 1), s_max) + 1;
-    const int tiles = mixed ? slot_tiles_mixed(W, rows) : ((W + cols - 1) / cols) * ((W + tile_rows - 1) / tile_rows);
-    icount[q] = (n > 0) ? ((n + SLOT_CHUNK - 1) / SLOT_CHUNK) * tiles : 0;
+    icount[q] = (n > 0) ? ((n + SLOT_CHUNK - 1) / SLOT_CHUNK) * slot_tiles_mixed(W, rows) : 0;
 }
 
 template <int ROWS>
@@ -163,7 +161,7 @@ __global__ void __launch_bounds__(SLOT_WARPS * 32, 3) k_degrid_slot(int N, int P
         if (lane == 0) it = atomicAdd(&ctrl[0], 1);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n_items) break;
-        slot_walk<ROWS, false, true>(it, N, P, s_max, support, offsets, cache, vstart, istart, srec, nullptr,
+        slot_item<ROWS, false, true>(it, N, P, s_max, support, offsets, cache, vstart, istart, srec, nullptr,
                                      const_cast<float2*>(grid), vis_out, V);
     }
 }
@@ -204,8 +202,7 @@ int grid_slot(const Geom& g, const wp_wkernels* kern, const float* uvw, const fl
 // of the sorted records (k_gather_slot / slot_gather_one) is left to the caller.
 int grid_slot_prepare(const Geom& g, const wp_wkernels* kern, const float* uvw, const float* weight, int64_t V,
                       const GridWork& w, cudaStream_t st, const uint32_t** idx_sorted, bool degrid) {
-    // the tile shape of the walk that will consume the items
-    const int cols = SLOT_COLS, tile_rows = (32 / SLOT_COLS) * (degrid ? SLOT_DEGRID_ROWS : SLOT_ROWS);
+    // the slot rows per lane of the walk that will consume the items
     const int P = kern->P;
     int rc = WP_OK;
     WP_CUDA(cudaMemsetAsync(w.ctrl, 0, sizeof(int) * 8, st));
@@ -229,8 +226,8 @@ int grid_slot_prepare(const Geom& g, const wp_wkernels* kern, const float* uvw, 
     const uint32_t* idx = in_alt ? w.sidx_alt : w.sidx;
     k_plane_bounds<<<(unsigned)(V > 0 ? (V + 255) / 256 : 1), 256, 0, st>>>(V, P, mb, keys, w.vstart);
     WP_LAUNCH_CHECK("k_plane_bounds");
-    k_plane_items<<<(unsigned)((P + 1 + 255) / 256), 256, 0, st>>>(P, g.s_max, w.vstart, w.seff, cols, tile_rows,
-                                                                    degrid ? 0 : 1, SLOT_ROWS, w.icount);
+    k_plane_items<<<(unsigned)((P + 1 + 255) / 256), 256, 0, st>>>(P, g.s_max, w.vstart, w.seff,
+                                                                    degrid ? SLOT_DEGRID_ROWS : SLOT_ROWS, w.icount);
     WP_LAUNCH_CHECK("k_plane_items");
     rc = exclusive_scan_i32(w.icount, w.istart, (int64_t)P + 1, w.scan_tmp, st);
     if (rc) return rc;

@@ -20,7 +20,6 @@ namespace wp {
 
 constexpr int SLOT_ROWS = 10;        // slot rows per lane of the gridder (registers: sum, cell offset each)
 constexpr int SLOT_DEGRID_ROWS = 8;  // slot rows per lane of the degridder
-constexpr int SLOT_COLS = 32;        // slot columns of a warp tile (32; 16 with two row groups measured slower)
 constexpr int SLOT_CHUNK = 512;      // visibilities per work item
 constexpr int SLOT_WARPS = 8;        // warps per block
 
@@ -101,8 +100,7 @@ __device__ __forceinline__ int slot_plane(int it, int P, const int* __restrict__
     return lo;
 }
 
-// Slot tiles per chunk of a plane with footprint width W.  Plain: ceil(W / COLS) x
-// ceil(W / TR) tiles of COLS x TR slots.  Mixed (the gridder): the floor(W / 32) full columns of
+// Slot tiles per chunk of a plane with footprint width W: the floor(W / 32) full columns of
 // 32 x ROWS tiles, and the remaining c = W mod 32 columns (if any) in 16 x 2 ROWS tiles when
 // c <= 16 -- two row groups of 16 lanes, half the idle lanes of a 32-wide tile -- else in
 // 32 x ROWS tiles.
@@ -278,33 +276,15 @@ __device__ __forceinline__ void slot_walk_tile(int p, int W, int chunk, int txs,
     }
 }
 
-// Item `it` of a plain item list (ceil(W / COLS) x ceil(W / TR) tiles per chunk): the degridder.
-template <int ROWS, bool COHERENT, bool DEGRID, int COLS = SLOT_COLS>
-__device__ __forceinline__ void slot_walk(int it, int N, int P, int s_max, const int32_t* __restrict__ support,
-                                          const int64_t* __restrict__ offsets, const float2* __restrict__ cache,
-                                          const int* __restrict__ vstart, const int* __restrict__ istart,
-                                          const int4* __restrict__ srec, const float2* __restrict__ svis,
-                                          float2* __restrict__ grid, float2* __restrict__ vis_out, int64_t n_vis) {
-    const int p = slot_plane(it, P, istart);
-    const int W = 2 * min(max(support[p], 1), s_max) + 1;
-    constexpr int TR = (32 / COLS) * ROWS;
-    const int nxs = (W + COLS - 1) / COLS, nys = (W + TR - 1) / TR;
-    const int local = it - istart[p];
-    const int chunk = local / (nxs * nys);
-    const int tt = local - chunk * (nxs * nys);
-    const int tys = tt / nxs, txs = tt - tys * nxs;
-    slot_walk_tile<ROWS, COHERENT, DEGRID, COLS>(p, W, chunk, txs, tys, N, offsets, cache, vstart, srec, svis, grid,
-                                                 vis_out, n_vis);
-}
-
-// Item `it` of the gridder's mixed item list (slot_tiles_mixed tiles per chunk), shared by the
-// per-call kernel and the persistent batch.
-template <int ROWS, bool COHERENT>
+// Item `it` of an item list of slot_tiles_mixed tiles per chunk: the gridder (per call and in
+// the persistent batch) and, with DEGRID, the slot degridder.
+template <int ROWS, bool COHERENT, bool DEGRID = false>
 __device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const int32_t* __restrict__ support,
                                           const int64_t* __restrict__ offsets, const float2* __restrict__ cache,
                                           const int* __restrict__ vstart, const int* __restrict__ istart,
                                           const int4* __restrict__ srec, const float2* __restrict__ svis,
-                                          float2* __restrict__ grid) {
+                                          float2* __restrict__ grid, float2* __restrict__ vis_out = nullptr,
+                                          int64_t n_vis = 0) {
     const int p = slot_plane(it, P, istart);
     const int W = 2 * min(max(support[p], 1), s_max) + 1;
     const int nys = (W + ROWS - 1) / ROWS, nf = W / 32, c = W - 32 * nf;
@@ -314,14 +294,14 @@ __device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const
     const int tt = local - chunk * T;
     if (tt < nf * nys) {                      // a full 32-column tile
         const int tys = tt / nf;
-        slot_walk_tile<ROWS, COHERENT, false, 32>(p, W, chunk, tt - tys * nf, tys, N, offsets, cache, vstart, srec,
-                                                  svis, grid, nullptr, 0);
+        slot_walk_tile<ROWS, COHERENT, DEGRID, 32>(p, W, chunk, tt - tys * nf, tys, N, offsets, cache, vstart, srec,
+                                                   svis, grid, vis_out, n_vis);
     } else if (c <= 16) {                     // the remaining columns, 16 x 2 ROWS tiles
-        slot_walk_tile<ROWS, COHERENT, false, 16>(p, W, chunk, 2 * nf, tt - nf * nys, N, offsets, cache, vstart,
-                                                  srec, svis, grid, nullptr, 0);
+        slot_walk_tile<ROWS, COHERENT, DEGRID, 16>(p, W, chunk, 2 * nf, tt - nf * nys, N, offsets, cache, vstart,
+                                                   srec, svis, grid, vis_out, n_vis);
     } else {                                  // the remaining columns, 32 x ROWS tiles
-        slot_walk_tile<ROWS, COHERENT, false, 32>(p, W, chunk, nf, tt - nf * nys, N, offsets, cache, vstart, srec,
-                                                  svis, grid, nullptr, 0);
+        slot_walk_tile<ROWS, COHERENT, DEGRID, 32>(p, W, chunk, nf, tt - nf * nys, N, offsets, cache, vstart, srec,
+                                                   svis, grid, vis_out, n_vis);
     }
 }
 

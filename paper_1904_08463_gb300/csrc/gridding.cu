@@ -1038,6 +1038,8 @@ int grid_run(const Geom& g, const wp_wkernels* kern, const GridWork& w, float2* 
 // =======================================================================================
 // K11: degridding (adjoint).  One warp per binned visibility.
 // =======================================================================================
+constexpr int DEGRID_UNROLL = 2;     // warp passes of 32 taps per loop trip of the degridder
+
 __global__ void __launch_bounds__(256) k_degrid(int N, int os, int s_max, int nbins,
                                                 const int32_t* __restrict__ support,
                                                 const int64_t* __restrict__ offsets,
@@ -1061,34 +1063,31 @@ __global__ void __launch_bounds__(256) k_degrid(int N, int os, int s_max, int nb
     const float2* g0 = grid + (int64_t)(iv - S) * N + (iu - S);
     const float2 zero = make_float2(0.0f, 0.0f);
     float sr = 0.0f, si = 0.0f;
-    // two footprint rows per pass: their tap and grid loads (L2) are in flight together
-    int jy = 0;
-    for (; jy + 1 < W; jy += 2) {
-        const float2* trow = sub + jy * W;
-        const float2* grow = g0 + (int64_t)jy * N;
-        for (int jx = lane; jx < W; jx += 32) {
-            const bool cx_ok = in_bounds(iu - S + jx, N, BS_GRID);
-            const float2 tp0 = in_bounds(sb + jy * W + jx, blk, BS_TAP) ? __ldg(trow + jx) : zero;
-            const float2 tp1 = in_bounds(sb + (jy + 1) * W + jx, blk, BS_TAP) ? __ldg(trow + W + jx) : zero;
-            const float2 gv0 = (cx_ok && in_bounds(iv - S + jy, N, BS_GRID)) ? grow[jx] : zero;
-            const float2 gv1 = (cx_ok && in_bounds(iv - S + jy + 1, N, BS_GRID)) ? grow[N + jx] : zero;
-            // conj(K) * g
-            const float ti0 = sgn * tp0.y, ti1 = sgn * tp1.y;
-            sr = fmaf(tp0.x, gv0.x, fmaf(ti0, gv0.y, sr));
-            si = fmaf(tp0.x, gv0.y, fmaf(-ti0, gv0.x, si));
-            sr = fmaf(tp1.x, gv1.x, fmaf(ti1, gv1.y, sr));
-            si = fmaf(tp1.x, gv1.y, fmaf(-ti1, gv1.x, si));
+    // The footprint's W^2 taps in storage order t = jy W + jx, 32 consecutive taps per warp pass
+    // (every lane busy up to the last pass, whatever W), DEGRID_UNROLL passes per loop trip with
+    // their tap and grid loads (L2) in flight together.  Lane position (jy, jx) of tap t advances
+    // by 32 taps a pass: sy rows and sx columns, plus one row when the column wraps.
+    const int W2 = W * W;
+    const int sy = 32 / W, sx = 32 - sy * W;
+    int jy = lane / W, jx = lane - (lane / W) * W;
+    for (int t0 = 0; t0 < W2; t0 += 32 * DEGRID_UNROLL) {
+        float2 tp[DEGRID_UNROLL], gv[DEGRID_UNROLL];
+#pragma unroll
+        for (int i = 0; i < DEGRID_UNROLL; ++i) {
+            const int t = t0 + 32 * i + lane;
+            const bool ok = t < W2;
+            tp[i] = (ok && in_bounds(sb + t, blk, BS_TAP)) ? __ldg(sub + t) : zero;
+            gv[i] = (ok && in_bounds(iu - S + jx, N, BS_GRID) && in_bounds(iv - S + jy, N, BS_GRID))
+                        ? g0[(int64_t)jy * N + jx] : zero;
+            jx += sx;
+            jy += sy;
+            if (jx >= W) { jx -= W; ++jy; }
         }
-    }
-    if (jy < W) {
-        const float2* trow = sub + jy * W;
-        const float2* grow = g0 + (int64_t)jy * N;
-        for (int jx = lane; jx < W; jx += 32) {
-            const float2 tp = in_bounds(sb + jy * W + jx, blk, BS_TAP) ? __ldg(trow + jx) : zero;
-            const float ti = sgn * tp.y;
-            const float2 gv = (in_bounds(iu - S + jx, N, BS_GRID) && in_bounds(iv - S + jy, N, BS_GRID)) ? grow[jx] : zero;
-            sr = fmaf(tp.x, gv.x, fmaf(ti, gv.y, sr));
-            si = fmaf(tp.x, gv.y, fmaf(-ti, gv.x, si));
+#pragma unroll
+        for (int i = 0; i < DEGRID_UNROLL; ++i) {   // conj(K) * g
+            const float ti = sgn * tp[i].y;
+            sr = fmaf(tp[i].x, gv[i].x, fmaf(ti, gv[i].y, sr));
+            si = fmaf(tp[i].x, gv[i].y, fmaf(-ti, gv[i].x, si));
         }
     }
     for (int o = 16; o; o >>= 1) {
