@@ -818,8 +818,8 @@ def run_batch(args, dev):
         by_streams[ns] = timeit(b.replay)
     best_ns = min(by_streams, key=by_streams.get)
     ms_graph = by_streams[best_ns]
-    # the same problems with their gridding in ONE persistent launch (device work queue over
-    # every problem's scatter and (plane, tile) items, bounded waits), kernel generation and
+    # the same problems with their gridding in persistent launches (one device work queue over
+    # every problem's record orderings, then its (plane, tile) or slot items), kernel generation and
     # images as before; captured in a graph
     b.persistent = True
     by_streams_p = {}

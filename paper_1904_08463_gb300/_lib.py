@@ -140,6 +140,7 @@ _SIGS = {
     "wp_dirty_image_stats": (c_int32, [P_(WpPlan), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "wp_grid_batch_workspace_bytes": (c_size_t, []),
     "wp_grid_batch": (c_int32, [c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "wp_grid_batch_fused": (c_int32, [c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
     "wp_grid_batch_status": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "wp_grid_batch_selftest": (c_int32, [c_int32, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),
     "wp_probe_fp32_fma": (c_int32, [c_int32, c_int32, c_void_p, P_(c_double), c_void_p]),

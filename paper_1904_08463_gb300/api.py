@@ -395,11 +395,14 @@ def _job_array(jobs: list[GridJob]):
     return arr
 
 
-def grid_batch(jobs: list[GridJob], bws: torch.Tensor, stream=None) -> None:
-    """Grid every job in one persistent launch (see ``wp_grid_batch``); each job's grid and
-    stats as ``grid`` would leave them.  Order the jobs largest first."""
+def grid_batch(jobs: list[GridJob], bws: torch.Tensor, stream=None, fused: bool = False) -> None:
+    """Grid every job in persistent launches pulling work from one device queue per gridder kind
+    (see ``wp_grid_batch``; ``fused``: ``wp_grid_batch_fused``, orderings and items in one
+    launch with bounded waits); each job's grid and stats as ``grid`` would leave them.  Order
+    the jobs largest first."""
     arr = _job_array(jobs)
-    _lib.check("wp_grid_batch", _lib.load().wp_grid_batch(len(jobs), arr, _ptr(bws), bws.numel(), _stream(stream)))
+    name = "wp_grid_batch_fused" if fused else "wp_grid_batch"
+    _lib.check(name, getattr(_lib.load(), name)(len(jobs), arr, _ptr(bws), bws.numel(), _stream(stream)))
 
 
 def grid_batch_status(bws: torch.Tensor, stream=None) -> int:

@@ -8,8 +8,8 @@ step of every problem is captured into one CUDA graph: the problems are spread o
 side streams (largest first, round robin) forked from and joined back into the capture
 stream, so small problems overlap with large ones and the host issues one launch for the
 whole batch.  `run_sequential` runs the same steps one problem at a time for comparison.
-With persistent=True the gridding of all problems is instead one persistent launch that pulls
-(problem, plane, tile) work from a single device queue (``api.grid_batch``).
+With persistent=True the gridding of all problems instead runs in persistent launches that pull
+(problem, plane, tile) work from one device queue per gridder kind (``api.grid_batch``).
 """
 from __future__ import annotations
 
@@ -102,8 +102,8 @@ class _State:
 class BatchImager:
     """persistent=False: each problem's whole step (its own tuned gridder) on one of a few forked
     streams.  persistent=True: kernel generation of every problem on the forked streams, then
-    the gridding of ALL problems in one persistent launch pulling work from one device queue
-    (``api.grid_batch``: slot items for problems tuned to the slot gridder, row-owned tiles of 64
+    the gridding of ALL problems in persistent launches pulling work from one device queue per
+    gridder kind (``api.grid_batch``: the record orderings of every problem, then slot items for problems tuned to the slot gridder, row-owned tiles of 64
     cells for the rest, largest problems first), then the images."""
 
     def __init__(self, problems: list[Problem], n_streams: int = 4, tuner: Autotuner | None = None,

@@ -326,7 +326,8 @@ int grid_batch_prepare(const Geom& g, const wp_wkernels* kern, const float* uvw,
                        const GridWork& w, cudaStream_t st);
 int grid_batch_run(int n_jobs, const Geom* geoms, const wp_wkernels* kerns, const float* const* vis,
                    const float* const* weight, const int64_t* Vs, const GridWork* works, float* const* grids,
-                   const uint32_t* const* sidx, int tile, void* bws, long long budget, int withhold, cudaStream_t st);
+                   const uint32_t* const* sidx, int tile, void* bws, long long budget, int withhold, int fused,
+                   cudaStream_t st);
 int grid_run(const Geom& g, const wp_wkernels* k, const GridWork& w, float2* grid, double* stats,
              cudaStream_t st);
 int write_items(int64_t n, const GridWork& w, cudaStream_t st);   // compact live items (flags scanned into cursor)

@@ -144,9 +144,9 @@ def test_batch_normalises_by_the_weights_actually_gridded():
 
 
 def test_persistent_batch_matches_per_problem_gridding_and_the_oracle():
-    """The persistent multi-problem gridder (one launch, one device queue for every problem's
-    scatter and (plane, tile) items, bounded waits between them) against each problem's own
-    wp_grid and, for the images, the oracle; replayed from a CUDA graph."""
+    """The persistent multi-problem gridder (one device queue for every problem's scatter and
+    (plane, tile) items: a launch for the orderings, one for the items) against each problem's
+    own wp_grid and, for the images, the oracle; replayed from a CUDA graph."""
     import paper_1904_08463_gb300 as wp
     from paper_1904_08463_gb300.batch import BatchImager
 
@@ -189,11 +189,13 @@ def _jobs(dev, methods, seed, vis_range=(2000, 6000)):
     return jobs, refs
 
 
+@pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("methods", [(9, 9, 9), (3, 9, 3, 9), (9,)])
-def test_persistent_batch_with_slot_jobs_matches_per_job_gridding(methods):
-    """Slot jobs (grid_method 9) -- alone or mixed with row-owned ones -- in one persistent launch:
-    the in-launch gather orders each slot job's records before its items run; every grid and
-    its stats equal the job's own wp_grid, twice in a row."""
+def test_persistent_batch_with_slot_jobs_matches_per_job_gridding(methods, fused):
+    """Slot jobs (grid_method 9) -- alone or mixed with row-owned ones -- in the persistent
+    launches: the gathers order each slot job's records before its items run (in a launch of
+    their own, or fused: in the same launch, the items waiting for them); every grid and its
+    stats equal the job's own wp_grid, twice in a row."""
     from paper_1904_08463_gb300 import api
 
     dev = torch.device("cuda")
@@ -203,7 +205,7 @@ def test_persistent_batch_with_slot_jobs_matches_per_job_gridding(methods):
         for j in jobs:
             j.grid.zero_()
             j.stats.zero_()
-        api.grid_batch(jobs, bws)
+        api.grid_batch(jobs, bws, fused=fused)
         torch.cuda.synchronize()
         assert api.grid_batch_status(bws) == 0
         for j, (G, st) in zip(jobs, refs):
@@ -235,8 +237,11 @@ def test_persistent_batch_bounded_wait_expires_and_context_survives(methods):
     assert api.grid_batch_selftest(jobs, bws) == -6
     for j in jobs:
         assert float(torch.abs(j.grid).max()) == 0.0
-    api.grid_batch(jobs, bws)
-    torch.cuda.synchronize()
-    assert api.grid_batch_status(bws) == 0
-    for j, r in zip(jobs, refs):
-        assert np.abs(j.grid.cpu().numpy() - r).max() <= 1e-5 * np.abs(r).max()
+    for fused in (True, False):   # the same context grids correctly afterwards, in both forms
+        for j in jobs:
+            j.grid.zero_()
+        api.grid_batch(jobs, bws, fused=fused)
+        torch.cuda.synchronize()
+        assert api.grid_batch_status(bws) == 0
+        for j, r in zip(jobs, refs):
+            assert np.abs(j.grid.cpu().numpy() - r).max() <= 1e-5 * np.abs(r).max()
