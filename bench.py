@@ -863,9 +863,10 @@ def run_grad(args, dev):
     uvw = torch.tensor(d["uvw"], device=dev).reshape(-1)
     vobs = synth.predict_torch(d["uvw"], d["sky"], dev)
     planes = wp.plane_values(uvw, P)
-    # the backward pass grids with the slot walk (grid_method 9); the forward prediction degrids
-    # with whichever degridder is faster on these inputs (timed below: the warp per visibility,
-    # grid_method 0, or the slot walk in reverse, 9)
+    # the backward pass grids with whichever gridder is faster on these inputs (timed below: the
+    # slot walk, 9, the row-owned tile, 3, or the register tile, 0); the forward prediction
+    # degrids with whichever degridder is faster (the warp per visibility, 0, or the slot walk in
+    # reverse, 9)
     plan0 = wp.Plan(N, dl, OS, 127, 3, 0.01, R, "cubic", "tf32x3", 64, 9)
     taper0 = torch.tensor(synth.gaussian_taper_samples(N, dl, R), dtype=torch.float32, device=dev)
     ws = wp.kernelgen_prepare(plan0, P)
@@ -874,10 +875,25 @@ def run_grad(args, dev):
     V = vobs.numel()
     wk = wp.make_wkernels(p_fix, taper0, planes, supports=sup.cpu().tolist())
     X = torch.randn((N, N), dtype=torch.complex64, device=dev)
-    dws = wp.workspace(max(wp.grid_workspace_bytes(p_fix.replace(grid_method=m), P, V) for m in (0, 9)), dev)
+    dws = wp.workspace(max(wp.grid_workspace_bytes(p_fix.replace(grid_method=m), P, V) for m in (0, 3, 9)), dev)
     dout = torch.empty(V, dtype=torch.complex64, device=dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n = 3
+    grid_ms_by = {}
+    Gt = torch.zeros((N, N), dtype=torch.complex64, device=dev)
+    for m in (9, 3, 0):
+        pm = p_fix.replace(grid_method=m)
+        for _ in range(2):
+            wp.grid(pm, wk, uvw, vobs, None, Gt, dws)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(n):
+            wp.grid(pm, wk, uvw, vobs, None, Gt, dws)
+        b.record()
+        torch.cuda.synchronize()
+        grid_ms_by[m] = a.elapsed_time(b) / n
+    gm = min(grid_ms_by, key=grid_ms_by.get)
+    del Gt
     degrid_ms_by = {}
     for m in (0, 9):
         pm = p_fix.replace(grid_method=m)
@@ -892,7 +908,7 @@ def run_grad(args, dev):
         degrid_ms_by[m] = a.elapsed_time(b) / n
     dm = min(degrid_ms_by, key=degrid_ms_by.get)
     del X, dws, dout
-    pr = Predictor(p_fix, planes.cpu().numpy(), sup.cpu().tolist(), uvw, degrid_method=dm)
+    pr = Predictor(p_fix.replace(grid_method=gm), planes.cpu().numpy(), sup.cpu().tolist(), uvw, degrid_method=dm)
     # model image: the sky's point sources on their pixels (non-zero, so that the taper enters)
     img0 = torch.zeros((N, N), dtype=torch.float32)
     for l_, m_, f_ in zip(d["sky"].l, d["sky"].m, d["sky"].flux):
@@ -931,7 +947,8 @@ def run_grad(args, dev):
     return {"workload": f"{V} visibilities, 4096^2 float32 model image, 512 planes, 512-sample taper, chi^2",
             "ms_per_forward_backward": ms, "mvis_per_s": V / (ms * 1e-3) / 1e6,
             "grad_image_norm": float(image.grad.norm()), "grad_taper_norm": float(taper.grad.norm()),
-            "gridder_backward": "slots (grid_method 9)",
+            "gridder_backward": GRID_METHOD_NAMES[gm],
+            "grid_ms_by_method": {GRID_METHOD_NAMES[m]: t for m, t in grid_ms_by.items()},
             "degrid_ms": degrid_ms, "degrid_method": names[dm],
             "degrid_ms_by_method": {names[m]: t for m, t in degrid_ms_by.items()},
             "degrid_taps_per_vis": taps / V,
