@@ -264,6 +264,33 @@ def oracle_kernel_rate(n_planes: int = 512):
                            f"transform matrix excluded; OpenMP over planes' transform rows and sub-kernels")
 
 
+def oracle_grid_rate(n_vis: int = 65536, seed: int = 12):
+    """The FP64 oracle's gridding as it stands (binning decisions + gridding, one thread), on a
+    seeded subset of n_vis visibilities of the full-imaging workload (8M-visibility track set,
+    512 planes from the subset's |w|, 1 % truncation supports, S_max 127); its kernel cache is
+    built first and not timed.  Returns (Mvis/s, sample description)."""
+    from oracle import oracle as o
+
+    d = synth.full_imaging()
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(d["uvw"].shape[0], n_vis, replace=False))
+    uvw = np.ascontiguousarray(d["uvw"][idx])
+    vis = synth.predict(uvw, d["sky"]).astype(np.complex64)
+    N, dl, R = d["N"], d["cell_size"], 512
+    g = o.Geometry(N, dl, OS, 127, 3, 0.01, R)
+    tap = synth.gaussian_taper_samples(N, dl, R).astype(np.float32).astype(np.float64)
+    planes = o.mean_w_planes(uvw[:, 2].astype(np.float64), 512)
+    ks = o.wkernels(g, tap, planes)
+    t0 = time.perf_counter()
+    b = o.bin_vis(g, uvw, planes, ks.support)
+    o.grid(g, ks, b, vis)
+    dt = time.perf_counter() - t0
+    taps = float(np.sum((2 * ks.support[b.plane[b.drop == 0]].astype(np.float64) + 1) ** 2))
+    return n_vis / dt / 1e6, (f"{n_vis} seeded visibilities of the 8M full-imaging workload ({taps / n_vis:.0f} "
+                              f"taps each), binning + gridding in {dt:.1f} s on one thread; kernel cache built "
+                              "beforehand, not timed")
+
+
 def oracle_rate_one_thread(n_planes: int = 64):
     """The same oracle timing with one OpenMP thread (a child process: the thread count of
     the loaded oracle library is fixed), on n_planes planes spread over the batch."""
@@ -740,7 +767,13 @@ def run_imaging(args, dev):
     fp32_src = ("measured in this run (register FMA chains on every SM)" if pk.get("fp32_fma_tflops")
                 else "nominal: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz")
     st = stats.cpu().numpy()
+    cpu = None
+    if getattr(args, "cpu_baseline", False) and int(os.environ.get("RANK", "0")) == 0:
+        log("imaging: CPU oracle on a subset")
+        rate, sample = oracle_grid_rate()
+        cpu = {"value": rate, "unit": "Mvis/s", "cores": 1, "kind": "oracle", "sample": sample}
     return {
+        "cpu_baseline": cpu,
         "workload": f"full imaging: {V} visibilities (64-antenna 8 h track, dec -30, 1.4 GHz, uvw x "
                     f"{d['scale']:.3f}), 200 sources + 1 mJy noise, {P} |w|-planes (mean of "
                     f"equal-count chunks), 1% truncation, S_max 127, os 8, R 512, 4096^2 grid, 8 deg",
