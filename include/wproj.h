@@ -432,10 +432,11 @@ int wp_grid_batch(int32_t n_jobs, const wp_grid_job* jobs, void* batch_workspace
 
 /*
  * The same gridding as wp_grid_batch with the orderings and the items of each kind in ONE
- * launch: an item waits for its job's orderings, done by blocks that took them from the queue
- * earlier.  The wait is bounded (about a second of SM clock); on expiry the item is skipped and
- * the batch status records WP_ERR_TIMEOUT (read it with wp_grid_batch_status).  Measured about
- * 6 % slower than wp_grid_batch on 48 problems (its items read their records through L2).
+ * launch, each job's ordering chunks queued right before its items: an item waits for its job's
+ * orderings, done by blocks that took them from the queue earlier.  The wait is bounded (about a
+ * second of SM clock); on expiry the item is skipped and the batch status records
+ * WP_ERR_TIMEOUT (read it with wp_grid_batch_status).  Measured about 4 % slower than
+ * wp_grid_batch on 48 problems (its items read their records through L2).
  */
 int wp_grid_batch_fused(int32_t n_jobs, const wp_grid_job* jobs, void* batch_workspace,
                         size_t batch_workspace_bytes, void* stream);

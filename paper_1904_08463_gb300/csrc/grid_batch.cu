@@ -4,21 +4,23 @@
 // Per job the binning runs as for wp_grid up to the list of live work items (FP64 decisions,
 // bin counts and their scan, item flags and their scan, the item list) -- but not the scatter
 // of the records into bin order (the gather into sorted order for slot jobs).  Then persistent
-// launches take work from one device queue per gridder kind: first the producer chunks of every
-// job (scatter or gather, SCATTER_CHUNK / SLOT_GATHER records each), then the gridding items of
-// every job ((plane, output tile) blocks, or slot tiles per warp), largest jobs first as the
-// caller ordered them; small jobs' items fill the GPU beside large ones', with no tail per job.
+// launches take work from one device queue per gridder kind: the producer chunks of every job
+// (scatter or gather, SCATTER_CHUNK / SLOT_GATHER records each) and the gridding items of every
+// job ((plane, output tile) blocks, or slot tiles per warp), largest jobs first as the caller
+// ordered them; small jobs' items fill the GPU beside large ones', with no tail per job.
 //
-// Two forms.  Default (wp_grid_batch): per kind, one launch that runs the producer chunks and a
-// second that runs the items, which read the ordered records through the read-only path.
-// Fused (wp_grid_batch_fused): per kind, ONE launch for both; a gridding item of job j reads the
-// records that job j's producer chunks write in the same launch, so it first waits until all of
-// them are done: a counter per job that every finished chunk increments after a fence.  The
-// queue hands out work in order, so every chunk an item waits for was taken earlier by a block
-// that is running and waits for nothing -- the wait always ends; it is nevertheless bounded by a
-// clock budget, after which the item is skipped and WP_ERR_TIMEOUT recorded in the batch status.
-// On 48 problems the default form grids 6 % faster than the fused one (measured on one GB300:
-// 283 vs 300 ms), which reads its records through L2 and overlaps them with their writes.
+// Two forms.  Default (wp_grid_batch): per kind, one launch that runs the producer chunks of
+// every job and a second that runs the items of every job, which read the ordered records
+// through the read-only path.  Fused (wp_grid_batch_fused): per kind, ONE launch whose queue
+// holds each job's producer chunks right before its items, job after job; a gridding item of
+// job j reads the records that job j's producer chunks write in the same launch, so it first
+// waits until all of them are done: a counter per job that every finished chunk increments after
+// a fence.  The queue hands out work in order, so every chunk an item waits for was taken earlier
+// by a block that is running and waits for nothing -- the wait always ends; it is nevertheless
+// bounded by a clock budget, after which the item is skipped and WP_ERR_TIMEOUT recorded in the
+// batch status.  On 48 problems (one GB300) the default form takes 278-283 ms per call, the fused
+// one 289-294 ms (300 ms with every job's chunks ahead of every job's items), both above the
+// 250-253 ms of the same jobs gridded one wp_grid call at a time.
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -99,7 +101,9 @@ __device__ __forceinline__ int wait_done(int* done, int need, int* status, long 
 // ctrl layout: [0] queue head, [1] status, [2 .. 2 + n_jobs) finished scatter chunks per job
 // Job prefixes of both kernels' queues, once per batch (one warp): producer chunks and gridding
 // work of every job, counted where the binning left them on the device.  Layout after the
-// counters: pre[0 .. 4][n_jobs + 1] = row-owned chunks, row-owned items, slot chunks, slot items.
+// counters: pre[0 .. 6][n_jobs + 1] = row-owned chunks, row-owned items, slot chunks, slot items,
+// row-owned chunks + items, slot chunks + items (the fused form's queue: each job's producer
+// chunks right before its items).
 constexpr int SLOT_GATHER = 32 * 32;     // sorted positions per gather work unit (one warp)
 
 __global__ void k_batch_prefix(const __grid_constant__ BatchTable tab, int n_jobs, int* __restrict__ pre) {
@@ -110,6 +114,8 @@ __global__ void k_batch_prefix(const __grid_constant__ BatchTable tab, int n_job
         pre[(n_jobs + 1) + k] = b;
         pre[2 * (n_jobs + 1) + k] = c;
         pre[3 * (n_jobs + 1) + k] = d;
+        pre[4 * (n_jobs + 1) + k] = a + b;
+        pre[5 * (n_jobs + 1) + k] = c + d;
         if (k == n_jobs) break;
         const BatchJob& J = tab.j[k];
         if (J.mode == 9) {
@@ -132,6 +138,30 @@ __device__ __forceinline__ int job_of(const int* __restrict__ pre, int n_jobs, i
     return lo;
 }
 
+// Queue position idx -> (job jb, producer chunk or item `loc` of that job); true for a producer
+// chunk.  Fused form (phase 0): each job's chunks then its items, job after job (pre_cb); the
+// split forms: every job's chunks (pre_sc), then every job's items (pre_gi).
+__device__ __forceinline__ bool batch_decode(int phase, int idx, int n_jobs, int n_sc, const int* __restrict__ pre_sc,
+                                             const int* __restrict__ pre_gi, const int* __restrict__ pre_cb, int& jb,
+                                             int& loc) {
+    if (phase == 0) {
+        jb = job_of(pre_cb, n_jobs, idx);
+        loc = idx - __ldg(pre_cb + jb);
+        const int ns = __ldg(pre_sc + jb + 1) - __ldg(pre_sc + jb);
+        if (loc < ns) return true;
+        loc -= ns;
+        return false;
+    }
+    if (idx < n_sc) {
+        jb = job_of(pre_sc, n_jobs, idx);
+        loc = idx - __ldg(pre_sc + jb);
+        return true;
+    }
+    jb = job_of(pre_gi, n_jobs, idx - n_sc);
+    loc = idx - n_sc - __ldg(pre_gi + jb);
+    return false;
+}
+
 // Row-owned jobs: block-level work (a scatter chunk, or one (plane, tile) item per block).
 template <int TILE>
 __global__ void __launch_bounds__(GRID_WARPS * 32, 6) k_grid_batch_ro(const __grid_constant__ BatchTable tab, int n_jobs,
@@ -144,6 +174,7 @@ __global__ void __launch_bounds__(GRID_WARPS * 32, 6) k_grid_batch_ro(const __gr
     __shared__ int s_idx, s_n, s_ok;
     const int* pre_sc = bctrl + BATCH_PRE;                    // prefix of scatter chunks
     const int* pre_gi = pre_sc + (n_jobs + 1);                // prefix of gridding items
+    const int* pre_cb = pre_sc + 4 * (n_jobs + 1);            // prefix of both (fused queue)
     for (int i = threadIdx.x; i < TILE * TILE; i += blockDim.x) tile[i] = make_float2(0.0f, 0.0f);
     __syncthreads();
     const int n_sc = pre_sc[n_jobs], n_gi = pre_gi[n_jobs];
@@ -155,12 +186,13 @@ __global__ void __launch_bounds__(GRID_WARPS * 32, 6) k_grid_batch_ro(const __gr
         const int idx = s_idx;
         __syncthreads();
         if (idx >= (phase == 1 ? n_sc : n_sc + n_gi)) break;
-        if (idx < n_sc) {
+        int jb, loc;
+        const bool prod = batch_decode(phase, idx, n_jobs, n_sc, pre_sc, pre_gi, pre_cb, jb, loc);
+        if (prod) {
             // ---- scatter chunk: records and weighted values into bin order
-            const int jb = job_of(pre_sc, n_jobs, idx);
             const BatchJob& J = tab.j[jb];
             if (withhold_scatter) continue;       // self-test: the chunk is never done
-            const int64_t k0 = (int64_t)(idx - pre_sc[jb]) * SCATTER_CHUNK;
+            const int64_t k0 = (int64_t)loc * SCATTER_CHUNK;
             for (int64_t k = k0 + threadIdx.x; k < min(J.V, k0 + SCATTER_CHUNK); k += blockDim.x) {
                 const int kk = J.key[k];
                 if (kk < 0) continue;
@@ -177,10 +209,8 @@ __global__ void __launch_bounds__(GRID_WARPS * 32, 6) k_grid_batch_ro(const __gr
             }
         } else {
             // ---- gridding item: wait (bounded) for the job's scatter, then the row-owned tile
-            const int g = idx - n_sc;
-            const int jb = job_of(pre_gi, n_jobs, g);
             const BatchJob& J = tab.j[jb];
-            const int item = J.items[g - pre_gi[jb]];
+            const int item = J.items[loc];
             if (phase == 2) {
                 ro_item<TILE, false>(item, J.N, J.os, J.s_max, J.ntx, J.ntiles, J.seff, J.offsets, J.cache, J.start,
                                      J.srec, J.svis, J.grid, tile, l_off, l_geo, l_vv, &s_n);
@@ -204,6 +234,7 @@ __global__ void __launch_bounds__(SLOT_WARPS * 32, 3) k_grid_batch_slot(const __
                                                                         int phase) {
     const int* pre_sc = bctrl + BATCH_PRE + 2 * (n_jobs + 1);  // prefix of gather chunks
     const int* pre_gi = pre_sc + (n_jobs + 1);                // prefix of slot items
+    const int* pre_cb = pre_sc + 3 * (n_jobs + 1);            // prefix of both (fused queue)
     const int lane = threadIdx.x & 31;
     const int n_sc = pre_sc[n_jobs], n_gi = pre_gi[n_jobs];
     int* head = bctrl + 2 + WP_GRID_BATCH_MAX_JOBS;
@@ -214,11 +245,12 @@ __global__ void __launch_bounds__(SLOT_WARPS * 32, 3) k_grid_batch_slot(const __
         if (lane == 0) idx = (phase == 2) ? n_sc + atomicAdd(&bctrl[HEAD2_SLOT], 1) : atomicAdd(head, 1);
         idx = __shfl_sync(0xffffffffu, idx, 0);
         if (idx >= (phase == 1 ? n_sc : n_sc + n_gi)) break;
-        if (idx < n_sc) {
-            const int jb = job_of(pre_sc, n_jobs, idx);
+        int jb, loc;
+        const bool prod = batch_decode(phase, idx, n_jobs, n_sc, pre_sc, pre_gi, pre_cb, jb, loc);
+        if (prod) {
             const BatchJob& J = tab.j[jb];
             if (withhold_gather) continue;        // self-test: the chunk is never done
-            const int64_t i0 = (int64_t)(idx - pre_sc[jb]) * SLOT_GATHER;
+            const int64_t i0 = (int64_t)loc * SLOT_GATHER;
             const int64_t n_kept = J.vstart[J.P];
             for (int64_t i = i0 + lane; i < min(n_kept, i0 + SLOT_GATHER); i += 32)
                 slot_gather_one(i, J.os, J.s_max, J.sidx, J.rec, J.seff, J.vis, J.weight, J.srec, J.svis);
@@ -228,18 +260,16 @@ __global__ void __launch_bounds__(SLOT_WARPS * 32, 3) k_grid_batch_slot(const __
                 atomicAdd(&done[jb], 1);
             }
         } else {
-            const int g = idx - n_sc;
-            const int jb = job_of(pre_gi, n_jobs, g);
             const BatchJob& J = tab.j[jb];
             if (phase == 2) {
-                slot_item<SLOT_ROWS, false>(g - pre_gi[jb], J.N, J.P, J.s_max, J.seff, J.offsets, J.cache, J.vstart,
+                slot_item<SLOT_ROWS, false>(loc, J.N, J.P, J.s_max, J.seff, J.offsets, J.cache, J.vstart,
                                             J.istart, J.srec, J.svis, J.grid);
                 continue;
             }
             int ok = 0;
             if (lane == 0) ok = wait_done(&done[jb], (int)((J.V + SLOT_GATHER - 1) / SLOT_GATHER), status, budget);
             if (!__shfl_sync(0xffffffffu, ok, 0)) continue;
-            slot_item<SLOT_ROWS, true>(g - pre_gi[jb], J.N, J.P, J.s_max, J.seff, J.offsets, J.cache, J.vstart,
+            slot_item<SLOT_ROWS, true>(loc, J.N, J.P, J.s_max, J.seff, J.offsets, J.cache, J.vstart,
                                        J.istart, J.srec, J.svis, J.grid);
         }
     }
@@ -255,7 +285,7 @@ __global__ void __launch_bounds__(256) k_item_write_pos(int64_t n, const int* __
 }
 
 size_t grid_batch_ctrl_bytes() {
-    return (size_t)(BATCH_PRE + 4 * (WP_GRID_BATCH_MAX_JOBS + 1)) * sizeof(int) + 256;
+    return (size_t)(BATCH_PRE + 6 * (WP_GRID_BATCH_MAX_JOBS + 1)) * sizeof(int) + 256;
 }
 
 // Binning of one job up to its item list (no scatter); the batch kernel scatters.
