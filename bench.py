@@ -9,7 +9,11 @@ matrix product) + spline + resampling of all 512 planes into the oversampled cac
 
 Also measured in the same run (reported under "imaging"): full imaging with 8M
 visibilities (64-antenna 8 h track at dec -30, 1.4 GHz), 512 |w|-planes, 1 % truncation,
-S_max 127, 4096^2 grid: kernel generation + gridding + dirty image per step.
+S_max 127, 4096^2 grid: kernel generation + gridding + dirty image per step, with the FP64
+oracle's gridding rate on a seeded 65,536-visibility subset beside it.  Under "batched": 48
+independent problems of uneven size as one CUDA graph, one at a time, and through the
+persistent batch gridder.  Under "differentiation": forward prediction + hand-written backward
+of a chi-squared loss to a 4096^2 model image and the radial taper, 2M visibilities.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
