@@ -262,14 +262,14 @@ __global__ void __launch_bounds__(SLOT_WARPS * 32, 3) k_grid_batch_slot(const __
         } else {
             const BatchJob J = tab.j[jb];   // copied once per item: 3 % faster than reading the table in the walk
             if (phase == 2) {
-                slot_item<SLOT_ROWS, false>(loc, J.N, J.P, J.s_max, J.seff, J.offsets, J.cache, J.vstart,
+                slot_item<SLOT_ROWS, false, false, true>(loc, J.N, J.P, J.s_max, J.seff, J.offsets, J.cache, J.vstart,
                                             J.istart, J.srec, J.svis, J.grid);
                 continue;
             }
             int ok = 0;
             if (lane == 0) ok = wait_done(&done[jb], (int)((J.V + SLOT_GATHER - 1) / SLOT_GATHER), status, budget);
             if (!__shfl_sync(0xffffffffu, ok, 0)) continue;
-            slot_item<SLOT_ROWS, true>(loc, J.N, J.P, J.s_max, J.seff, J.offsets, J.cache, J.vstart,
+            slot_item<SLOT_ROWS, true, false, true>(loc, J.N, J.P, J.s_max, J.seff, J.offsets, J.cache, J.vstart,
                                        J.istart, J.srec, J.svis, J.grid);
         }
     }

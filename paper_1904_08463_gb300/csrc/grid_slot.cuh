@@ -115,8 +115,10 @@ __host__ __device__ __forceinline__ int slot_tiles_mixed(int W, int rows) {
 // `grid` at its cell, reloaded when the cell changes; per visibility the warp sums conj(tap) x
 // value over its slots and adds the sum into vis_out[original index]; svis is not read).
 // One tile: plane p (width W), chunk `chunk` of its sorted visibilities, slot columns
-// txs COLS .. + COLS - 1 and rows tys TR .. + TR - 1.
-template <int ROWS, bool COHERENT, bool DEGRID, int COLS>
+// txs COLS .. + COLS - 1 and rows tys TR .. + TR - 1.  PREFETCH: the chunk's records are
+// prefetched into L2 first (the persistent batch, whose records may have left L2 since they
+// were sorted; a per-call walk runs right after its own sort and gather).
+template <int ROWS, bool COHERENT, bool DEGRID, int COLS, bool PREFETCH = false>
 __device__ __forceinline__ void slot_walk_tile(int p, int W, int chunk, int txs, int tys, int N,
                                                const int64_t* __restrict__ offsets, const float2* __restrict__ cache,
                                                const int* __restrict__ vstart, const int4* __restrict__ srec,
@@ -129,10 +131,9 @@ __device__ __forceinline__ void slot_walk_tile(int p, int W, int chunk, int txs,
     const int v0 = vstart[p] + chunk * SLOT_CHUNK;
     const int v1 = min(v0 + SLOT_CHUNK, vstart[p + 1]);
     if (v0 >= v1) return;   // no visibility (only an item list built for another tile shape gets here)
-    {
+    if (PREFETCH) {
         // the chunk's records and values into L2 ahead of the walk (one prefetch per 128-byte
-        // line): the walk's own loads run only one record ahead, and a chunk's records may have
-        // left L2 since they were sorted (in a batch, every job is sorted before any is gridded)
+        // line): the walk's own loads run only one record ahead
         const int lane_ = threadIdx.x & 31;
         const char* r0 = reinterpret_cast<const char*>(srec + v0);
         const int rb = (v1 - v0) * (int)sizeof(int4);
@@ -292,7 +293,7 @@ __device__ __forceinline__ void slot_walk_tile(int p, int W, int chunk, int txs,
 
 // Item `it` of an item list of slot_tiles_mixed tiles per chunk: the gridder (per call and in
 // the persistent batch) and, with DEGRID, the slot degridder.
-template <int ROWS, bool COHERENT, bool DEGRID = false>
+template <int ROWS, bool COHERENT, bool DEGRID = false, bool PREFETCH = false>
 __device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const int32_t* __restrict__ support,
                                           const int64_t* __restrict__ offsets, const float2* __restrict__ cache,
                                           const int* __restrict__ vstart, const int* __restrict__ istart,
@@ -308,13 +309,13 @@ __device__ __forceinline__ void slot_item(int it, int N, int P, int s_max, const
     const int tt = local - chunk * T;
     if (tt < nf * nys) {                      // a full 32-column tile
         const int tys = tt / nf;
-        slot_walk_tile<ROWS, COHERENT, DEGRID, 32>(p, W, chunk, tt - tys * nf, tys, N, offsets, cache, vstart, srec,
+        slot_walk_tile<ROWS, COHERENT, DEGRID, 32, PREFETCH>(p, W, chunk, tt - tys * nf, tys, N, offsets, cache, vstart, srec,
                                                    svis, grid, vis_out, n_vis);
     } else if (c <= 16) {                     // the remaining columns, 16 x 2 ROWS tiles
-        slot_walk_tile<ROWS, COHERENT, DEGRID, 16>(p, W, chunk, 2 * nf, tt - nf * nys, N, offsets, cache, vstart,
+        slot_walk_tile<ROWS, COHERENT, DEGRID, 16, PREFETCH>(p, W, chunk, 2 * nf, tt - nf * nys, N, offsets, cache, vstart,
                                                    srec, svis, grid, vis_out, n_vis);
     } else {                                  // the remaining columns, 32 x ROWS tiles
-        slot_walk_tile<ROWS, COHERENT, DEGRID, 32>(p, W, chunk, nf, tt - nf * nys, N, offsets, cache, vstart, srec,
+        slot_walk_tile<ROWS, COHERENT, DEGRID, 32, PREFETCH>(p, W, chunk, nf, tt - nf * nys, N, offsets, cache, vstart, srec,
                                                    svis, grid, vis_out, n_vis);
     }
 }
