@@ -130,18 +130,17 @@ __device__ __forceinline__ void slot_walk_tile(int p, int W, int chunk, int txs,
     static_assert(TR <= 32, "one lane per tile row");
     const int v0 = vstart[p] + chunk * SLOT_CHUNK;
     const int v1 = min(v0 + SLOT_CHUNK, vstart[p + 1]);
-    if (v0 >= v1) return;   // no visibility (only an item list built for another tile shape gets here)
+    if (v0 >= v1) return;   // no visibility (a safety net: item lists count whole chunks)
     if (PREFETCH) {
         // the chunk's records and values into L2 ahead of the walk (one prefetch per 128-byte
         // line): the walk's own loads run only one record ahead
-        const int lane_ = threadIdx.x & 31;
         const char* r0 = reinterpret_cast<const char*>(srec + v0);
         const int rb = (v1 - v0) * (int)sizeof(int4);
-        for (int o = lane_ * 128; o < rb; o += 32 * 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(r0 + o));
+        for (int o = lane * 128; o < rb; o += 32 * 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(r0 + o));
         if (!DEGRID) {
             const char* s0 = reinterpret_cast<const char*>(svis + v0);
             const int sb = (v1 - v0) * (int)sizeof(float2);
-            for (int o = lane_ * 128; o < sb; o += 32 * 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(s0 + o));
+            for (int o = lane * 128; o < sb; o += 32 * 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(s0 + o));
         }
     }
     const float2* pc = cache + offsets[p];
