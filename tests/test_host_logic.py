@@ -1,5 +1,6 @@
-"""Host-side logic that needs no GPU: the autotuner's problem classes and saved table, and the
-library build reusing only objects that are up to date and made on this kind of machine."""
+"""Host-side logic that needs no GPU: the autotuner's problem classes and saved table, the
+library build reusing only objects that are up to date and made on this kind of machine, the
+cache layout and geometry helpers against the oracle, and the binding's tensor checks."""
 import json
 import os
 import shutil
@@ -67,3 +68,34 @@ def test_build_recompiles_only_stale_objects_and_never_foreign_ones():
         if open(stamp).read() != good:
             with open(stamp, "w") as fh:
                 fh.write(good)
+
+
+def test_python_layout_and_geometry_agree_with_the_oracle():
+    """The library's host helpers through the Python binding: the compact cache layout of given
+    supports and the derived geometry equal the oracle's (os^2 (2S+1)^2 taps per plane; K_out,
+    du, r_max from the plan)."""
+    import numpy as np
+
+    import paper_1904_08463_gb300 as wp
+    from oracle import oracle as o
+
+    rng = np.random.default_rng(5)
+    for N, os_, s_max in ((256, 8, 15), (4096, 8, 127), (640, 2, 140), (96, 5, 12)):
+        dl = np.deg2rad(4.0) / N
+        plan = wp.Plan(N, dl, os_, s_max, 1, 0.0, 512)
+        g = o.Geometry(N, dl, os_, s_max, 1, 0.0, 512)
+        sup = rng.integers(1, s_max + 1, 17)
+        assert wp.api.kernel_layout(plan, sup.tolist()) == o.layout(g, sup).tolist()
+        assert wp.api.kernel_layout_max(plan, 3) == [0, *(o.layout(g, [s_max] * 3)[1:]).tolist()]
+        geo = plan.geometry()
+        assert geo.k_out == g.k_out
+        assert geo.du == pytest.approx(g.du, rel=1e-15) and geo.r_max == pytest.approx(g.r_max, rel=1e-15)
+
+
+def test_python_binding_refuses_host_tensors_before_any_device_work():
+    import torch
+
+    import paper_1904_08463_gb300 as wp
+
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        wp.plane_values(torch.zeros(30, dtype=torch.float32), 4)
